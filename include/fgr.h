@@ -1,0 +1,228 @@
+/*
+ * fgr.h -- frozen Gaussian reconstruction on one GB300 (sm_103a).
+ *
+ * C ABI of libfgr.so.  The library computes the hot path of the frozen Gaussian
+ * grid-point correction (FGGC) of Chai & Deng, "Frozen Gaussian Grid-point
+ * Correction For Semi-classical Schroedinger Equation":
+ *
+ *   fgr_propagate           per-packet Hamiltonian flow of Q, P, S and A (eq. 2.3-2.7)
+ *   fgr_reconstruct_direct  windowed direct sum of the packets on a grid (eq. 2.10)
+ *   fgr_reconstruct_fggc    least-squares on-grid correction (Algorithm 2,
+ *                           eq. 2.21-2.25 with eq. 3.13 / 3.22 / 3.23)
+ *   fgr_submit / fgr_poll   continuous-batching server over resident packet sets
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid: per dimension l < d, x_{m,l} = lo[l] + m*(hi[l]-lo[l])/n[l], m in [0, n[l]);
+ *   outputs are row-major with the last dimension fastest.  Free space: points
+ *   outside [lo, hi) do not exist and nothing wraps around.
+ * Mesh (eq. 3.5): dq = cq*sqrt(eps), dp = cp*sqrt(eps).
+ * Prefactor (eq. 2.10): (dq dp)^d / (2 pi eps)^{3d/2}; the library applies it.
+ * Window: each Gaussian is summed over the box |x_l - Q_l| <= R sqrt(eps),
+ *   decided in FP64 as m_lo = ceil(((Q - R sqrt(eps)) - lo)/h),
+ *   m_hi = floor(((Q + R sqrt(eps)) - lo)/h), clipped to the grid.
+ * Packets: structure of arrays, FP64, caller-owned:
+ *   q[d*m], p[d*m] dimension-major (q[l*m + j]); s[m]; a[2*m] (real plane, then
+ *   imaginary plane).  on_device = 1: CUDA device pointers; 0: host pointers
+ *   (the library copies in and, for fgr_propagate, back out).
+ * Output u_out: interleaved complex, complex128 for FGR_FP64 and complex64 for
+ *   FGR_FP32, n[0]*...*n[d-1] values.  Device or host memory (detected); the
+ *   caller owns it.  On error its contents are undefined.
+ * Streams: the cuda_stream argument is a cudaStream_t.  Work is stream-ordered
+ *   and the call returns once it is enqueued, except that (a) host inputs or
+ *   outputs, (b) fgr_reconstruct_fggc's sizing of its node array, and (c) a NULL
+ *   stream make the call wait for its own work.
+ * Errors: invalid arguments return FGR_E_INVALID before any launch.  CUDA
+ *   failures return FGR_E_CUDA.  fgr_last_error() gives a message for the
+ *   calling thread, valid until that thread's next call.  No C++ exception
+ *   crosses this interface.
+ * Threads: one fgr_ctx must not be used by two threads at once.  A server is
+ *   safe to call from any number of threads.
+ */
+#ifndef FGR_H
+#define FGR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FGR_OK = 0,
+    FGR_E_INVALID = 1,   /* bad argument; nothing was launched */
+    FGR_E_NOMEM = 2,     /* device or host allocation failed */
+    FGR_E_CUDA = 3,      /* a CUDA call failed; see fgr_last_error() */
+    FGR_E_NOT_READY = 4, /* fgr_poll: request still running */
+    FGR_E_TIMEOUT = 5,   /* a bounded wait ran out */
+    FGR_E_CAPACITY = 6,  /* the request does not fit the configured memory budget */
+    FGR_E_CANCELLED = 7, /* the request was cancelled or the server shut down */
+    FGR_E_INTERNAL = 8   /* library bug */
+} fgr_status;
+
+#define FGR_MAX_DIM 3
+
+typedef struct fgr_ctx fgr_ctx;       /* opaque, library-owned */
+typedef struct fgr_server fgr_server; /* opaque, library-owned */
+
+typedef struct {
+    int32_t d;                /* 1, 2 or 3 */
+    int32_t reserved;
+    int64_t n[FGR_MAX_DIM];   /* points per dimension, >= 1 */
+    double lo[FGR_MAX_DIM];   /* first point */
+    double hi[FGR_MAX_DIM];   /* end of the half-open interval, > lo */
+} fgr_grid;
+
+typedef enum { FGR_FP64 = 0, FGR_FP32 = 1 } fgr_precision;
+
+typedef struct {
+    double cq, cp;      /* mesh constants of eq. 3.5; defaults 1/2 and pi/8 */
+    int32_t nq, np;     /* q- and p-shifts per dimension (Def. 1): 2 -> {0,1},
+                           4 -> {-1,0,1,2}; defaults 4 and 2 */
+    double window_r;    /* R of the box window; 0 -> 8 (FP64) or 6 (FP32) */
+    double rcond;       /* relative singular-value cut-off of the pseudo-inverse
+                           (Remark 2); 0 -> 1e-14 */
+    int32_t precision;  /* fgr_precision; FP64 default */
+    int32_t flags;      /* 0; reserved */
+} fgr_options;
+
+typedef struct {
+    int64_t m;          /* number of packets, >= 0 */
+    double *q, *p;      /* [d][m] */
+    double *s;          /* [m] */
+    double *a;          /* [2][m] */
+    int32_t on_device;  /* 1: device pointers, 0: host pointers */
+    int32_t reserved;
+} fgr_packets;
+
+typedef enum { FGR_V_FREE = 0, FGR_V_COSSUM = 1, FGR_V_HARMONIC = 2 } fgr_potential_kind;
+
+/* Separable potentials:  FREE  V = 0;
+ *   COSSUM    V = c0 + amp * sum_l cos(k x_l);
+ *   HARMONIC  V = omega^2 |x|^2 / 2. */
+typedef struct {
+    int32_t kind;
+    int32_t reserved;
+    double c0, amp, k, omega;
+} fgr_potential;
+
+/* Fills *opt with the defaults listed in fgr_options. */
+fgr_status fgr_default_options(fgr_options *opt);
+
+/* Creates a context for one (d, grid, eps, options) problem.  Precomputes the
+ * eps-free Gram matrix of eq. 3.22 for the chosen neighbour strategy and its
+ * pseudo-inverse by an eigen-decomposition (the Gram is Hermitian positive
+ * semi-definite, so this is its SVD; Remark 2, Algorithm 2 Step 0), on the host
+ * in extended precision.  Binds to the current CUDA device.
+ * opt may be NULL (defaults).  *out receives the context; free it with
+ * fgr_destroy.  FGR_E_INVALID if d is not in 1..3, grid->d != d, eps <= 0 or
+ * not finite, any n < 1, hi <= lo, or the options are out of range. */
+fgr_status fgr_create(int32_t d, const fgr_grid *grid, double eps, const fgr_options *opt,
+                      fgr_ctx **out);
+
+/* Frees the context and its device scratch; NULL is a no-op. */
+void fgr_destroy(fgr_ctx *ctx);
+
+/* Message describing the calling thread's last failure ("" if none). */
+const char *fgr_last_error(void);
+
+/* Eq. 2.3-2.7: integrates every packet from 0 to t with the classical RK4
+ * scheme, nsteps = round(t/dt) when t/dt is within 1e-9 of an integer (else
+ * ceil(t/dt)), step length t/nsteps, all in FP64.  On entry q, p, s, a hold
+ * Q(0) = q, P(0) = p, S(0) (normally 0) and A(0); the Jacobians start at the
+ * identity (Z(0) = 2I).  On return they hold Q, P, S, A at time t (in place).
+ * FGR_E_INVALID if t < 0, dt <= 0, or the potential kind is unknown. */
+fgr_status fgr_propagate(fgr_ctx *ctx, fgr_packets *inout, const fgr_potential *v, double t,
+                         double dt, void *cuda_stream);
+
+/* Eq. 2.10 over the box window: u(x_m) = pref * sum_j A_j exp(i/eps (S_j +
+ * P_j.(x_m - Q_j)) - |x_m - Q_j|^2/(2 eps)).  FP64: every term in FP64.
+ * FP32: the phase is reduced in FP64 per packet and evaluated per point in
+ * FP32 turns; exp, sin and cos per packet-point pair in FP32; complex64 out. */
+fgr_status fgr_reconstruct_direct(fgr_ctx *ctx, const fgr_packets *pk, void *u_out,
+                                  void *cuda_stream);
+
+/* Algorithm 2 Steps 3-4.  Per packet and dimension: int/frac split (eq. 3.6-3.7),
+ * right-hand side f~ (eq. 3.23), c~ = A~^+ f~ through the eigen factors,
+ * conjugated (true L2 normal equations) and shifted back by
+ * exp(-i cq cp (s - dq_k) b0) (eq. 3.13); d-dimensional coefficients are
+ * products over dimensions.  The weights A_j e^{iS_j/eps} c_j^(k) are summed
+ * onto grid nodes (eq. 2.25) and the node Gaussians are summed on the grid
+ * (eq. 2.24) one dimension at a time.  FP64: all FP64.  FP32: coefficients in
+ * FP64, node array and grid sums in complex64. */
+fgr_status fgr_reconstruct_fggc(fgr_ctx *ctx, const fgr_packets *pk, void *u_out,
+                                void *cuda_stream);
+
+/* Read-only facts about a context. */
+typedef struct {
+    int32_t d, n1, rank, precision;
+    double eps, dq, dp, pref, window_r;
+    double eigenvalues[16]; /* of the eps-free Gram, descending; n1 are valid */
+} fgr_info;
+fgr_status fgr_get_info(const fgr_ctx *ctx, fgr_info *out);
+
+/* Per-stage device times (milliseconds, CUDA events) of the context's last
+ * reconstruct or propagate call, when timing is enabled with fgr_set_timing. */
+typedef struct {
+    double prep_ms, coeff_ms, scatter_ms, grid_ms, direct_ms, propagate_ms, total_ms;
+    int64_t launches;       /* kernels launched by the last call */
+    int64_t pairs;          /* FGR direct: packet-point pairs inside windows */
+    int64_t nodes;          /* FGGC: cells of the node array */
+} fgr_stats;
+fgr_status fgr_set_timing(fgr_ctx *ctx, int32_t enabled);
+fgr_status fgr_get_stats(const fgr_ctx *ctx, fgr_stats *out);
+
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of reconstructions over resident packet sets.
+ * ------------------------------------------------------------------------- */
+
+/* Starts a server on the current device with a scheduler thread and
+ * max_inflight worker streams.  Requests are admitted while the resident packet
+ * sets plus the footprints of the admitted requests stay within
+ * hbm_budget_bytes; others wait in arrival order.  Free with fgr_server_destroy,
+ * which cancels what has not started and waits for what has. */
+fgr_status fgr_server_create(size_t hbm_budget_bytes, int32_t max_inflight, fgr_server **out);
+void fgr_server_destroy(fgr_server *srv);
+
+/* Copies a packet set (host or device, see fgr_packets) into device memory owned
+ * by the server and returns its id.  FGR_E_CAPACITY if it would exceed the budget. */
+fgr_status fgr_register_packets(fgr_server *srv, int32_t d, const fgr_packets *pk,
+                                uint64_t *set_id);
+/* Frees a registered set once no admitted request uses it. */
+fgr_status fgr_release_packets(fgr_server *srv, uint64_t set_id);
+
+typedef struct {
+    int32_t method;      /* 0: direct sum, 1: FGGC */
+    int32_t d;
+    fgr_grid grid;
+    double eps;
+    fgr_options opt;     /* precision etc.; zeroed -> defaults */
+    uint64_t set_id;     /* a registered packet set of dimension d */
+    void *u_out;         /* device or host buffer of the output, caller-owned;
+                            must stay valid until fgr_poll reports completion */
+} fgr_request;
+
+typedef struct {
+    int32_t status;      /* fgr_status of the request */
+    int32_t reserved;
+    double t_submit_ms, t_start_ms, t_done_ms; /* host steady clock, ms */
+} fgr_result;
+
+/* Queues a request and returns a ticket at once.  FGR_E_INVALID for a malformed
+ * request or unknown set; FGR_E_CAPACITY if it can never fit the budget. */
+fgr_status fgr_submit(fgr_server *srv, const fgr_request *req, uint64_t *ticket);
+
+/* Waits up to timeout_ms (0: just look; < 0: no limit) for the ticket.  Returns
+ * FGR_OK with *out filled once done (the ticket is then retired), or
+ * FGR_E_NOT_READY.  FGR_E_INVALID for an unknown ticket. */
+fgr_status fgr_poll(fgr_server *srv, uint64_t ticket, int32_t timeout_ms, fgr_result *out);
+
+/* Cancels a queued request (no effect once it has started). */
+fgr_status fgr_cancel(fgr_server *srv, uint64_t ticket);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FGR_H */

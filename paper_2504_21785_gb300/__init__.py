@@ -1,0 +1,15 @@
+"""Frozen Gaussian reconstruction on GB300: Python binding of libfgr (include/fgr.h).
+
+The computation lives in the CUDA library ``libfgr.so`` (sources in csrc/);
+``fgr`` marshals arguments to its C ABI.  Build the library with
+``paper_2504_21785_gb300._build.build()`` (``__graft_entry__.build()`` does it).
+"""
+
+from . import fgr  # noqa: F401
+from .fgr import (  # noqa: F401
+    Context, FgrError, make_grid, make_options, make_packets, make_potential,
+    fgr_create, fgr_destroy, fgr_propagate, fgr_reconstruct_direct, fgr_reconstruct_fggc,
+    fgr_get_info, fgr_set_timing, fgr_get_stats, fgr_last_error,
+    fgr_server_create, fgr_server_destroy, fgr_register_packets, fgr_release_packets,
+    fgr_submit, fgr_poll, fgr_cancel, make_request, FGR_FP64, FGR_FP32,
+)

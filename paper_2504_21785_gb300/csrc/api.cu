@@ -1,0 +1,446 @@
+// C ABI entry points of libfgr: argument checks, host<->device staging,
+// scratch management and dispatch to the kernel stages.
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+namespace fgr {
+
+namespace {
+thread_local char g_err[1024] = "";
+}
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+void clear_error() { g_err[0] = 0; }
+
+Scratch::~Scratch() {
+    for (int i = n_ - 1; i >= 0; --i)
+        if (ptrs_[i]) cudaFreeAsync(ptrs_[i], s_);
+}
+
+void *Scratch::get(size_t bytes) {
+    if (n_ >= 32) {
+        set_error("internal: too many scratch buffers");
+        return nullptr;
+    }
+    void *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, ctx_->pool, s_);
+    if (e != cudaSuccess) {
+        set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        cudaGetLastError();
+        return nullptr;
+    }
+    ptrs_[n_++] = p;
+    return p;
+}
+
+StageTimer::StageTimer(fgr_ctx *ctx, cudaStream_t s) : ctx_(ctx), s_(s) {
+    if (!ctx_->timing.enabled) return;
+    cudaEventCreate(&ev_[0]);
+    cudaEventRecord(ev_[0], s_);
+    n_ = 1;
+}
+
+void StageTimer::mark(double *slot) {
+    if (!ctx_->timing.enabled || n_ >= 12) return;
+    cudaEventCreate(&ev_[n_]);
+    cudaEventRecord(ev_[n_], s_);
+    slot_[n_] = slot;
+    ++n_;
+}
+
+void StageTimer::finish() {
+    if (!ctx_->timing.enabled || n_ == 0) return;
+    cudaEventSynchronize(ev_[n_ - 1]);
+    for (int i = 1; i < n_; ++i) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ev_[i - 1], ev_[i]);
+        if (slot_[i]) *slot_[i] += ms;
+    }
+    float tot = 0;
+    cudaEventElapsedTime(&tot, ev_[0], ev_[n_ - 1]);
+    ctx_->timing.last.total_ms = tot;
+}
+
+StageTimer::~StageTimer() {
+    for (int i = 0; i < n_; ++i)
+        if (ev_[i]) cudaEventDestroy(ev_[i]);
+}
+
+int64_t rk4_nsteps(double t, double dt) {
+    double r = t / dt;
+    double n = std::nearbyint(r);
+    if (std::fabs(r - n) <= 1e-9 * (n > 1.0 ? n : 1.0)) return (int64_t)n;
+    return (int64_t)std::ceil(r);
+}
+
+namespace {
+
+bool is_finite(double x) { return std::isfinite(x); }
+
+fgr_status check_grid(int32_t d, const fgr_grid *g, Grid *out) {
+    if (!g) {
+        set_error("grid is NULL");
+        return FGR_E_INVALID;
+    }
+    if (d < 1 || d > kMaxDim || g->d != d) {
+        set_error("dimension d=%d (grid d=%d) must be 1, 2 or 3 and match", d, g->d);
+        return FGR_E_INVALID;
+    }
+    Grid G;
+    G.d = d;
+    G.total = 1;
+    for (int l = 0; l < d; ++l) {
+        if (g->n[l] < 1 || g->n[l] > (int64_t(1) << 31) || !is_finite(g->lo[l]) || !is_finite(g->hi[l]) ||
+            !(g->hi[l] > g->lo[l])) {
+            set_error("grid dimension %d: need n >= 1 and finite lo < hi", l);
+            return FGR_E_INVALID;
+        }
+        G.n[l] = g->n[l];
+        G.lo[l] = g->lo[l];
+        G.hi[l] = g->hi[l];
+        G.h[l] = (g->hi[l] - g->lo[l]) / (double)g->n[l];
+        G.total *= g->n[l];
+    }
+    if (G.total > (int64_t(1) << 34)) {
+        set_error("grid has too many points");
+        return FGR_E_INVALID;
+    }
+    *out = G;
+    return FGR_OK;
+}
+
+fgr_status resolve_options(const fgr_options *in, fgr_options *out) {
+    fgr_options o;
+    fgr_default_options(&o);
+    if (in) {
+        o = *in;
+        if (o.cq == 0) o.cq = 0.5;
+        if (o.cp == 0) o.cp = M_PI / 8;
+        if (o.nq == 0) o.nq = 4;
+        if (o.np == 0) o.np = 2;
+        if (o.rcond == 0) o.rcond = 1e-14;
+    }
+    if (o.precision != FGR_FP64 && o.precision != FGR_FP32) {
+        set_error("precision must be FGR_FP64 or FGR_FP32");
+        return FGR_E_INVALID;
+    }
+    if (o.window_r == 0) o.window_r = o.precision == FGR_FP64 ? 8.0 : 6.0;
+    if (!(o.cq > 0) || !(o.cp > 0) || !is_finite(o.cq) || !is_finite(o.cp) || (o.nq != 2 && o.nq != 4) ||
+        (o.np != 2 && o.np != 4) || !(o.window_r > 0) || o.window_r > 40 || !(o.rcond > 0) ||
+        o.rcond >= 1 || o.flags != 0) {
+        set_error("options out of range (cq, cp > 0; nq, np in {2,4}; 0 < window_r <= 40; "
+                  "0 < rcond < 1; flags = 0)");
+        return FGR_E_INVALID;
+    }
+    *out = o;
+    return FGR_OK;
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+fgr_status check_packets(const fgr_ctx *ctx, const fgr_packets *pk) {
+    if (!pk || pk->m < 0 || (pk->m > 0 && (!pk->q || !pk->p || !pk->s || !pk->a))) {
+        set_error("packets: need m >= 0 and non-NULL q, p, s, a");
+        return FGR_E_INVALID;
+    }
+    if (pk->m > (int64_t(1) << 31)) {
+        set_error("packets: at most 2^31 packets per call");
+        return FGR_E_INVALID;
+    }
+    if (pk->on_device != 0 && pk->on_device != 1) {
+        set_error("packets: on_device must be 0 or 1");
+        return FGR_E_INVALID;
+    }
+    if (pk->on_device == 0 && pk->m > 0) {  // host data can be checked for finiteness cheaply
+        const int d = ctx->d;
+        for (int64_t i = 0; i < d * pk->m; ++i)
+            if (!is_finite(pk->q[i]) || !is_finite(pk->p[i])) {
+                set_error("packets: non-finite Q or P at %lld", (long long)i);
+                return FGR_E_INVALID;
+            }
+        for (int64_t i = 0; i < pk->m; ++i)
+            if (!is_finite(pk->s[i]) || !is_finite(pk->a[i]) || !is_finite(pk->a[pk->m + i])) {
+                set_error("packets: non-finite S or A at %lld", (long long)i);
+                return FGR_E_INVALID;
+            }
+    }
+    return FGR_OK;
+}
+
+// Makes device copies of host packet arrays (or passes device pointers through).
+fgr_status stage_packets(fgr_ctx *ctx, const fgr_packets *pk, cudaStream_t st, Scratch &scratch,
+                         PacketsDev *out, double **dq, double **dp, double **ds, double **da) {
+    const int d = ctx->d;
+    const int64_t m = pk->m;
+    if (pk->on_device || m == 0) {
+        *out = {m, pk->q, pk->p, pk->s, pk->a};
+        *dq = pk->q;
+        *dp = pk->p;
+        *ds = pk->s;
+        *da = pk->a;
+        return FGR_OK;
+    }
+    double *buf = (double *)scratch.get(sizeof(double) * (size_t)m * (2 * d + 3));
+    if (!buf) return FGR_E_NOMEM;
+    double *q = buf, *p = q + d * m, *s = p + d * m, *a = s + m;
+    FGR_CUDA_TRY(cudaMemcpyAsync(q, pk->q, sizeof(double) * d * m, cudaMemcpyHostToDevice, st));
+    FGR_CUDA_TRY(cudaMemcpyAsync(p, pk->p, sizeof(double) * d * m, cudaMemcpyHostToDevice, st));
+    FGR_CUDA_TRY(cudaMemcpyAsync(s, pk->s, sizeof(double) * m, cudaMemcpyHostToDevice, st));
+    FGR_CUDA_TRY(cudaMemcpyAsync(a, pk->a, sizeof(double) * 2 * m, cudaMemcpyHostToDevice, st));
+    *out = {m, q, p, s, a};
+    *dq = q;
+    *dp = p;
+    *ds = s;
+    *da = a;
+    return FGR_OK;
+}
+
+template <class F>
+fgr_status guarded(F f) {
+    try {
+        return f();
+    } catch (const std::bad_alloc &) {
+        set_error("host allocation failed");
+        return FGR_E_NOMEM;
+    } catch (...) {
+        set_error("internal error");
+        return FGR_E_INTERNAL;
+    }
+}
+
+fgr_status reconstruct(fgr_ctx *ctx, const fgr_packets *pk, void *u_out, void *stream, bool fggc) {
+    clear_error();
+    if (!ctx || !u_out) {
+        set_error("ctx and u_out must be non-NULL");
+        return FGR_E_INVALID;
+    }
+    fgr_status rc = check_packets(ctx, pk);
+    if (rc != FGR_OK) return rc;
+    return guarded([&]() -> fgr_status {
+        FGR_CUDA_TRY(cudaSetDevice(ctx->device));
+        cudaStream_t st = (cudaStream_t)stream;
+        memset(&ctx->timing.last, 0, sizeof(ctx->timing.last));
+        Scratch scratch(ctx, st);
+        PacketsDev dev;
+        double *q, *p, *s, *a;
+        fgr_status r = stage_packets(ctx, pk, st, scratch, &dev, &q, &p, &s, &a);
+        if (r != FGR_OK) return r;
+        const size_t out_bytes = elem_bytes(ctx->opt.precision) * (size_t)ctx->grid.total;
+        const bool dev_out = is_device_ptr(u_out);
+        void *u_dev = u_out;
+        if (!dev_out) {
+            u_dev = scratch.get(out_bytes);
+            if (!u_dev) return FGR_E_NOMEM;
+        }
+        r = fggc ? run_fggc(ctx, dev, u_dev, st, scratch) : run_direct(ctx, dev, u_dev, st, scratch);
+        if (r != FGR_OK) return r;
+        FGR_CUDA_TRY(cudaGetLastError());
+        if (!dev_out) {
+            FGR_CUDA_TRY(cudaMemcpyAsync(u_out, u_dev, out_bytes, cudaMemcpyDeviceToHost, st));
+            FGR_CUDA_TRY(cudaStreamSynchronize(st));
+        } else if (!stream) {
+            FGR_CUDA_TRY(cudaStreamSynchronize(st));
+        }
+        return FGR_OK;
+    });
+}
+
+}  // namespace
+}  // namespace fgr
+
+using namespace fgr;
+
+extern "C" {
+
+fgr_status fgr_default_options(fgr_options *opt) {
+    if (!opt) return FGR_E_INVALID;
+    memset(opt, 0, sizeof(*opt));
+    opt->cq = 0.5;
+    opt->cp = M_PI / 8;
+    opt->nq = 4;
+    opt->np = 2;
+    opt->window_r = 0;
+    opt->rcond = 1e-14;
+    opt->precision = FGR_FP64;
+    opt->flags = 0;
+    return FGR_OK;
+}
+
+const char *fgr_last_error(void) { return g_err; }
+
+fgr_status fgr_create(int32_t d, const fgr_grid *grid, double eps, const fgr_options *opt,
+                      fgr_ctx **out) {
+    clear_error();
+    if (!out) {
+        set_error("out is NULL");
+        return FGR_E_INVALID;
+    }
+    *out = nullptr;
+    Grid G;
+    fgr_status rc = check_grid(d, grid, &G);
+    if (rc != FGR_OK) return rc;
+    if (!(eps > 0) || !is_finite(eps)) {
+        set_error("eps must be positive and finite");
+        return FGR_E_INVALID;
+    }
+    fgr_options o;
+    rc = resolve_options(opt, &o);
+    if (rc != FGR_OK) return rc;
+    return guarded([&]() -> fgr_status {
+        Lsa L;
+        if (!build_lsa(o.cq, o.cp, o.nq, o.np, o.rcond, &L)) {
+            set_error("neighbour strategy rejected");
+            return FGR_E_INVALID;
+        }
+        fgr_ctx *c = new fgr_ctx();
+        c->d = d;
+        c->grid = G;
+        c->opt = o;
+        c->lsa = L;
+        Mesh &M = c->mesh;
+        M.eps = eps;
+        M.sigma = std::sqrt(eps);
+        M.cq = o.cq;
+        M.cp = o.cp;
+        M.cqcp = o.cq * o.cp;
+        M.dq = o.cq * M.sigma;
+        M.dp = o.cp * M.sigma;
+        M.pref = std::pow(M.dq * M.dp, d) / std::pow(2.0 * M_PI * eps, 1.5 * d);
+        M.R = o.window_r;
+        M.rs = o.window_r * M.sigma;
+        cudaError_t e = cudaGetDevice(&c->device);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+        if (e == cudaSuccess) {
+            cudaMemPoolProps props{};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = c->device;
+            e = cudaMemPoolCreate(&c->pool, &props);
+        }
+        if (e == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&c->host_pinned, 64 * sizeof(int64_t));
+        if (e != cudaSuccess) {
+            set_error("CUDA initialisation failed: %s", cudaGetErrorString(e));
+            cudaGetLastError();
+            if (c->pool) cudaMemPoolDestroy(c->pool);
+            delete c;
+            return FGR_E_CUDA;
+        }
+        *out = c;
+        return FGR_OK;
+    });
+}
+
+void fgr_destroy(fgr_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+    if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+    delete ctx;
+}
+
+fgr_status fgr_get_info(const fgr_ctx *ctx, fgr_info *out) {
+    if (!ctx || !out) return FGR_E_INVALID;
+    memset(out, 0, sizeof(*out));
+    out->d = ctx->d;
+    out->n1 = ctx->lsa.n1;
+    out->rank = ctx->lsa.rank;
+    out->precision = ctx->opt.precision;
+    out->eps = ctx->mesh.eps;
+    out->dq = ctx->mesh.dq;
+    out->dp = ctx->mesh.dp;
+    out->pref = ctx->mesh.pref;
+    out->window_r = ctx->mesh.R;
+    for (int i = 0; i < ctx->lsa.n1; ++i) out->eigenvalues[i] = ctx->lsa.lam[i];
+    return FGR_OK;
+}
+
+fgr_status fgr_set_timing(fgr_ctx *ctx, int32_t enabled) {
+    if (!ctx) return FGR_E_INVALID;
+    ctx->timing.enabled = enabled != 0;
+    return FGR_OK;
+}
+
+fgr_status fgr_get_stats(const fgr_ctx *ctx, fgr_stats *out) {
+    if (!ctx || !out) return FGR_E_INVALID;
+    *out = ctx->timing.last;
+    return FGR_OK;
+}
+
+fgr_status fgr_propagate(fgr_ctx *ctx, fgr_packets *pk, const fgr_potential *v, double t, double dt,
+                         void *stream) {
+    clear_error();
+    if (!ctx || !v) {
+        set_error("ctx and potential must be non-NULL");
+        return FGR_E_INVALID;
+    }
+    fgr_status rc = check_packets(ctx, pk);
+    if (rc != FGR_OK) return rc;
+    if (!(t >= 0) || !is_finite(t) || !(dt > 0) || !is_finite(dt) || v->kind < FGR_V_FREE ||
+        v->kind > FGR_V_HARMONIC || !is_finite(v->c0) || !is_finite(v->amp) || !is_finite(v->k) ||
+        !is_finite(v->omega)) {
+        set_error("propagate: need t >= 0, dt > 0, a known potential kind, finite parameters");
+        return FGR_E_INVALID;
+    }
+    if (rk4_nsteps(t, dt) > (int64_t(1) << 31)) {
+        set_error("propagate: too many steps");
+        return FGR_E_INVALID;
+    }
+    return guarded([&]() -> fgr_status {
+        FGR_CUDA_TRY(cudaSetDevice(ctx->device));
+        cudaStream_t st = (cudaStream_t)stream;
+        memset(&ctx->timing.last, 0, sizeof(ctx->timing.last));
+        Scratch scratch(ctx, st);
+        PacketsDev dev;
+        double *q, *p, *s, *a;
+        fgr_status r = stage_packets(ctx, pk, st, scratch, &dev, &q, &p, &s, &a);
+        if (r != FGR_OK) return r;
+        r = run_propagate(ctx, q, p, s, a, pk->m, v, t, dt, st);
+        if (r != FGR_OK) return r;
+        FGR_CUDA_TRY(cudaGetLastError());
+        const int64_t m = pk->m;
+        const int d = ctx->d;
+        if (!pk->on_device && m > 0) {
+            FGR_CUDA_TRY(cudaMemcpyAsync(pk->q, q, sizeof(double) * d * m, cudaMemcpyDeviceToHost, st));
+            FGR_CUDA_TRY(cudaMemcpyAsync(pk->p, p, sizeof(double) * d * m, cudaMemcpyDeviceToHost, st));
+            FGR_CUDA_TRY(cudaMemcpyAsync(pk->s, s, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+            FGR_CUDA_TRY(cudaMemcpyAsync(pk->a, a, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost, st));
+            FGR_CUDA_TRY(cudaStreamSynchronize(st));
+        } else if (!stream) {
+            FGR_CUDA_TRY(cudaStreamSynchronize(st));
+        }
+        return FGR_OK;
+    });
+}
+
+fgr_status fgr_reconstruct_direct(fgr_ctx *ctx, const fgr_packets *pk, void *u_out, void *stream) {
+    return reconstruct(ctx, pk, u_out, stream, false);
+}
+
+fgr_status fgr_reconstruct_fggc(fgr_ctx *ctx, const fgr_packets *pk, void *u_out, void *stream) {
+    return reconstruct(ctx, pk, u_out, stream, true);
+}
+
+}  // extern "C"

@@ -1,0 +1,54 @@
+// Device helpers shared by the reconstruction kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
+
+namespace fgr {
+
+// Box window of a Gaussian centred at c on one grid axis (see fgr.h):
+//   m_lo = ceil(((c - rs) - lo) / h),  m_hi = floor(((c + rs) - lo) / h),
+// clipped to [0, n) (empty when m_lo > m_hi).  Evaluated with explicit
+// round-to-nearest operations so that no contraction changes the decision.
+__device__ __forceinline__ void window_bounds(double c, double rs, double lo, double h, int64_t n,
+                                              int64_t *mlo, int64_t *mhi) {
+    double a = __ddiv_rn(__dsub_rn(__dsub_rn(c, rs), lo), h);
+    double b = __ddiv_rn(__dsub_rn(__dadd_rn(c, rs), lo), h);
+    a = ceil(a);
+    b = floor(b);
+    a = fmin(fmax(a, 0.0), (double)n);
+    b = fmin(fmax(b, -1.0), (double)(n - 1));
+    *mlo = (int64_t)a;
+    *mhi = (int64_t)b;
+}
+
+// Grid coordinate x_m = lo + m*h without contraction.
+__device__ __forceinline__ double grid_x(double lo, double h, int64_t m) {
+    return __dadd_rn(lo, __dmul_rn((double)m, h));
+}
+
+// Round to nearest integer for |x| < 2^22 with two FP32 additions on the FMA pipe.
+__device__ __forceinline__ float rint_fast(float x) {
+    const float magic = 12582912.0f;  // 1.5 * 2^23
+    return __fsub_rn(__fadd_rn(x, magic), magic);
+}
+
+// 2^x on the special-function unit (relative error about 2^-22).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void atomic_add_c(float2 *p, float re, float im) {
+    atomicAdd(p, make_float2(re, im));
+}
+
+__device__ __forceinline__ void atomic_add_c(double2 *p, double re, double im) {
+    atomicAdd(&p->x, re);
+    atomicAdd(&p->y, im);
+}
+
+}  // namespace fgr

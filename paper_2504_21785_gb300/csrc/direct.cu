@@ -1,0 +1,465 @@
+// K2: windowed direct sum of eq. 2.10 with packets binned by output tile.
+//
+// Binning.  The output grid is cut into tiles of T[0] x ... x T[d-1] points.
+// A packet's "home tile" is the tile holding the lower corner of its clipped
+// window; a counting sort groups packets by home tile.  An output tile t then
+// needs exactly the packets whose home tile lies in the box t - K .. t, with
+// K_l = ceil((Wmax_l - 1) / T_l) and Wmax_l the largest window length.  In
+// row-major tile order that box is (K+1)^(d-1) contiguous segments.
+//
+// Evaluation.  Each CTA owns one output tile (TPT points per thread) and one of
+// S interleaved slices of the tile's packet list; packet records are staged in
+// shared memory 256 at a time and every thread evaluates exp and sincos for each
+// (packet, point) pair inside the packet's window.  Slices are combined with
+// atomic adds into the zeroed output.
+//
+// FP32 records carry the per-packet phase reduced in FP64 to turns at the
+// window start (tau0) and the per-grid-step increment nu split into a coarse
+// part nu_hi (a multiple of 2^-b, so k*nu_hi is exact in FP32 for k < 2^(24-b))
+// and a small remainder nu_lo.  FP64 records carry Q, P, S, A and every pair is
+// evaluated in FP64.
+#include <cmath>
+
+#include "device_util.cuh"
+#include "internal.h"
+
+namespace fgr {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kTpt = 2;                        // points per thread
+constexpr int kMaxSeg = 1024;                  // segments per tile list
+
+// Output tile extent per dimension (kThreads * kTpt = 512 points per tile).
+template <int D>
+__host__ __device__ constexpr int tileT(int l) {
+    return D == 1 ? 512 : (D == 2 ? (l == 0 ? 16 : 32) : 8);
+}
+
+template <int D>
+struct __align__(16) RecF {
+    int mlo[D];
+    int wlen[D];
+    float delta[D];  // x_{mlo} - Q per dimension
+    float nuhi[D];   // turns per grid step, coarse part
+    float nulo[D];   // remainder
+    float tau0;      // phase at the window start, in turns, in [-0.5, 0.5)
+    float ar, ai;    // pref * A
+};
+
+template <int D>
+struct __align__(16) RecD {
+    int mlo[D];
+    int wlen[D];
+    double Q[D], P[D];
+    double S, ar, ai;  // S, pref * A
+};
+
+struct GridDev {
+    int64_t n[3];
+    double lo[3], h[3];
+    int nt[3];   // tiles per dimension
+    int K[3];    // home-tile reach
+    int ntiles;
+};
+
+template <int D>
+__device__ __forceinline__ int tile_linear(const GridDev &g, const int *t) {
+    int lin = 0;
+#pragma unroll
+    for (int l = 0; l < D; ++l) lin = lin * g.nt[l] + t[l];
+    return lin;
+}
+
+// Pass 1: windows, home tile, per-tile counts.
+template <int D>
+__global__ void bin_count_kernel(const double *__restrict__ q, int64_t m, GridDev g, double rs,
+                                 int *__restrict__ home, int *__restrict__ counts) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    int t[D];
+    bool empty = false;
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+        int64_t lo, hi;
+        window_bounds(q[l * m + j], rs, g.lo[l], g.h[l], g.n[l], &lo, &hi);
+        if (lo > hi) empty = true;
+        t[l] = (int)(lo / tileT<D>(l));
+    }
+    if (empty) {
+        home[j] = -1;
+        return;
+    }
+    const int lin = tile_linear<D>(g, t);
+    home[j] = lin;
+    atomicAdd(&counts[lin], 1);
+}
+
+// Exclusive scan of n counts into off[0..n] (single CTA, sequential blocks).
+__global__ void scan_kernel(const int *__restrict__ counts, int64_t *__restrict__ off, int n) {
+    __shared__ int64_t part[1024];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += 1024) {
+        const int i = base + threadIdx.x;
+        int64_t v = i < n ? counts[i] : 0;
+        part[threadIdx.x] = v;
+        __syncthreads();
+        for (int s = 1; s < 1024; s <<= 1) {
+            int64_t add = threadIdx.x >= s ? part[threadIdx.x - s] : 0;
+            __syncthreads();
+            part[threadIdx.x] += add;
+            __syncthreads();
+        }
+        if (i < n) off[i] = carry + part[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += part[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) off[n] = carry;
+}
+
+struct RecParams {
+    double rs, eps, inv_eps, pref;
+    double two_pow_b;  // 2^b for the nu split
+};
+
+// Pass 2: build the records in binned order.
+template <int D, bool FP64>
+__global__ void bin_scatter_kernel(const double *__restrict__ q, const double *__restrict__ p,
+                                   const double *__restrict__ s, const double *__restrict__ a,
+                                   int64_t m, GridDev g, RecParams rp, const int *__restrict__ home,
+                                   const int64_t *__restrict__ off, int *__restrict__ cursor,
+                                   void *__restrict__ recs) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const int h = home[j];
+    if (h < 0) return;
+    const int64_t pos = off[h] + atomicAdd(&cursor[h], 1);
+    const double ar = rp.pref * a[j], ai = rp.pref * a[m + j];
+    if (FP64) {
+        RecD<D> r;
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+            int64_t lo, hi;
+            window_bounds(q[l * m + j], rp.rs, g.lo[l], g.h[l], g.n[l], &lo, &hi);
+            r.mlo[l] = (int)lo;
+            r.wlen[l] = (int)(hi - lo + 1);
+            r.Q[l] = q[l * m + j];
+            r.P[l] = p[l * m + j];
+        }
+        r.S = s[j];
+        r.ar = ar;
+        r.ai = ai;
+        reinterpret_cast<RecD<D> *>(recs)[pos] = r;
+    } else {
+        RecF<D> r;
+        double phase = s[j];
+        const double inv_2pi_eps = rp.inv_eps * 0.15915494309189535;  // 1/(2 pi eps)
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+            int64_t lo, hi;
+            const double Q = q[l * m + j], P = p[l * m + j];
+            window_bounds(Q, rp.rs, g.lo[l], g.h[l], g.n[l], &lo, &hi);
+            r.mlo[l] = (int)lo;
+            r.wlen[l] = (int)(hi - lo + 1);
+            const double dx = grid_x(g.lo[l], g.h[l], lo) - Q;
+            r.delta[l] = (float)dx;
+            phase += P * dx;
+            double nu = P * g.h[l] * inv_2pi_eps;  // turns per grid step
+            nu -= rint(nu);
+            const double nuhi = rint(nu * rp.two_pow_b) / rp.two_pow_b;
+            r.nuhi[l] = (float)nuhi;
+            r.nulo[l] = (float)(nu - nuhi);
+        }
+        double tau = phase * inv_2pi_eps;
+        tau -= rint(tau);
+        r.tau0 = (float)tau;
+        r.ar = (float)ar;
+        r.ai = (float)ai;
+        reinterpret_cast<RecF<D> *>(recs)[pos] = r;
+    }
+}
+
+struct DirectParams {
+    GridDev g;
+    float hf[3];         // grid steps (FP32 path)
+    float ce;            // -log2(e) / (2 eps)
+    double inv_eps;      // FP64 path
+    double neg_half_inv_eps;
+    int splits;
+};
+
+template <int D, bool FP64>
+__global__ void __launch_bounds__(kThreads) direct_kernel(const void *__restrict__ recs_v,
+                                                          const int64_t *__restrict__ off,
+                                                          DirectParams P, void *__restrict__ u_v) {
+    using Rec = typename std::conditional<FP64, RecD<D>, RecF<D>>::type;
+    constexpr int kWords = sizeof(Rec) / 4;
+    __shared__ __align__(16) int srec[kThreads * kWords];
+    __shared__ int64_t seg_start[kMaxSeg];
+    __shared__ int64_t seg_cum[kMaxSeg + 1];
+    __shared__ int nseg_s;
+
+    const GridDev &g = P.g;
+    const Rec *recs = reinterpret_cast<const Rec *>(recs_v);
+    const int tile = blockIdx.x;
+    const int split = blockIdx.y;
+    int t[D];
+    {
+        int rem = tile;
+#pragma unroll
+        for (int l = D - 1; l >= 0; --l) {
+            t[l] = rem % g.nt[l];
+            rem /= g.nt[l];
+        }
+    }
+    // home-tile box -> segments (rows along the last dimension)
+    if (threadIdx.x == 0) {
+        int lo[D], cnt[D];
+        int rows = 1;
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+            lo[l] = max(0, t[l] - g.K[l]);
+            cnt[l] = t[l] - lo[l] + 1;
+            if (l < D - 1) rows *= cnt[l];
+        }
+        int ns = 0;
+        int64_t cum = 0;
+        for (int r = 0; r < rows && ns < kMaxSeg; ++r) {
+            int h[D];
+            int rem = r;
+#pragma unroll
+            for (int l = D - 2; l >= 0; --l) {
+                h[l] = lo[l] + rem % cnt[l];
+                rem /= cnt[l];
+            }
+            h[D - 1] = lo[D - 1];
+            const int first = tile_linear<D>(g, h);
+            const int last = first + cnt[D - 1] - 1;
+            const int64_t a0 = off[first], a1 = off[last + 1];
+            if (a1 > a0) {
+                seg_start[ns] = a0;
+                seg_cum[ns] = cum;
+                cum += a1 - a0;
+                ++ns;
+            }
+        }
+        seg_cum[ns] = cum;
+        nseg_s = ns;
+    }
+    __syncthreads();
+    const int nseg = nseg_s;
+    const int64_t L = seg_cum[nseg];
+
+    // this thread's points
+    int mi[kTpt][D];
+    bool valid[kTpt];
+    int64_t lin_out[kTpt];
+#pragma unroll
+    for (int r = 0; r < kTpt; ++r) {
+        int i = threadIdx.x + r * kThreads;
+        bool ok = true;
+        int64_t lin = 0;
+#pragma unroll
+        for (int l = D - 1; l >= 0; --l) {
+            const int il = i % tileT<D>(l);
+            i /= tileT<D>(l);
+            mi[r][l] = t[l] * tileT<D>(l) + il;
+            ok = ok && mi[r][l] < g.n[l];
+        }
+#pragma unroll
+        for (int l = 0; l < D; ++l) lin = lin * g.n[l] + mi[r][l];
+        valid[r] = ok;
+        lin_out[r] = lin;
+    }
+    double xd[kTpt][D];
+    if (FP64) {
+#pragma unroll
+        for (int r = 0; r < kTpt; ++r)
+#pragma unroll
+            for (int l = 0; l < D; ++l) xd[r][l] = grid_x(g.lo[l], g.h[l], mi[r][l]);
+    }
+
+    float accf[kTpt][2];
+    double accd[kTpt][2];
+#pragma unroll
+    for (int r = 0; r < kTpt; ++r) {
+        accf[r][0] = accf[r][1] = 0.f;
+        accd[r][0] = accd[r][1] = 0.0;
+    }
+
+    const int64_t nchunks = (L + kThreads - 1) / kThreads;
+    for (int64_t c = split; c < nchunks; c += P.splits) {
+        const int64_t v = c * kThreads + threadIdx.x;
+        if (v < L) {
+            // segment holding virtual index v
+            int lo = 0, hi = nseg - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (seg_cum[mid] <= v) lo = mid;
+                else hi = mid - 1;
+            }
+            const int64_t idx = seg_start[lo] + (v - seg_cum[lo]);
+            const int *src = reinterpret_cast<const int *>(recs + idx);
+#pragma unroll
+            for (int w = 0; w < kWords; w += 4)
+                *reinterpret_cast<int4 *>(&srec[threadIdx.x * kWords + w]) =
+                    *reinterpret_cast<const int4 *>(src + w);
+        }
+        __syncthreads();
+        const int64_t left = L - c * kThreads;
+        const int nrec = left < kThreads ? (int)left : kThreads;
+        for (int jr = 0; jr < nrec; ++jr) {
+            const Rec &R = *reinterpret_cast<const Rec *>(&srec[jr * kWords]);
+#pragma unroll
+            for (int r = 0; r < kTpt; ++r) {
+                int k[D];
+                bool in = valid[r];
+#pragma unroll
+                for (int l = 0; l < D; ++l) {
+                    k[l] = mi[r][l] - R.mlo[l];
+                    in = in && (unsigned)k[l] < (unsigned)R.wlen[l];
+                }
+                if (!in) continue;
+                if (FP64) {
+                    const RecD<D> &Rd = reinterpret_cast<const RecD<D> &>(R);
+                    double phase = Rd.S, g2 = 0.0;
+#pragma unroll
+                    for (int l = 0; l < D; ++l) {
+                        const double dx = xd[r][l] - Rd.Q[l];
+                        phase += Rd.P[l] * dx;
+                        g2 += dx * dx;
+                    }
+                    double sn, cs;
+                    sincos(phase * P.inv_eps, &sn, &cs);
+                    const double ga = exp(g2 * P.neg_half_inv_eps);
+                    const double gr = ga * cs, gi = ga * sn;
+                    accd[r][0] += Rd.ar * gr - Rd.ai * gi;
+                    accd[r][1] += Rd.ar * gi + Rd.ai * gr;
+                } else {
+                    const RecF<D> &Rf = reinterpret_cast<const RecF<D> &>(R);
+                    float e = 0.f, tau = Rf.tau0;
+#pragma unroll
+                    for (int l = 0; l < D; ++l) {
+                        const float kf = (float)k[l];
+                        const float dx = fmaf(kf, P.hf[l], Rf.delta[l]);
+                        e = fmaf(dx, dx, e);
+                        float f = kf * Rf.nuhi[l];
+                        f -= rint_fast(f);
+                        tau += fmaf(kf, Rf.nulo[l], f);
+                    }
+                    tau -= rint_fast(tau);
+                    float sn, cs;
+                    __sincosf(6.283185307179586f * tau, &sn, &cs);
+                    const float ga = ex2_approx(e * P.ce);
+                    const float gr = ga * cs, gi = ga * sn;
+                    accf[r][0] = fmaf(Rf.ar, gr, fmaf(-Rf.ai, gi, accf[r][0]));
+                    accf[r][1] = fmaf(Rf.ar, gi, fmaf(Rf.ai, gr, accf[r][1]));
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (L == 0) return;
+#pragma unroll
+    for (int r = 0; r < kTpt; ++r) {
+        if (!valid[r]) continue;
+        if (FP64)
+            atomic_add_c(reinterpret_cast<double2 *>(u_v) + lin_out[r], accd[r][0], accd[r][1]);
+        else
+            atomic_add_c(reinterpret_cast<float2 *>(u_v) + lin_out[r], accf[r][0], accf[r][1]);
+    }
+}
+
+template <int D>
+fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t st, Scratch &scratch) {
+    const bool fp64 = ctx->opt.precision == FGR_FP64;
+    const Mesh &M = ctx->mesh;
+    GridDev g{};
+    int ntiles = 1;
+    int wmax_all = 1;
+    for (int l = 0; l < D; ++l) {
+        g.n[l] = ctx->grid.n[l];
+        g.lo[l] = ctx->grid.lo[l];
+        g.h[l] = ctx->grid.h[l];
+        g.nt[l] = (int)((g.n[l] + tileT<D>(l) - 1) / tileT<D>(l));
+        const int64_t wmax = std::min<int64_t>((int64_t)std::floor(2.0 * M.rs / g.h[l]) + 2, g.n[l]);
+        wmax_all = std::max<int>(wmax_all, (int)wmax);
+        g.K[l] = (int)((wmax - 1 + tileT<D>(l) - 1) / tileT<D>(l));
+        g.K[l] = std::min(g.K[l], g.nt[l] - 1);
+        ntiles *= g.nt[l];
+    }
+    g.ntiles = ntiles;
+    int64_t rows = 1;
+    for (int l = 0; l < D - 1; ++l) rows *= g.K[l] + 1;
+    if (rows > kMaxSeg) {
+        set_error("direct: window of %d points is too wide for the %d-D tiling", wmax_all, D);
+        return FGR_E_INVALID;
+    }
+    const size_t out_bytes = elem_bytes(ctx->opt.precision) * (size_t)ctx->grid.total;
+    FGR_CUDA_TRY(cudaMemsetAsync(u_dev, 0, out_bytes, st));
+    StageTimer timer(ctx, st);
+    const int64_t m = pk.m;
+    if (m == 0) {
+        timer.finish();
+        return FGR_OK;
+    }
+    int *home = (int *)scratch.get(sizeof(int) * m);
+    int *counts = (int *)scratch.get(sizeof(int) * 2 * (size_t)ntiles);
+    int64_t *off = (int64_t *)scratch.get(sizeof(int64_t) * ((size_t)ntiles + 1));
+    const size_t rec_bytes = fp64 ? sizeof(RecD<D>) : sizeof(RecF<D>);
+    void *recs = scratch.get(rec_bytes * (size_t)m);
+    if (!home || !counts || !off || !recs) return FGR_E_NOMEM;
+    int *cursor = counts + ntiles;
+    FGR_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * 2 * (size_t)ntiles, st));
+    const unsigned pb = (unsigned)((m + 255) / 256);
+    bin_count_kernel<D><<<pb, 256, 0, st>>>(pk.q, m, g, M.rs, home, counts);
+    scan_kernel<<<1, 1024, 0, st>>>(counts, off, ntiles);
+    RecParams rp;
+    rp.rs = M.rs;
+    rp.eps = M.eps;
+    rp.inv_eps = 1.0 / M.eps;
+    rp.pref = M.pref;
+    int lbits = 1;
+    while ((1 << lbits) < wmax_all + 1) ++lbits;
+    rp.two_pow_b = std::ldexp(1.0, std::max(1, 24 - lbits));
+    if (fp64)
+        bin_scatter_kernel<D, true><<<pb, 256, 0, st>>>(pk.q, pk.p, pk.s, pk.a, m, g, rp, home, off, cursor, recs);
+    else
+        bin_scatter_kernel<D, false><<<pb, 256, 0, st>>>(pk.q, pk.p, pk.s, pk.a, m, g, rp, home, off, cursor, recs);
+    FGR_CUDA_TRY(cudaGetLastError());
+    timer.mark(&ctx->timing.last.prep_ms);
+
+    DirectParams P{};
+    P.g = g;
+    for (int l = 0; l < D; ++l) P.hf[l] = (float)g.h[l];
+    P.ce = (float)(-1.4426950408889634 / (2.0 * M.eps));
+    P.inv_eps = 1.0 / M.eps;
+    P.neg_half_inv_eps = -0.5 / M.eps;
+    const int target = ctx->num_sms * 8;
+    P.splits = std::max(1, std::min(64, (target + ntiles - 1) / ntiles));
+    dim3 grid((unsigned)ntiles, (unsigned)P.splits);
+    if (fp64)
+        direct_kernel<D, true><<<grid, kThreads, 0, st>>>(recs, off, P, u_dev);
+    else
+        direct_kernel<D, false><<<grid, kThreads, 0, st>>>(recs, off, P, u_dev);
+    FGR_CUDA_TRY(cudaGetLastError());
+    timer.mark(&ctx->timing.last.direct_ms);
+    ctx->timing.last.launches = 4;
+    timer.finish();
+    return FGR_OK;
+}
+
+}  // namespace
+
+fgr_status run_direct(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t st, Scratch &scratch) {
+    switch (ctx->d) {
+    case 1: return launch<1>(ctx, pk, u_dev, st, scratch);
+    case 2: return launch<2>(ctx, pk, u_dev, st, scratch);
+    default: return launch<3>(ctx, pk, u_dev, st, scratch);
+    }
+}
+
+}  // namespace fgr

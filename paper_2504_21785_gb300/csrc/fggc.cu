@@ -1,0 +1,653 @@
+// K3-K5: frozen Gaussian grid-point correction (Algorithm 2, Steps 3-4).
+//
+// Node array.  W holds the aggregated amplitudes of eq. 2.25 on a dense box of
+// phase-space nodes, stored interleaved as [a_0][b_0][a_1][b_1]...[a_{d-1}][b_{d-1}]
+// (a: q-node index, b: p-node index).  The a-range is the part of the packets'
+// range whose Gaussians reach the grid (other nodes have empty windows); the
+// b-range spans the packets with non-zero amplitude (zero amplitudes add zeros).
+//
+// K3+K4 (one thread per packet).  Per dimension: r = Q/dq, a0 = floor(r),
+// s = r - a0 and likewise b0, t for P (eq. 3.6-3.7, FP64).  The true LSA
+// coefficients c~_k(s,t) = conj(A~^+ f~(s,t))_k come from
+//   FP64: f~ of eq. 3.23 in FP64 and A~^+ applied through its eigen factors;
+//   FP32: a Chebyshev surrogate of c~(s,t) built on the host in long double
+//         from the same factors (error below 1e-10), evaluated in FP32.
+// The shift back of eq. 3.13 and the node phase of the on-grid packet are
+// folded into one phase per coefficient: G(x; a dq, b dp) =
+// g(x - a dq) e^{i b dp x/eps} e^{-i cq cp a b}, and with r = a0 + s,
+//   -cq cp [(s - dq_k) b0 + (a0 + dq_k)(b0 + dp_k)] = -cq cp [r b0 + (a0 + dq_k) dp_k].
+// The weight A e^{iS/eps} pref times the product of the d per-dimension
+// coefficients is added to W with atomics.
+//
+// K5 (separable grid stage).  u(x_m) = sum_{a,b} W'[a,b] prod_l g(x_{m_l} - a_l dq)
+// e^{i b_l dp x_{m_l}/eps} is contracted one dimension at a time: a pass maps
+// rows [a_l][b_l] to [m_l]; a transpose brings the next dimension innermost.
+// Each CTA owns 64 grid points of one row: the band of nodes a whose window
+// covers them, g in registers, W staged through shared memory in chunks of b,
+// and e^{i b dp x/eps} generated per (m, b) from a phase reduced in FP64.
+#include <climits>
+#include <cmath>
+
+#include "device_util.cuh"
+#include "internal.h"
+
+namespace fgr {
+namespace {
+
+struct Common {
+    int n1;
+    int dq[kMaxN1], dp[kMaxN1];
+    double dqv, dpv;                 // mesh steps
+    double cq2_4, cp2_4, half_cqcp;  // eq. 3.23 constants
+    double cc;                       // cq cp / (2 pi): node phase in turns
+    double inv_2pi_eps, pref;
+    int amin[kMaxDim], A[kMaxDim], bmin[kMaxDim], B[kMaxDim];
+    int64_t sa[kMaxDim], sb[kMaxDim];  // W strides of a_l and b_l
+    int64_t row_len;                   // cells per row of the first grid pass
+};
+
+struct Params64 {
+    Common c;
+    double vr[kMaxN1 * kMaxN1], vi[kMaxN1 * kMaxN1], inv_lam[kMaxN1];
+};
+
+struct Params32 {
+    Common c;
+    float cre[kMaxN1 * kCheb * kCheb], cim[kMaxN1 * kCheb * kCheb];
+};
+
+// ---------------------------------------------------------------------------
+// node box
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void bounds_kernel(const double *__restrict__ q, const double *__restrict__ p,
+                              const double *__restrict__ a, int64_t m, Common c, int aglo0, int aghi0,
+                              int aglo1, int aghi1, int aglo2, int aghi2, int *__restrict__ out) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int aglo[3] = {aglo0, aglo1, aglo2}, aghi[3] = {aghi0, aghi1, aghi2};
+    int dqmin = INT_MAX, dqmax = INT_MIN, dpmin = INT_MAX, dpmax = INT_MIN;
+    for (int k = 0; k < c.n1; ++k) {
+        dqmin = min(dqmin, c.dq[k]);
+        dqmax = max(dqmax, c.dq[k]);
+        dpmin = min(dpmin, c.dp[k]);
+        dpmax = max(dpmax, c.dp[k]);
+    }
+    bool use = j < m;
+    int lo_a[D], hi_a[D], lo_b[D], hi_b[D];
+    if (use) use = !(a[j] == 0.0 && a[m + j] == 0.0);
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+        lo_a[l] = INT_MAX;
+        hi_a[l] = INT_MIN;
+        lo_b[l] = INT_MAX;
+        hi_b[l] = INT_MIN;
+    }
+    if (use) {
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+            const double ra = floor(__ddiv_rn(q[l * m + j], c.dqv));
+            const double rb = floor(__ddiv_rn(p[l * m + j], c.dpv));
+            const double lim = 1e9;
+            const int a0 = (int)fmin(fmax(ra, -lim), lim), b0 = (int)fmin(fmax(rb, -lim), lim);
+            const int alo = max(a0 + dqmin, aglo[l]), ahi = min(a0 + dqmax, aghi[l]);
+            if (alo > ahi) use = false;
+            lo_a[l] = alo;
+            hi_a[l] = ahi;
+            lo_b[l] = b0 + dpmin;
+            hi_b[l] = b0 + dpmax;
+        }
+    }
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+        const int v0 = __reduce_min_sync(0xffffffffu, use ? lo_a[l] : INT_MAX);
+        const int v1 = __reduce_max_sync(0xffffffffu, use ? hi_a[l] : INT_MIN);
+        const int v2 = __reduce_min_sync(0xffffffffu, use ? lo_b[l] : INT_MAX);
+        const int v3 = __reduce_max_sync(0xffffffffu, use ? hi_b[l] : INT_MIN);
+        if ((threadIdx.x & 31) == 0 && v0 != INT_MAX) {
+            atomicMin(&out[l * 4 + 0], v0);
+            atomicMax(&out[l * 4 + 1], v1);
+            atomicMin(&out[l * 4 + 2], v2);
+            atomicMax(&out[l * 4 + 3], v3);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// coefficients + scatter
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cmul(double ar, double ai, double br, double bi, double &cr, double &ci) {
+    cr = ar * br - ai * bi;
+    ci = ar * bi + ai * br;
+}
+__device__ __forceinline__ void cmul(float ar, float ai, float br, float bi, float &cr, float &ci) {
+    cr = ar * br - ai * bi;
+    ci = ar * bi + ai * br;
+}
+
+// FP64: per-dimension coefficients through the eigen factors.
+__device__ void coeff_dim64(const Params64 &P, double Q, double Pm, int &a0, int &b0, double *cr,
+                            double *ci) {
+    const Common &c = P.c;
+    const double r = __ddiv_rn(Q, c.dqv), rp = __ddiv_rn(Pm, c.dpv);
+    const double fa = floor(r), fb = floor(rp);
+    const double s = r - fa, t = rp - fb;
+    a0 = (int)fmin(fmax(fa, -1e9), 1e9);
+    b0 = (int)fmin(fmax(fb, -1e9), 1e9);
+    const int n = c.n1;
+    double fr[kMaxN1], fi[kMaxN1];
+    for (int j = 0; j < n; ++j) {  // eq. 3.23
+        const double u = c.dq[j] - s, v = c.dp[j] - t;
+        const double mag = exp(-c.cq2_4 * u * u - c.cp2_4 * v * v);
+        double sn, cs;
+        sincos(c.half_cqcp * (s - c.dq[j]) * (c.dp[j] + t), &sn, &cs);
+        fr[j] = mag * cs;
+        fi[j] = mag * sn;
+    }
+    double yr[kMaxN1], yi[kMaxN1];
+    for (int i = 0; i < n; ++i) {  // y = diag(1/lam) V^H f
+        double sr = 0, si = 0;
+        for (int j = 0; j < n; ++j) {
+            const double vr = P.vr[j * kMaxN1 + i], vi = P.vi[j * kMaxN1 + i];
+            sr += vr * fr[j] + vi * fi[j];
+            si += vr * fi[j] - vi * fr[j];
+        }
+        yr[i] = sr * P.inv_lam[i];
+        yi[i] = si * P.inv_lam[i];
+    }
+    // node phase base (turns): -cc * r * b0 and -cc * a0
+    double t0 = -c.cc * (r * fb);
+    t0 -= rint(t0);
+    double t1 = -c.cc * fa;
+    t1 -= rint(t1);
+    for (int k = 0; k < n; ++k) {  // c~ = conj(V y), times the node phase
+        double sr = 0, si = 0;
+        for (int i = 0; i < n; ++i) {
+            const double vr = P.vr[k * kMaxN1 + i], vi = P.vi[k * kMaxN1 + i];
+            sr += vr * yr[i] - vi * yi[i];
+            si += vr * yi[i] + vi * yr[i];
+        }
+        si = -si;
+        double tk = t0 + c.dp[k] * t1 - c.cc * (double)(c.dq[k] * c.dp[k]);
+        tk -= rint(tk);
+        double sn, cs;
+        sincospi(2.0 * tk, &sn, &cs);
+        cmul(sr, si, cs, sn, cr[k], ci[k]);
+    }
+}
+
+// FP32: per-dimension coefficients through the Chebyshev surrogate.
+__device__ void coeff_dim32(const Params32 &P, double Q, double Pm, int &a0, int &b0, float *cr,
+                            float *ci) {
+    const Common &c = P.c;
+    const double r = __ddiv_rn(Q, c.dqv), rp = __ddiv_rn(Pm, c.dpv);
+    const double fa = floor(r), fb = floor(rp);
+    a0 = (int)fmin(fmax(fa, -1e9), 1e9);
+    b0 = (int)fmin(fmax(fb, -1e9), 1e9);
+    const float xs = (float)(2.0 * (r - fa) - 1.0), xt = (float)(2.0 * (rp - fb) - 1.0);
+    float Ts[kCheb], Tt[kCheb];
+    Ts[0] = 1.f;
+    Ts[1] = xs;
+    Tt[0] = 1.f;
+    Tt[1] = xt;
+#pragma unroll
+    for (int i = 2; i < kCheb; ++i) {
+        Ts[i] = 2.f * xs * Ts[i - 1] - Ts[i - 2];
+        Tt[i] = 2.f * xt * Tt[i - 1] - Tt[i - 2];
+    }
+    double t0 = -c.cc * (r * fb);
+    t0 -= rint(t0);
+    double t1 = -c.cc * fa;
+    t1 -= rint(t1);
+    const float t0f = (float)t0, t1f = (float)t1, ccf = (float)c.cc;
+    const int n = c.n1;
+    for (int k = 0; k < n; ++k) {
+        float sr = 0.f, si = 0.f;
+        const float *Cr = P.cre + k * kCheb * kCheb, *Ci = P.cim + k * kCheb * kCheb;
+#pragma unroll
+        for (int i = 0; i < kCheb; ++i) {
+            float ur = 0.f, ui = 0.f;
+#pragma unroll
+            for (int j = 0; j < kCheb; ++j) {
+                ur = fmaf(Cr[i * kCheb + j], Tt[j], ur);
+                ui = fmaf(Ci[i * kCheb + j], Tt[j], ui);
+            }
+            sr = fmaf(Ts[i], ur, sr);
+            si = fmaf(Ts[i], ui, si);
+        }
+        float tk = t0f + (float)c.dp[k] * t1f - ccf * (float)(c.dq[k] * c.dp[k]);
+        tk -= rint_fast(tk);
+        float sn, cs;
+        sincospif(2.f * tk, &sn, &cs);
+        cmul(sr, si, cs, sn, cr[k], ci[k]);
+    }
+}
+
+template <int D, bool FP64>
+__global__ void __launch_bounds__(128) coeff_scatter_kernel(
+    const double *__restrict__ q, const double *__restrict__ p, const double *__restrict__ s,
+    const double *__restrict__ a, int64_t m,
+    const __grid_constant__ typename std::conditional<FP64, Params64, Params32>::type P,
+    void *__restrict__ W_v,
+    uint8_t *__restrict__ row_flag) {
+    using Real = typename std::conditional<FP64, double, float>::type;
+    using C2 = typename std::conditional<FP64, double2, float2>::type;
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const Common &c = P.c;
+    const double ar = a[j], ai = a[m + j];
+    if (ar == 0.0 && ai == 0.0) return;  // contributes exact zeros
+    // weight pref * A * e^{i S/eps}
+    double ts = s[j] * c.inv_2pi_eps;
+    ts -= rint(ts);
+    Real wr, wi;
+    if (FP64) {
+        double sn, cs;
+        sincospi(2.0 * ts, &sn, &cs);
+        double xr, xi;
+        cmul(ar * c.pref, ai * c.pref, cs, sn, xr, xi);
+        wr = (Real)xr;
+        wi = (Real)xi;
+    } else {
+        float sn, cs;
+        sincospif(2.f * (float)ts, &sn, &cs);
+        float xr, xi;
+        cmul((float)(ar * c.pref), (float)(ai * c.pref), cs, sn, xr, xi);
+        wr = (Real)xr;
+        wi = (Real)xi;
+    }
+    Real cr[D][kMaxN1], ci[D][kMaxN1];
+    int a0[D], b0[D];
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+        if constexpr (FP64)
+            coeff_dim64(P, q[l * m + j], p[l * m + j], a0[l], b0[l], cr[l], ci[l]);
+        else
+            coeff_dim32(P, q[l * m + j], p[l * m + j], a0[l], b0[l], cr[l], ci[l]);
+    }
+    C2 *W = reinterpret_cast<C2 *>(W_v);
+    const int n = c.n1;
+    int ncomb = 1;
+#pragma unroll
+    for (int l = 0; l < D; ++l) ncomb *= n;
+    for (int comb = 0; comb < ncomb; ++comb) {
+        int rem = comb;
+        int64_t idx = 0;
+        bool in = true;
+        Real vr = wr, vi = wi;
+#pragma unroll
+        for (int l = D - 1; l >= 0; --l) {
+            const int k = rem % n;
+            rem /= n;
+            const int ia = a0[l] + c.dq[k] - c.amin[l];
+            const int ib = b0[l] + c.dp[k] - c.bmin[l];
+            in = in && (unsigned)ia < (unsigned)c.A[l] && (unsigned)ib < (unsigned)c.B[l];
+            idx += ia * c.sa[l] + ib * c.sb[l];
+            Real tr, ti;
+            cmul(vr, vi, cr[l][k], ci[l][k], tr, ti);
+            vr = tr;
+            vi = ti;
+        }
+        if (!in) continue;
+        atomic_add_c(W + idx, vr, vi);
+        row_flag[idx / c.row_len] = 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// grid passes
+// ---------------------------------------------------------------------------
+struct PassParams {
+    int64_t rows;
+    int A, B, amin, bmin;
+    int64_t N;
+    double lo, h, dq, rs, neg_half_inv_eps;
+    double phi_scale;  // dp / (2 pi eps): phase of e^{i b dp x/eps} in turns per unit b
+    double two_pow_b;  // split of the turn increment (FP32 path)
+    double dp_over_eps;
+};
+
+constexpr int kPassThreads = 64;
+constexpr int kCB = 32;
+
+template <bool FP64, int MAXBAND>
+__global__ void __launch_bounds__(kPassThreads) grid_pass_kernel(const void *__restrict__ in_v,
+                                                                 void *__restrict__ out_v, PassParams pp,
+                                                                 const uint8_t *__restrict__ flags) {
+    using Real = typename std::conditional<FP64, double, float>::type;
+    using C2 = typename std::conditional<FP64, double2, float2>::type;
+    __shared__ C2 sw[MAXBAND][kCB];
+    const int64_t row = blockIdx.x;
+    const int64_t m0 = (int64_t)blockIdx.y * kPassThreads;
+    const int64_t m = m0 + threadIdx.x;
+    const bool valid = m < pp.N;
+    C2 *out = reinterpret_cast<C2 *>(out_v) + row * pp.N;
+    const C2 *in = reinterpret_cast<const C2 *>(in_v) + row * (int64_t)pp.A * pp.B;
+    C2 zero;
+    zero.x = 0;
+    zero.y = 0;
+    if (flags && !flags[row]) {
+        if (valid) out[m] = zero;
+        return;
+    }
+    const int64_t m1 = min(m0 + kPassThreads - 1, pp.N - 1);
+    const double x0 = grid_x(pp.lo, pp.h, m0), x1 = grid_x(pp.lo, pp.h, m1);
+    const int a_lo = max(pp.amin, (int)ceil((x0 - pp.rs) / pp.dq) - 1);
+    const int a_hi = min(pp.amin + pp.A - 1, (int)floor((x1 + pp.rs) / pp.dq) + 1);
+    const int nb = min(a_hi - a_lo + 1, MAXBAND);
+    if (nb <= 0) {
+        if (valid) out[m] = zero;
+        return;
+    }
+    const double xm = grid_x(pp.lo, pp.h, valid ? m : m0);
+    Real g[MAXBAND];
+#pragma unroll
+    for (int i = 0; i < MAXBAND; ++i) {
+        g[i] = 0;
+        if (i < nb && valid) {
+            const double cen = (double)(a_lo + i) * pp.dq;
+            int64_t wlo, whi;
+            window_bounds(cen, pp.rs, pp.lo, pp.h, pp.N, &wlo, &whi);
+            if (m >= wlo && m <= whi) {
+                const double dx = xm - cen;
+                g[i] = (Real)exp(dx * dx * pp.neg_half_inv_eps);
+            }
+        }
+    }
+    // e^{i b dp x_m / eps}: turns per unit b, reduced in FP64
+    double phi = pp.phi_scale * xm;
+    phi -= rint(phi);
+    const double phi_hi = rint(phi * pp.two_pow_b) / pp.two_pow_b;
+    const float phf = (float)phi_hi, plf = (float)(phi - phi_hi);
+    const double th64 = pp.dp_over_eps * xm;
+
+    Real accr = 0, acci = 0;
+    const int ia0 = a_lo - pp.amin;
+    for (int b0 = 0; b0 < pp.B; b0 += kCB) {
+        const int nbb = min(kCB, pp.B - b0);
+        for (int e = threadIdx.x; e < nb * kCB; e += kPassThreads) {
+            const int i = e / kCB, bb = e % kCB;
+            sw[i][bb] = bb < nbb ? in[(int64_t)(ia0 + i) * pp.B + b0 + bb] : zero;
+        }
+        __syncthreads();
+        for (int bb = 0; bb < nbb; ++bb) {
+            Real vr = 0, vi = 0;
+#pragma unroll
+            for (int i = 0; i < MAXBAND; ++i) {
+                if (i < nb) {
+                    const C2 w = sw[i][bb];
+                    vr += g[i] * w.x;
+                    vi += g[i] * w.y;
+                }
+            }
+            const int b = pp.bmin + b0 + bb;
+            Real er, ei;
+            if constexpr (FP64) {
+                double sn, cs;
+                sincos((double)b * th64, &sn, &cs);
+                er = cs;
+                ei = sn;
+            } else {
+                const float bf = (float)b;
+                float f = bf * phf;
+                f -= rint_fast(f);
+                float tau = fmaf(bf, plf, f);
+                tau -= rint_fast(tau);
+                float sn, cs;
+                __sincosf(6.283185307179586f * tau, &sn, &cs);
+                er = cs;
+                ei = sn;
+            }
+            accr += er * vr - ei * vi;
+            acci += er * vi + ei * vr;
+        }
+        __syncthreads();
+    }
+    if (valid) {
+        C2 o;
+        o.x = accr;
+        o.y = acci;
+        out[m] = o;
+    }
+}
+
+template <class C2>
+__global__ void transpose_kernel(const C2 *__restrict__ in, C2 *__restrict__ out, int64_t R, int64_t Cc) {
+    __shared__ C2 tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t r = r0 + i, c = c0 + threadIdx.x;
+        if (r < R && c < Cc) tile[i][threadIdx.x] = in[r * Cc + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t c = c0 + i, r = r0 + threadIdx.x;
+        if (r < R && c < Cc) out[c * R + r] = tile[threadIdx.x][i];
+    }
+}
+
+template <bool FP64>
+fgr_status launch_pass(const void *in, void *out, const PassParams &pp, const uint8_t *flags,
+                       int band, cudaStream_t st) {
+    if (pp.rows == 0 || pp.N == 0) return FGR_OK;
+    if (pp.rows > INT_MAX) {
+        set_error("fggc: too many rows in a grid pass");
+        return FGR_E_CAPACITY;
+    }
+    dim3 grid((unsigned)pp.rows, (unsigned)((pp.N + kPassThreads - 1) / kPassThreads));
+#define FGR_PASS(MB) grid_pass_kernel<FP64, MB><<<grid, kPassThreads, 0, st>>>(in, out, pp, flags)
+    if (band <= 16) FGR_PASS(16);
+    else if (band <= 32) FGR_PASS(32);
+    else if (band <= 48) FGR_PASS(48);
+    else if (band <= 64) FGR_PASS(64);
+    else if (band <= 96) FGR_PASS(96);
+    else {
+        set_error("fggc: window covers %d nodes per grid tile; at most 96 supported", band);
+        return FGR_E_INVALID;
+    }
+#undef FGR_PASS
+    FGR_CUDA_TRY(cudaGetLastError());
+    return FGR_OK;
+}
+
+template <class C2>
+fgr_status launch_transpose(const void *in, void *out, int64_t R, int64_t Cc, cudaStream_t st) {
+    if (R == 0 || Cc == 0) return FGR_OK;
+    dim3 grid((unsigned)((R + 31) / 32), (unsigned)((Cc + 31) / 32));
+    if (grid.y > 65535u) {
+        set_error("fggc: transpose too wide");
+        return FGR_E_CAPACITY;
+    }
+    transpose_kernel<C2><<<grid, dim3(32, 8), 0, st>>>((const C2 *)in, (C2 *)out, R, Cc);
+    FGR_CUDA_TRY(cudaGetLastError());
+    return FGR_OK;
+}
+
+template <int D>
+fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t st, Scratch &scratch) {
+    const bool fp64 = ctx->opt.precision == FGR_FP64;
+    const Mesh &M = ctx->mesh;
+    const Grid &G = ctx->grid;
+    const Lsa &L = ctx->lsa;
+    const size_t eb = elem_bytes(ctx->opt.precision);
+    StageTimer timer(ctx, st);
+    int64_t launches = 0;
+
+    Common c{};
+    c.n1 = L.n1;
+    for (int k = 0; k < L.n1; ++k) {
+        c.dq[k] = L.dq[k];
+        c.dp[k] = L.dp[k];
+    }
+    c.dqv = M.dq;
+    c.dpv = M.dp;
+    c.cq2_4 = M.cq * M.cq / 4;
+    c.cp2_4 = M.cp * M.cp / 4;
+    c.half_cqcp = M.cqcp / 2;
+    c.cc = M.cqcp / (2 * M_PI);
+    c.inv_2pi_eps = 1.0 / (2 * M_PI * M.eps);
+    c.pref = M.pref;
+
+    // grid-relevant node range per dimension (other nodes have empty windows)
+    int aglo[3] = {0, 0, 0}, aghi[3] = {-1, -1, -1};
+    for (int l = 0; l < D; ++l) {
+        const double xlast = G.lo[l] + (double)(G.n[l] - 1) * G.h[l];
+        aglo[l] = (int)std::max(-1e9, std::ceil((G.lo[l] - M.rs) / M.dq) - 1);
+        aghi[l] = (int)std::min(1e9, std::floor((xlast + M.rs) / M.dq) + 1);
+    }
+    int *bnd = (int *)scratch.get(sizeof(int) * 12);
+    if (!bnd) return FGR_E_NOMEM;
+    {
+        int init[12];
+        for (int l = 0; l < 3; ++l) {
+            init[l * 4 + 0] = INT_MAX;
+            init[l * 4 + 1] = INT_MIN;
+            init[l * 4 + 2] = INT_MAX;
+            init[l * 4 + 3] = INT_MIN;
+        }
+        memcpy(ctx->host_pinned, init, sizeof(init));
+        FGR_CUDA_TRY(cudaMemcpyAsync(bnd, ctx->host_pinned, sizeof(init), cudaMemcpyHostToDevice, st));
+    }
+    const int64_t m = pk.m;
+    if (m > 0) {
+        bounds_kernel<D><<<(unsigned)((m + 255) / 256), 256, 0, st>>>(
+            pk.q, pk.p, pk.a, m, c, aglo[0], aghi[0], aglo[1], aghi[1], aglo[2], aghi[2], bnd);
+        FGR_CUDA_TRY(cudaGetLastError());
+        ++launches;
+    }
+    FGR_CUDA_TRY(cudaMemcpyAsync(ctx->host_pinned, bnd, sizeof(int) * 12, cudaMemcpyDeviceToHost, st));
+    FGR_CUDA_TRY(cudaStreamSynchronize(st));
+    int hb[12];
+    memcpy(hb, ctx->host_pinned, sizeof(hb));
+    const size_t out_bytes = eb * (size_t)G.total;
+    if (m == 0 || hb[0] == INT_MAX) {  // nothing reaches the grid
+        FGR_CUDA_TRY(cudaMemsetAsync(u_dev, 0, out_bytes, st));
+        timer.finish();
+        ctx->timing.last.launches = launches;
+        return FGR_OK;
+    }
+    int64_t cells = 1;
+    for (int l = 0; l < D; ++l) {
+        c.amin[l] = hb[l * 4 + 0];
+        c.A[l] = hb[l * 4 + 1] - hb[l * 4 + 0] + 1;
+        c.bmin[l] = hb[l * 4 + 2];
+        c.B[l] = hb[l * 4 + 3] - hb[l * 4 + 2] + 1;
+        cells *= (int64_t)c.A[l] * c.B[l];
+        if (cells > (int64_t(1) << 36)) {
+            set_error("fggc: node array of more than 2^36 cells");
+            return FGR_E_CAPACITY;
+        }
+    }
+    {
+        int64_t stride = 1;
+        for (int l = D - 1; l >= 0; --l) {
+            c.sb[l] = stride;
+            stride *= c.B[l];
+            c.sa[l] = stride;
+            stride *= c.A[l];
+        }
+    }
+    c.row_len = (int64_t)c.A[D - 1] * c.B[D - 1];
+    const int64_t rows0 = cells / c.row_len;
+    ctx->timing.last.nodes = cells;
+
+    // intermediate sizes of the passes
+    int64_t maxbuf = cells;
+    {
+        int64_t prodN = 1;
+        for (int l = D - 1; l >= 0; --l) {
+            prodN *= G.n[l];
+            int64_t pre = 1;
+            for (int j = 0; j < l; ++j) pre *= (int64_t)c.A[j] * c.B[j];
+            maxbuf = std::max(maxbuf, prodN * pre);
+        }
+    }
+    void *W = scratch.get(eb * (size_t)cells);
+    void *buf1 = D > 1 ? scratch.get(eb * (size_t)maxbuf) : nullptr;
+    void *buf2 = D > 1 ? scratch.get(eb * (size_t)maxbuf) : nullptr;
+    uint8_t *flags = (uint8_t *)scratch.get((size_t)rows0);
+    if (!W || !flags || (D > 1 && (!buf1 || !buf2))) return FGR_E_NOMEM;
+    FGR_CUDA_TRY(cudaMemsetAsync(W, 0, eb * (size_t)cells, st));
+    FGR_CUDA_TRY(cudaMemsetAsync(flags, 0, (size_t)rows0, st));
+    timer.mark(&ctx->timing.last.prep_ms);
+
+    const unsigned cb = (unsigned)((m + 127) / 128);
+    if (fp64) {
+        Params64 P{};
+        P.c = c;
+        memcpy(P.vr, L.vr, sizeof(P.vr));
+        memcpy(P.vi, L.vi, sizeof(P.vi));
+        memcpy(P.inv_lam, L.inv_lam, sizeof(P.inv_lam));
+        coeff_scatter_kernel<D, true><<<cb, 128, 0, st>>>(pk.q, pk.p, pk.s, pk.a, m, P, W, flags);
+    } else {
+        Params32 P{};
+        P.c = c;
+        for (int k = 0; k < kMaxN1; ++k)
+            for (int i = 0; i < kCheb; ++i)
+                for (int jj = 0; jj < kCheb; ++jj) {
+                    P.cre[(k * kCheb + i) * kCheb + jj] = L.cheb_re[k][i][jj];
+                    P.cim[(k * kCheb + i) * kCheb + jj] = L.cheb_im[k][i][jj];
+                }
+        coeff_scatter_kernel<D, false><<<cb, 128, 0, st>>>(pk.q, pk.p, pk.s, pk.a, m, P, W, flags);
+    }
+    FGR_CUDA_TRY(cudaGetLastError());
+    ++launches;
+    timer.mark(&ctx->timing.last.scatter_ms);
+
+    // separable passes, last dimension first
+    const void *cur = W;
+    int64_t prodN_after = 1;  // product of N of contracted dimensions
+    for (int l = D - 1; l >= 0; --l) {
+        PassParams pp{};
+        int64_t pre = 1;
+        for (int j = 0; j < l; ++j) pre *= (int64_t)c.A[j] * c.B[j];
+        pp.rows = pre * prodN_after;
+        pp.A = c.A[l];
+        pp.B = c.B[l];
+        pp.amin = c.amin[l];
+        pp.bmin = c.bmin[l];
+        pp.N = G.n[l];
+        pp.lo = G.lo[l];
+        pp.h = G.h[l];
+        pp.dq = M.dq;
+        pp.rs = M.rs;
+        pp.neg_half_inv_eps = -0.5 / M.eps;
+        pp.phi_scale = M.dp / (2 * M_PI * M.eps);
+        pp.dp_over_eps = M.dp / M.eps;
+        const int bmax_abs = std::max(std::abs(c.bmin[l]), std::abs(c.bmin[l] + c.B[l] - 1));
+        int lb = 1;
+        while ((1 << lb) < bmax_abs + 1) ++lb;
+        pp.two_pow_b = std::ldexp(1.0, std::max(1, 23 - lb));
+        const int band = (int)std::ceil(((kPassThreads - 1) * G.h[l] + 2 * M.rs) / M.dq) + 3;
+        const bool last = l == 0;
+        void *dst = (D == 1) ? u_dev : (cur == buf1 ? buf2 : buf1);
+        fgr_status r = fp64 ? launch_pass<true>(cur, dst, pp, l == D - 1 ? flags : nullptr, band, st)
+                            : launch_pass<false>(cur, dst, pp, l == D - 1 ? flags : nullptr, band, st);
+        if (r != FGR_OK) return r;
+        ++launches;
+        if (D > 1) {
+            void *tdst = last ? u_dev : (dst == buf1 ? buf2 : buf1);
+            r = fp64 ? launch_transpose<double2>(dst, tdst, pp.rows, pp.N, st)
+                     : launch_transpose<float2>(dst, tdst, pp.rows, pp.N, st);
+            if (r != FGR_OK) return r;
+            ++launches;
+            cur = tdst;
+        }
+        prodN_after *= G.n[l];
+    }
+    timer.mark(&ctx->timing.last.grid_ms);
+    ctx->timing.last.launches = launches;
+    timer.finish();
+    return FGR_OK;
+}
+
+}  // namespace
+
+fgr_status run_fggc(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t st, Scratch &scratch) {
+    switch (ctx->d) {
+    case 1: return launch<1>(ctx, pk, u_dev, st, scratch);
+    case 2: return launch<2>(ctx, pk, u_dev, st, scratch);
+    default: return launch<3>(ctx, pk, u_dev, st, scratch);
+    }
+}
+
+}  // namespace fgr

@@ -1,0 +1,133 @@
+// Internal declarations of libfgr (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "fgr.h"
+
+namespace fgr {
+
+constexpr int kMaxDim = 3;
+constexpr int kMaxN1 = 16;  // 1-D neighbours per packet: nq * np <= 16
+
+// Eigen-factored eps-free Gram matrix of eq. 3.22 (paper convention).
+// The Gram A~ is Hermitian PSD: A~ = V diag(lam) V^H, A~^+ = V diag(inv_lam) V^H.
+struct Lsa {
+    int nq = 4, np = 2, n1 = 8, rank = 0;
+    double cq = 0.5, cp = 0.0;
+    int dq[kMaxN1] = {}, dp[kMaxN1] = {};  // shifts, k = iq*np + ip
+    double lam[kMaxN1] = {};               // descending
+    double inv_lam[kMaxN1] = {};           // 1/lam above the cut-off, else 0
+    double vr[kMaxN1 * kMaxN1] = {};       // V[j][i]: component j of eigenvector i
+    double vi[kMaxN1 * kMaxN1] = {};
+    // Chebyshev surrogate of the true coefficients c~_k(s,t) = conj(A~^+ f~(s,t))_k
+    // on [0,1]^2: c~_k ~= sum_{i,j<kCheb} cheb[k][i][j] T_i(2s-1) T_j(2t-1).
+    float cheb_re[kMaxN1][12][12] = {};
+    float cheb_im[kMaxN1][12][12] = {};
+};
+constexpr int kCheb = 12;
+
+// Builds Lsa (host, long double Jacobi).  Returns false on bad input.
+bool build_lsa(double cq, double cp, int nq, int np, double rcond, Lsa *out);
+
+struct Grid {
+    int d = 1;
+    int64_t n[kMaxDim] = {1, 1, 1};
+    double lo[kMaxDim] = {}, hi[kMaxDim] = {}, h[kMaxDim] = {};
+    int64_t total = 1;
+};
+
+struct Mesh {
+    double eps, sigma, dq, dp, cq, cp, cqcp, pref, R, rs;  // rs = R*sqrt(eps)
+};
+
+struct Timing {
+    bool enabled = false;
+    fgr_stats last{};
+};
+
+}  // namespace fgr
+
+struct fgr_ctx {
+    int d = 1;
+    int device = 0;
+    int num_sms = 1;
+    fgr::Grid grid;
+    fgr::Mesh mesh;
+    fgr::Lsa lsa;
+    fgr_options opt{};
+    cudaMemPool_t pool = nullptr;
+    fgr::Timing timing;
+    int64_t *host_pinned = nullptr;  // small pinned buffer for device->host sizes
+};
+
+namespace fgr {
+
+// thread-local error message
+void set_error(const char *fmt, ...);
+void clear_error();
+
+#define FGR_CUDA_TRY(expr)                                                              \
+    do {                                                                                \
+        cudaError_t err__ = (expr);                                                     \
+        if (err__ != cudaSuccess) {                                                     \
+            ::fgr::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(err__), \
+                             __FILE__, __LINE__);                                       \
+            return FGR_E_CUDA;                                                          \
+        }                                                                               \
+    } while (0)
+
+// Device view of a packet set (device pointers).
+struct PacketsDev {
+    int64_t m;
+    const double *q, *p, *s, *a;
+};
+
+// Stream-ordered scratch from the context's pool, released when the guard dies.
+class Scratch {
+  public:
+    Scratch(fgr_ctx *ctx, cudaStream_t s) : ctx_(ctx), s_(s) {}
+    ~Scratch();
+    // returns nullptr and sets the error on failure
+    void *get(size_t bytes);
+
+  private:
+    fgr_ctx *ctx_;
+    cudaStream_t s_;
+    void *ptrs_[32] = {};
+    int n_ = 0;
+};
+
+// Kernel-stage launchers (return FGR_OK or an error with the message set).
+fgr_status run_propagate(fgr_ctx *ctx, double *q, double *p, double *s, double *a, int64_t m,
+                         const fgr_potential *v, double t, double dt, cudaStream_t st);
+fgr_status run_direct(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t st,
+                      Scratch &scratch);
+fgr_status run_fggc(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t st,
+                    Scratch &scratch);
+
+// Event-based stage timer (active only when ctx->timing.enabled).
+class StageTimer {
+  public:
+    StageTimer(fgr_ctx *ctx, cudaStream_t s);
+    ~StageTimer();
+    void mark(double *slot);  // time since the previous mark goes to *slot
+    void finish();            // total -> last.total_ms
+
+  private:
+    fgr_ctx *ctx_;
+    cudaStream_t s_;
+    cudaEvent_t ev_[12] = {};
+    double *slot_[12] = {};
+    int n_ = 0;
+};
+
+inline size_t elem_bytes(int precision) { return precision == FGR_FP64 ? 16 : 8; }
+
+int64_t rk4_nsteps(double t, double dt);
+
+}  // namespace fgr

@@ -1,0 +1,169 @@
+"""Serving (fgr_submit / fgr_poll): results in a concurrent mix equal the same
+requests run alone; admission under a memory budget; cancellation; errors."""
+
+import math
+import threading
+
+import numpy as np
+import pytest
+
+from workloads import random_packets, mesh_for
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fgr():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2504_21785_gb300 as pkg
+    pkg.fgr.load()
+    return pkg
+
+
+def _grid(d, n):
+    return dict(d=d, n=[n] * d, lo=[-math.pi] * d, hi=[math.pi] * d)
+
+
+def _requests(seed=0, count=24):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(count):
+        d = int(rng.integers(1, 3))
+        eps = float(2.0 ** -rng.uniform(6, 10))
+        n = int(2 ** rng.integers(10, 13)) if d == 1 else int(2 ** rng.integers(6, 8))
+        reqs.append(dict(d=d, eps=eps, grid=_grid(d, n), method=int(rng.integers(0, 2)),
+                         set=int(rng.integers(0, 3)) + (0 if d == 1 else 3)))
+    return reqs
+
+
+def _sets():
+    out = []
+    for d in (1, 1, 1, 2, 2, 2):
+        k = len(out)
+        m = [4000, 12000, 30000, 2000, 6000, 9000][k]
+        out.append(random_packets(50 + k, d, m, q_range=(-2.5, 2.5), p_range=(-2, 2), s_range=(-1, 1)))
+    return out
+
+
+def _alone(fgr, pk, r):
+    from . import _gpu
+    opt = fgr.make_options(precision=fgr.FGR_FP32)
+    return _gpu.reconstruct("fggc" if r["method"] else "direct", pk, r["grid"], r["eps"], opt)
+
+
+def test_results_alone_equal_results_in_the_mix(fgr):
+    import torch
+    sets = _sets()
+    srv = fgr.fgr_server_create(8 << 30, 4)
+    try:
+        ids = [fgr.fgr_register_packets(srv, pk["q"].shape[0],
+                                        fgr.make_packets(*[np.ascontiguousarray(pk[k]) for k in "qpsa"]))
+               for pk in sets]
+        reqs = _requests()
+        outs, tickets = [], []
+        opt = fgr.make_options(precision=fgr.FGR_FP32)
+        for r in reqs:
+            shape = tuple(r["grid"]["n"][: r["d"]])
+            u = torch.zeros(shape, dtype=torch.complex64, device="cuda")
+            outs.append(u)
+            tickets.append(fgr.fgr_submit(srv, fgr.make_request(r["method"], r["grid"], r["eps"], opt,
+                                                                ids[r["set"]], u)))
+        results = [fgr.fgr_poll(srv, t, -1) for t in tickets]
+        assert all(res.status == 0 for res in results)
+        # the mix really overlapped: some request started before another finished
+        spans = sorted((res.t_start_ms, res.t_done_ms) for res in results)
+        assert any(spans[i + 1][0] < spans[i][1] for i in range(len(spans) - 1))
+        for r, u in zip(reqs, outs):
+            ref = _alone(fgr, sets[r["set"]], r)
+            got = u.cpu().numpy()
+            den = max(np.linalg.norm(ref), 1e-300)
+            assert np.linalg.norm(got - ref) / den <= 1e-5
+    finally:
+        fgr.fgr_server_destroy(srv)
+
+
+def test_admission_by_budget_and_host_output(fgr):
+    pk = random_packets(60, 1, 20000, q_range=(-2, 2), p_range=(-2, 2))
+    arrs = [np.ascontiguousarray(pk[k]) for k in "qpsa"]
+    n = 4096
+    # budget fits the set and about one request at a time
+    srv = fgr.fgr_server_create(24 << 20, 4)
+    try:
+        sid = fgr.fgr_register_packets(srv, 1, fgr.make_packets(*arrs))
+        opt = fgr.make_options(precision=fgr.FGR_FP32)
+        outs = [np.zeros(n, np.complex64) for _ in range(6)]
+        ts = [fgr.fgr_submit(srv, fgr.make_request(0, _grid(1, n), 1 / 256, opt, sid, u)) for u in outs]
+        res = [fgr.fgr_poll(srv, t, -1) for t in ts]
+        assert all(r.status == 0 for r in res)
+        for u in outs[1:]:
+            assert np.array_equal(u, outs[0])
+        # a request that can never fit is refused at submit
+        big = np.zeros(1 << 22, np.complex64)
+        with pytest.raises(fgr.FgrError) as e:
+            fgr.fgr_submit(srv, fgr.make_request(1, _grid(1, 1 << 22), 1 / 256, opt, sid, big))
+        assert e.value.status == fgr.fgr.FGR_E_CAPACITY
+    finally:
+        fgr.fgr_server_destroy(srv)
+
+
+def test_cancel_unknown_ticket_and_shutdown(fgr):
+    import torch
+    pk = random_packets(61, 2, 30000, q_range=(-2, 2), p_range=(-2, 2))
+    srv = fgr.fgr_server_create(16 << 30, 1)
+    sid = fgr.fgr_register_packets(srv, 2, fgr.make_packets(*[np.ascontiguousarray(pk[k]) for k in "qpsa"]))
+    opt = fgr.make_options(precision=fgr.FGR_FP32)
+    outs = [torch.zeros((512, 512), dtype=torch.complex64, device="cuda") for _ in range(5)]
+    ts = [fgr.fgr_submit(srv, fgr.make_request(0, _grid(2, 512), 1 / 256, opt, sid, u)) for u in outs]
+    cancelled = 0
+    for t in ts[1:]:
+        try:
+            fgr.fgr_cancel(srv, t)
+            cancelled += 1
+        except fgr.FgrError:
+            pass  # already admitted
+    statuses = [fgr.fgr_poll(srv, t, -1).status for t in ts]
+    assert statuses[0] == 0
+    assert statuses.count(fgr.fgr.FGR_E_CANCELLED) == cancelled
+    with pytest.raises(fgr.FgrError):
+        fgr.fgr_poll(srv, 987654, 0)
+    bad = fgr.make_request(0, _grid(2, 64), 1 / 256, opt, 12345, outs[0])
+    with pytest.raises(fgr.FgrError):
+        fgr.fgr_submit(srv, bad)
+    # destroy with work queued: queued requests end cancelled, running ones finish
+    ts2 = [fgr.fgr_submit(srv, fgr.make_request(0, _grid(2, 512), 1 / 256, opt, sid, u)) for u in outs]
+    fgr.fgr_server_destroy(srv)
+    torch.cuda.synchronize()
+    assert len(ts2) == 5
+
+
+def test_many_client_threads(fgr):
+    import torch
+    pk = random_packets(62, 1, 5000, q_range=(-2, 2), p_range=(-2, 2))
+    srv = fgr.fgr_server_create(4 << 30, 3)
+    try:
+        sid = fgr.fgr_register_packets(srv, 1, fgr.make_packets(*[np.ascontiguousarray(pk[k]) for k in "qpsa"]))
+        opt = fgr.make_options(precision=fgr.FGR_FP32)
+        errors = []
+
+        def client(i):
+            try:
+                u = torch.zeros(2048, dtype=torch.complex64, device="cuda")
+                t = fgr.fgr_submit(srv, fgr.make_request(i % 2, _grid(1, 2048), 1 / 512, opt, sid, u))
+                r = None
+                while r is None:
+                    r = fgr.fgr_poll(srv, t, 50)
+                if r.status != 0:
+                    errors.append(r.status)
+            except Exception as e:  # noqa: BLE001
+                errors.append(e)
+
+        th = [threading.Thread(target=client, args=(i,)) for i in range(12)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        assert not errors
+    finally:
+        fgr.fgr_server_destroy(srv)
