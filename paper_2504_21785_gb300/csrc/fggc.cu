@@ -333,26 +333,12 @@ __global__ void __launch_bounds__(kPassThreads) grid_pass_kernel(const void *__r
     const double x0 = grid_x(pp.lo, pp.h, m0), x1 = grid_x(pp.lo, pp.h, m1);
     const int a_lo = max(pp.amin, (int)ceil((x0 - pp.rs) / pp.dq) - 1);
     const int a_hi = min(pp.amin + pp.A - 1, (int)floor((x1 + pp.rs) / pp.dq) + 1);
-    const int nb = min(a_hi - a_lo + 1, MAXBAND);
-    if (nb <= 0) {
+    const int nb_total = a_hi - a_lo + 1;
+    if (nb_total <= 0) {
         if (valid) out[m] = zero;
         return;
     }
     const double xm = grid_x(pp.lo, pp.h, valid ? m : m0);
-    Real g[MAXBAND];
-#pragma unroll
-    for (int i = 0; i < MAXBAND; ++i) {
-        g[i] = 0;
-        if (i < nb && valid) {
-            const double cen = (double)(a_lo + i) * pp.dq;
-            int64_t wlo, whi;
-            window_bounds(cen, pp.rs, pp.lo, pp.h, pp.N, &wlo, &whi);
-            if (m >= wlo && m <= whi) {
-                const double dx = xm - cen;
-                g[i] = (Real)exp(dx * dx * pp.neg_half_inv_eps);
-            }
-        }
-    }
     // e^{i b dp x_m / eps}: turns per unit b, reduced in FP64
     double phi = pp.phi_scale * xm;
     phi -= rint(phi);
@@ -361,46 +347,65 @@ __global__ void __launch_bounds__(kPassThreads) grid_pass_kernel(const void *__r
     const double th64 = pp.dp_over_eps * xm;
 
     Real accr = 0, acci = 0;
-    const int ia0 = a_lo - pp.amin;
-    for (int b0 = 0; b0 < pp.B; b0 += kCB) {
-        const int nbb = min(kCB, pp.B - b0);
-        for (int e = threadIdx.x; e < nb * kCB; e += kPassThreads) {
-            const int i = e / kCB, bb = e % kCB;
-            sw[i][bb] = bb < nbb ? in[(int64_t)(ia0 + i) * pp.B + b0 + bb] : zero;
-        }
-        __syncthreads();
-        for (int bb = 0; bb < nbb; ++bb) {
-            Real vr = 0, vi = 0;
+    // the band of nodes is processed MAXBAND at a time (coarse grids need more)
+    for (int c0 = 0; c0 < nb_total; c0 += MAXBAND) {
+        const int nb = min(MAXBAND, nb_total - c0);
+        const int a_first = a_lo + c0;
+        Real g[MAXBAND];
 #pragma unroll
-            for (int i = 0; i < MAXBAND; ++i) {
-                if (i < nb) {
-                    const C2 w = sw[i][bb];
-                    vr += g[i] * w.x;
-                    vi += g[i] * w.y;
+        for (int i = 0; i < MAXBAND; ++i) {
+            g[i] = 0;
+            if (i < nb && valid) {
+                const double cen = (double)(a_first + i) * pp.dq;
+                int64_t wlo, whi;
+                window_bounds(cen, pp.rs, pp.lo, pp.h, pp.N, &wlo, &whi);
+                if (m >= wlo && m <= whi) {
+                    const double dx = xm - cen;
+                    g[i] = (Real)exp(dx * dx * pp.neg_half_inv_eps);
                 }
             }
-            const int b = pp.bmin + b0 + bb;
-            Real er, ei;
-            if constexpr (FP64) {
-                double sn, cs;
-                sincos((double)b * th64, &sn, &cs);
-                er = cs;
-                ei = sn;
-            } else {
-                const float bf = (float)b;
-                float f = bf * phf;
-                f -= rint_fast(f);
-                float tau = fmaf(bf, plf, f);
-                tau -= rint_fast(tau);
-                float sn, cs;
-                __sincosf(6.283185307179586f * tau, &sn, &cs);
-                er = cs;
-                ei = sn;
-            }
-            accr += er * vr - ei * vi;
-            acci += er * vi + ei * vr;
         }
-        __syncthreads();
+        const int ia0 = a_first - pp.amin;
+        for (int b0 = 0; b0 < pp.B; b0 += kCB) {
+            const int nbb = min(kCB, pp.B - b0);
+            for (int e = threadIdx.x; e < nb * kCB; e += kPassThreads) {
+                const int i = e / kCB, bb = e % kCB;
+                sw[i][bb] = bb < nbb ? in[(int64_t)(ia0 + i) * pp.B + b0 + bb] : zero;
+            }
+            __syncthreads();
+            for (int bb = 0; bb < nbb; ++bb) {
+                Real vr = 0, vi = 0;
+#pragma unroll
+                for (int i = 0; i < MAXBAND; ++i) {
+                    if (i < nb) {
+                        const C2 w = sw[i][bb];
+                        vr += g[i] * w.x;
+                        vi += g[i] * w.y;
+                    }
+                }
+                const int b = pp.bmin + b0 + bb;
+                Real er, ei;
+                if constexpr (FP64) {
+                    double sn, cs;
+                    sincos((double)b * th64, &sn, &cs);
+                    er = cs;
+                    ei = sn;
+                } else {
+                    const float bf = (float)b;
+                    float f = bf * phf;
+                    f -= rint_fast(f);
+                    float tau = fmaf(bf, plf, f);
+                    tau -= rint_fast(tau);
+                    float sn, cs;
+                    __sincosf(6.283185307179586f * tau, &sn, &cs);
+                    er = cs;
+                    ei = sn;
+                }
+                accr += er * vr - ei * vi;
+                acci += er * vi + ei * vr;
+            }
+            __syncthreads();
+        }
     }
     if (valid) {
         C2 o;
@@ -438,12 +443,7 @@ fgr_status launch_pass(const void *in, void *out, const PassParams &pp, const ui
     if (band <= 16) FGR_PASS(16);
     else if (band <= 32) FGR_PASS(32);
     else if (band <= 48) FGR_PASS(48);
-    else if (band <= 64) FGR_PASS(64);
-    else if (band <= 96) FGR_PASS(96);
-    else {
-        set_error("fggc: window covers %d nodes per grid tile; at most 96 supported", band);
-        return FGR_E_INVALID;
-    }
+    else FGR_PASS(64);  // wider bands are processed in chunks of 64
 #undef FGR_PASS
     FGR_CUDA_TRY(cudaGetLastError());
     return FGR_OK;

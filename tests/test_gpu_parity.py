@@ -100,12 +100,15 @@ CASES = {
     2: (2, (70, 101), 300, 1 / 64),
     3: (3, (20, 17, 23), 60, 1 / 16),
 }
+# phase-space region of the random packets: a dense node box spans it, so the
+# 3-D case stays compact (as the packets of a WKB problem are)
+RANGES = {1: ((-3.6, 3.6), (-2.5, 2.5)), 2: ((-3.6, 3.6), (-2.5, 2.5)), 3: ((-1.2, 1.2), (-1.0, 1.0))}
 
 
 def _case(d, seed=1):
     d, n, m, eps = CASES[d]
     mesh = mesh_for(d, eps)
-    pk = random_packets(seed, d, m, q_range=(-3.6, 3.6), p_range=(-2.5, 2.5), s_range=(-3, 3),
+    pk = random_packets(seed, d, m, q_range=RANGES[d][0], p_range=RANGES[d][1], s_range=(-3, 3),
                         mesh=mesh, on_node_fraction=0.1)
     return pk, _grid(d, n), eps, mesh
 

@@ -97,8 +97,9 @@ def test_admission_by_budget_and_host_output(fgr):
         ts = [fgr.fgr_submit(srv, fgr.make_request(0, _grid(1, n), 1 / 256, opt, sid, u)) for u in outs]
         res = [fgr.fgr_poll(srv, t, -1) for t in ts]
         assert all(r.status == 0 for r in res)
+        # same request six times; atomics make the summation order (not the sum) vary
         for u in outs[1:]:
-            assert np.array_equal(u, outs[0])
+            assert np.linalg.norm(u - outs[0]) <= 1e-6 * np.linalg.norm(outs[0])
         # a request that can never fit is refused at submit
         big = np.zeros(1 << 22, np.complex64)
         with pytest.raises(fgr.FgrError) as e:
