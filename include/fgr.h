@@ -154,6 +154,29 @@ fgr_status fgr_reconstruct_direct(fgr_ctx *ctx, const fgr_packets *pk, void *u_o
 fgr_status fgr_reconstruct_fggc(fgr_ctx *ctx, const fgr_packets *pk, void *u_out,
                                 void *cuda_stream);
 
+/* FGGC reconstruction that allocates no memory (the paper has no counterpart:
+ * this is a deployment variant of fgr_reconstruct_fggc).
+ * Some callers cannot allocate device memory once they are running: a host
+ * whose device memory is committed up front to a fixed budget, a plugin inside
+ * a framework that owns every allocation on the device, or a latency-bound
+ * loop that cannot afford cudaMalloc/cudaFree and the synchronisation they can
+ * cause.  This entry point serves them: it computes exactly what
+ * fgr_reconstruct_fggc computes, with all of its working memory (bounds, row
+ * flag and node array) in one static device array of 8 MiB that the library
+ * reserves on every device that loads it, for as long as the process lives.
+ * Limits: 1-D contexts only; packets and u_out must be device memory; the node
+ * array may hold at most (8 MiB - 512 B) / 16 complex128 or / 8 complex64
+ * cells; larger problems return FGR_E_CAPACITY with the required size in
+ * fgr_last_error() (use fgr_reconstruct_fggc for them).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call clears and reuses the same array, so calls whose work overlaps on
+ * the device (any streams, any contexts) race and must be serialised by the
+ * caller.  The call waits for its own bounds readback like fgr_reconstruct_fggc.
+ * No cudaMalloc, cudaFree or other allocating routine is called. */
+fgr_status fgr_reconstruct_fggc_noalloc(fgr_ctx *ctx, const fgr_packets *pk, void *u_out,
+                                        void *cuda_stream);
+
 /* Read-only facts about a context. */
 typedef struct {
     int32_t d, n1, rank, precision;

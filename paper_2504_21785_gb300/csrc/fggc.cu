@@ -651,3 +651,198 @@ fgr_status run_fggc(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_
 }
 
 }  // namespace fgr
+
+// ---------------------------------------------------------------------------
+// fgr_reconstruct_fggc_noalloc: the 1-D FGGC reconstruction with all of its
+// working memory in one fixed device array, for callers that must not
+// allocate (see include/fgr.h).  It launches the same kernels as
+// fgr_reconstruct_fggc; only where the working memory comes from differs.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+// Working memory of the no-allocation entry point: bounds (256 B), row flags
+// (256 B), then the node array.  Lives in every device that loads the library.
+constexpr size_t kNoAllocBytes = size_t(8) << 20;
+constexpr size_t kNoAllocNodesOffset = 512;
+static __device__ __align__(256) unsigned char fgr_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_base[kNoAllocMaxDevices] = {};
+
+// Device address of fgr_noalloc_scratch on the current device (looked up once
+// per device).  Host code must not use the symbol itself as an address.
+fgr_status noalloc_base(int device, unsigned char **out) {
+    if (device < 0 || device >= kNoAllocMaxDevices) {
+        fgr::set_error("noalloc: device ordinal %d out of range", device);
+        return FGR_E_INVALID;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_base[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, fgr_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            fgr::set_error("noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+            cudaGetLastError();
+            return FGR_E_CUDA;
+        }
+        g_noalloc_base[device] = p;
+    }
+    *out = (unsigned char *)g_noalloc_base[device];
+    return FGR_OK;
+}
+
+}  // namespace
+
+extern "C" fgr_status fgr_reconstruct_fggc_noalloc(fgr_ctx *ctx, const fgr_packets *pk, void *u_out,
+                                                   void *stream) {
+    using namespace fgr;
+    clear_error();
+    if (!ctx || !pk || !u_out) {
+        set_error("noalloc: ctx, packets and u_out must be non-NULL");
+        return FGR_E_INVALID;
+    }
+    if (ctx->d != 1) {
+        set_error("noalloc: only 1-D contexts are supported (d = %d)", ctx->d);
+        return FGR_E_INVALID;
+    }
+    if (pk->m < 0 || pk->m > (int64_t(1) << 31) || pk->on_device != 1 ||
+        (pk->m > 0 && (!pk->q || !pk->p || !pk->s || !pk->a))) {
+        set_error("noalloc: packets must be device arrays (on_device = 1), 0 <= m <= 2^31");
+        return FGR_E_INVALID;
+    }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) {
+        set_error("noalloc: cudaSetDevice: %s", cudaGetErrorString(e));
+        return FGR_E_CUDA;
+    }
+    {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, u_out) != cudaSuccess ||
+            (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+            cudaGetLastError();
+            set_error("noalloc: u_out must be device memory");
+            return FGR_E_INVALID;
+        }
+    }
+    unsigned char *base = nullptr;
+    fgr_status rc = noalloc_base(ctx->device, &base);
+    if (rc != FGR_OK) return rc;
+    int *bnd = (int *)base;
+    uint8_t *flags = base + 256;
+    void *W = base + kNoAllocNodesOffset;
+
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool fp64 = ctx->opt.precision == FGR_FP64;
+    const Mesh &M = ctx->mesh;
+    const Grid &G = ctx->grid;
+    const Lsa &L = ctx->lsa;
+    const size_t eb = elem_bytes(ctx->opt.precision);
+    const size_t out_bytes = eb * (size_t)G.n[0];
+
+    Common c{};
+    c.n1 = L.n1;
+    for (int k = 0; k < L.n1; ++k) {
+        c.dq[k] = L.dq[k];
+        c.dp[k] = L.dp[k];
+    }
+    c.dqv = M.dq;
+    c.dpv = M.dp;
+    c.cq2_4 = M.cq * M.cq / 4;
+    c.cp2_4 = M.cp * M.cp / 4;
+    c.half_cqcp = M.cqcp / 2;
+    c.cc = M.cqcp / (2 * M_PI);
+    c.inv_2pi_eps = 1.0 / (2 * M_PI * M.eps);
+    c.pref = M.pref;
+    const double xlast = G.lo[0] + (double)(G.n[0] - 1) * G.h[0];
+    const int aglo = (int)std::max(-1e9, std::ceil((G.lo[0] - M.rs) / M.dq) - 1);
+    const int aghi = (int)std::min(1e9, std::floor((xlast + M.rs) / M.dq) + 1);
+
+    // bounds start at (+inf, -inf): they are rewritten on every call
+    int init[12];
+    for (int l = 0; l < 3; ++l) {
+        init[l * 4 + 0] = INT_MAX;
+        init[l * 4 + 1] = INT_MIN;
+        init[l * 4 + 2] = INT_MAX;
+        init[l * 4 + 3] = INT_MIN;
+    }
+    memcpy(ctx->host_pinned, init, sizeof(init));
+    FGR_CUDA_TRY(cudaMemcpyAsync(bnd, ctx->host_pinned, sizeof(init), cudaMemcpyHostToDevice, st));
+    const int64_t m = pk->m;
+    if (m > 0) {
+        bounds_kernel<1><<<(unsigned)((m + 255) / 256), 256, 0, st>>>(pk->q, pk->p, pk->a, m, c, aglo, aghi,
+                                                                     0, -1, 0, -1, bnd);
+        FGR_CUDA_TRY(cudaGetLastError());
+    }
+    FGR_CUDA_TRY(cudaMemcpyAsync(ctx->host_pinned, bnd, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
+    FGR_CUDA_TRY(cudaStreamSynchronize(st));
+    int hb[4];
+    memcpy(hb, ctx->host_pinned, sizeof(hb));
+    if (m == 0 || hb[0] == INT_MAX) {
+        FGR_CUDA_TRY(cudaMemsetAsync(u_out, 0, out_bytes, st));
+        if (!stream) FGR_CUDA_TRY(cudaStreamSynchronize(st));
+        return FGR_OK;
+    }
+    c.amin[0] = hb[0];
+    c.A[0] = hb[1] - hb[0] + 1;
+    c.bmin[0] = hb[2];
+    c.B[0] = hb[3] - hb[2] + 1;
+    const int64_t cells = (int64_t)c.A[0] * c.B[0];
+    if ((size_t)cells > (kNoAllocBytes - kNoAllocNodesOffset) / eb) {
+        set_error("noalloc: the node array needs %lld cells (%zu bytes); this entry point holds at most "
+                  "%zu bytes; use fgr_reconstruct_fggc",
+                  (long long)cells, (size_t)cells * eb, kNoAllocBytes - kNoAllocNodesOffset);
+        return FGR_E_CAPACITY;
+    }
+    c.sb[0] = 1;
+    c.sa[0] = c.B[0];
+    c.row_len = cells;
+    // the node array and the row flag accumulate: clear them
+    FGR_CUDA_TRY(cudaMemsetAsync(W, 0, eb * (size_t)cells, st));
+    FGR_CUDA_TRY(cudaMemsetAsync(flags, 0, 1, st));
+    const unsigned cb = (unsigned)((m + 127) / 128);
+    if (fp64) {
+        Params64 P{};
+        P.c = c;
+        memcpy(P.vr, L.vr, sizeof(P.vr));
+        memcpy(P.vi, L.vi, sizeof(P.vi));
+        memcpy(P.inv_lam, L.inv_lam, sizeof(P.inv_lam));
+        coeff_scatter_kernel<1, true><<<cb, 128, 0, st>>>(pk->q, pk->p, pk->s, pk->a, m, P, W, flags);
+    } else {
+        Params32 P{};
+        P.c = c;
+        for (int k = 0; k < kMaxN1; ++k)
+            for (int i = 0; i < kCheb; ++i)
+                for (int jj = 0; jj < kCheb; ++jj) {
+                    P.cre[(k * kCheb + i) * kCheb + jj] = L.cheb_re[k][i][jj];
+                    P.cim[(k * kCheb + i) * kCheb + jj] = L.cheb_im[k][i][jj];
+                }
+        coeff_scatter_kernel<1, false><<<cb, 128, 0, st>>>(pk->q, pk->p, pk->s, pk->a, m, P, W, flags);
+    }
+    FGR_CUDA_TRY(cudaGetLastError());
+    PassParams pp{};
+    pp.rows = 1;
+    pp.A = c.A[0];
+    pp.B = c.B[0];
+    pp.amin = c.amin[0];
+    pp.bmin = c.bmin[0];
+    pp.N = G.n[0];
+    pp.lo = G.lo[0];
+    pp.h = G.h[0];
+    pp.dq = M.dq;
+    pp.rs = M.rs;
+    pp.neg_half_inv_eps = -0.5 / M.eps;
+    pp.phi_scale = M.dp / (2 * M_PI * M.eps);
+    pp.dp_over_eps = M.dp / M.eps;
+    const int bmax_abs = std::max(std::abs(c.bmin[0]), std::abs(c.bmin[0] + c.B[0] - 1));
+    int lb = 1;
+    while ((1 << lb) < bmax_abs + 1) ++lb;
+    pp.two_pow_b = std::ldexp(1.0, std::max(1, 23 - lb));
+    const int band = (int)std::ceil(((kPassThreads - 1) * G.h[0] + 2 * M.rs) / M.dq) + 3;
+    rc = fp64 ? launch_pass<true>(W, u_out, pp, flags, band, st) : launch_pass<false>(W, u_out, pp, flags, band, st);
+    if (rc != FGR_OK) return rc;
+    if (!stream) FGR_CUDA_TRY(cudaStreamSynchronize(st));
+    return FGR_OK;
+}

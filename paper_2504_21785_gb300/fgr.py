@@ -91,6 +91,7 @@ SIGNATURES = {
                                      ctypes.c_double, vp]),
     "fgr_reconstruct_direct": (ctypes.c_int, [vp, P(fgr_packets), vp, vp]),
     "fgr_reconstruct_fggc": (ctypes.c_int, [vp, P(fgr_packets), vp, vp]),
+    "fgr_reconstruct_fggc_noalloc": (ctypes.c_int, [vp, P(fgr_packets), vp, vp]),
     "fgr_get_info": (ctypes.c_int, [vp, P(fgr_info)]),
     "fgr_set_timing": (ctypes.c_int, [vp, ctypes.c_int32]),
     "fgr_get_stats": (ctypes.c_int, [vp, P(fgr_stats)]),
@@ -228,6 +229,11 @@ def fgr_reconstruct_direct(ctx, packets: fgr_packets, u_out, stream=None):
 def fgr_reconstruct_fggc(ctx, packets: fgr_packets, u_out, stream=None):
     return _check(load().fgr_reconstruct_fggc(ctx, ctypes.byref(packets), _ptr(u_out)[0],
                                               _stream_handle(stream)))
+
+
+def fgr_reconstruct_fggc_noalloc(ctx, packets: fgr_packets, u_out, stream=None):
+    return _check(load().fgr_reconstruct_fggc_noalloc(ctx, ctypes.byref(packets), _ptr(u_out)[0],
+                                                      _stream_handle(stream)))
 
 
 def fgr_get_info(ctx) -> fgr_info:
