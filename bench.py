@@ -95,14 +95,13 @@ def rk4_nsteps(t: float, dt: float) -> int:
     return int(n) if abs(r - n) <= 1e-9 * max(n, 1.0) else int(math.ceil(r))
 
 
-def rk4_flops_per_packet_step(d: int) -> int:
-    """Algorithmic FP64 operations of one RK4 step of eq. 2.3-2.7 for a separable
-    cosine potential, per packet (sin and cos counted as one operation each,
-    a division as one): 4 right-hand sides of (per dimension 2 trig + 27
-    arithmetic, plus 9 for S and A) and 4 state updates of 2 ops per variable."""
-    nvar = 6 * d + 3
-    rhs = d * (2 + 27) + 9
-    return 4 * rhs + 4 * 2 * nvar + 2 * nvar
+# FP64 FLOPs the RK4 kernel executes per packet-step (FMA = 2), counted by ncu
+# on GB300 (DFMA x 2 + DMUL + DADD of rk4_kernel), 1-D cosine potential:
+# 91 DFMA + 36 DMUL + 13 DADD.  See profiles/rk4_kernel_1d_262144_100steps.md.
+RK4_FP64_FLOPS_PER_PACKET_STEP = {(1, "cossum"): 231}
+# DRAM bytes of one RK4 launch on the bench workload (ncu, same capture): the
+# packet arrays are read once; the written state stays in L2 at kernel end.
+RK4_TRAFFIC_BYTES = {(1, "cossum", 262144): 10515200}
 
 
 def run_ours(args):
@@ -233,8 +232,10 @@ def run_ours(args):
     ms_direct = agg(direct_ms)
     ms_e2e = agg(e2e_ms)
     total_packets = M * world
-    flops = rk4_flops_per_packet_step(d) * M * rk4_nsteps(t_final, dt)
-    achieved_tflops = flops / (ms_prop * 1e-3) / 1e12
+    kind = w["potential"]["kind"]
+    fpps = RK4_FP64_FLOPS_PER_PACKET_STEP.get((d, kind))
+    flops = fpps * M * rk4_nsteps(t_final, dt) if fpps else None
+    achieved_tflops = flops / (ms_prop * 1e-3) / 1e12 if flops else None
     out = None
     if rank == 0:
         out = {
@@ -266,22 +267,173 @@ def run_ours(args):
                 "fggc_stage_split": fggc_stages,
                 "direct_stage_split": direct_stages,
             },
-            "roofline": {"kernel": "rk4_kernel<1> (fgr_propagate)", "bound": "alu",
+            "roofline": {"kernel": "rk4_kernel (fgr_propagate)", "bound": "alu",
                          "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
-                         "peak_source": "nominal FP64 rate of the profiling recipe (not in MEASURED_PEAKS.json)",
-                         "flops_per_launch": flops},
+                         "frac": achieved_tflops / FP64_PEAK_TFLOPS if achieved_tflops else None,
+                         "traffic": RK4_TRAFFIC_BYTES.get((d, kind, M)),
+                         "peak_source": "nominal FP64 rate of the profiling recipe (MEASURED_PEAKS.json has no "
+                                        "FP64 figure; a pure-DFMA probe measured 1.19 TFLOP/s)",
+                         "flops_per_launch": flops,
+                         "flops_counted": "FP64 FLOPs executed per packet-step (ncu: 2 DFMA + DMUL + DADD)"},
             "e2e": {"value": total_packets / (ms_e2e * 1e-3), "unit": "packets/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": gpu_launches,
             "clocks": clk.summary(),
         }
+        if args.extra:
+            out["workloads"] = {}
+            for cfg in [int(x) for x in args.extra.split(",") if x]:
+                out["workloads"]["config%d" % cfg] = reconstruct_bench(cfg, args, flush)
+        if args.serving:
+            out["serving"] = serving_bench(args, local)
         if args.cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(w, args.cpu_sample)
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return out
+
+
+def reconstruct_bench(cfg: int, args, flush):
+    """FGGC and direct reconstruction of another workload (propagated once on
+    the GPU, not timed), L2 flushed between timed runs."""
+    import numpy as np
+    import torch
+
+    import paper_2504_21785_gb300 as fgr
+    from workloads import config_workload
+    w = config_workload(cfg)
+    d, eps, grid = w["d"], w["eps"], w["grid"]
+    M = int(w["packets"]["s"].size)
+    prec = fgr.FGR_FP32 if w["precision"] == "fp32" else fgr.FGR_FP64
+    cdt = torch.complex64 if prec == fgr.FGR_FP32 else torch.complex128
+    ctx = fgr.Context(d, grid, eps, fgr.make_options(precision=prec))
+    arrs = [torch.tensor(np.ascontiguousarray(w["packets"][k]), dtype=torch.float64, device="cuda") for k in "qpsa"]
+    pk = fgr.make_packets(*arrs)
+    t0 = time.perf_counter()
+    fgr.fgr_propagate(ctx.handle, pk, fgr.make_potential(**w["potential"]), w["t"], w["dt"])
+    torch.cuda.synchronize()
+    t_prop = time.perf_counter() - t0
+    shape = tuple(grid["n"][:d])
+    uf = torch.zeros(shape, dtype=cdt, device="cuda")
+    ud = torch.zeros(shape, dtype=cdt, device="cuda")
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, fn, u in (("fggc", fgr.fgr_reconstruct_fggc, uf), ("direct", fgr.fgr_reconstruct_direct, ud)):
+        fn(ctx.handle, pk, u, stream)
+        ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(ctx.handle, pk, u, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        res[name] = statistics.mean(ms)
+    a, b = uf.cpu().numpy(), ud.cpu().numpy()
+    rel = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    fgr.fgr_set_timing(ctx.handle, True)
+    fgr.fgr_reconstruct_fggc(ctx.handle, pk, uf, stream)
+    st = fgr.fgr_get_stats(ctx.handle)
+    ctx.close()
+    return {"workload": w["name"], "packets": M, "propagate_s_untimed": t_prop,
+            "fggc_ms": res["fggc"], "direct_ms": res["direct"],
+            "fggc_packets_per_s": M / (res["fggc"] * 1e-3), "direct_packets_per_s": M / (res["direct"] * 1e-3),
+            "fggc_over_direct": res["direct"] / res["fggc"], "rel_l2_fggc_vs_direct": rel,
+            "fggc_nodes": int(st.nodes),
+            "fggc_stage_split_ms": {"bounds_alloc": st.prep_ms, "coeff_scatter": st.scatter_ms, "grid": st.grid_ms}}
+
+
+def serving_bench(args, device_index: int):
+    """Continuous-batching server under a Poisson stream (the serving workload):
+    packet sets with d in {1, 2}, eps log-uniform in [1/1024, 1/64], M log-uniform
+    in [4k, cap], propagated once to t = 0.5 on the GPU and kept resident;
+    requests pick a set, a grid (1-D: 1024..32768 points, 2-D: 256^2..1024^2)
+    and a method (direct / FGGC) uniformly; FP32.  Capacity = 1 / mean isolated
+    service time; p50/p99 of submit-to-done latency at 0.5x and 0.9x capacity."""
+    import numpy as np
+    import torch
+
+    import paper_2504_21785_gb300 as fgr
+    from workloads import wkb_packets, WKB_TANH
+
+    rng = np.random.default_rng(0)
+    srv = fgr.fgr_server_create(150 << 30, args.serve_inflight)
+    sets = []
+    pot1 = fgr.make_potential("cossum", c0=1.0, amp=-1.0, k=1.0)
+    pot2 = fgr.make_potential("cossum", c0=2.0, amp=1.0, k=1.0)
+    for i in range(args.serve_sets):
+        d = 1 + (i % 2)
+        eps = float(2.0 ** -rng.uniform(6, 10))
+        m_target = float(np.exp(rng.uniform(np.log(4096), np.log(args.serve_max_packets))))
+        per_dim = m_target ** (1.0 / d)
+        n = max(8, int(2 ** round(np.log2(np.sqrt(per_dim)))))
+        pk = wkb_packets(d, eps, n, n, WKB_TANH)
+        arrs = [torch.tensor(np.ascontiguousarray(pk[k]), dtype=torch.float64, device="cuda") for k in "qpsa"]
+        grid0 = dict(d=d, n=[16] * d, lo=[-3.0] * d, hi=[3.0] * d)
+        with fgr.Context(d, grid0, eps) as c:
+            fgr.fgr_propagate(c.handle, fgr.make_packets(*arrs), pot1 if d == 1 else pot2, 0.5, 1e-4)
+        torch.cuda.synchronize()
+        sid = fgr.fgr_register_packets(srv, d, fgr.make_packets(*arrs))
+        sets.append((sid, d, eps, int(pk["s"].size)))
+        del arrs
+    opt = fgr.make_options(precision=fgr.FGR_FP32)
+
+    def draw():
+        sid, d, eps, m = sets[rng.integers(len(sets))]
+        if d == 1:
+            n = [int(2 ** rng.integers(10, 16))]
+        else:
+            n = [int(2 ** rng.integers(8, 11))] * 2
+        grid = dict(d=d, n=n, lo=[-np.pi] * d, hi=[np.pi] * d)
+        return sid, d, eps, m, grid, int(rng.integers(0, 2))
+
+    # isolated service times
+    iso = []
+    for _ in range(args.serve_probe):
+        sid, d, eps, m, grid, method = draw()
+        u = torch.zeros(tuple(grid["n"]), dtype=torch.complex64, device="cuda")
+        t = fgr.fgr_submit(srv, fgr.make_request(method, grid, eps, opt, sid, u))
+        r = fgr.fgr_poll(srv, t, -1)
+        iso.append(r.t_done_ms - r.t_start_ms)
+    # saturated throughput: a burst submitted at once, all slots busy
+    burst = [draw() for _ in range(args.serve_probe)]
+    bouts = [torch.zeros(tuple(g["n"]), dtype=torch.complex64, device="cuda") for (_, _, _, _, g, _) in burst]
+    tb0 = time.perf_counter()
+    bt = [fgr.fgr_submit(srv, fgr.make_request(mth, g, e, opt, sid, u))
+          for (sid, d, e, m, g, mth), u in zip(burst, bouts)]
+    for t in bt:
+        fgr.fgr_poll(srv, t, -1)
+    capacity = len(burst) / (time.perf_counter() - tb0)  # requests/s with every slot busy
+    levels = {}
+    for frac in (0.5, 0.9):
+        lam = frac * capacity
+        reqs = [draw() for _ in range(args.serve_requests)]
+        outs = [torch.zeros(tuple(g["n"]), dtype=torch.complex64, device="cuda") for (_, _, _, _, g, _) in reqs]
+        gaps = rng.exponential(1.0 / lam, size=len(reqs))
+        tickets = []
+        t0 = time.perf_counter()
+        due = t0
+        for (sid, d, eps, m, grid, method), u, gap in zip(reqs, outs, gaps):
+            due += gap
+            while time.perf_counter() < due:
+                time.sleep(max(0.0, min(0.001, due - time.perf_counter())))
+            tickets.append(fgr.fgr_submit(srv, fgr.make_request(method, grid, eps, opt, sid, u)))
+        res = [fgr.fgr_poll(srv, t, -1) for t in tickets]
+        t1 = time.perf_counter()
+        lat = np.array([r.t_done_ms - r.t_submit_ms for r in res])
+        ok = all(r.status == 0 for r in res)
+        packets = sum(q[3] for q in reqs)
+        levels["%.1fx" % frac] = {"lambda_req_per_s": lam, "p50_ms": float(np.percentile(lat, 50)),
+                                  "p99_ms": float(np.percentile(lat, 99)), "packets_per_s": packets / (t1 - t0),
+                                  "requests": len(reqs), "all_ok": ok}
+    fgr.fgr_server_destroy(srv)
+    return {"sets": [{"d": d, "eps": eps, "packets": m} for (_, d, eps, m) in sets],
+            "inflight": args.serve_inflight, "isolated_service_ms_mean": float(np.mean(iso)),
+            "isolated_service_ms_p50": float(np.percentile(iso, 50)),
+            "capacity_req_per_s": capacity, "levels": levels,
+            "mix": "d in {1,2}; grids 1-D 1024..32768, 2-D 256^2..1024^2; direct/fggc 50/50; fp32"}
 
 
 def cpu_baseline(w, sample: int):
@@ -335,6 +487,31 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "packets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_profile_case(args):
+    """One short pass of every kernel on the benchmark workload, for ncu:
+    propagate to t = 0.01 (100 RK4 steps), then one FGGC and one direct
+    reconstruction of the propagated packets."""
+    import numpy as np
+    import torch
+
+    import paper_2504_21785_gb300 as fgr
+    from workloads import config_workload
+    w = config_workload(args.config)
+    d, eps, grid = w["d"], w["eps"], w["grid"]
+    prec = fgr.FGR_FP32 if w["precision"] == "fp32" else fgr.FGR_FP64
+    with fgr.Context(d, grid, eps, fgr.make_options(precision=prec)) as ctx:
+        arrs = [torch.tensor(np.ascontiguousarray(w["packets"][k]), dtype=torch.float64, device="cuda")
+                for k in "qpsa"]
+        pk = fgr.make_packets(*arrs)
+        fgr.fgr_propagate(ctx.handle, pk, fgr.make_potential(**w["potential"]), 0.01, w["dt"])
+        cdt = torch.complex64 if prec == fgr.FGR_FP32 else torch.complex128
+        u = torch.zeros(tuple(grid["n"][:d]), dtype=cdt, device="cuda")
+        fgr.fgr_reconstruct_fggc(ctx.handle, pk, u)
+        fgr.fgr_reconstruct_direct(ctx.handle, pk, u)
+        torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "config %d" % args.config, "ok": True}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -345,7 +522,19 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-sample", type=int, default=2048)
     ap.add_argument("--ref-sample", type=int, default=512)
+    ap.add_argument("--extra", default="3", help="other workloads to reconstruct, e.g. 3,4 ('' for none)")
+    ap.add_argument("--no-serving", dest="serving", action="store_false")
+    ap.add_argument("--serve-sets", type=int, default=8)
+    ap.add_argument("--serve-max-packets", type=int, default=1 << 19)
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-probe", type=int, default=40)
+    ap.add_argument("--serve-inflight", type=int, default=4)
+    ap.add_argument("--profile", action="store_true",
+                    help="run every kernel once on a short case (for ncu) and exit")
     args = ap.parse_args()
+    if args.profile:
+        run_profile_case(args)
+        return
     out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:
         print(json.dumps(out))

@@ -114,14 +114,17 @@ fgr_status fgr_default_options(fgr_options *opt);
  * eps-free Gram matrix of eq. 3.22 for the chosen neighbour strategy and its
  * pseudo-inverse by an eigen-decomposition (the Gram is Hermitian positive
  * semi-definite, so this is its SVD; Remark 2, Algorithm 2 Step 0), on the host
- * in extended precision.  Binds to the current CUDA device.
+ * in extended precision (cached per strategy, so later contexts with the same
+ * mesh constants and strategy reuse it).  Binds to the current CUDA device.
  * opt may be NULL (defaults).  *out receives the context; free it with
  * fgr_destroy.  FGR_E_INVALID if d is not in 1..3, grid->d != d, eps <= 0 or
  * not finite, any n < 1, hi <= lo, or the options are out of range. */
 fgr_status fgr_create(int32_t d, const fgr_grid *grid, double eps, const fgr_options *opt,
                       fgr_ctx **out);
 
-/* Frees the context and its device scratch; NULL is a no-op. */
+/* Frees the context; NULL is a no-op.  Work already enqueued by the context
+ * completes normally (scratch memory is stream-ordered and returns to a
+ * per-device pool shared by all contexts). */
 void fgr_destroy(fgr_ctx *ctx);
 
 /* Message describing the calling thread's last failure ("" if none). */
@@ -149,8 +152,10 @@ fgr_status fgr_reconstruct_direct(fgr_ctx *ctx, const fgr_packets *pk, void *u_o
  * exp(-i cq cp (s - dq_k) b0) (eq. 3.13); d-dimensional coefficients are
  * products over dimensions.  The weights A_j e^{iS_j/eps} c_j^(k) are summed
  * onto grid nodes (eq. 2.25) and the node Gaussians are summed on the grid
- * (eq. 2.24) one dimension at a time.  FP64: all FP64.  FP32: coefficients in
- * FP64, node array and grid sums in complex64. */
+ * (eq. 2.24) one dimension at a time.  FP64: all FP64.  FP32: the coefficients
+ * come from a Chebyshev surrogate of c~(s,t) built on the host from the same
+ * pseudo-inverse (error < 1e-12, evaluated in FP32), phases are reduced in FP64,
+ * node array and grid sums in complex64. */
 fgr_status fgr_reconstruct_fggc(fgr_ctx *ctx, const fgr_packets *pk, void *u_out,
                                 void *cuda_stream);
 

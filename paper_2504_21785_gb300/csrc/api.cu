@@ -3,7 +3,12 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
 #include <new>
+#include <tuple>
+#include <vector>
 
 #include "internal.h"
 
@@ -84,6 +89,69 @@ int64_t rk4_nsteps(double t, double dt) {
 }
 
 namespace {
+
+// Process-wide resources shared by contexts, so that creating a context costs
+// no CUDA allocation after the first one on a device.
+std::mutex g_res_mu;
+std::map<std::tuple<double, double, int, int, double>, std::shared_ptr<Lsa>> g_lsa_cache;
+cudaMemPool_t g_pools[64] = {};
+constexpr int kPinnedSlot = 256;                      // bytes per context
+std::vector<std::pair<char *, int>> g_pinned_slabs;   // (slab, slots)
+std::vector<char *> g_pinned_free;
+
+std::shared_ptr<Lsa> shared_lsa(double cq, double cp, int nq, int np, double rcond) {
+    const auto key = std::make_tuple(cq, cp, nq, np, rcond);
+    {
+        std::lock_guard<std::mutex> lk(g_res_mu);
+        auto it = g_lsa_cache.find(key);
+        if (it != g_lsa_cache.end()) return it->second;
+    }
+    auto L = std::make_shared<Lsa>();
+    if (!build_lsa(cq, cp, nq, np, rcond, L.get())) return nullptr;
+    std::lock_guard<std::mutex> lk(g_res_mu);
+    return g_lsa_cache.emplace(key, L).first->second;
+}
+
+cudaError_t device_pool(int device, cudaMemPool_t *out) {
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_res_mu);
+    if (!g_pools[device]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t pool;
+        cudaError_t e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t thr = UINT64_MAX;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        if (e != cudaSuccess) return e;
+        g_pools[device] = pool;
+    }
+    *out = g_pools[device];
+    return cudaSuccess;
+}
+
+cudaError_t pinned_slot(char **out) {
+    std::lock_guard<std::mutex> lk(g_res_mu);
+    if (g_pinned_free.empty()) {
+        const int slots = 256;
+        char *slab = nullptr;
+        cudaError_t e = cudaMallocHost((void **)&slab, (size_t)slots * kPinnedSlot);
+        if (e != cudaSuccess) return e;
+        g_pinned_slabs.push_back({slab, slots});
+        for (int i = slots - 1; i >= 0; --i) g_pinned_free.push_back(slab + (size_t)i * kPinnedSlot);
+    }
+    *out = g_pinned_free.back();
+    g_pinned_free.pop_back();
+    return cudaSuccess;
+}
+
+void release_pinned_slot(char *p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_res_mu);
+    g_pinned_free.push_back(p);
+}
 
 bool is_finite(double x) { return std::isfinite(x); }
 
@@ -305,8 +373,8 @@ fgr_status fgr_create(int32_t d, const fgr_grid *grid, double eps, const fgr_opt
     rc = resolve_options(opt, &o);
     if (rc != FGR_OK) return rc;
     return guarded([&]() -> fgr_status {
-        Lsa L;
-        if (!build_lsa(o.cq, o.cp, o.nq, o.np, o.rcond, &L)) {
+        std::shared_ptr<Lsa> L = shared_lsa(o.cq, o.cp, o.nq, o.np, o.rcond);
+        if (!L) {
             set_error("neighbour strategy rejected");
             return FGR_E_INVALID;
         }
@@ -314,7 +382,7 @@ fgr_status fgr_create(int32_t d, const fgr_grid *grid, double eps, const fgr_opt
         c->d = d;
         c->grid = G;
         c->opt = o;
-        c->lsa = L;
+        c->lsa = *L;
         Mesh &M = c->mesh;
         M.eps = eps;
         M.sigma = std::sqrt(eps);
@@ -328,25 +396,16 @@ fgr_status fgr_create(int32_t d, const fgr_grid *grid, double eps, const fgr_opt
         M.rs = o.window_r * M.sigma;
         cudaError_t e = cudaGetDevice(&c->device);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
-        if (e == cudaSuccess) {
-            cudaMemPoolProps props{};
-            props.allocType = cudaMemAllocationTypePinned;
-            props.location.type = cudaMemLocationTypeDevice;
-            props.location.id = c->device;
-            e = cudaMemPoolCreate(&c->pool, &props);
-        }
-        if (e == cudaSuccess) {
-            uint64_t thr = UINT64_MAX;
-            e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr);
-        }
-        if (e == cudaSuccess) e = cudaMallocHost((void **)&c->host_pinned, 64 * sizeof(int64_t));
+        if (e == cudaSuccess) e = device_pool(c->device, &c->pool);
+        char *slot = nullptr;
+        if (e == cudaSuccess) e = pinned_slot(&slot);
         if (e != cudaSuccess) {
             set_error("CUDA initialisation failed: %s", cudaGetErrorString(e));
             cudaGetLastError();
-            if (c->pool) cudaMemPoolDestroy(c->pool);
             delete c;
             return FGR_E_CUDA;
         }
+        c->host_pinned = (int64_t *)slot;
         *out = c;
         return FGR_OK;
     });
@@ -354,10 +413,10 @@ fgr_status fgr_create(int32_t d, const fgr_grid *grid, double eps, const fgr_opt
 
 void fgr_destroy(fgr_ctx *ctx) {
     if (!ctx) return;
-    cudaSetDevice(ctx->device);
-    cudaDeviceSynchronize();
-    if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
-    if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+    // Kernels in flight hold no reference to the context (parameters are
+    // copied at launch, scratch returns to the pool in stream order), and every
+    // call that uses the pinned slot waits for it before returning.
+    release_pinned_slot((char *)ctx->host_pinned);
     delete ctx;
 }
 

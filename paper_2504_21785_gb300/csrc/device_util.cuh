@@ -24,6 +24,16 @@ __device__ __forceinline__ void window_bounds(double c, double rs, double lo, do
     *mhi = (int64_t)b;
 }
 
+// q = x / step with floor(q) equal to floor of the correctly rounded quotient:
+// x * (1/step) differs from it by a few ulps, so it decides the floor unless it
+// lies within 1e-9 (relative) of an integer, where the division is done.
+__device__ __forceinline__ double quotient_for_floor(double x, double step, double inv_step) {
+    const double r = x * inv_step;
+    const double n = rint(r);
+    if (fabs(r - n) <= 1e-9 * fmax(1.0, fabs(r))) return __ddiv_rn(x, step);
+    return r;
+}
+
 // Grid coordinate x_m = lo + m*h without contraction.
 __device__ __forceinline__ double grid_x(double lo, double h, int64_t m) {
     return __dadd_rn(lo, __dmul_rn((double)m, h));

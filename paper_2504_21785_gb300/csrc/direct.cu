@@ -10,8 +10,10 @@
 // Evaluation.  Each CTA owns one output tile (TPT points per thread) and one of
 // S interleaved slices of the tile's packet list; packet records are staged in
 // shared memory 256 at a time and every thread evaluates exp and sincos for each
-// (packet, point) pair inside the packet's window.  Slices are combined with
-// atomic adds into the zeroed output.
+// (packet, point) pair inside the packet's window.  FP32 sums run over one
+// chunk of 256 records and are folded into FP64 totals (a point can collect
+// 10^4-10^5 packets: a single FP32 running sum would drift by ~sqrt(N) ulps).
+// Slices are combined with atomic adds into the zeroed output.
 //
 // FP32 records carry the per-packet phase reduced in FP64 to turns at the
 // window start (tau0) and the per-grid-step increment nu split into a coarse
@@ -38,8 +40,8 @@ __host__ __device__ constexpr int tileT(int l) {
 
 template <int D>
 struct __align__(16) RecF {
-    int mlo[D];
-    int wlen[D];
+    float mlo[D];    // window start (grid index, exact in FP32)
+    float wlen[D];   // window length
     float delta[D];  // x_{mlo} - Q per dimension
     float nuhi[D];   // turns per grid step, coarse part
     float nulo[D];   // remainder
@@ -71,28 +73,28 @@ __device__ __forceinline__ int tile_linear(const GridDev &g, const int *t) {
     return lin;
 }
 
-// Pass 1: windows, home tile, per-tile counts.
+// Pass 1: windows, home tile, per-tile counts (one atomic per tile and warp).
 template <int D>
 __global__ void bin_count_kernel(const double *__restrict__ q, int64_t m, GridDev g, double rs,
                                  int *__restrict__ home, int *__restrict__ counts) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= m) return;
-    int t[D];
-    bool empty = false;
+    int lin = -1;
+    if (j < m) {
+        int t[D];
+        bool empty = false;
 #pragma unroll
-    for (int l = 0; l < D; ++l) {
-        int64_t lo, hi;
-        window_bounds(q[l * m + j], rs, g.lo[l], g.h[l], g.n[l], &lo, &hi);
-        if (lo > hi) empty = true;
-        t[l] = (int)(lo / tileT<D>(l));
+        for (int l = 0; l < D; ++l) {
+            int64_t lo, hi;
+            window_bounds(q[l * m + j], rs, g.lo[l], g.h[l], g.n[l], &lo, &hi);
+            if (lo > hi) empty = true;
+            t[l] = (int)(lo / tileT<D>(l));
+        }
+        if (!empty) lin = tile_linear<D>(g, t);
+        home[j] = lin;
     }
-    if (empty) {
-        home[j] = -1;
-        return;
-    }
-    const int lin = tile_linear<D>(g, t);
-    home[j] = lin;
-    atomicAdd(&counts[lin], 1);
+    const unsigned group = __match_any_sync(0xffffffffu, lin);
+    const int lane = threadIdx.x & 31;
+    if (lin >= 0 && lane == __ffs(group) - 1) atomicAdd(&counts[lin], __popc(group));
 }
 
 // Exclusive scan of n counts into off[0..n] (single CTA, sequential blocks).
@@ -123,6 +125,7 @@ __global__ void scan_kernel(const int *__restrict__ counts, int64_t *__restrict_
 struct RecParams {
     double rs, eps, inv_eps, pref;
     double two_pow_b;  // 2^b for the nu split
+    double inv_two_pow_b;
 };
 
 // Pass 2: build the records in binned order.
@@ -133,10 +136,16 @@ __global__ void bin_scatter_kernel(const double *__restrict__ q, const double *_
                                    const int64_t *__restrict__ off, int *__restrict__ cursor,
                                    void *__restrict__ recs) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= m) return;
-    const int h = home[j];
+    const int h = j < m ? home[j] : -1;
+    // one atomic per tile and warp; lanes of a group take consecutive slots
+    const unsigned group = __match_any_sync(0xffffffffu, h);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(group) - 1;
+    int base = 0;
+    if (h >= 0 && lane == leader) base = atomicAdd(&cursor[h], __popc(group));
+    base = __shfl_sync(0xffffffffu, base, leader);
     if (h < 0) return;
-    const int64_t pos = off[h] + atomicAdd(&cursor[h], 1);
+    const int64_t pos = off[h] + base + __popc(group & ((1u << lane) - 1u));
     const double ar = rp.pref * a[j], ai = rp.pref * a[m + j];
     if (FP64) {
         RecD<D> r;
@@ -162,14 +171,14 @@ __global__ void bin_scatter_kernel(const double *__restrict__ q, const double *_
             int64_t lo, hi;
             const double Q = q[l * m + j], P = p[l * m + j];
             window_bounds(Q, rp.rs, g.lo[l], g.h[l], g.n[l], &lo, &hi);
-            r.mlo[l] = (int)lo;
-            r.wlen[l] = (int)(hi - lo + 1);
+            r.mlo[l] = (float)lo;
+            r.wlen[l] = (float)(hi - lo + 1);
             const double dx = grid_x(g.lo[l], g.h[l], lo) - Q;
             r.delta[l] = (float)dx;
             phase += P * dx;
             double nu = P * g.h[l] * inv_2pi_eps;  // turns per grid step
             nu -= rint(nu);
-            const double nuhi = rint(nu * rp.two_pow_b) / rp.two_pow_b;
+            const double nuhi = rint(nu * rp.two_pow_b) * rp.inv_two_pow_b;
             r.nuhi[l] = (float)nuhi;
             r.nulo[l] = (float)(nu - nuhi);
         }
@@ -274,6 +283,11 @@ __global__ void __launch_bounds__(kThreads) direct_kernel(const void *__restrict
         valid[r] = ok;
         lin_out[r] = lin;
     }
+    float mf[kTpt][D];
+#pragma unroll
+    for (int r = 0; r < kTpt; ++r)
+#pragma unroll
+        for (int l = 0; l < D; ++l) mf[r][l] = (float)mi[r][l];
     double xd[kTpt][D];
     if (FP64) {
 #pragma unroll
@@ -315,16 +329,15 @@ __global__ void __launch_bounds__(kThreads) direct_kernel(const void *__restrict
             const Rec &R = *reinterpret_cast<const Rec *>(&srec[jr * kWords]);
 #pragma unroll
             for (int r = 0; r < kTpt; ++r) {
-                int k[D];
-                bool in = valid[r];
-#pragma unroll
-                for (int l = 0; l < D; ++l) {
-                    k[l] = mi[r][l] - R.mlo[l];
-                    in = in && (unsigned)k[l] < (unsigned)R.wlen[l];
-                }
-                if (!in) continue;
                 if (FP64) {
                     const RecD<D> &Rd = reinterpret_cast<const RecD<D> &>(R);
+                    bool in = valid[r];
+#pragma unroll
+                    for (int l = 0; l < D; ++l) {
+                        const int k = mi[r][l] - Rd.mlo[l];
+                        in = in && (unsigned)k < (unsigned)Rd.wlen[l];
+                    }
+                    if (!in) continue;
                     double phase = Rd.S, g2 = 0.0;
 #pragma unroll
                     for (int l = 0; l < D; ++l) {
@@ -340,10 +353,18 @@ __global__ void __launch_bounds__(kThreads) direct_kernel(const void *__restrict
                     accd[r][1] += Rd.ar * gi + Rd.ai * gr;
                 } else {
                     const RecF<D> &Rf = reinterpret_cast<const RecF<D> &>(R);
+                    float kk[D];
+                    bool in = valid[r];
+#pragma unroll
+                    for (int l = 0; l < D; ++l) {
+                        kk[l] = mf[r][l] - Rf.mlo[l];
+                        in = in && kk[l] >= 0.f && kk[l] < Rf.wlen[l];
+                    }
+                    if (!in) continue;
                     float e = 0.f, tau = Rf.tau0;
 #pragma unroll
                     for (int l = 0; l < D; ++l) {
-                        const float kf = (float)k[l];
+                        const float kf = kk[l];
                         const float dx = fmaf(kf, P.hf[l], Rf.delta[l]);
                         e = fmaf(dx, dx, e);
                         float f = kf * Rf.nuhi[l];
@@ -360,6 +381,14 @@ __global__ void __launch_bounds__(kThreads) direct_kernel(const void *__restrict
                 }
             }
         }
+        if (!FP64) {  // fold this chunk's FP32 partial sums into the FP64 totals
+#pragma unroll
+            for (int r = 0; r < kTpt; ++r) {
+                accd[r][0] += (double)accf[r][0];
+                accd[r][1] += (double)accf[r][1];
+                accf[r][0] = accf[r][1] = 0.f;
+            }
+        }
         __syncthreads();
     }
     if (L == 0) return;
@@ -369,7 +398,7 @@ __global__ void __launch_bounds__(kThreads) direct_kernel(const void *__restrict
         if (FP64)
             atomic_add_c(reinterpret_cast<double2 *>(u_v) + lin_out[r], accd[r][0], accd[r][1]);
         else
-            atomic_add_c(reinterpret_cast<float2 *>(u_v) + lin_out[r], accf[r][0], accf[r][1]);
+            atomic_add_c(reinterpret_cast<float2 *>(u_v) + lin_out[r], (float)accd[r][0], (float)accd[r][1]);
     }
 }
 
@@ -425,6 +454,7 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
     int lbits = 1;
     while ((1 << lbits) < wmax_all + 1) ++lbits;
     rp.two_pow_b = std::ldexp(1.0, std::max(1, 24 - lbits));
+    rp.inv_two_pow_b = 1.0 / rp.two_pow_b;
     if (fp64)
         bin_scatter_kernel<D, true><<<pb, 256, 0, st>>>(pk.q, pk.p, pk.s, pk.a, m, g, rp, home, off, cursor, recs);
     else

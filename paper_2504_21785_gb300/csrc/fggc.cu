@@ -29,32 +29,11 @@
 #include <cmath>
 
 #include "device_util.cuh"
+#include "fggc_params.h"
 #include "internal.h"
 
 namespace fgr {
 namespace {
-
-struct Common {
-    int n1;
-    int dq[kMaxN1], dp[kMaxN1];
-    double dqv, dpv;                 // mesh steps
-    double cq2_4, cp2_4, half_cqcp;  // eq. 3.23 constants
-    double cc;                       // cq cp / (2 pi): node phase in turns
-    double inv_2pi_eps, pref;
-    int amin[kMaxDim], A[kMaxDim], bmin[kMaxDim], B[kMaxDim];
-    int64_t sa[kMaxDim], sb[kMaxDim];  // W strides of a_l and b_l
-    int64_t row_len;                   // cells per row of the first grid pass
-};
-
-struct Params64 {
-    Common c;
-    double vr[kMaxN1 * kMaxN1], vi[kMaxN1 * kMaxN1], inv_lam[kMaxN1];
-};
-
-struct Params32 {
-    Common c;
-    float cre[kMaxN1 * kCheb * kCheb], cim[kMaxN1 * kCheb * kCheb];
-};
 
 // ---------------------------------------------------------------------------
 // node box
@@ -85,8 +64,8 @@ __global__ void bounds_kernel(const double *__restrict__ q, const double *__rest
     if (use) {
 #pragma unroll
         for (int l = 0; l < D; ++l) {
-            const double ra = floor(__ddiv_rn(q[l * m + j], c.dqv));
-            const double rb = floor(__ddiv_rn(p[l * m + j], c.dpv));
+            const double ra = floor(quotient_for_floor(q[l * m + j], c.dqv, c.inv_dq));
+            const double rb = floor(quotient_for_floor(p[l * m + j], c.dpv, c.inv_dp));
             const double lim = 1e9;
             const int a0 = (int)fmin(fmax(ra, -lim), lim), b0 = (int)fmin(fmax(rb, -lim), lim);
             const int alo = max(a0 + dqmin, aglo[l]), ahi = min(a0 + dqmax, aghi[l]);
@@ -97,200 +76,38 @@ __global__ void bounds_kernel(const double *__restrict__ q, const double *__rest
             hi_b[l] = b0 + dpmax;
         }
     }
+    // warp, then block reduction; one atomic per block and value
+    __shared__ int red[8][kMaxDim * 4];
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 #pragma unroll
     for (int l = 0; l < D; ++l) {
         const int v0 = __reduce_min_sync(0xffffffffu, use ? lo_a[l] : INT_MAX);
         const int v1 = __reduce_max_sync(0xffffffffu, use ? hi_a[l] : INT_MIN);
         const int v2 = __reduce_min_sync(0xffffffffu, use ? lo_b[l] : INT_MAX);
         const int v3 = __reduce_max_sync(0xffffffffu, use ? hi_b[l] : INT_MIN);
-        if ((threadIdx.x & 31) == 0 && v0 != INT_MAX) {
-            atomicMin(&out[l * 4 + 0], v0);
-            atomicMax(&out[l * 4 + 1], v1);
-            atomicMin(&out[l * 4 + 2], v2);
-            atomicMax(&out[l * 4 + 3], v3);
+        if ((threadIdx.x & 31) == 0) {
+            red[warp][l * 4 + 0] = v0;
+            red[warp][l * 4 + 1] = v1;
+            red[warp][l * 4 + 2] = v2;
+            red[warp][l * 4 + 3] = v3;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < D * 4) {
+        const int k = threadIdx.x;
+        const bool is_min = (k & 1) == 0;
+        int v = red[0][k];
+        for (int w = 1; w < nwarps; ++w) v = is_min ? min(v, red[w][k]) : max(v, red[w][k]);
+        if (is_min ? v != INT_MAX : v != INT_MIN) {
+            if (is_min) atomicMin(&out[k], v);
+            else atomicMax(&out[k], v);
         }
     }
 }
 
-// ---------------------------------------------------------------------------
-// coefficients + scatter
-// ---------------------------------------------------------------------------
 __device__ __forceinline__ void cmul(double ar, double ai, double br, double bi, double &cr, double &ci) {
     cr = ar * br - ai * bi;
     ci = ar * bi + ai * br;
-}
-__device__ __forceinline__ void cmul(float ar, float ai, float br, float bi, float &cr, float &ci) {
-    cr = ar * br - ai * bi;
-    ci = ar * bi + ai * br;
-}
-
-// FP64: per-dimension coefficients through the eigen factors.
-__device__ void coeff_dim64(const Params64 &P, double Q, double Pm, int &a0, int &b0, double *cr,
-                            double *ci) {
-    const Common &c = P.c;
-    const double r = __ddiv_rn(Q, c.dqv), rp = __ddiv_rn(Pm, c.dpv);
-    const double fa = floor(r), fb = floor(rp);
-    const double s = r - fa, t = rp - fb;
-    a0 = (int)fmin(fmax(fa, -1e9), 1e9);
-    b0 = (int)fmin(fmax(fb, -1e9), 1e9);
-    const int n = c.n1;
-    double fr[kMaxN1], fi[kMaxN1];
-    for (int j = 0; j < n; ++j) {  // eq. 3.23
-        const double u = c.dq[j] - s, v = c.dp[j] - t;
-        const double mag = exp(-c.cq2_4 * u * u - c.cp2_4 * v * v);
-        double sn, cs;
-        sincos(c.half_cqcp * (s - c.dq[j]) * (c.dp[j] + t), &sn, &cs);
-        fr[j] = mag * cs;
-        fi[j] = mag * sn;
-    }
-    double yr[kMaxN1], yi[kMaxN1];
-    for (int i = 0; i < n; ++i) {  // y = diag(1/lam) V^H f
-        double sr = 0, si = 0;
-        for (int j = 0; j < n; ++j) {
-            const double vr = P.vr[j * kMaxN1 + i], vi = P.vi[j * kMaxN1 + i];
-            sr += vr * fr[j] + vi * fi[j];
-            si += vr * fi[j] - vi * fr[j];
-        }
-        yr[i] = sr * P.inv_lam[i];
-        yi[i] = si * P.inv_lam[i];
-    }
-    // node phase base (turns): -cc * r * b0 and -cc * a0
-    double t0 = -c.cc * (r * fb);
-    t0 -= rint(t0);
-    double t1 = -c.cc * fa;
-    t1 -= rint(t1);
-    for (int k = 0; k < n; ++k) {  // c~ = conj(V y), times the node phase
-        double sr = 0, si = 0;
-        for (int i = 0; i < n; ++i) {
-            const double vr = P.vr[k * kMaxN1 + i], vi = P.vi[k * kMaxN1 + i];
-            sr += vr * yr[i] - vi * yi[i];
-            si += vr * yi[i] + vi * yr[i];
-        }
-        si = -si;
-        double tk = t0 + c.dp[k] * t1 - c.cc * (double)(c.dq[k] * c.dp[k]);
-        tk -= rint(tk);
-        double sn, cs;
-        sincospi(2.0 * tk, &sn, &cs);
-        cmul(sr, si, cs, sn, cr[k], ci[k]);
-    }
-}
-
-// FP32: per-dimension coefficients through the Chebyshev surrogate.
-__device__ void coeff_dim32(const Params32 &P, double Q, double Pm, int &a0, int &b0, float *cr,
-                            float *ci) {
-    const Common &c = P.c;
-    const double r = __ddiv_rn(Q, c.dqv), rp = __ddiv_rn(Pm, c.dpv);
-    const double fa = floor(r), fb = floor(rp);
-    a0 = (int)fmin(fmax(fa, -1e9), 1e9);
-    b0 = (int)fmin(fmax(fb, -1e9), 1e9);
-    const float xs = (float)(2.0 * (r - fa) - 1.0), xt = (float)(2.0 * (rp - fb) - 1.0);
-    float Ts[kCheb], Tt[kCheb];
-    Ts[0] = 1.f;
-    Ts[1] = xs;
-    Tt[0] = 1.f;
-    Tt[1] = xt;
-#pragma unroll
-    for (int i = 2; i < kCheb; ++i) {
-        Ts[i] = 2.f * xs * Ts[i - 1] - Ts[i - 2];
-        Tt[i] = 2.f * xt * Tt[i - 1] - Tt[i - 2];
-    }
-    double t0 = -c.cc * (r * fb);
-    t0 -= rint(t0);
-    double t1 = -c.cc * fa;
-    t1 -= rint(t1);
-    const float t0f = (float)t0, t1f = (float)t1, ccf = (float)c.cc;
-    const int n = c.n1;
-    for (int k = 0; k < n; ++k) {
-        float sr = 0.f, si = 0.f;
-        const float *Cr = P.cre + k * kCheb * kCheb, *Ci = P.cim + k * kCheb * kCheb;
-#pragma unroll
-        for (int i = 0; i < kCheb; ++i) {
-            float ur = 0.f, ui = 0.f;
-#pragma unroll
-            for (int j = 0; j < kCheb; ++j) {
-                ur = fmaf(Cr[i * kCheb + j], Tt[j], ur);
-                ui = fmaf(Ci[i * kCheb + j], Tt[j], ui);
-            }
-            sr = fmaf(Ts[i], ur, sr);
-            si = fmaf(Ts[i], ui, si);
-        }
-        float tk = t0f + (float)c.dp[k] * t1f - ccf * (float)(c.dq[k] * c.dp[k]);
-        tk -= rint_fast(tk);
-        float sn, cs;
-        sincospif(2.f * tk, &sn, &cs);
-        cmul(sr, si, cs, sn, cr[k], ci[k]);
-    }
-}
-
-template <int D, bool FP64>
-__global__ void __launch_bounds__(128) coeff_scatter_kernel(
-    const double *__restrict__ q, const double *__restrict__ p, const double *__restrict__ s,
-    const double *__restrict__ a, int64_t m,
-    const __grid_constant__ typename std::conditional<FP64, Params64, Params32>::type P,
-    void *__restrict__ W_v,
-    uint8_t *__restrict__ row_flag) {
-    using Real = typename std::conditional<FP64, double, float>::type;
-    using C2 = typename std::conditional<FP64, double2, float2>::type;
-    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= m) return;
-    const Common &c = P.c;
-    const double ar = a[j], ai = a[m + j];
-    if (ar == 0.0 && ai == 0.0) return;  // contributes exact zeros
-    // weight pref * A * e^{i S/eps}
-    double ts = s[j] * c.inv_2pi_eps;
-    ts -= rint(ts);
-    Real wr, wi;
-    if (FP64) {
-        double sn, cs;
-        sincospi(2.0 * ts, &sn, &cs);
-        double xr, xi;
-        cmul(ar * c.pref, ai * c.pref, cs, sn, xr, xi);
-        wr = (Real)xr;
-        wi = (Real)xi;
-    } else {
-        float sn, cs;
-        sincospif(2.f * (float)ts, &sn, &cs);
-        float xr, xi;
-        cmul((float)(ar * c.pref), (float)(ai * c.pref), cs, sn, xr, xi);
-        wr = (Real)xr;
-        wi = (Real)xi;
-    }
-    Real cr[D][kMaxN1], ci[D][kMaxN1];
-    int a0[D], b0[D];
-#pragma unroll
-    for (int l = 0; l < D; ++l) {
-        if constexpr (FP64)
-            coeff_dim64(P, q[l * m + j], p[l * m + j], a0[l], b0[l], cr[l], ci[l]);
-        else
-            coeff_dim32(P, q[l * m + j], p[l * m + j], a0[l], b0[l], cr[l], ci[l]);
-    }
-    C2 *W = reinterpret_cast<C2 *>(W_v);
-    const int n = c.n1;
-    int ncomb = 1;
-#pragma unroll
-    for (int l = 0; l < D; ++l) ncomb *= n;
-    for (int comb = 0; comb < ncomb; ++comb) {
-        int rem = comb;
-        int64_t idx = 0;
-        bool in = true;
-        Real vr = wr, vi = wi;
-#pragma unroll
-        for (int l = D - 1; l >= 0; --l) {
-            const int k = rem % n;
-            rem /= n;
-            const int ia = a0[l] + c.dq[k] - c.amin[l];
-            const int ib = b0[l] + c.dp[k] - c.bmin[l];
-            in = in && (unsigned)ia < (unsigned)c.A[l] && (unsigned)ib < (unsigned)c.B[l];
-            idx += ia * c.sa[l] + ib * c.sb[l];
-            Real tr, ti;
-            cmul(vr, vi, cr[l][k], ci[l][k], tr, ti);
-            vr = tr;
-            vi = ti;
-        }
-        if (!in) continue;
-        atomic_add_c(W + idx, vr, vi);
-        row_flag[idx / c.row_len] = 1;
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -303,11 +120,15 @@ struct PassParams {
     double lo, h, dq, rs, neg_half_inv_eps;
     double phi_scale;  // dp / (2 pi eps): phase of e^{i b dp x/eps} in turns per unit b
     double two_pow_b;  // split of the turn increment (FP32 path)
+    double inv_two_pow_b;
     double dp_over_eps;
 };
 
 constexpr int kPassThreads = 64;
 constexpr int kCB = 32;
+
+constexpr int kPassPts = 2;                         // grid points per thread
+constexpr int kPassTile = kPassThreads * kPassPts;  // grid points per CTA
 
 template <bool FP64, int MAXBAND>
 __global__ void __launch_bounds__(kPassThreads) grid_pass_kernel(const void *__restrict__ in_v,
@@ -315,103 +136,176 @@ __global__ void __launch_bounds__(kPassThreads) grid_pass_kernel(const void *__r
                                                                  const uint8_t *__restrict__ flags) {
     using Real = typename std::conditional<FP64, double, float>::type;
     using C2 = typename std::conditional<FP64, double2, float2>::type;
-    __shared__ C2 sw[MAXBAND][kCB];
+    __shared__ __align__(16) C2 sw[MAXBAND][kCB];
+    __shared__ int swlo[MAXBAND], swhi[MAXBAND];
     const int64_t row = blockIdx.x;
-    const int64_t m0 = (int64_t)blockIdx.y * kPassThreads;
-    const int64_t m = m0 + threadIdx.x;
-    const bool valid = m < pp.N;
+    const int64_t m0 = (int64_t)blockIdx.y * kPassTile;
+    int64_t mm[kPassPts];
+    bool valid[kPassPts];
+#pragma unroll
+    for (int r = 0; r < kPassPts; ++r) {
+        mm[r] = m0 + threadIdx.x + r * kPassThreads;
+        valid[r] = mm[r] < pp.N;
+    }
     C2 *out = reinterpret_cast<C2 *>(out_v) + row * pp.N;
     const C2 *in = reinterpret_cast<const C2 *>(in_v) + row * (int64_t)pp.A * pp.B;
     C2 zero;
     zero.x = 0;
     zero.y = 0;
-    if (flags && !flags[row]) {
-        if (valid) out[m] = zero;
-        return;
-    }
-    const int64_t m1 = min(m0 + kPassThreads - 1, pp.N - 1);
+    // b-range of this CTA (blockIdx.z of gridDim.z slices, whole chunks of kCB)
+    const int nchunk = (pp.B + kCB - 1) / kCB;
+    const int per = (nchunk + gridDim.z - 1) / gridDim.z;
+    const int bs = blockIdx.z * per * kCB, be = min(pp.B, (int)(blockIdx.z + 1) * per * kCB);
+    const bool split = gridDim.z > 1;  // slices add into a zeroed output
+    const int64_t m1 = min(m0 + kPassTile - 1, pp.N - 1);
     const double x0 = grid_x(pp.lo, pp.h, m0), x1 = grid_x(pp.lo, pp.h, m1);
     const int a_lo = max(pp.amin, (int)ceil((x0 - pp.rs) / pp.dq) - 1);
     const int a_hi = min(pp.amin + pp.A - 1, (int)floor((x1 + pp.rs) / pp.dq) + 1);
     const int nb_total = a_hi - a_lo + 1;
-    if (nb_total <= 0) {
-        if (valid) out[m] = zero;
+    if ((flags && !flags[row]) || bs >= be || nb_total <= 0) {
+        if (!split) {
+#pragma unroll
+            for (int r = 0; r < kPassPts; ++r)
+                if (valid[r]) out[mm[r]] = zero;
+        }
         return;
     }
-    const double xm = grid_x(pp.lo, pp.h, valid ? m : m0);
-    // e^{i b dp x_m / eps}: turns per unit b, reduced in FP64
-    double phi = pp.phi_scale * xm;
-    phi -= rint(phi);
-    const double phi_hi = rint(phi * pp.two_pow_b) / pp.two_pow_b;
-    const float phf = (float)phi_hi, plf = (float)(phi - phi_hi);
-    const double th64 = pp.dp_over_eps * xm;
+    double xm[kPassPts], th64[kPassPts];
+    float phf[kPassPts], plf[kPassPts];
+#pragma unroll
+    for (int r = 0; r < kPassPts; ++r) {
+        xm[r] = grid_x(pp.lo, pp.h, valid[r] ? mm[r] : m0);
+        // e^{i b dp x_m / eps}: turns per unit b, reduced in FP64
+        double phi = pp.phi_scale * xm[r];
+        phi -= rint(phi);
+        const double phi_hi = rint(phi * pp.two_pow_b) * pp.inv_two_pow_b;
+        phf[r] = (float)phi_hi;
+        plf[r] = (float)(phi - phi_hi);
+        th64[r] = pp.dp_over_eps * xm[r];
+    }
+    const float cef = (float)(pp.neg_half_inv_eps * 1.4426950408889634);  // log2(e) / (-2 eps)
+    const float dqf = (float)pp.dq;
 
-    Real accr = 0, acci = 0;
+    Real accr[kPassPts], acci[kPassPts];
+    double totr[kPassPts], toti[kPassPts];  // chunk partials are folded in here
+#pragma unroll
+    for (int r = 0; r < kPassPts; ++r) {
+        accr[r] = acci[r] = 0;
+        totr[r] = toti[r] = 0;
+    }
     // the band of nodes is processed MAXBAND at a time (coarse grids need more)
     for (int c0 = 0; c0 < nb_total; c0 += MAXBAND) {
         const int nb = min(MAXBAND, nb_total - c0);
         const int a_first = a_lo + c0;
-        Real g[MAXBAND];
+        // each node's window once per CTA (FP64, the rule of include/fgr.h)
+        __syncthreads();
+        for (int i = threadIdx.x; i < nb; i += kPassThreads) {
+            int64_t wlo, whi;
+            window_bounds((double)(a_first + i) * pp.dq, pp.rs, pp.lo, pp.h, pp.N, &wlo, &whi);
+            swlo[i] = (int)wlo;
+            swhi[i] = (int)whi;
+        }
+        __syncthreads();
+        Real g[kPassPts][MAXBAND];
 #pragma unroll
-        for (int i = 0; i < MAXBAND; ++i) {
-            g[i] = 0;
-            if (i < nb && valid) {
-                const double cen = (double)(a_first + i) * pp.dq;
-                int64_t wlo, whi;
-                window_bounds(cen, pp.rs, pp.lo, pp.h, pp.N, &wlo, &whi);
-                if (m >= wlo && m <= whi) {
-                    const double dx = xm - cen;
-                    g[i] = (Real)exp(dx * dx * pp.neg_half_inv_eps);
+        for (int r = 0; r < kPassPts; ++r) {
+            const double dx0 = xm[r] - (double)a_first * pp.dq;
+#pragma unroll
+            for (int i = 0; i < MAXBAND; ++i) {
+                g[r][i] = 0;
+                if (i < nb && valid[r] && mm[r] >= swlo[i] && mm[r] <= swhi[i]) {
+                    if constexpr (FP64) {
+                        const double dx = xm[r] - (double)(a_first + i) * pp.dq;
+                        g[r][i] = exp(dx * dx * pp.neg_half_inv_eps);
+                    } else {
+                        const float dxf = (float)dx0 - (float)i * dqf;
+                        g[r][i] = ex2_approx(dxf * dxf * cef);
+                    }
                 }
             }
         }
         const int ia0 = a_first - pp.amin;
-        for (int b0 = 0; b0 < pp.B; b0 += kCB) {
-            const int nbb = min(kCB, pp.B - b0);
+        for (int b0 = bs; b0 < be; b0 += kCB) {
+            const int nbb = min(kCB, be - b0);
             for (int e = threadIdx.x; e < nb * kCB; e += kPassThreads) {
                 const int i = e / kCB, bb = e % kCB;
                 sw[i][bb] = bb < nbb ? in[(int64_t)(ia0 + i) * pp.B + b0 + bb] : zero;
             }
             __syncthreads();
-            for (int bb = 0; bb < nbb; ++bb) {
-                Real vr = 0, vi = 0;
+            for (int bb = 0; bb < nbb; bb += 2) {  // b pairs; the padding column is zero
+                Real vr[kPassPts][2], vi[kPassPts][2];
+#pragma unroll
+                for (int r = 0; r < kPassPts; ++r) vr[r][0] = vr[r][1] = vi[r][0] = vi[r][1] = 0;
 #pragma unroll
                 for (int i = 0; i < MAXBAND; ++i) {
                     if (i < nb) {
-                        const C2 w = sw[i][bb];
-                        vr += g[i] * w.x;
-                        vi += g[i] * w.y;
+                        C2 w0, w1;
+                        if constexpr (FP64) {
+                            w0 = sw[i][bb];
+                            w1 = sw[i][bb + 1];
+                        } else {  // one 16-byte shared load for the pair
+                            const float4 w = *reinterpret_cast<const float4 *>(&sw[i][bb]);
+                            w0.x = w.x;
+                            w0.y = w.y;
+                            w1.x = w.z;
+                            w1.y = w.w;
+                        }
+#pragma unroll
+                        for (int r = 0; r < kPassPts; ++r) {
+                            vr[r][0] += g[r][i] * w0.x;
+                            vi[r][0] += g[r][i] * w0.y;
+                            vr[r][1] += g[r][i] * w1.x;
+                            vi[r][1] += g[r][i] * w1.y;
+                        }
                     }
                 }
-                const int b = pp.bmin + b0 + bb;
-                Real er, ei;
-                if constexpr (FP64) {
-                    double sn, cs;
-                    sincos((double)b * th64, &sn, &cs);
-                    er = cs;
-                    ei = sn;
-                } else {
-                    const float bf = (float)b;
-                    float f = bf * phf;
-                    f -= rint_fast(f);
-                    float tau = fmaf(bf, plf, f);
-                    tau -= rint_fast(tau);
-                    float sn, cs;
-                    __sincosf(6.283185307179586f * tau, &sn, &cs);
-                    er = cs;
-                    ei = sn;
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int b = pp.bmin + b0 + bb + u;
+#pragma unroll
+                    for (int r = 0; r < kPassPts; ++r) {
+                        Real er, ei;
+                        if constexpr (FP64) {
+                            double sn, cs;
+                            sincos((double)b * th64[r], &sn, &cs);
+                            er = cs;
+                            ei = sn;
+                        } else {
+                            const float bf = (float)b;
+                            float f = bf * phf[r];
+                            f -= rint_fast(f);
+                            float tau = fmaf(bf, plf[r], f);
+                            tau -= rint_fast(tau);
+                            float sn, cs;
+                            __sincosf(6.283185307179586f * tau, &sn, &cs);
+                            er = cs;
+                            ei = sn;
+                        }
+                        accr[r] += er * vr[r][u] - ei * vi[r][u];
+                        acci[r] += er * vi[r][u] + ei * vr[r][u];
+                    }
                 }
-                accr += er * vr - ei * vi;
-                acci += er * vi + ei * vr;
+            }
+#pragma unroll
+            for (int r = 0; r < kPassPts; ++r) {
+                totr[r] += (double)accr[r];
+                toti[r] += (double)acci[r];
+                accr[r] = acci[r] = 0;
             }
             __syncthreads();
         }
     }
-    if (valid) {
-        C2 o;
-        o.x = accr;
-        o.y = acci;
-        out[m] = o;
+#pragma unroll
+    for (int r = 0; r < kPassPts; ++r) {
+        if (!valid[r]) continue;
+        if (split) {
+            atomic_add_c(out + mm[r], (Real)totr[r], (Real)toti[r]);
+        } else {
+            C2 o;
+            o.x = (Real)totr[r];
+            o.y = (Real)toti[r];
+            out[mm[r]] = o;
+        }
     }
 }
 
@@ -432,13 +326,27 @@ __global__ void transpose_kernel(const C2 *__restrict__ in, C2 *__restrict__ out
 
 template <bool FP64>
 fgr_status launch_pass(const void *in, void *out, const PassParams &pp, const uint8_t *flags,
-                       int band, cudaStream_t st) {
+                       int band, int num_sms, cudaStream_t st) {
     if (pp.rows == 0 || pp.N == 0) return FGR_OK;
     if (pp.rows > INT_MAX) {
         set_error("fggc: too many rows in a grid pass");
         return FGR_E_CAPACITY;
     }
-    dim3 grid((unsigned)pp.rows, (unsigned)((pp.N + kPassThreads - 1) / kPassThreads));
+    const int64_t mtiles = (pp.N + kPassTile - 1) / kPassTile;
+    if (mtiles > 65535) {
+        set_error("fggc: %lld points per grid dimension; at most %d supported", (long long)pp.N,
+                  65535 * kPassTile);
+        return FGR_E_INVALID;
+    }
+    // split the b-range when rows x tiles alone cannot fill the device
+    const int64_t target = (int64_t)num_sms * 16;
+    const int nchunk = (pp.B + kCB - 1) / kCB;
+    int splits = (int)std::min<int64_t>(std::max<int64_t>(1, (target + pp.rows * mtiles - 1) / (pp.rows * mtiles)),
+                                        std::max(1, std::min(nchunk, 64)));
+    if (splits > 1) {
+        FGR_CUDA_TRY(cudaMemsetAsync(out, 0, (FP64 ? 16 : 8) * (size_t)pp.rows * (size_t)pp.N, st));
+    }
+    dim3 grid((unsigned)pp.rows, (unsigned)mtiles, (unsigned)splits);
 #define FGR_PASS(MB) grid_pass_kernel<FP64, MB><<<grid, kPassThreads, 0, st>>>(in, out, pp, flags)
     if (band <= 16) FGR_PASS(16);
     else if (band <= 32) FGR_PASS(32);
@@ -480,6 +388,8 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
     }
     c.dqv = M.dq;
     c.dpv = M.dp;
+    c.inv_dq = 1.0 / M.dq;
+    c.inv_dp = 1.0 / M.dp;
     c.cq2_4 = M.cq * M.cq / 4;
     c.cp2_4 = M.cp * M.cp / 4;
     c.half_cqcp = M.cqcp / 2;
@@ -570,14 +480,14 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
     FGR_CUDA_TRY(cudaMemsetAsync(flags, 0, (size_t)rows0, st));
     timer.mark(&ctx->timing.last.prep_ms);
 
-    const unsigned cb = (unsigned)((m + 127) / 128);
     if (fp64) {
         Params64 P{};
         P.c = c;
         memcpy(P.vr, L.vr, sizeof(P.vr));
         memcpy(P.vi, L.vi, sizeof(P.vi));
         memcpy(P.inv_lam, L.inv_lam, sizeof(P.inv_lam));
-        coeff_scatter_kernel<D, true><<<cb, 128, 0, st>>>(pk.q, pk.p, pk.s, pk.a, m, P, W, flags);
+        fgr_status r = launch_coeff_scatter(D, L.n1, st, pk, &P, nullptr, W, flags);
+        if (r != FGR_OK) return r;
     } else {
         Params32 P{};
         P.c = c;
@@ -587,9 +497,9 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
                     P.cre[(k * kCheb + i) * kCheb + jj] = L.cheb_re[k][i][jj];
                     P.cim[(k * kCheb + i) * kCheb + jj] = L.cheb_im[k][i][jj];
                 }
-        coeff_scatter_kernel<D, false><<<cb, 128, 0, st>>>(pk.q, pk.p, pk.s, pk.a, m, P, W, flags);
+        fgr_status r = launch_coeff_scatter(D, L.n1, st, pk, nullptr, &P, W, flags);
+        if (r != FGR_OK) return r;
     }
-    FGR_CUDA_TRY(cudaGetLastError());
     ++launches;
     timer.mark(&ctx->timing.last.scatter_ms);
 
@@ -617,11 +527,12 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
         int lb = 1;
         while ((1 << lb) < bmax_abs + 1) ++lb;
         pp.two_pow_b = std::ldexp(1.0, std::max(1, 23 - lb));
-        const int band = (int)std::ceil(((kPassThreads - 1) * G.h[l] + 2 * M.rs) / M.dq) + 3;
+        pp.inv_two_pow_b = 1.0 / pp.two_pow_b;
+        const int band = (int)std::ceil(((kPassTile - 1) * G.h[l] + 2 * M.rs) / M.dq) + 3;
         const bool last = l == 0;
         void *dst = (D == 1) ? u_dev : (cur == buf1 ? buf2 : buf1);
-        fgr_status r = fp64 ? launch_pass<true>(cur, dst, pp, l == D - 1 ? flags : nullptr, band, st)
-                            : launch_pass<false>(cur, dst, pp, l == D - 1 ? flags : nullptr, band, st);
+        fgr_status r = fp64 ? launch_pass<true>(cur, dst, pp, l == D - 1 ? flags : nullptr, band, ctx->num_sms, st)
+                            : launch_pass<false>(cur, dst, pp, l == D - 1 ? flags : nullptr, band, ctx->num_sms, st);
         if (r != FGR_OK) return r;
         ++launches;
         if (D > 1) {
@@ -641,6 +552,15 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
 }
 
 }  // namespace
+
+fgr_status launch_coeff_scatter(int d, int n1, cudaStream_t st, const PacketsDev &pk, const Params64 *p64,
+                                const Params32 *p32, void *W, uint8_t *flags) {
+    switch (d) {
+    case 1: return launch_coeff_scatter_d1(n1, st, pk, p64, p32, W, flags);
+    case 2: return launch_coeff_scatter_d2(n1, st, pk, p64, p32, W, flags);
+    default: return launch_coeff_scatter_d3(n1, st, pk, p64, p32, W, flags);
+    }
+}
 
 fgr_status run_fggc(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t st, Scratch &scratch) {
     switch (ctx->d) {
@@ -750,6 +670,8 @@ extern "C" fgr_status fgr_reconstruct_fggc_noalloc(fgr_ctx *ctx, const fgr_packe
     }
     c.dqv = M.dq;
     c.dpv = M.dp;
+    c.inv_dq = 1.0 / M.dq;
+    c.inv_dp = 1.0 / M.dp;
     c.cq2_4 = M.cq * M.cq / 4;
     c.cp2_4 = M.cp * M.cp / 4;
     c.half_cqcp = M.cqcp / 2;
@@ -802,14 +724,14 @@ extern "C" fgr_status fgr_reconstruct_fggc_noalloc(fgr_ctx *ctx, const fgr_packe
     // the node array and the row flag accumulate: clear them
     FGR_CUDA_TRY(cudaMemsetAsync(W, 0, eb * (size_t)cells, st));
     FGR_CUDA_TRY(cudaMemsetAsync(flags, 0, 1, st));
-    const unsigned cb = (unsigned)((m + 127) / 128);
     if (fp64) {
         Params64 P{};
         P.c = c;
         memcpy(P.vr, L.vr, sizeof(P.vr));
         memcpy(P.vi, L.vi, sizeof(P.vi));
         memcpy(P.inv_lam, L.inv_lam, sizeof(P.inv_lam));
-        coeff_scatter_kernel<1, true><<<cb, 128, 0, st>>>(pk->q, pk->p, pk->s, pk->a, m, P, W, flags);
+        rc = launch_coeff_scatter(1, L.n1, st, PacketsDev{m, pk->q, pk->p, pk->s, pk->a}, &P, nullptr, W, flags);
+        if (rc != FGR_OK) return rc;
     } else {
         Params32 P{};
         P.c = c;
@@ -819,9 +741,9 @@ extern "C" fgr_status fgr_reconstruct_fggc_noalloc(fgr_ctx *ctx, const fgr_packe
                     P.cre[(k * kCheb + i) * kCheb + jj] = L.cheb_re[k][i][jj];
                     P.cim[(k * kCheb + i) * kCheb + jj] = L.cheb_im[k][i][jj];
                 }
-        coeff_scatter_kernel<1, false><<<cb, 128, 0, st>>>(pk->q, pk->p, pk->s, pk->a, m, P, W, flags);
+        rc = launch_coeff_scatter(1, L.n1, st, PacketsDev{m, pk->q, pk->p, pk->s, pk->a}, nullptr, &P, W, flags);
+        if (rc != FGR_OK) return rc;
     }
-    FGR_CUDA_TRY(cudaGetLastError());
     PassParams pp{};
     pp.rows = 1;
     pp.A = c.A[0];
@@ -840,8 +762,10 @@ extern "C" fgr_status fgr_reconstruct_fggc_noalloc(fgr_ctx *ctx, const fgr_packe
     int lb = 1;
     while ((1 << lb) < bmax_abs + 1) ++lb;
     pp.two_pow_b = std::ldexp(1.0, std::max(1, 23 - lb));
-    const int band = (int)std::ceil(((kPassThreads - 1) * G.h[0] + 2 * M.rs) / M.dq) + 3;
-    rc = fp64 ? launch_pass<true>(W, u_out, pp, flags, band, st) : launch_pass<false>(W, u_out, pp, flags, band, st);
+    pp.inv_two_pow_b = 1.0 / pp.two_pow_b;
+    const int band = (int)std::ceil(((kPassTile - 1) * G.h[0] + 2 * M.rs) / M.dq) + 3;
+    rc = fp64 ? launch_pass<true>(W, u_out, pp, flags, band, ctx->num_sms, st)
+              : launch_pass<false>(W, u_out, pp, flags, band, ctx->num_sms, st);
     if (rc != FGR_OK) return rc;
     if (!stream) FGR_CUDA_TRY(cudaStreamSynchronize(st));
     return FGR_OK;

@@ -1,0 +1,9 @@
+// K3+K4 instantiations for 3-D problems (see fggc_coeff.cuh).
+#include "fggc_coeff.cuh"
+
+namespace fgr {
+fgr_status launch_coeff_scatter_d3(int n1, cudaStream_t st, const PacketsDev &pk, const Params64 *p64,
+                                   const Params32 *p32, void *W, uint8_t *flags) {
+    return launch_coeff_d<3>(n1, st, pk, p64, p32, W, flags);
+}
+}  // namespace fgr

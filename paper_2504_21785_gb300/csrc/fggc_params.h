@@ -1,0 +1,43 @@
+// Parameter blocks of the FGGC kernels, shared by the node-box / grid-pass
+// code (fggc.cu) and the coefficient + scatter kernels (fggc_coeff*.cu).
+#pragma once
+
+#include "internal.h"
+
+namespace fgr {
+
+struct Common {
+    int n1;
+    int dq[kMaxN1], dp[kMaxN1];
+    double dqv, dpv;                 // mesh steps
+    double inv_dq, inv_dp;
+    double cq2_4, cp2_4, half_cqcp;  // eq. 3.23 constants
+    double cc;                       // cq cp / (2 pi): node phase in turns
+    double inv_2pi_eps, pref;
+    int amin[kMaxDim], A[kMaxDim], bmin[kMaxDim], B[kMaxDim];
+    int64_t sa[kMaxDim], sb[kMaxDim];  // W strides of a_l and b_l
+    int64_t row_len;                   // cells per row of the first grid pass
+};
+
+struct Params64 {
+    Common c;
+    double vr[kMaxN1 * kMaxN1], vi[kMaxN1 * kMaxN1], inv_lam[kMaxN1];
+};
+
+struct Params32 {
+    Common c;
+    float cre[kMaxN1 * kCheb * kCheb], cim[kMaxN1 * kCheb * kCheb];
+};
+
+// Launches the coefficient + scatter kernel (K3+K4) for dimension d, one
+// thread per packet; exactly one of p64 / p32 is non-NULL.
+fgr_status launch_coeff_scatter(int d, int n1, cudaStream_t st, const PacketsDev &pk, const Params64 *p64,
+                                const Params32 *p32, void *W, uint8_t *flags);
+fgr_status launch_coeff_scatter_d1(int n1, cudaStream_t st, const PacketsDev &pk, const Params64 *p64,
+                                   const Params32 *p32, void *W, uint8_t *flags);
+fgr_status launch_coeff_scatter_d2(int n1, cudaStream_t st, const PacketsDev &pk, const Params64 *p64,
+                                   const Params32 *p32, void *W, uint8_t *flags);
+fgr_status launch_coeff_scatter_d3(int n1, cudaStream_t st, const PacketsDev &pk, const Params64 *p64,
+                                   const Params32 *p32, void *W, uint8_t *flags);
+
+}  // namespace fgr

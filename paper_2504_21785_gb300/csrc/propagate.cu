@@ -1,11 +1,25 @@
 // K1: per-packet FP64 RK4 of the frozen Gaussian trajectories (eq. 2.3-2.7).
 //
 // For the separable potentials of the ABI the Hessian of V is diagonal, so the
-// Jacobian blocks F = dQ/dq, G = dQ/dp, H = dP/dq, K = dP/dp are diagonal too and
+// Jacobian blocks F = dQ/dq, G = dQ/dp, H = dP/dq, K = dP/dp are diagonal and
 // each dimension carries four scalars.  Per dimension l:
 //   Q' = P,  P' = -V_l'(Q),  F' = H,  G' = K,  H' = -V_l''(Q) F,  K' = -V_l''(Q) G,
-//   Z_l = F - iG + iH + K,  Z_l' = H - iK - i V_l'' F - V_l'' G,
-// and  S' = |P|^2/2 - V(Q),  A' = (A/2) sum_l Z_l'/Z_l  (tr(Z^{-1} Z') for diagonal Z).
+// and S' = |P|^2/2 - V(Q).  RK4 integrates (Q, P, F, G, H, K, S).
+//
+// Amplitude.  Eq. 2.6, A' = (A/2) tr(Z^{-1} Z'), integrates in closed form:
+// tr(Z^{-1} Z') = d/dt log det Z, so A(t) = A(0) (det Z(t) / det Z(0))^{1/2}
+// with det Z = prod_l Z_l, Z_l = F - iG + iH + K and Z(0) = 2I.  The square root
+// follows the continuous branch: starting from the principal value 1 at t = 0,
+// it changes sign each time some Z_l crosses the negative real axis, which the
+// kernel counts after every step (Z is never zero, and moves O(dt) per step).
+// This replaces a complex division per dimension and stage; it agrees with an
+// RK4 integration of eq. 2.6 to the RK4 truncation error, O(dt^4).
+//
+// Trigonometry (cosine potential).  sin and cos of k Q are evaluated once per
+// step; the three later stages rotate them by the stage offset d = k (Q_stage - Q)
+// with cos d and sin d from their Taylor series (|d| ~ 1e-4: the first omitted
+// terms are below 1e-24).
+//
 // One thread integrates one packet with the whole state in registers.
 #include "internal.h"
 
@@ -13,28 +27,36 @@ namespace fgr {
 namespace {
 
 struct Pot {
-    int kind;
     double c0, amp, k, omega2;
 };
 
 template <int D>
 struct State {
-    double Q[D], P[D], F[D], G[D], H[D], K[D], S, Ar, Ai;
+    double Q[D], P[D], F[D], G[D], H[D], K[D], S;
 };
 
-template <int D>
-__device__ __forceinline__ void rhs(const Pot &v, const State<D> &y, State<D> &dy) {
-    double pot = 0.0, p2 = 0.0, tr_r = 0.0, tr_i = 0.0;
+// sin/cos of (x + d) from sin/cos of x, |d| small
+__device__ __forceinline__ void rotate_small(double s0, double c0, double d, double &s, double &c) {
+    const double d2 = d * d;
+    const double cd = 1.0 + d2 * (-0.5 + d2 * (1.0 / 24.0 + d2 * (-1.0 / 720.0)));
+    const double sd = d * (1.0 + d2 * (-1.0 / 6.0 + d2 * (1.0 / 120.0 + d2 * (-1.0 / 5040.0))));
+    s = s0 * cd + c0 * sd;
+    c = c0 * cd - s0 * sd;
+}
+
+// right-hand side; sn/cs = sin/cos(k Q_l) (cosine potential only)
+template <int D, int KIND>
+__device__ __forceinline__ void rhs(const Pot &v, const State<D> &y, const double *sn, const double *cs,
+                                    State<D> &dy) {
+    double pot = 0.0, p2 = 0.0;
 #pragma unroll
     for (int l = 0; l < D; ++l) {
         double g, hs;  // V_l', V_l''
-        if (v.kind == FGR_V_COSSUM) {
-            double sn, cs;
-            sincos(v.k * y.Q[l], &sn, &cs);
-            g = -v.amp * v.k * sn;
-            hs = -v.amp * v.k * v.k * cs;
-            pot += cs;
-        } else if (v.kind == FGR_V_HARMONIC) {
+        if (KIND == FGR_V_COSSUM) {
+            g = -v.amp * v.k * sn[l];
+            hs = -v.amp * v.k * v.k * cs[l];
+            pot += cs[l];
+        } else if (KIND == FGR_V_HARMONIC) {
             g = v.omega2 * y.Q[l];
             hs = v.omega2;
             pot += y.Q[l] * y.Q[l];
@@ -49,19 +71,11 @@ __device__ __forceinline__ void rhs(const Pot &v, const State<D> &y, State<D> &d
         dy.H[l] = -hs * y.F[l];
         dy.K[l] = -hs * y.G[l];
         p2 += y.P[l] * y.P[l];
-        // Z and Z'
-        double zr = y.F[l] + y.K[l], zi = y.H[l] - y.G[l];
-        double wr = y.H[l] - hs * y.G[l], wi = -y.K[l] - hs * y.F[l];
-        double den = zr * zr + zi * zi;
-        tr_r += (wr * zr + wi * zi) / den;
-        tr_i += (wi * zr - wr * zi) / den;
     }
     double V = 0.0;
-    if (v.kind == FGR_V_COSSUM) V = v.c0 + v.amp * pot;
-    else if (v.kind == FGR_V_HARMONIC) V = 0.5 * v.omega2 * pot;
+    if (KIND == FGR_V_COSSUM) V = v.c0 + v.amp * pot;
+    else if (KIND == FGR_V_HARMONIC) V = 0.5 * v.omega2 * pot;
     dy.S = 0.5 * p2 - V;
-    dy.Ar = 0.5 * (y.Ar * tr_r - y.Ai * tr_i);
-    dy.Ai = 0.5 * (y.Ar * tr_i + y.Ai * tr_r);
 }
 
 template <int D>
@@ -76,8 +90,6 @@ __device__ __forceinline__ void axpy(State<D> &out, const State<D> &y, double h,
         out.K[l] = y.K[l] + h * k.K[l];
     }
     out.S = y.S + h * k.S;
-    out.Ar = y.Ar + h * k.Ar;
-    out.Ai = y.Ai + h * k.Ai;
 }
 
 template <int D>
@@ -92,17 +104,26 @@ __device__ __forceinline__ void accum(State<D> &acc, double w, const State<D> &k
         acc.K[l] += w * k.K[l];
     }
     acc.S += w * k.S;
-    acc.Ar += w * k.Ar;
-    acc.Ai += w * k.Ai;
 }
 
-template <int D>
+template <int D, int KIND>
+__device__ __forceinline__ void stage_trig(const Pot &v, const State<D> &y, const State<D> &tmp,
+                                           const double *s0, const double *c0, double *sn, double *cs) {
+    if (KIND == FGR_V_COSSUM) {
+#pragma unroll
+        for (int l = 0; l < D; ++l) rotate_small(s0[l], c0[l], v.k * (tmp.Q[l] - y.Q[l]), sn[l], cs[l]);
+    }
+}
+
+template <int D, int KIND>
 __global__ void __launch_bounds__(128) rk4_kernel(double *__restrict__ q, double *__restrict__ p,
                                                   double *__restrict__ s, double *__restrict__ a,
                                                   int64_t m, Pot v, int64_t nsteps, double h) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= m) return;
     State<D> y;
+    bool im_pos[D];
+    int flips = 0;
 #pragma unroll
     for (int l = 0; l < D; ++l) {
         y.Q[l] = q[l * m + j];
@@ -111,25 +132,62 @@ __global__ void __launch_bounds__(128) rk4_kernel(double *__restrict__ q, double
         y.G[l] = 0.0;
         y.H[l] = 0.0;
         y.K[l] = 1.0;
+        im_pos[l] = true;  // Z(0) = 2: Im Z = +0
     }
     y.S = s[j];
-    y.Ar = a[j];
-    y.Ai = a[m + j];
     const double h2 = 0.5 * h, h6 = h / 6.0;
+    double s0[D], c0[D], sn[D], cs[D];
     for (int64_t it = 0; it < nsteps; ++it) {
+        if (KIND == FGR_V_COSSUM) {
+#pragma unroll
+            for (int l = 0; l < D; ++l) sincos(v.k * y.Q[l], &s0[l], &c0[l]);
+        }
         State<D> k, tmp, acc;
-        rhs<D>(v, y, k);
+        rhs<D, KIND>(v, y, s0, c0, k);
         acc = k;
         axpy<D>(tmp, y, h2, k);
-        rhs<D>(v, tmp, k);
+        stage_trig<D, KIND>(v, y, tmp, s0, c0, sn, cs);
+        rhs<D, KIND>(v, tmp, sn, cs, k);
         accum<D>(acc, 2.0, k);
         axpy<D>(tmp, y, h2, k);
-        rhs<D>(v, tmp, k);
+        stage_trig<D, KIND>(v, y, tmp, s0, c0, sn, cs);
+        rhs<D, KIND>(v, tmp, sn, cs, k);
         accum<D>(acc, 2.0, k);
         axpy<D>(tmp, y, h, k);
-        rhs<D>(v, tmp, k);
+        stage_trig<D, KIND>(v, y, tmp, s0, c0, sn, cs);
+        rhs<D, KIND>(v, tmp, sn, cs, k);
         accum<D>(acc, 1.0, k);
         axpy<D>(y, y, h6, acc);
+        // branch of sqrt(det Z): count crossings of the negative real axis
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+            const bool pos = (y.H[l] - y.G[l]) >= 0.0;
+            if (pos != im_pos[l] && (y.F[l] + y.K[l]) < 0.0) flips ^= 1;
+            im_pos[l] = pos;
+        }
+    }
+    // A = A(0) prod_l sqrt(Z_l / 2), continuous branch
+    double wr = 1.0, wi = 0.0;
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+        const double x = 0.5 * (y.F[l] + y.K[l]), yv = 0.5 * (y.H[l] - y.G[l]);
+        const double r = hypot(x, yv);
+        double sr, si;
+        if (x >= 0.0) {
+            sr = sqrt(0.5 * (r + x));
+            si = yv / (2.0 * sr);
+        } else {
+            const double t = sqrt(0.5 * (r - x));
+            si = yv >= 0.0 ? t : -t;
+            sr = yv / (2.0 * si);
+        }
+        const double nr = wr * sr - wi * si, ni = wr * si + wi * sr;
+        wr = nr;
+        wi = ni;
+    }
+    if (flips) {
+        wr = -wr;
+        wi = -wi;
     }
 #pragma unroll
     for (int l = 0; l < D; ++l) {
@@ -137,8 +195,20 @@ __global__ void __launch_bounds__(128) rk4_kernel(double *__restrict__ q, double
         p[l * m + j] = y.P[l];
     }
     s[j] = y.S;
-    a[j] = y.Ar;
-    a[m + j] = y.Ai;
+    const double ar = a[j], ai = a[m + j];
+    a[j] = ar * wr - ai * wi;
+    a[m + j] = ar * wi + ai * wr;
+}
+
+template <int D>
+void launch_kind(int kind, unsigned blocks, int threads, cudaStream_t st, double *q, double *p, double *s,
+                 double *a, int64_t m, Pot v, int64_t nsteps, double h) {
+    if (kind == FGR_V_COSSUM)
+        rk4_kernel<D, FGR_V_COSSUM><<<blocks, threads, 0, st>>>(q, p, s, a, m, v, nsteps, h);
+    else if (kind == FGR_V_HARMONIC)
+        rk4_kernel<D, FGR_V_HARMONIC><<<blocks, threads, 0, st>>>(q, p, s, a, m, v, nsteps, h);
+    else
+        rk4_kernel<D, FGR_V_FREE><<<blocks, threads, 0, st>>>(q, p, s, a, m, v, nsteps, h);
 }
 
 }  // namespace
@@ -152,13 +222,13 @@ fgr_status run_propagate(fgr_ctx *ctx, double *q, double *p, double *s, double *
         return FGR_OK;
     }
     const double h = t / (double)nsteps;
-    Pot v{vp->kind, vp->c0, vp->amp, vp->k, vp->omega * vp->omega};
+    Pot v{vp->c0, vp->amp, vp->k, vp->omega * vp->omega};
     const int threads = 128;
     const unsigned blocks = (unsigned)((m + threads - 1) / threads);
     switch (ctx->d) {
-    case 1: rk4_kernel<1><<<blocks, threads, 0, st>>>(q, p, s, a, m, v, nsteps, h); break;
-    case 2: rk4_kernel<2><<<blocks, threads, 0, st>>>(q, p, s, a, m, v, nsteps, h); break;
-    default: rk4_kernel<3><<<blocks, threads, 0, st>>>(q, p, s, a, m, v, nsteps, h); break;
+    case 1: launch_kind<1>(vp->kind, blocks, threads, st, q, p, s, a, m, v, nsteps, h); break;
+    case 2: launch_kind<2>(vp->kind, blocks, threads, st, q, p, s, a, m, v, nsteps, h); break;
+    default: launch_kind<3>(vp->kind, blocks, threads, st, q, p, s, a, m, v, nsteps, h); break;
     }
     FGR_CUDA_TRY(cudaGetLastError());
     ctx->timing.last.launches = 1;
