@@ -133,11 +133,13 @@ constexpr int kPassTile = kPassThreads * kPassPts;  // grid points per CTA
 template <bool FP64, int MAXBAND>
 __global__ void __launch_bounds__(kPassThreads) grid_pass_kernel(const void *__restrict__ in_v,
                                                                  void *__restrict__ out_v, PassParams pp,
-                                                                 const uint8_t *__restrict__ flags) {
+                                                                 const uint8_t *__restrict__ flags,
+                                                                 const int2 *__restrict__ brange) {
     using Real = typename std::conditional<FP64, double, float>::type;
     using C2 = typename std::conditional<FP64, double2, float2>::type;
     __shared__ __align__(16) C2 sw[MAXBAND][kCB];
     __shared__ int swlo[MAXBAND], swhi[MAXBAND];
+    __shared__ int s_blo, s_bhi;
     const int64_t row = blockIdx.x;
     const int64_t m0 = (int64_t)blockIdx.y * kPassTile;
     int64_t mm[kPassPts];
@@ -152,16 +154,36 @@ __global__ void __launch_bounds__(kPassThreads) grid_pass_kernel(const void *__r
     C2 zero;
     zero.x = 0;
     zero.y = 0;
-    // b-range of this CTA (blockIdx.z of gridDim.z slices, whole chunks of kCB)
-    const int nchunk = (pp.B + kCB - 1) / kCB;
-    const int per = (nchunk + gridDim.z - 1) / gridDim.z;
-    const int bs = blockIdx.z * per * kCB, be = min(pp.B, (int)(blockIdx.z + 1) * per * kCB);
     const bool split = gridDim.z > 1;  // slices add into a zeroed output
     const int64_t m1 = min(m0 + kPassTile - 1, pp.N - 1);
     const double x0 = grid_x(pp.lo, pp.h, m0), x1 = grid_x(pp.lo, pp.h, m1);
     const int a_lo = max(pp.amin, (int)ceil((x0 - pp.rs) / pp.dq) - 1);
     const int a_hi = min(pp.amin + pp.A - 1, (int)floor((x1 + pp.rs) / pp.dq) + 1);
     const int nb_total = a_hi - a_lo + 1;
+    // occupied b-range: the union over the band of the per-node ranges
+    int ulo = 0, uhi = pp.B - 1;
+    if (brange && nb_total > 0) {
+        if (threadIdx.x == 0) {
+            s_blo = INT_MAX;
+            s_bhi = INT_MIN;
+        }
+        __syncthreads();
+        int lo = INT_MAX, hi = INT_MIN;
+        for (int i = threadIdx.x; i < nb_total; i += kPassThreads) {
+            const int2 r = brange[row * (int64_t)pp.A + (a_lo - pp.amin) + i];
+            lo = min(lo, r.x);
+            hi = max(hi, r.y);
+        }
+        atomicMin(&s_blo, lo);
+        atomicMax(&s_bhi, hi);
+        __syncthreads();
+        ulo = s_blo;
+        uhi = s_bhi;
+    }
+    // b-slice of this CTA: blockIdx.z of gridDim.z parts of [ulo, uhi], whole chunks
+    const int nchunk = uhi >= ulo ? (uhi - ulo + kCB) / kCB : 0;
+    const int per = (nchunk + gridDim.z - 1) / gridDim.z;
+    const int bs = ulo + blockIdx.z * per * kCB, be = min(uhi + 1, bs + per * kCB);
     if ((flags && !flags[row]) || bs >= be || nb_total <= 0) {
         if (!split) {
 #pragma unroll
@@ -324,9 +346,43 @@ __global__ void transpose_kernel(const C2 *__restrict__ in, C2 *__restrict__ out
     }
 }
 
+// Occupied b-range of every line [row][a][0..B): first and last b with a
+// non-zero value ((B, -1) for an empty line).  One warp per line.
+template <class C2>
+__global__ void brange_kernel(const C2 *__restrict__ in, int64_t lines, int B, int2 *__restrict__ out) {
+    const int64_t line = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (line >= lines) return;
+    const int lane = threadIdx.x & 31;
+    const C2 *p = in + line * (int64_t)B;
+    int lo = INT_MAX, hi = INT_MIN;
+    for (int b = lane; b < B; b += 32) {
+        const C2 v = p[b];
+        if (v.x != 0 || v.y != 0) {
+            lo = min(lo, b);
+            hi = max(hi, b);
+        }
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if (lane == 0) out[line] = make_int2(lo == INT_MAX ? B : lo, hi);
+}
+
+template <bool FP64>
+fgr_status launch_brange(const void *in, int64_t rows, int A, int B, int2 *out, cudaStream_t st) {
+    const int64_t lines = rows * (int64_t)A;
+    if (lines == 0) return FGR_OK;
+    const unsigned blocks = (unsigned)((lines + 7) / 8);
+    if (FP64)
+        brange_kernel<double2><<<blocks, 256, 0, st>>>((const double2 *)in, lines, B, out);
+    else
+        brange_kernel<float2><<<blocks, 256, 0, st>>>((const float2 *)in, lines, B, out);
+    FGR_CUDA_TRY(cudaGetLastError());
+    return FGR_OK;
+}
+
 template <bool FP64>
 fgr_status launch_pass(const void *in, void *out, const PassParams &pp, const uint8_t *flags,
-                       int band, int num_sms, cudaStream_t st) {
+                       const int2 *brange, int band, int num_sms, cudaStream_t st) {
     if (pp.rows == 0 || pp.N == 0) return FGR_OK;
     if (pp.rows > INT_MAX) {
         set_error("fggc: too many rows in a grid pass");
@@ -347,7 +403,7 @@ fgr_status launch_pass(const void *in, void *out, const PassParams &pp, const ui
         FGR_CUDA_TRY(cudaMemsetAsync(out, 0, (FP64 ? 16 : 8) * (size_t)pp.rows * (size_t)pp.N, st));
     }
     dim3 grid((unsigned)pp.rows, (unsigned)mtiles, (unsigned)splits);
-#define FGR_PASS(MB) grid_pass_kernel<FP64, MB><<<grid, kPassThreads, 0, st>>>(in, out, pp, flags)
+#define FGR_PASS(MB) grid_pass_kernel<FP64, MB><<<grid, kPassThreads, 0, st>>>(in, out, pp, flags, brange)
     if (band <= 16) FGR_PASS(16);
     else if (band <= 32) FGR_PASS(32);
     else if (band <= 48) FGR_PASS(48);
@@ -475,7 +531,18 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
     void *buf1 = D > 1 ? scratch.get(eb * (size_t)maxbuf) : nullptr;
     void *buf2 = D > 1 ? scratch.get(eb * (size_t)maxbuf) : nullptr;
     uint8_t *flags = (uint8_t *)scratch.get((size_t)rows0);
-    if (!W || !flags || (D > 1 && (!buf1 || !buf2))) return FGR_E_NOMEM;
+    int64_t max_lines = 0;
+    {
+        int64_t prodN = 1;
+        for (int l = D - 1; l >= 0; --l) {
+            int64_t pre = 1;
+            for (int j = 0; j < l; ++j) pre *= (int64_t)c.A[j] * c.B[j];
+            max_lines = std::max(max_lines, pre * prodN * c.A[l]);
+            prodN *= G.n[l];
+        }
+    }
+    int2 *brange = (int2 *)scratch.get(sizeof(int2) * (size_t)max_lines);
+    if (!W || !flags || !brange || (D > 1 && (!buf1 || !buf2))) return FGR_E_NOMEM;
     FGR_CUDA_TRY(cudaMemsetAsync(W, 0, eb * (size_t)cells, st));
     FGR_CUDA_TRY(cudaMemsetAsync(flags, 0, (size_t)rows0, st));
     timer.mark(&ctx->timing.last.prep_ms);
@@ -531,8 +598,12 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
         const int band = (int)std::ceil(((kPassTile - 1) * G.h[l] + 2 * M.rs) / M.dq) + 3;
         const bool last = l == 0;
         void *dst = (D == 1) ? u_dev : (cur == buf1 ? buf2 : buf1);
-        fgr_status r = fp64 ? launch_pass<true>(cur, dst, pp, l == D - 1 ? flags : nullptr, band, ctx->num_sms, st)
-                            : launch_pass<false>(cur, dst, pp, l == D - 1 ? flags : nullptr, band, ctx->num_sms, st);
+        fgr_status r = fp64 ? launch_brange<true>(cur, pp.rows, pp.A, pp.B, brange, st)
+                            : launch_brange<false>(cur, pp.rows, pp.A, pp.B, brange, st);
+        if (r != FGR_OK) return r;
+        ++launches;
+        r = fp64 ? launch_pass<true>(cur, dst, pp, l == D - 1 ? flags : nullptr, brange, band, ctx->num_sms, st)
+                 : launch_pass<false>(cur, dst, pp, l == D - 1 ? flags : nullptr, brange, band, ctx->num_sms, st);
         if (r != FGR_OK) return r;
         ++launches;
         if (D > 1) {
@@ -764,8 +835,8 @@ extern "C" fgr_status fgr_reconstruct_fggc_noalloc(fgr_ctx *ctx, const fgr_packe
     pp.two_pow_b = std::ldexp(1.0, std::max(1, 23 - lb));
     pp.inv_two_pow_b = 1.0 / pp.two_pow_b;
     const int band = (int)std::ceil(((kPassTile - 1) * G.h[0] + 2 * M.rs) / M.dq) + 3;
-    rc = fp64 ? launch_pass<true>(W, u_out, pp, flags, band, ctx->num_sms, st)
-              : launch_pass<false>(W, u_out, pp, flags, band, ctx->num_sms, st);
+    rc = fp64 ? launch_pass<true>(W, u_out, pp, flags, nullptr, band, ctx->num_sms, st)
+              : launch_pass<false>(W, u_out, pp, flags, nullptr, band, ctx->num_sms, st);
     if (rc != FGR_OK) return rc;
     if (!stream) FGR_CUDA_TRY(cudaStreamSynchronize(st));
     return FGR_OK;

@@ -15,10 +15,13 @@
 // This replaces a complex division per dimension and stage; it agrees with an
 // RK4 integration of eq. 2.6 to the RK4 truncation error, O(dt^4).
 //
-// Trigonometry (cosine potential).  sin and cos of k Q are evaluated once per
-// step; the three later stages rotate them by the stage offset d = k (Q_stage - Q)
-// with cos d and sin d from their Taylor series (|d| ~ 1e-4: the first omitted
-// terms are below 1e-24).
+// Trigonometry (cosine potential).  sin and cos of k Q at a stage are obtained
+// by rotating a nearby known value by d = k (Q_stage - Q_known), with cos d and
+// sin d from their Taylor series (|d| ~ 1e-4; terms beyond d^5 are dropped when
+// |d| < 2e-3, where they are below 3e-16 |d|).  The three later stages rotate
+// from the step's start; the step's start rotates from the previous step's last
+// stage (an O(dt^2) offset), and a true sincos re-anchors the chain every
+// kAnchor steps so that rounding cannot accumulate.
 //
 // One thread integrates one packet with the whole state in registers.
 #include "internal.h"
@@ -28,18 +31,35 @@ namespace {
 
 struct Pot {
     double c0, amp, k, omega2;
+    double ampk, ampk2;  // amp*k, amp*k^2
 };
+
+constexpr int kAnchor = 32;
 
 template <int D>
 struct State {
     double Q[D], P[D], F[D], G[D], H[D], K[D], S;
 };
 
-// sin/cos of (x + d) from sin/cos of x, |d| small
-__device__ __forceinline__ void rotate_small(double s0, double c0, double d, double &s, double &c) {
+// sin/cos of x_target = x + d from sin/cos of x.  Taylor series of cos d and
+// sin d for |d| < 0.05 (to d^5 below 2e-3, to d^9 above: the first omitted term
+// is under 1e-19 either way); a direct sincos beyond.
+__device__ __forceinline__ void rotate_small(double x_target, double s0, double c0, double d, double &s,
+                                             double &c) {
+    const double ad = fabs(d);
+    if (ad >= 0.05) {
+        sincos(x_target, &s, &c);
+        return;
+    }
     const double d2 = d * d;
-    const double cd = 1.0 + d2 * (-0.5 + d2 * (1.0 / 24.0 + d2 * (-1.0 / 720.0)));
-    const double sd = d * (1.0 + d2 * (-1.0 / 6.0 + d2 * (1.0 / 120.0 + d2 * (-1.0 / 5040.0))));
+    double cd, sd;
+    if (ad < 2e-3) {
+        cd = 1.0 + d2 * (-0.5 + d2 * (1.0 / 24.0));
+        sd = d * (1.0 + d2 * (-1.0 / 6.0 + d2 * (1.0 / 120.0)));
+    } else {
+        cd = 1.0 + d2 * (-0.5 + d2 * (1.0 / 24.0 + d2 * (-1.0 / 720.0 + d2 * (1.0 / 40320.0))));
+        sd = d * (1.0 + d2 * (-1.0 / 6.0 + d2 * (1.0 / 120.0 + d2 * (-1.0 / 5040.0 + d2 * (1.0 / 362880.0)))));
+    }
     s = s0 * cd + c0 * sd;
     c = c0 * cd - s0 * sd;
 }
@@ -53,8 +73,8 @@ __device__ __forceinline__ void rhs(const Pot &v, const State<D> &y, const doubl
     for (int l = 0; l < D; ++l) {
         double g, hs;  // V_l', V_l''
         if (KIND == FGR_V_COSSUM) {
-            g = -v.amp * v.k * sn[l];
-            hs = -v.amp * v.k * v.k * cs[l];
+            g = -v.ampk * sn[l];
+            hs = -v.ampk2 * cs[l];
             pot += cs[l];
         } else if (KIND == FGR_V_HARMONIC) {
             g = v.omega2 * y.Q[l];
@@ -111,7 +131,8 @@ __device__ __forceinline__ void stage_trig(const Pot &v, const State<D> &y, cons
                                            const double *s0, const double *c0, double *sn, double *cs) {
     if (KIND == FGR_V_COSSUM) {
 #pragma unroll
-        for (int l = 0; l < D; ++l) rotate_small(s0[l], c0[l], v.k * (tmp.Q[l] - y.Q[l]), sn[l], cs[l]);
+        for (int l = 0; l < D; ++l)
+            rotate_small(v.k * tmp.Q[l], s0[l], c0[l], v.k * (tmp.Q[l] - y.Q[l]), sn[l], cs[l]);
     }
 }
 
@@ -136,11 +157,23 @@ __global__ void __launch_bounds__(128) rk4_kernel(double *__restrict__ q, double
     }
     y.S = s[j];
     const double h2 = 0.5 * h, h6 = h / 6.0;
-    double s0[D], c0[D], sn[D], cs[D];
+    double s0[D], c0[D], sn[D], cs[D], qlast[D];
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+        sn[l] = cs[l] = qlast[l] = 0.0;
+    }
+    int anchor = 0;
     for (int64_t it = 0; it < nsteps; ++it) {
         if (KIND == FGR_V_COSSUM) {
+            if (anchor == 0) {
 #pragma unroll
-            for (int l = 0; l < D; ++l) sincos(v.k * y.Q[l], &s0[l], &c0[l]);
+                for (int l = 0; l < D; ++l) sincos(v.k * y.Q[l], &s0[l], &c0[l]);
+            } else {  // from the previous step's last stage
+#pragma unroll
+                for (int l = 0; l < D; ++l)
+                    rotate_small(v.k * y.Q[l], sn[l], cs[l], v.k * (y.Q[l] - qlast[l]), s0[l], c0[l]);
+            }
+            anchor = anchor + 1 == kAnchor ? 0 : anchor + 1;
         }
         State<D> k, tmp, acc;
         rhs<D, KIND>(v, y, s0, c0, k);
@@ -157,6 +190,8 @@ __global__ void __launch_bounds__(128) rk4_kernel(double *__restrict__ q, double
         stage_trig<D, KIND>(v, y, tmp, s0, c0, sn, cs);
         rhs<D, KIND>(v, tmp, sn, cs, k);
         accum<D>(acc, 1.0, k);
+#pragma unroll
+        for (int l = 0; l < D; ++l) qlast[l] = tmp.Q[l];  // sn, cs hold this stage's values
         axpy<D>(y, y, h6, acc);
         // branch of sqrt(det Z): count crossings of the negative real axis
 #pragma unroll
@@ -222,7 +257,7 @@ fgr_status run_propagate(fgr_ctx *ctx, double *q, double *p, double *s, double *
         return FGR_OK;
     }
     const double h = t / (double)nsteps;
-    Pot v{vp->c0, vp->amp, vp->k, vp->omega * vp->omega};
+    Pot v{vp->c0, vp->amp, vp->k, vp->omega * vp->omega, vp->amp * vp->k, vp->amp * vp->k * vp->k};
     const int threads = 128;
     const unsigned blocks = (unsigned)((m + threads - 1) / threads);
     switch (ctx->d) {

@@ -70,6 +70,19 @@ def test_propagate_matches_oracle(d, pot):
     assert np.max(np.abs(A - Ar) / np.abs(Ar)) <= 1e-12
 
 
+def test_propagate_large_steps():
+    # dt * |P| up to 0.1 takes the direct sincos branch of the stage trigonometry;
+    # Q, P, S are the same RK4 as the oracle's; A (closed form in det Z) differs
+    # from an RK4-integrated A by O(dt^4)
+    pk = random_packets(31, 1, 300, q_range=(-2, 2), p_range=(-2, 2), s_range=(0, 0))
+    ref = tr.propagate(pk, POTS["cos"], 1.0, 0.05)
+    got = _gpu.propagate(pk, 1, POTS["cos"], 1.0, 0.05)
+    for k in ("q", "p", "s"):
+        assert np.max(np.abs(got[k] - ref[k])) <= 1e-12 * max(1.0, np.max(np.abs(ref[k])))
+    A, Ar = got["a"][0] + 1j * got["a"][1], ref["a"][0] + 1j * ref["a"][1]
+    assert np.max(np.abs(A - Ar) / np.abs(Ar)) <= 1e-5
+
+
 def test_propagate_host_buffers_and_empty():
     pk = random_packets(7, 2, 257, s_range=(0, 0))
     ref = tr.propagate(pk, POTS["cos"], 0.2, 1e-4)
