@@ -15,13 +15,11 @@
 // This replaces a complex division per dimension and stage; it agrees with an
 // RK4 integration of eq. 2.6 to the RK4 truncation error, O(dt^4).
 //
-// Trigonometry (cosine potential).  sin and cos of k Q at a stage are obtained
-// by rotating a nearby known value by d = k (Q_stage - Q_known), with cos d and
-// sin d from their Taylor series (|d| ~ 1e-4; terms beyond d^5 are dropped when
-// |d| < 2e-3, where they are below 3e-16 |d|).  The three later stages rotate
-// from the step's start; the step's start rotates from the previous step's last
-// stage (an O(dt^2) offset), and a true sincos re-anchors the chain every
-// kAnchor steps so that rounding cannot accumulate.
+// Trigonometry (cosine potential).  sin and cos of k Q are evaluated once per
+// step; the three later stages rotate them by the stage offset
+// d = k (Q_stage - Q) with cos d and sin d from their Taylor series (|d| ~ 1e-4;
+// terms beyond d^5 are dropped when |d| < 2e-3, where they are below 3e-16 |d|;
+// offsets of 0.05 or more take a direct sincos).
 //
 // One thread integrates one packet with the whole state in registers.
 #include "internal.h"
@@ -33,8 +31,6 @@ struct Pot {
     double c0, amp, k, omega2;
     double ampk, ampk2;  // amp*k, amp*k^2
 };
-
-constexpr int kAnchor = 32;
 
 template <int D>
 struct State {
@@ -157,23 +153,11 @@ __global__ void __launch_bounds__(128) rk4_kernel(double *__restrict__ q, double
     }
     y.S = s[j];
     const double h2 = 0.5 * h, h6 = h / 6.0;
-    double s0[D], c0[D], sn[D], cs[D], qlast[D];
-#pragma unroll
-    for (int l = 0; l < D; ++l) {
-        sn[l] = cs[l] = qlast[l] = 0.0;
-    }
-    int anchor = 0;
+    double s0[D], c0[D], sn[D], cs[D];
     for (int64_t it = 0; it < nsteps; ++it) {
         if (KIND == FGR_V_COSSUM) {
-            if (anchor == 0) {
 #pragma unroll
-                for (int l = 0; l < D; ++l) sincos(v.k * y.Q[l], &s0[l], &c0[l]);
-            } else {  // from the previous step's last stage
-#pragma unroll
-                for (int l = 0; l < D; ++l)
-                    rotate_small(v.k * y.Q[l], sn[l], cs[l], v.k * (y.Q[l] - qlast[l]), s0[l], c0[l]);
-            }
-            anchor = anchor + 1 == kAnchor ? 0 : anchor + 1;
+            for (int l = 0; l < D; ++l) sincos(v.k * y.Q[l], &s0[l], &c0[l]);
         }
         State<D> k, tmp, acc;
         rhs<D, KIND>(v, y, s0, c0, k);
@@ -190,8 +174,6 @@ __global__ void __launch_bounds__(128) rk4_kernel(double *__restrict__ q, double
         stage_trig<D, KIND>(v, y, tmp, s0, c0, sn, cs);
         rhs<D, KIND>(v, tmp, sn, cs, k);
         accum<D>(acc, 1.0, k);
-#pragma unroll
-        for (int l = 0; l < D; ++l) qlast[l] = tmp.Q[l];  // sn, cs hold this stage's values
         axpy<D>(y, y, h6, acc);
         // branch of sqrt(det Z): count crossings of the negative real axis
 #pragma unroll
