@@ -88,6 +88,19 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """Maximum of x over the ranks of the default process group (x itself for
+    one rank).  Only timings cross ranks; every rank reconstructs its own batch."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def rk4_nsteps(t: float, dt: float) -> int:
     """Step count rule of fgr_propagate (include/fgr.h)."""
     r = t / dt
@@ -158,6 +171,9 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    # launch shapes picked by the library's autotuner on the propagated batch
+    fgr.fgr_autotune(ctx.handle, packets, u_d, 3, stream)
+    tuning = fgr.fgr_get_tuning(ctx.handle)
     launches["n"] = 0
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     if world > 1:
@@ -221,10 +237,7 @@ def run_ours(args):
     d2h = pbytes + hu.nbytes
 
     def agg(xs):
-        t = torch.tensor([statistics.mean(xs)], dtype=torch.float64, device=dev)
-        if world > 1:
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(statistics.mean(xs), world)
 
     ms_step = agg(step_ms)
     ms_prop = agg(prop_ms)
@@ -254,7 +267,8 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "packets_per_gpu": M, "grid": list(shape), "eps": eps,
                        "t": t_final, "dt": dt, "strategy": "Q4P2 cq=1/2 cp=pi/8",
                        "step": "propagate (A1) + fggc reconstruct (A3-A5)",
-                       "l2": "flushed (512 MiB write) between timed steps", "parallelism": "replicas"},
+                       "l2": "flushed (512 MiB write) between timed steps", "parallelism": "replicas",
+                       "autotuned_ctas_per_sm": {"direct": tuning[0], "grid_pass": tuning[1]}},
             "stages": {
                 "propagate_ms": ms_prop,
                 "fggc_reconstruct_ms": ms_fggc,
@@ -318,6 +332,7 @@ def reconstruct_bench(cfg: int, args, flush):
     uf = torch.zeros(shape, dtype=cdt, device="cuda")
     ud = torch.zeros(shape, dtype=cdt, device="cuda")
     stream = torch.cuda.current_stream()
+    fgr.fgr_autotune(ctx.handle, pk, ud, 3, stream)
     res = {}
     for name, fn, u in (("fggc", fgr.fgr_reconstruct_fggc, uf), ("direct", fgr.fgr_reconstruct_direct, ud)):
         fn(ctx.handle, pk, u, stream)
@@ -336,12 +351,13 @@ def reconstruct_bench(cfg: int, args, flush):
     fgr.fgr_set_timing(ctx.handle, True)
     fgr.fgr_reconstruct_fggc(ctx.handle, pk, uf, stream)
     st = fgr.fgr_get_stats(ctx.handle)
+    tuned = list(fgr.fgr_get_tuning(ctx.handle))
     ctx.close()
     return {"workload": w["name"], "packets": M, "propagate_s_untimed": t_prop,
             "fggc_ms": res["fggc"], "direct_ms": res["direct"],
             "fggc_packets_per_s": M / (res["fggc"] * 1e-3), "direct_packets_per_s": M / (res["direct"] * 1e-3),
             "fggc_over_direct": res["direct"] / res["fggc"], "rel_l2_fggc_vs_direct": rel,
-            "fggc_nodes": int(st.nodes),
+            "fggc_nodes": int(st.nodes), "autotuned_ctas_per_sm": tuned,
             "fggc_stage_split_ms": {"bounds_alloc": st.prep_ms, "coeff_scatter": st.scatter_ms, "grid": st.grid_ms}}
 
 

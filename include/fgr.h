@@ -182,6 +182,20 @@ fgr_status fgr_reconstruct_fggc(fgr_ctx *ctx, const fgr_packets *pk, void *u_out
 fgr_status fgr_reconstruct_fggc_noalloc(fgr_ctx *ctx, const fgr_packets *pk, void *u_out,
                                         void *cuda_stream);
 
+/* Autotuner of the launch shapes (not in the paper: it serves the batching and
+ * serving side of the library).  Times, with CUDA events on the given
+ * stream, the candidate CTA-per-SM targets of the direct sum (methods & 1:
+ * 2, 4, 8, 16, 32) and of the FGGC grid passes (methods & 2: 4, 8, 16, 32, 64)
+ * on these packets and this context's grid (u_out receives the last result),
+ * keeps the fastest in the context and in a process-wide table keyed by
+ * (d, precision, packets and grid points rounded to powers of two) that seeds
+ * later contexts; with FGR_TUNE_FILE set, the table is loaded from and appended
+ * to that file.  Waits for its own timing runs. */
+fgr_status fgr_autotune(fgr_ctx *ctx, const fgr_packets *pk, void *u_out, int32_t methods,
+                        void *cuda_stream);
+fgr_status fgr_get_tuning(const fgr_ctx *ctx, int32_t *direct_ctas_per_sm, int32_t *pass_ctas_per_sm);
+fgr_status fgr_set_tuning(fgr_ctx *ctx, int32_t direct_ctas_per_sm, int32_t pass_ctas_per_sm);
+
 /* Read-only facts about a context. */
 typedef struct {
     int32_t d, n1, rank, precision;

@@ -1,7 +1,9 @@
 // C ABI entry points of libfgr: argument checks, host<->device staging,
 // scratch management and dispatch to the kernel stages.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -31,9 +33,28 @@ Scratch::~Scratch() {
         if (ptrs_[i]) cudaFreeAsync(ptrs_[i], s_);
 }
 
+namespace {
+// Failure injection for tests: FGR_INJECT_ALLOC_FAILURE=n makes the n-th
+// scratch allocation of the process fail (as if the device were out of memory).
+std::atomic<long> g_alloc_count{0};
+long injected_failure_index() {
+    static const long at = [] {
+        const char *e = getenv("FGR_INJECT_ALLOC_FAILURE");
+        return e ? atol(e) : -1L;
+    }();
+    return at;
+}
+}  // namespace
+
 void *Scratch::get(size_t bytes) {
     if (n_ >= 32) {
         set_error("internal: too many scratch buffers");
+        return nullptr;
+    }
+    const long fail_at = injected_failure_index();
+    if (fail_at > 0 && ++g_alloc_count == fail_at) {
+        set_error("device allocation of %zu bytes failed: injected failure (FGR_INJECT_ALLOC_FAILURE=%ld)",
+                  bytes, fail_at);
         return nullptr;
     }
     void *p = nullptr;
@@ -406,6 +427,7 @@ fgr_status fgr_create(int32_t d, const fgr_grid *grid, double eps, const fgr_opt
             return FGR_E_CUDA;
         }
         c->host_pinned = (int64_t *)slot;
+        seed_tuning(c);
         *out = c;
         return FGR_OK;
     });

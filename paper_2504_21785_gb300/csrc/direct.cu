@@ -468,7 +468,7 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
     P.ce = (float)(-1.4426950408889634 / (2.0 * M.eps));
     P.inv_eps = 1.0 / M.eps;
     P.neg_half_inv_eps = -0.5 / M.eps;
-    const int target = ctx->num_sms * 8;
+    const int target = ctx->num_sms * ctx->tune.direct_ctas_per_sm;
     P.splits = std::max(1, std::min(64, (target + ntiles - 1) / ntiles));
     dim3 grid((unsigned)ntiles, (unsigned)P.splits);
     if (fp64)

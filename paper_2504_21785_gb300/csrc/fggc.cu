@@ -382,7 +382,7 @@ fgr_status launch_brange(const void *in, int64_t rows, int A, int B, int2 *out, 
 
 template <bool FP64>
 fgr_status launch_pass(const void *in, void *out, const PassParams &pp, const uint8_t *flags,
-                       const int2 *brange, int band, int num_sms, cudaStream_t st) {
+                       const int2 *brange, int band, int64_t target_ctas, cudaStream_t st) {
     if (pp.rows == 0 || pp.N == 0) return FGR_OK;
     if (pp.rows > INT_MAX) {
         set_error("fggc: too many rows in a grid pass");
@@ -395,7 +395,7 @@ fgr_status launch_pass(const void *in, void *out, const PassParams &pp, const ui
         return FGR_E_INVALID;
     }
     // split the b-range when rows x tiles alone cannot fill the device
-    const int64_t target = (int64_t)num_sms * 16;
+    const int64_t target = target_ctas;
     const int nchunk = (pp.B + kCB - 1) / kCB;
     int splits = (int)std::min<int64_t>(std::max<int64_t>(1, (target + pp.rows * mtiles - 1) / (pp.rows * mtiles)),
                                         std::max(1, std::min(nchunk, 64)));
@@ -602,8 +602,9 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
                             : launch_brange<false>(cur, pp.rows, pp.A, pp.B, brange, st);
         if (r != FGR_OK) return r;
         ++launches;
-        r = fp64 ? launch_pass<true>(cur, dst, pp, l == D - 1 ? flags : nullptr, brange, band, ctx->num_sms, st)
-                 : launch_pass<false>(cur, dst, pp, l == D - 1 ? flags : nullptr, brange, band, ctx->num_sms, st);
+        const int64_t target = (int64_t)ctx->num_sms * ctx->tune.pass_ctas_per_sm;
+        r = fp64 ? launch_pass<true>(cur, dst, pp, l == D - 1 ? flags : nullptr, brange, band, target, st)
+                 : launch_pass<false>(cur, dst, pp, l == D - 1 ? flags : nullptr, brange, band, target, st);
         if (r != FGR_OK) return r;
         ++launches;
         if (D > 1) {
@@ -835,8 +836,9 @@ extern "C" fgr_status fgr_reconstruct_fggc_noalloc(fgr_ctx *ctx, const fgr_packe
     pp.two_pow_b = std::ldexp(1.0, std::max(1, 23 - lb));
     pp.inv_two_pow_b = 1.0 / pp.two_pow_b;
     const int band = (int)std::ceil(((kPassTile - 1) * G.h[0] + 2 * M.rs) / M.dq) + 3;
-    rc = fp64 ? launch_pass<true>(W, u_out, pp, flags, nullptr, band, ctx->num_sms, st)
-              : launch_pass<false>(W, u_out, pp, flags, nullptr, band, ctx->num_sms, st);
+    const int64_t target = (int64_t)ctx->num_sms * ctx->tune.pass_ctas_per_sm;
+    rc = fp64 ? launch_pass<true>(W, u_out, pp, flags, nullptr, band, target, st)
+              : launch_pass<false>(W, u_out, pp, flags, nullptr, band, target, st);
     if (rc != FGR_OK) return rc;
     if (!stream) FGR_CUDA_TRY(cudaStreamSynchronize(st));
     return FGR_OK;

@@ -50,6 +50,15 @@ struct Timing {
     fgr_stats last{};
 };
 
+// Launch-shape parameters picked by the autotuner (autotune.cu).
+struct Tuning {
+    int direct_ctas_per_sm = 8;  // direct sum: tiles x slices >= this x SMs
+    int pass_ctas_per_sm = 16;   // grid passes: rows x tiles x b-slices >= this x SMs
+};
+
+// Seeds a new context's tuning from the process-wide table (autotune.cu).
+void seed_tuning(fgr_ctx *ctx);
+
 }  // namespace fgr
 
 struct fgr_ctx {
@@ -62,6 +71,7 @@ struct fgr_ctx {
     fgr_options opt{};
     cudaMemPool_t pool = nullptr;
     fgr::Timing timing;
+    fgr::Tuning tune;
     int64_t *host_pinned = nullptr;  // small pinned buffer for device->host sizes
 };
 

@@ -17,9 +17,9 @@
 //
 // Trigonometry (cosine potential).  sin and cos of k Q are evaluated once per
 // step; the three later stages rotate them by the stage offset
-// d = k (Q_stage - Q) with cos d and sin d from their Taylor series (|d| ~ 1e-4;
-// terms beyond d^5 are dropped when |d| < 2e-3, where they are below 3e-16 |d|;
-// offsets of 0.05 or more take a direct sincos).
+// d = k (Q_stage - Q), |d| <= k h (|P| + h |amp| k), with cos d and sin d from
+// their Taylor series.  When that bound exceeds 0.02 (large steps or momenta)
+// the step evaluates sincos at every stage instead.
 //
 // One thread integrates one packet with the whole state in registers.
 #include "internal.h"
@@ -37,25 +37,12 @@ struct State {
     double Q[D], P[D], F[D], G[D], H[D], K[D], S;
 };
 
-// sin/cos of x_target = x + d from sin/cos of x.  Taylor series of cos d and
-// sin d for |d| < 0.05 (to d^5 below 2e-3, to d^9 above: the first omitted term
-// is under 1e-19 either way); a direct sincos beyond.
-__device__ __forceinline__ void rotate_small(double x_target, double s0, double c0, double d, double &s,
-                                             double &c) {
-    const double ad = fabs(d);
-    if (ad >= 0.05) {
-        sincos(x_target, &s, &c);
-        return;
-    }
+// sin/cos of (x + d) from sin/cos of x by the Taylor series of cos d and sin d
+// (to d^6 and d^7; for |d| <= 0.025 the first omitted term is below 2e-18).
+__device__ __forceinline__ void rotate_small(double s0, double c0, double d, double &s, double &c) {
     const double d2 = d * d;
-    double cd, sd;
-    if (ad < 2e-3) {
-        cd = 1.0 + d2 * (-0.5 + d2 * (1.0 / 24.0));
-        sd = d * (1.0 + d2 * (-1.0 / 6.0 + d2 * (1.0 / 120.0)));
-    } else {
-        cd = 1.0 + d2 * (-0.5 + d2 * (1.0 / 24.0 + d2 * (-1.0 / 720.0 + d2 * (1.0 / 40320.0))));
-        sd = d * (1.0 + d2 * (-1.0 / 6.0 + d2 * (1.0 / 120.0 + d2 * (-1.0 / 5040.0 + d2 * (1.0 / 362880.0)))));
-    }
+    const double cd = 1.0 + d2 * (-0.5 + d2 * (1.0 / 24.0 + d2 * (-1.0 / 720.0)));
+    const double sd = d * (1.0 + d2 * (-1.0 / 6.0 + d2 * (1.0 / 120.0 + d2 * (-1.0 / 5040.0))));
     s = s0 * cd + c0 * sd;
     c = c0 * cd - s0 * sd;
 }
@@ -124,11 +111,16 @@ __device__ __forceinline__ void accum(State<D> &acc, double w, const State<D> &k
 
 template <int D, int KIND>
 __device__ __forceinline__ void stage_trig(const Pot &v, const State<D> &y, const State<D> &tmp,
-                                           const double *s0, const double *c0, double *sn, double *cs) {
+                                           const double *s0, const double *c0, const bool *big, double *sn,
+                                           double *cs) {
     if (KIND == FGR_V_COSSUM) {
 #pragma unroll
-        for (int l = 0; l < D; ++l)
-            rotate_small(v.k * tmp.Q[l], s0[l], c0[l], v.k * (tmp.Q[l] - y.Q[l]), sn[l], cs[l]);
+        for (int l = 0; l < D; ++l) {
+            if (big[l])
+                sincos(v.k * tmp.Q[l], &sn[l], &cs[l]);
+            else
+                rotate_small(s0[l], c0[l], v.k * (tmp.Q[l] - y.Q[l]), sn[l], cs[l]);
+        }
     }
 }
 
@@ -154,24 +146,29 @@ __global__ void __launch_bounds__(128) rk4_kernel(double *__restrict__ q, double
     y.S = s[j];
     const double h2 = 0.5 * h, h6 = h / 6.0;
     double s0[D], c0[D], sn[D], cs[D];
+    bool big[D];
+    const double kh = fabs(v.k) * h, kh_margin = kh * h * fabs(v.ampk);
     for (int64_t it = 0; it < nsteps; ++it) {
         if (KIND == FGR_V_COSSUM) {
 #pragma unroll
-            for (int l = 0; l < D; ++l) sincos(v.k * y.Q[l], &s0[l], &c0[l]);
+            for (int l = 0; l < D; ++l) {
+                sincos(v.k * y.Q[l], &s0[l], &c0[l]);
+                big[l] = fabs(y.P[l]) * kh + kh_margin > 0.02;
+            }
         }
         State<D> k, tmp, acc;
         rhs<D, KIND>(v, y, s0, c0, k);
         acc = k;
         axpy<D>(tmp, y, h2, k);
-        stage_trig<D, KIND>(v, y, tmp, s0, c0, sn, cs);
+        stage_trig<D, KIND>(v, y, tmp, s0, c0, big, sn, cs);
         rhs<D, KIND>(v, tmp, sn, cs, k);
         accum<D>(acc, 2.0, k);
         axpy<D>(tmp, y, h2, k);
-        stage_trig<D, KIND>(v, y, tmp, s0, c0, sn, cs);
+        stage_trig<D, KIND>(v, y, tmp, s0, c0, big, sn, cs);
         rhs<D, KIND>(v, tmp, sn, cs, k);
         accum<D>(acc, 2.0, k);
         axpy<D>(tmp, y, h, k);
-        stage_trig<D, KIND>(v, y, tmp, s0, c0, sn, cs);
+        stage_trig<D, KIND>(v, y, tmp, s0, c0, big, sn, cs);
         rhs<D, KIND>(v, tmp, sn, cs, k);
         accum<D>(acc, 1.0, k);
         axpy<D>(y, y, h6, acc);

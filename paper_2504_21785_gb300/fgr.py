@@ -93,6 +93,9 @@ SIGNATURES = {
     "fgr_reconstruct_fggc": (ctypes.c_int, [vp, P(fgr_packets), vp, vp]),
     "fgr_reconstruct_fggc_noalloc": (ctypes.c_int, [vp, P(fgr_packets), vp, vp]),
     "fgr_get_info": (ctypes.c_int, [vp, P(fgr_info)]),
+    "fgr_autotune": (ctypes.c_int, [vp, P(fgr_packets), vp, ctypes.c_int32, vp]),
+    "fgr_get_tuning": (ctypes.c_int, [vp, P(ctypes.c_int32), P(ctypes.c_int32)]),
+    "fgr_set_tuning": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.c_int32]),
     "fgr_set_timing": (ctypes.c_int, [vp, ctypes.c_int32]),
     "fgr_get_stats": (ctypes.c_int, [vp, P(fgr_stats)]),
     "fgr_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int32, P(vp)]),
@@ -234,6 +237,21 @@ def fgr_reconstruct_fggc(ctx, packets: fgr_packets, u_out, stream=None):
 def fgr_reconstruct_fggc_noalloc(ctx, packets: fgr_packets, u_out, stream=None):
     return _check(load().fgr_reconstruct_fggc_noalloc(ctx, ctypes.byref(packets), _ptr(u_out)[0],
                                                       _stream_handle(stream)))
+
+
+def fgr_autotune(ctx, packets: fgr_packets, u_out, methods: int = 3, stream=None):
+    return _check(load().fgr_autotune(ctx, ctypes.byref(packets), _ptr(u_out)[0], int(methods),
+                                      _stream_handle(stream)))
+
+
+def fgr_get_tuning(ctx):
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().fgr_get_tuning(ctx, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def fgr_set_tuning(ctx, direct_ctas_per_sm: int, pass_ctas_per_sm: int):
+    return _check(load().fgr_set_tuning(ctx, int(direct_ctas_per_sm), int(pass_ctas_per_sm)))
 
 
 def fgr_get_info(ctx) -> fgr_info:
