@@ -146,6 +146,22 @@ fgr_status fgr_propagate(fgr_ctx *ctx, fgr_packets *inout, const fgr_potential *
 fgr_status fgr_reconstruct_direct(fgr_ctx *ctx, const fgr_packets *pk, void *u_out,
                                   void *cuda_stream);
 
+/* Batched eq. 2.10 (not in the paper: it serves many small reconstructions
+ * at once).  Request r sums the packets pks[r] onto the grid of ctxs[r] into
+ * u_outs[r], exactly as fgr_reconstruct_direct would, but all n requests share
+ * one persistent launch of the summation kernel whose CTAs take (request,
+ * tile, packet-split) items from a device counter until none remain, so many
+ * requests with small grids fill the GPU together.  1 <= n <= 64; all contexts
+ * must have the same dimension, precision and device; every u_outs[r] must be
+ * device memory of its context's output size and the outputs must not
+ * overlap.  Packets may be host memory (staged like fgr_reconstruct_direct);
+ * with device packets and a non-NULL stream the call enqueues only
+ * stream-ordered work, so it can be captured into a CUDA graph.  The caller
+ * owns every array; nothing is retained after the call.  FGR_E_INVALID names
+ * the first offending request in fgr_last_error(). */
+fgr_status fgr_reconstruct_direct_batch(int32_t n, fgr_ctx *const *ctxs, const fgr_packets *const *pks,
+                                        void *const *u_outs, void *cuda_stream);
+
 /* Algorithm 2 Steps 3-4.  Per packet and dimension: int/frac split (eq. 3.6-3.7),
  * right-hand side f~ (eq. 3.23), c~ = A~^+ f~ through the eigen factors,
  * conjugated (true L2 normal equations) and shifted back by

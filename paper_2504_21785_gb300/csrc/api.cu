@@ -59,7 +59,13 @@ void *Scratch::get(size_t bytes) {
     }
     void *p = nullptr;
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, ctx_->pool, s_);
+    // Under stream capture the allocation becomes a graph memory node, which
+    // the graph owns; otherwise it comes from the per-device pool.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = s_ ? cudaStreamIsCapturing(s_, &cap) : cudaSuccess;
+    if (e == cudaSuccess)
+        e = cap == cudaStreamCaptureStatusActive ? cudaMallocAsync(&p, bytes, s_)
+                                                 : cudaMallocFromPoolAsync(&p, bytes, ctx_->pool, s_);
     if (e != cudaSuccess) {
         set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
         cudaGetLastError();
@@ -352,6 +358,52 @@ fgr_status reconstruct(fgr_ctx *ctx, const fgr_packets *pk, void *u_out, void *s
     });
 }
 
+fgr_status reconstruct_direct_batch(int32_t n, fgr_ctx *const *ctxs, const fgr_packets *const *pks,
+                                    void *const *u_outs, void *stream) {
+    clear_error();
+    if (n < 1 || n > 64 || !ctxs || !pks || !u_outs) {
+        set_error("batch: n must be in 1..64 and the arrays non-NULL");
+        return FGR_E_INVALID;
+    }
+    for (int r = 0; r < n; ++r) {
+        if (!ctxs[r] || !u_outs[r]) {
+            set_error("batch: request %d has a NULL context or output", r);
+            return FGR_E_INVALID;
+        }
+        if (ctxs[r]->d != ctxs[0]->d || ctxs[r]->opt.precision != ctxs[0]->opt.precision ||
+            ctxs[r]->device != ctxs[0]->device) {
+            set_error("batch: request %d differs from request 0 in dimension, precision or device", r);
+            return FGR_E_INVALID;
+        }
+        if (!is_device_ptr(u_outs[r])) {
+            set_error("batch: output of request %d is not device memory", r);
+            return FGR_E_INVALID;
+        }
+        fgr_status rc = check_packets(ctxs[r], pks[r]);
+        if (rc != FGR_OK) return rc;
+    }
+    return guarded([&]() -> fgr_status {
+        FGR_CUDA_TRY(cudaSetDevice(ctxs[0]->device));
+        cudaStream_t st = (cudaStream_t)stream;
+        std::vector<std::unique_ptr<Scratch>> owned;
+        std::vector<Scratch *> scratch;
+        std::vector<PacketsDev> dev((size_t)n);
+        for (int r = 0; r < n; ++r) {
+            owned.emplace_back(new Scratch(ctxs[r], st));
+            scratch.push_back(owned.back().get());
+            double *q, *p, *s, *a;
+            fgr_status rc = stage_packets(ctxs[r], pks[r], st, *owned.back(), &dev[(size_t)r], &q, &p, &s, &a);
+            if (rc != FGR_OK) return rc;
+        }
+        Scratch shared(ctxs[0], st);
+        fgr_status rc = run_direct_batch(n, ctxs, dev.data(), u_outs, st, scratch.data(), shared);
+        if (rc != FGR_OK) return rc;
+        FGR_CUDA_TRY(cudaGetLastError());
+        if (!stream) FGR_CUDA_TRY(cudaStreamSynchronize(st));
+        return FGR_OK;
+    });
+}
+
 }  // namespace
 }  // namespace fgr
 
@@ -518,6 +570,11 @@ fgr_status fgr_propagate(fgr_ctx *ctx, fgr_packets *pk, const fgr_potential *v, 
 
 fgr_status fgr_reconstruct_direct(fgr_ctx *ctx, const fgr_packets *pk, void *u_out, void *stream) {
     return reconstruct(ctx, pk, u_out, stream, false);
+}
+
+fgr_status fgr_reconstruct_direct_batch(int32_t n, fgr_ctx *const *ctxs, const fgr_packets *const *pks,
+                                        void *const *u_outs, void *stream) {
+    return reconstruct_direct_batch(n, ctxs, pks, u_outs, stream);
 }
 
 fgr_status fgr_reconstruct_fggc(fgr_ctx *ctx, const fgr_packets *pk, void *u_out, void *stream) {

@@ -21,6 +21,7 @@
 // and a small remainder nu_lo.  FP64 records carry Q, P, S, A and every pair is
 // evaluated in FP64.
 #include <cmath>
+#include <cstring>
 
 #include "device_util.cuh"
 #include "internal.h"
@@ -200,10 +201,12 @@ struct DirectParams {
     int splits;
 };
 
+// One (output tile, packet slice) work item of the direct sum, executed by the
+// whole CTA; shared by the one-request kernel and the batched persistent kernel.
 template <int D, bool FP64>
-__global__ void __launch_bounds__(kThreads) direct_kernel(const void *__restrict__ recs_v,
-                                                          const int64_t *__restrict__ off,
-                                                          DirectParams P, void *__restrict__ u_v) {
+__device__ __forceinline__ void direct_tile(const void *__restrict__ recs_v, const int64_t *__restrict__ off,
+                                            const DirectParams &P, void *__restrict__ u_v, const int tile,
+                                            const int split) {
     using Rec = typename std::conditional<FP64, RecD<D>, RecF<D>>::type;
     constexpr int kWords = sizeof(Rec) / 4;
     __shared__ __align__(16) int srec[kThreads * kWords];
@@ -213,8 +216,6 @@ __global__ void __launch_bounds__(kThreads) direct_kernel(const void *__restrict
 
     const GridDev &g = P.g;
     const Rec *recs = reinterpret_cast<const Rec *>(recs_v);
-    const int tile = blockIdx.x;
-    const int split = blockIdx.y;
     int t[D];
     {
         int rem = tile;
@@ -402,8 +403,71 @@ __global__ void __launch_bounds__(kThreads) direct_kernel(const void *__restrict
     }
 }
 
+template <int D, bool FP64>
+__global__ void __launch_bounds__(kThreads) direct_kernel(const void *__restrict__ recs_v,
+                                                          const int64_t *__restrict__ off,
+                                                          DirectParams P, void *__restrict__ u_v) {
+    direct_tile<D, FP64>(recs_v, off, P, u_v, blockIdx.x, blockIdx.y);
+}
+
+// Batched direct sum: one persistent launch over the work items of up to
+// kBatchMax requests.  Item i belongs to the request r with
+// item_start[r] <= i < item_start[r+1]; within it, tile = j / splits and
+// slice = j % splits.  CTAs pull items through one atomic counter.
+constexpr int kBatchMax = 64;
+
+struct BatchReq {
+    const void *recs;
+    const int64_t *off;
+    void *u;
+    DirectParams P;
+};
+
+struct BatchParams {
+    int n;
+    int64_t item_start[kBatchMax + 1];
+    BatchReq req[kBatchMax];
+};
+
+// kernel parameters may take up to 32764 bytes (sm_70 and later, CUDA 12.1+)
+static_assert(sizeof(BatchParams) <= 32000, "batch parameters exceed the kernel parameter space");
+
+template <int D, bool FP64>
+__global__ void __launch_bounds__(kThreads) direct_batch_kernel(const __grid_constant__ BatchParams B,
+                                                                unsigned long long *__restrict__ counter) {
+    __shared__ long long s_item;
+    const long long total = B.item_start[B.n];
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ULL);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= total) break;
+        int lo = 0, hi = B.n - 1;  // request holding this item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (B.item_start[mid] <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchReq &R = B.req[lo];
+        const long long j = item - B.item_start[lo];
+        direct_tile<D, FP64>(R.recs, R.off, R.P, R.u, (int)(j / R.P.splits), (int)(j % R.P.splits));
+    }
+}
+
+// Zeroes the output and bins one request's packets; fills the parameters of
+// its main kernel (pr->empty when nothing remains to sum).
+struct Prepared {
+    const void *recs = nullptr;
+    const int64_t *off = nullptr;
+    DirectParams P{};
+    int ntiles = 0;
+    bool empty = true;
+};
+
 template <int D>
-fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t st, Scratch &scratch) {
+fgr_status prepare(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t st, Scratch &scratch,
+                   Prepared *pr) {
     const bool fp64 = ctx->opt.precision == FGR_FP64;
     const Mesh &M = ctx->mesh;
     GridDev g{};
@@ -429,12 +493,9 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
     }
     const size_t out_bytes = elem_bytes(ctx->opt.precision) * (size_t)ctx->grid.total;
     FGR_CUDA_TRY(cudaMemsetAsync(u_dev, 0, out_bytes, st));
-    StageTimer timer(ctx, st);
+    pr->empty = true;
     const int64_t m = pk.m;
-    if (m == 0) {
-        timer.finish();
-        return FGR_OK;
-    }
+    if (m == 0) return FGR_OK;
     int *home = (int *)scratch.get(sizeof(int) * m);
     int *counts = (int *)scratch.get(sizeof(int) * 2 * (size_t)ntiles);
     int64_t *off = (int64_t *)scratch.get(sizeof(int64_t) * ((size_t)ntiles + 1));
@@ -460,9 +521,9 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
     else
         bin_scatter_kernel<D, false><<<pb, 256, 0, st>>>(pk.q, pk.p, pk.s, pk.a, m, g, rp, home, off, cursor, recs);
     FGR_CUDA_TRY(cudaGetLastError());
-    timer.mark(&ctx->timing.last.prep_ms);
 
-    DirectParams P{};
+    DirectParams &P = pr->P;
+    P = DirectParams{};
     P.g = g;
     for (int l = 0; l < D; ++l) P.hf[l] = (float)g.h[l];
     P.ce = (float)(-1.4426950408889634 / (2.0 * M.eps));
@@ -470,11 +531,30 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
     P.neg_half_inv_eps = -0.5 / M.eps;
     const int target = ctx->num_sms * ctx->tune.direct_ctas_per_sm;
     P.splits = std::max(1, std::min(64, (target + ntiles - 1) / ntiles));
-    dim3 grid((unsigned)ntiles, (unsigned)P.splits);
+    pr->recs = recs;
+    pr->off = off;
+    pr->ntiles = ntiles;
+    pr->empty = false;
+    return FGR_OK;
+}
+
+template <int D>
+fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t st, Scratch &scratch) {
+    const bool fp64 = ctx->opt.precision == FGR_FP64;
+    StageTimer timer(ctx, st);
+    Prepared pr;
+    fgr_status r = prepare<D>(ctx, pk, u_dev, st, scratch, &pr);
+    if (r != FGR_OK) return r;
+    timer.mark(&ctx->timing.last.prep_ms);
+    if (pr.empty) {
+        timer.finish();
+        return FGR_OK;
+    }
+    dim3 grid((unsigned)pr.ntiles, (unsigned)pr.P.splits);
     if (fp64)
-        direct_kernel<D, true><<<grid, kThreads, 0, st>>>(recs, off, P, u_dev);
+        direct_kernel<D, true><<<grid, kThreads, 0, st>>>(pr.recs, pr.off, pr.P, u_dev);
     else
-        direct_kernel<D, false><<<grid, kThreads, 0, st>>>(recs, off, P, u_dev);
+        direct_kernel<D, false><<<grid, kThreads, 0, st>>>(pr.recs, pr.off, pr.P, u_dev);
     FGR_CUDA_TRY(cudaGetLastError());
     timer.mark(&ctx->timing.last.direct_ms);
     ctx->timing.last.launches = 4;
@@ -482,7 +562,49 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
     return FGR_OK;
 }
 
+// Batched direct sum of n requests of the same dimension and precision: the
+// binning of each request, then one persistent launch over all work items.
+template <int D>
+fgr_status launch_batch(int n, fgr_ctx *const *ctxs, const PacketsDev *pks, void *const *us, cudaStream_t st,
+                        Scratch **scratch, Scratch &shared) {
+    const bool fp64 = ctxs[0]->opt.precision == FGR_FP64;
+    BatchParams B;
+    memset(&B, 0, sizeof(B));
+    int64_t total = 0;
+    for (int r = 0; r < n; ++r) {
+        Prepared pr;
+        fgr_status rc = prepare<D>(ctxs[r], pks[r], us[r], st, *scratch[r], &pr);
+        if (rc != FGR_OK) return rc;
+        if (pr.empty) continue;
+        B.req[B.n] = BatchReq{pr.recs, pr.off, us[r], pr.P};
+        B.item_start[B.n] = total;
+        total += (int64_t)pr.ntiles * pr.P.splits;
+        ++B.n;
+    }
+    B.item_start[B.n] = total;
+    if (B.n == 0) return FGR_OK;
+    auto *counter = (unsigned long long *)shared.get(sizeof(unsigned long long));
+    if (!counter) return FGR_E_NOMEM;
+    FGR_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+    const int64_t ctas = std::min<int64_t>(total, (int64_t)ctxs[0]->num_sms * 8);
+    if (fp64)
+        direct_batch_kernel<D, true><<<(unsigned)ctas, kThreads, 0, st>>>(B, counter);
+    else
+        direct_batch_kernel<D, false><<<(unsigned)ctas, kThreads, 0, st>>>(B, counter);
+    FGR_CUDA_TRY(cudaGetLastError());
+    return FGR_OK;
+}
+
 }  // namespace
+
+fgr_status run_direct_batch(int n, fgr_ctx *const *ctxs, const PacketsDev *pks, void *const *us, cudaStream_t st,
+                            Scratch **scratch, Scratch &shared) {
+    switch (ctxs[0]->d) {
+    case 1: return launch_batch<1>(n, ctxs, pks, us, st, scratch, shared);
+    case 2: return launch_batch<2>(n, ctxs, pks, us, st, scratch, shared);
+    default: return launch_batch<3>(n, ctxs, pks, us, st, scratch, shared);
+    }
+}
 
 fgr_status run_direct(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t st, Scratch &scratch) {
     switch (ctx->d) {

@@ -119,6 +119,9 @@ fgr_status run_direct(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStrea
                       Scratch &scratch);
 fgr_status run_fggc(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t st,
                     Scratch &scratch);
+// n <= 64 requests of one dimension and precision; scratch[r] belongs to request r
+fgr_status run_direct_batch(int n, fgr_ctx *const *ctxs, const PacketsDev *pks, void *const *us,
+                            cudaStream_t st, Scratch **scratch, Scratch &shared);
 
 // Event-based stage timer (active only when ctx->timing.enabled).
 class StageTimer {

@@ -92,6 +92,7 @@ SIGNATURES = {
     "fgr_reconstruct_direct": (ctypes.c_int, [vp, P(fgr_packets), vp, vp]),
     "fgr_reconstruct_fggc": (ctypes.c_int, [vp, P(fgr_packets), vp, vp]),
     "fgr_reconstruct_fggc_noalloc": (ctypes.c_int, [vp, P(fgr_packets), vp, vp]),
+    "fgr_reconstruct_direct_batch": (ctypes.c_int, [ctypes.c_int32, P(vp), P(P(fgr_packets)), P(vp), vp]),
     "fgr_get_info": (ctypes.c_int, [vp, P(fgr_info)]),
     "fgr_autotune": (ctypes.c_int, [vp, P(fgr_packets), vp, ctypes.c_int32, vp]),
     "fgr_get_tuning": (ctypes.c_int, [vp, P(ctypes.c_int32), P(ctypes.c_int32)]),
@@ -227,6 +228,17 @@ def fgr_propagate(ctx, packets: fgr_packets, potential: fgr_potential, t: float,
 def fgr_reconstruct_direct(ctx, packets: fgr_packets, u_out, stream=None):
     return _check(load().fgr_reconstruct_direct(ctx, ctypes.byref(packets), _ptr(u_out)[0],
                                                 _stream_handle(stream)))
+
+
+def fgr_reconstruct_direct_batch(ctxs, packets, u_outs, stream=None):
+    """One persistent direct-sum launch over len(ctxs) requests (<= 64)."""
+    n = len(ctxs)
+    if not (len(packets) == n == len(u_outs)):
+        raise ValueError("ctxs, packets and u_outs must have the same length")
+    c_ctx = (vp * n)(*[getattr(c, "handle", c) for c in ctxs])
+    c_pk = (P(fgr_packets) * n)(*[ctypes.pointer(p) for p in packets])
+    c_u = (vp * n)(*[_ptr(u)[0] for u in u_outs])
+    return _check(load().fgr_reconstruct_direct_batch(n, c_ctx, c_pk, c_u, _stream_handle(stream)))
 
 
 def fgr_reconstruct_fggc(ctx, packets: fgr_packets, u_out, stream=None):
