@@ -243,6 +243,12 @@ fgr_status fgr_get_stats(const fgr_ctx *ctx, fgr_stats *out);
 fgr_status fgr_server_create(size_t hbm_budget_bytes, int32_t max_inflight, fgr_server **out);
 void fgr_server_destroy(fgr_server *srv);
 
+/* Largest group of direct-sum requests (same d and precision, device outputs)
+ * that one worker runs as a single fgr_reconstruct_direct_batch launch
+ * (default 16; 1 turns grouping off; at most 64).  Applies to requests
+ * admitted after the call.  Not in the paper: a serving policy. */
+fgr_status fgr_server_set_max_batch(fgr_server *srv, int32_t max_batch);
+
 /* Copies a packet set (host or device, see fgr_packets) into device memory owned
  * by the server and returns its id.  FGR_E_CAPACITY if it would exceed the budget. */
 fgr_status fgr_register_packets(fgr_server *srv, int32_t d, const fgr_packets *pk,

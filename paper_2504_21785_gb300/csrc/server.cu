@@ -6,8 +6,12 @@
 // requests stay within the memory budget.  Each worker owns a CUDA stream and
 // a small cache of contexts, so the kernels of admitted requests overlap on the
 // device; a request that arrives while others run starts as soon as a slot and
-// memory free up.  Completion is reported through fgr_poll with host
-// timestamps (submit, start, done).
+// memory free up.  Direct-sum requests of one dimension and precision that
+// wait together (device outputs) are admitted as one group of up to max_batch
+// and run as a single persistent launch (fgr_reconstruct_direct_batch); a
+// group that the batched call rejects is retried request by request, so each
+// request gets its own status.  Completion is reported through fgr_poll with
+// host timestamps (submit, start, done).
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -43,9 +47,12 @@ struct Job {
     uint64_t ticket = 0;
     fgr_request req{};
     size_t footprint = 0;
+    bool dev_out = false;
     St st = St::Queued;
     fgr_result res{};
 };
+
+using Group = std::vector<std::shared_ptr<Job>>;
 
 struct CtxKey {
     int32_t d;
@@ -61,10 +68,11 @@ struct fgr_server {
     int device = 0;
     size_t budget = 0;
     int max_inflight = 1;
+    int max_batch = 16;
     std::mutex mu;
     std::condition_variable cv_sched, cv_work, cv_done;
     std::deque<std::shared_ptr<Job>> queue;      // arrival order
-    std::deque<std::shared_ptr<Job>> admitted;   // waiting for a worker
+    std::deque<Group> admitted;                  // waiting for a worker
     std::map<uint64_t, std::shared_ptr<Job>> jobs;
     std::map<uint64_t, PacketSet> sets;
     size_t resident = 0, reserved = 0;
@@ -93,76 +101,143 @@ size_t footprint(const fgr_request &r, const PacketSet &ps) {
     return f + (size_t)total * eb;  // staging of a host output
 }
 
-void worker_main(fgr_server *S) {
-    cudaSetDevice(S->device);
-    cudaStream_t stream;
-    cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
-    std::vector<std::pair<CtxKey, fgr_ctx *>> cache;  // small LRU
-    for (;;) {
-        std::shared_ptr<Job> job;
-        PacketSet ps;
-        {
-            std::unique_lock<std::mutex> lk(S->mu);
-            S->cv_work.wait(lk, [&] { return S->stop || !S->admitted.empty(); });
-            if (S->admitted.empty()) break;  // stop requested and nothing left
-            job = S->admitted.front();
-            S->admitted.pop_front();
-            job->st = St::Running;
-            job->res.t_start_ms = now_ms();
-            ps = S->sets[job->req.set_id];
-        }
-        const fgr_request &r = job->req;
+bool batchable(const Job &j) { return j.req.method == 0 && j.dev_out; }
+
+bool same_batch(const Job &a, const Job &b) {
+    return a.req.d == b.req.d && a.req.opt.precision == b.req.opt.precision;
+}
+
+fgr_packets packets_of(const PacketSet &ps) {
+    fgr_packets pk;
+    pk.m = ps.m;
+    pk.q = ps.buf;
+    pk.p = ps.buf + ps.d * ps.m;
+    pk.s = ps.buf + 2 * ps.d * ps.m;
+    pk.a = ps.buf + (2 * ps.d + 1) * ps.m;
+    pk.on_device = 1;
+    pk.reserved = 0;
+    return pk;
+}
+
+// Contexts keyed by (d, grid, eps, options), most recently used first.
+class CtxCache {
+  public:
+    ~CtxCache() {
+        for (auto &c : items_) fgr_destroy(c.second);
+    }
+    fgr_status get(const fgr_request &r, fgr_ctx **out) {
         CtxKey key;
         memset(&key, 0, sizeof(key));
         key.d = r.d;
         key.grid = r.grid;
         key.eps = r.eps;
         key.opt = r.opt;
-        fgr_ctx *ctx = nullptr;
-        for (size_t i = 0; i < cache.size(); ++i)
-            if (cache[i].first == key) {
-                ctx = cache[i].second;
-                std::rotate(cache.begin(), cache.begin() + i, cache.begin() + i + 1);
-                break;
+        for (size_t i = 0; i < items_.size(); ++i)
+            if (items_[i].first == key) {
+                std::rotate(items_.begin(), items_.begin() + i, items_.begin() + i + 1);
+                *out = items_[0].second;
+                return FGR_OK;
             }
-        fgr_status st = FGR_OK;
-        if (!ctx) {
-            st = fgr_create(r.d, &r.grid, r.eps, &r.opt, &ctx);
-            if (st == FGR_OK) {
-                cache.insert(cache.begin(), {key, ctx});
-                if (cache.size() > 8) {
-                    fgr_destroy(cache.back().second);
-                    cache.pop_back();
-                }
+        fgr_status st = fgr_create(r.d, &r.grid, r.eps, &r.opt, out);
+        if (st == FGR_OK) items_.insert(items_.begin(), {key, *out});
+        return st;
+    }
+    // called between groups, so no context of a running group is destroyed
+    void trim(size_t keep) {
+        while (items_.size() > keep) {
+            fgr_destroy(items_.back().second);
+            items_.pop_back();
+        }
+    }
+
+  private:
+    std::vector<std::pair<CtxKey, fgr_ctx *>> items_;
+};
+
+fgr_status run_one(const Job &job, const PacketSet &ps, CtxCache &cache, cudaStream_t stream) {
+    const fgr_request &r = job.req;
+    fgr_ctx *ctx = nullptr;
+    fgr_status st = cache.get(r, &ctx);
+    if (st != FGR_OK) return st;
+    fgr_packets pk = packets_of(ps);
+    st = r.method == 0 ? fgr_reconstruct_direct(ctx, &pk, r.u_out, stream)
+                       : fgr_reconstruct_fggc(ctx, &pk, r.u_out, stream);
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (st == FGR_OK && e != cudaSuccess) st = FGR_E_CUDA;
+    return st;
+}
+
+// One persistent launch for the whole group; on failure the requests are
+// retried one by one.
+void run_group(const Group &g, const std::vector<PacketSet> &ps, CtxCache &cache, cudaStream_t stream,
+               std::vector<fgr_status> &st) {
+    const size_t n = g.size();
+    std::vector<fgr_ctx *> ctxs(n);
+    std::vector<fgr_packets> pk(n);
+    std::vector<const fgr_packets *> pkp(n);
+    std::vector<void *> us(n);
+    fgr_status rc = FGR_OK;
+    for (size_t i = 0; i < n && rc == FGR_OK; ++i) {
+        rc = cache.get(g[i]->req, &ctxs[i]);
+        pk[i] = packets_of(ps[i]);
+        pkp[i] = &pk[i];
+        us[i] = g[i]->req.u_out;
+    }
+    if (rc == FGR_OK) {
+        rc = fgr_reconstruct_direct_batch((int32_t)n, ctxs.data(), pkp.data(), us.data(), stream);
+        cudaError_t e = cudaStreamSynchronize(stream);
+        if (rc == FGR_OK && e != cudaSuccess) rc = FGR_E_CUDA;
+    }
+    if (rc == FGR_OK) {
+        std::fill(st.begin(), st.end(), FGR_OK);
+        return;
+    }
+    for (size_t i = 0; i < n; ++i) st[i] = run_one(*g[i], ps[i], cache, stream);
+}
+
+void worker_main(fgr_server *S) {
+    cudaSetDevice(S->device);
+    cudaStream_t stream;
+    cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+    CtxCache cache;
+    for (;;) {
+        Group group;
+        std::vector<PacketSet> ps;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_work.wait(lk, [&] { return S->stop || !S->admitted.empty(); });
+            if (S->admitted.empty()) break;  // stop requested and nothing left
+            group = std::move(S->admitted.front());
+            S->admitted.pop_front();
+            const double t = now_ms();
+            for (auto &job : group) {
+                job->st = St::Running;
+                job->res.t_start_ms = t;
+                ps.push_back(S->sets[job->req.set_id]);
             }
         }
-        if (st == FGR_OK) {
-            fgr_packets pk;
-            pk.m = ps.m;
-            pk.q = ps.buf;
-            pk.p = ps.buf + ps.d * ps.m;
-            pk.s = ps.buf + 2 * ps.d * ps.m;
-            pk.a = ps.buf + (2 * ps.d + 1) * ps.m;
-            pk.on_device = 1;
-            pk.reserved = 0;
-            st = r.method == 0 ? fgr_reconstruct_direct(ctx, &pk, r.u_out, stream)
-                               : fgr_reconstruct_fggc(ctx, &pk, r.u_out, stream);
-            cudaError_t e = cudaStreamSynchronize(stream);
-            if (st == FGR_OK && e != cudaSuccess) st = FGR_E_CUDA;
-        }
+        std::vector<fgr_status> st(group.size(), FGR_OK);
+        if (group.size() == 1)
+            st[0] = run_one(*group[0], ps[0], cache, stream);
+        else
+            run_group(group, ps, cache, stream, st);
+        cache.trim(std::max<size_t>(8, 2 * (size_t)S->max_batch));
         {
             std::lock_guard<std::mutex> lk(S->mu);
-            job->res.status = st;
-            job->res.t_done_ms = now_ms();
-            job->st = St::Done;
-            S->reserved -= job->footprint;
+            const double t = now_ms();
+            for (size_t i = 0; i < group.size(); ++i) {
+                Job &job = *group[i];
+                job.res.status = st[i];
+                job.res.t_done_ms = t;
+                job.st = St::Done;
+                S->reserved -= job.footprint;
+                S->sets[job.req.set_id].users -= 1;
+            }
             S->running -= 1;
-            S->sets[r.set_id].users -= 1;
         }
         S->cv_done.notify_all();
         S->cv_sched.notify_all();
     }
-    for (auto &c : cache) fgr_destroy(c.second);
     cudaStreamDestroy(stream);
 }
 
@@ -176,14 +251,28 @@ void scheduler_main(fgr_server *S) {
             return S->running < S->max_inflight && S->resident + S->reserved + j->footprint <= S->budget;
         });
         if (S->stop) break;
-        // admit in arrival order while slots and memory allow
+        // admit in arrival order while slots and memory allow; a batchable
+        // request takes the later compatible ones with it
         while (!S->queue.empty() && S->running < S->max_inflight) {
             auto j = S->queue.front();
             if (S->resident + S->reserved + j->footprint > S->budget) break;
             S->queue.pop_front();
             S->reserved += j->footprint;
+            Group g{j};
+            if (batchable(*j))
+                for (auto it = S->queue.begin(); it != S->queue.end() && (int)g.size() < S->max_batch;) {
+                    const auto &k = *it;
+                    if (batchable(*k) && same_batch(*j, *k) &&
+                        S->resident + S->reserved + k->footprint <= S->budget) {
+                        S->reserved += k->footprint;
+                        g.push_back(k);
+                        it = S->queue.erase(it);
+                    } else {
+                        ++it;
+                    }
+                }
             S->running += 1;
-            S->admitted.push_back(j);
+            S->admitted.push_back(std::move(g));
         }
         S->cv_work.notify_all();
     }
@@ -253,6 +342,17 @@ void fgr_server_destroy(fgr_server *S) {
     cudaSetDevice(S->device);
     for (auto &kv : S->sets) cudaFree(kv.second.buf);
     delete S;
+}
+
+fgr_status fgr_server_set_max_batch(fgr_server *S, int32_t max_batch) {
+    clear_error();
+    if (!S || max_batch < 1 || max_batch > 64) {
+        set_error("server: max_batch must be in 1..64");
+        return FGR_E_INVALID;
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->max_batch = max_batch;
+    return FGR_OK;
 }
 
 fgr_status fgr_register_packets(fgr_server *S, int32_t d, const fgr_packets *pk, uint64_t *set_id) {
@@ -329,6 +429,11 @@ fgr_status fgr_submit(fgr_server *S, const fgr_request *req, uint64_t *ticket) {
     }
     auto j = std::make_shared<Job>();
     j->req = *req;
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, req->u_out) == cudaSuccess)
+        j->dev_out = attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+    else
+        cudaGetLastError();
     fgr_options o = req->opt;
     if (o.cq == 0 && o.cp == 0 && o.nq == 0 && o.np == 0 && o.rcond == 0) fgr_default_options(&o);
     j->req.opt = o;

@@ -101,6 +101,7 @@ SIGNATURES = {
     "fgr_get_stats": (ctypes.c_int, [vp, P(fgr_stats)]),
     "fgr_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int32, P(vp)]),
     "fgr_server_destroy": (None, [vp]),
+    "fgr_server_set_max_batch": (ctypes.c_int, [vp, ctypes.c_int32]),
     "fgr_register_packets": (ctypes.c_int, [vp, ctypes.c_int32, P(fgr_packets), P(ctypes.c_uint64)]),
     "fgr_release_packets": (ctypes.c_int, [vp, ctypes.c_uint64]),
     "fgr_submit": (ctypes.c_int, [vp, P(fgr_request), P(ctypes.c_uint64)]),
@@ -291,6 +292,10 @@ def fgr_server_create(hbm_budget_bytes: int, max_inflight: int):
 def fgr_server_destroy(srv):
     if srv:
         load().fgr_server_destroy(srv)
+
+
+def fgr_server_set_max_batch(srv, max_batch: int):
+    return _check(load().fgr_server_set_max_batch(srv, int(max_batch)))
 
 
 def fgr_register_packets(srv, d: int, packets: fgr_packets) -> int:

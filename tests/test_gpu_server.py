@@ -168,3 +168,46 @@ def test_many_client_threads(fgr):
         assert not errors
     finally:
         fgr.fgr_server_destroy(srv)
+
+
+def test_direct_requests_waiting_together_run_as_one_batch(fgr):
+    import torch
+    from . import _gpu
+    sets = [random_packets(70 + k, 1, m, q_range=(-2.5, 2.5), p_range=(-2, 2), s_range=(-1, 1))
+            for k, m in enumerate((3000, 8000))]
+    big = random_packets(72, 2, 200000, q_range=(-2.5, 2.5), p_range=(-2, 2))
+    srv = fgr.fgr_server_create(8 << 30, 1)
+    try:
+        fgr.fgr_server_set_max_batch(srv, 64)
+        with pytest.raises(fgr.FgrError):
+            fgr.fgr_server_set_max_batch(srv, 65)
+        ids = [fgr.fgr_register_packets(srv, 1, fgr.make_packets(*[np.ascontiguousarray(pk[k]) for k in "qpsa"]))
+               for pk in sets]
+        big_id = fgr.fgr_register_packets(srv, 2, fgr.make_packets(*[np.ascontiguousarray(big[k]) for k in "qpsa"]))
+        opt = fgr.make_options(precision=fgr.FGR_FP32)
+        # a long 2-D request holds the only slot while the 1-D ones queue up
+        ub = torch.zeros((1024, 1024), dtype=torch.complex64, device="cuda")
+        tickets = [fgr.fgr_submit(srv, fgr.make_request(1, _grid(2, 1024), 1 / 1024, opt, big_id, ub))]
+        rng = np.random.default_rng(5)
+        reqs, outs = [], []
+        for i in range(40):
+            r = dict(set=int(rng.integers(0, 2)), n=int(2 ** rng.integers(9, 13)),
+                     eps=float(2.0 ** -rng.uniform(6, 10)))
+            u = torch.zeros(r["n"], dtype=torch.complex64, device="cuda")
+            reqs.append(r)
+            outs.append(u)
+            tickets.append(fgr.fgr_submit(srv, fgr.make_request(0, _grid(1, r["n"]), r["eps"], opt,
+                                                                ids[r["set"]], u)))
+        res = [fgr.fgr_poll(srv, t, -1) for t in tickets]
+        assert all(x.status == 0 for x in res)
+        # a group shares its start and completion times
+        groups = {}
+        for x in res[1:]:
+            groups.setdefault((x.t_start_ms, x.t_done_ms), []).append(x)
+        assert max(len(g) for g in groups.values()) >= 2
+        for r, u in zip(reqs, outs):
+            ref = _gpu.reconstruct("direct", sets[r["set"]], _grid(1, r["n"]), r["eps"], opt)
+            got = u.cpu().numpy()
+            assert np.linalg.norm(got - ref) <= 1e-6 * max(np.linalg.norm(ref), 1e-300)
+    finally:
+        fgr.fgr_server_destroy(srv)
