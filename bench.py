@@ -110,11 +110,11 @@ def rk4_nsteps(t: float, dt: float) -> int:
 
 # FP64 FLOPs the RK4 kernel executes per packet-step (FMA = 2), counted by ncu
 # on GB300 (DFMA x 2 + DMUL + DADD of rk4_kernel), 1-D cosine potential:
-# 91 DFMA + 36 DMUL + 13 DADD.  See profiles/rk4_kernel_1d_262144_100steps.md.
-RK4_FP64_FLOPS_PER_PACKET_STEP = {(1, "cossum"): 231}
+# 83.27 DFMA + 35.21 DMUL + 13.06 DADD (262144 packets, 100 steps).
+RK4_FP64_FLOPS_PER_PACKET_STEP = {(1, "cossum"): 214.81}
 # DRAM bytes of one RK4 launch on the bench workload (ncu, same capture): the
 # packet arrays are read once; the written state stays in L2 at kernel end.
-RK4_TRAFFIC_BYTES = {(1, "cossum", 262144): 10515200}
+RK4_TRAFFIC_BYTES = {(1, "cossum", 262144): 10530048}
 
 
 def run_ours(args):
@@ -205,6 +205,10 @@ def run_ours(args):
     ud, uf = u_d.cpu().numpy(), u_f.cpu().numpy()
     rel = float(np.linalg.norm(uf - ud) / max(np.linalg.norm(ud), 1e-300))
 
+    # reconstruction alone on the propagated batch: median, min and max of 20
+    # runs each (L2 flushed before every run), FGGC with Q4P2 and Q2P2
+    recon = reconstruct_runs(fgr, ctx, packets, u_d, grid, d, eps, prec, flush, stream, ud, runs=20)
+
     # stage split of FGGC (context timing on; outside the timed region)
     fgr.fgr_set_timing(ctx.handle, True)
     fgr.fgr_reconstruct_fggc(ctx.handle, packets, u_f, stream)
@@ -278,6 +282,7 @@ def run_ours(args):
                 "fggc_over_direct_reconstruct": ms_direct / ms_fggc,
                 "fggc_over_direct_pipeline": (ms_prop + ms_direct) / (ms_prop + ms_fggc),
                 "rel_l2_fggc_vs_direct": rel,
+                "reconstruct_20_runs": recon,
                 "fggc_stage_split": fggc_stages,
                 "direct_stage_split": direct_stages,
             },
@@ -298,6 +303,8 @@ def run_ours(args):
             out["workloads"] = {}
             for cfg in [int(x) for x in args.extra.split(",") if x]:
                 out["workloads"]["config%d" % cfg] = reconstruct_bench(cfg, args, flush)
+        if args.batch:
+            out["batched_direct"] = batch_bench(args, flush)
         if args.serving:
             out["serving"] = serving_bench(args, local)
         if args.cpu_baseline:
@@ -305,6 +312,41 @@ def run_ours(args):
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+    return out
+
+
+def reconstruct_runs(fgr, ctx, packets, u_ref, grid, d, eps, prec, flush, stream, ud, runs=20):
+    """Median/min/max ms of `runs` reconstructions per method; FGGC with the
+    Q4P2 and Q2P2 neighbour sets, relative L2 difference from the direct sum."""
+    import numpy as np
+    import torch
+
+    q2 = fgr.Context(d, grid, eps, fgr.make_options(precision=prec, nq=2, np_=2))
+    u = torch.zeros_like(u_ref)
+    out = {}
+    for name, fn, c in (("direct", fgr.fgr_reconstruct_direct, ctx), ("fggc_q4p2", fgr.fgr_reconstruct_fggc, ctx),
+                        ("fggc_q2p2", fgr.fgr_reconstruct_fggc, q2)):
+        for _ in range(3):
+            fn(c.handle, packets, u, stream)
+        ms = []
+        for _ in range(runs):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(c.handle, packets, u, stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        got = u.cpu().numpy()
+        rel = float(np.linalg.norm(got - ud) / max(np.linalg.norm(ud), 1e-300))
+        med = statistics.median(ms)
+        out[name] = {"median_ms": med, "min_ms": min(ms), "max_ms": max(ms),
+                     "packets_per_s": int(packets.m) / (med * 1e-3), "rel_l2_vs_direct": rel}
+    q2.close()
+    for k in ("fggc_q4p2", "fggc_q2p2"):
+        ok = out[k]["rel_l2_vs_direct"] <= 1e-5
+        out[k]["speedup_vs_direct_at_equal_accuracy"] = (
+            out["direct"]["median_ms"] / out[k]["median_ms"] if ok else "not at equal accuracy")
     return out
 
 
@@ -333,21 +375,32 @@ def reconstruct_bench(cfg: int, args, flush):
     ud = torch.zeros(shape, dtype=cdt, device="cuda")
     stream = torch.cuda.current_stream()
     fgr.fgr_autotune(ctx.handle, pk, ud, 3, stream)
-    res = {}
-    for name, fn, u in (("fggc", fgr.fgr_reconstruct_fggc, uf), ("direct", fgr.fgr_reconstruct_direct, ud)):
-        fn(ctx.handle, pk, u, stream)
+    res, spread = {}, {}
+    q2 = fgr.Context(d, grid, eps, fgr.make_options(precision=prec, nq=2, np_=2))
+    uq2 = torch.zeros(shape, dtype=cdt, device="cuda")
+    for name, fn, c, u in (("direct", fgr.fgr_reconstruct_direct, ctx, ud),
+                           ("fggc", fgr.fgr_reconstruct_fggc, ctx, uf),
+                           ("fggc_q2p2", fgr.fgr_reconstruct_fggc, q2, uq2)):
+        t0 = time.perf_counter()
+        fn(c.handle, pk, u, stream)
+        torch.cuda.synchronize()
+        # 20 timed runs, fewer where one run takes seconds (the 3-D direct sum)
+        runs = 20 if time.perf_counter() - t0 < 1.0 else 3
         ms = []
-        for _ in range(args.steps):
+        for _ in range(runs):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            fn(ctx.handle, pk, u, stream)
+            fn(c.handle, pk, u, stream)
             e1.record(stream)
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
-        res[name] = statistics.mean(ms)
-    a, b = uf.cpu().numpy(), ud.cpu().numpy()
+        res[name] = statistics.median(ms)
+        spread[name] = {"runs": runs, "median_ms": res[name], "min_ms": min(ms), "max_ms": max(ms)}
+    q2.close()
+    a, b, c2 = uf.cpu().numpy(), ud.cpu().numpy(), uq2.cpu().numpy()
     rel = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    rel_q2 = float(np.linalg.norm(c2 - b) / max(np.linalg.norm(b), 1e-300))
     fgr.fgr_set_timing(ctx.handle, True)
     fgr.fgr_reconstruct_fggc(ctx.handle, pk, uf, stream)
     st = fgr.fgr_get_stats(ctx.handle)
@@ -357,17 +410,103 @@ def reconstruct_bench(cfg: int, args, flush):
             "fggc_ms": res["fggc"], "direct_ms": res["direct"],
             "fggc_packets_per_s": M / (res["fggc"] * 1e-3), "direct_packets_per_s": M / (res["direct"] * 1e-3),
             "fggc_over_direct": res["direct"] / res["fggc"], "rel_l2_fggc_vs_direct": rel,
+            "runs": spread, "fggc_q2p2_ms": res["fggc_q2p2"], "rel_l2_fggc_q2p2_vs_direct": rel_q2,
+            "fggc_q2p2_over_direct": (res["direct"] / res["fggc_q2p2"] if rel_q2 <= 1e-5
+                                      else "not at equal accuracy (rel L2 > 1e-5)"),
             "fggc_nodes": int(st.nodes), "autotuned_ctas_per_sm": tuned,
             "fggc_stage_split_ms": {"bounds_alloc": st.prep_ms, "coeff_scatter": st.scatter_ms, "grid": st.grid_ms}}
 
 
+def batch_bench(args, flush):
+    """Many small direct-sum requests: one fgr_reconstruct_direct call each on
+    one stream, against one fgr_reconstruct_direct_batch call, eager and replayed
+    from a CUDA graph.  64 1-D requests, grids 1024..8192 points, 2k..16k
+    uniformly placed packets, eps in [1/1024, 1/256], FP32; L2 flushed before
+    each timed run."""
+    import numpy as np
+    import torch
+
+    import paper_2504_21785_gb300 as fgr
+    from workloads import random_packets, mesh_for
+
+    rng = np.random.default_rng(11)
+    opt = fgr.make_options(precision=fgr.FGR_FP32)
+    ctxs, pks, outs, keep = [], [], [], []
+    packets = 0
+    for r in range(64):
+        n = int(2 ** rng.integers(10, 14))
+        eps = float(2.0 ** -rng.uniform(8, 10))
+        m = int(np.exp(rng.uniform(np.log(2048), np.log(16384))))
+        pk = random_packets(100 + r, 1, m, q_range=(-3.2, 3.2), p_range=(-4, 4), s_range=(-1, 1),
+                            mesh=mesh_for(1, eps))
+        arrs = [torch.tensor(np.ascontiguousarray(pk[k]), dtype=torch.float64, device="cuda") for k in "qpsa"]
+        grid = dict(d=1, n=[n], lo=[-np.pi], hi=[np.pi])
+        ctxs.append(fgr.Context(1, grid, eps, opt))
+        pks.append(fgr.make_packets(*arrs))
+        outs.append(torch.zeros(n, dtype=torch.complex64, device="cuda"))
+        keep.append(arrs)
+        packets += m
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+
+    def single():
+        for c, p, u in zip(ctxs, pks, outs):
+            fgr.fgr_reconstruct_direct(c.handle, p, u, s)
+
+    def batched():
+        fgr.fgr_reconstruct_direct_batch(ctxs, pks, outs, s)
+
+    ref = None
+    for fn in (single, batched):  # warm-up; results must agree
+        fn()
+        torch.cuda.synchronize()
+        cur = [u.clone() for u in outs]
+        if ref is None:
+            ref = cur
+    worst = max(float(torch.linalg.norm(a - b) / max(float(torch.linalg.norm(b)), 1e-30))
+                for a, b in zip(cur, ref))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        g.capture_begin()
+        batched()
+        g.capture_end()
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        ms = []
+        for _ in range(max(3, args.steps)):
+            with torch.cuda.stream(s):
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            fn()
+            e1.record(s)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    with torch.cuda.stream(s):
+        t_single = timed(single)
+        t_batch = timed(batched)
+        t_graph = timed(g.replay)
+    for c in ctxs:
+        c.close()
+    return {"requests": len(outs), "packets": packets, "single_calls_ms": t_single, "batch_ms": t_batch,
+            "graph_replay_ms": t_graph, "requests_per_s_graph": len(outs) / (t_graph * 1e-3),
+            "speedup_batch_vs_single": t_single / t_batch, "speedup_graph_vs_single": t_single / t_graph,
+            "max_rel_l2_batch_vs_single": worst,
+            "mix": "64 x 1-D, grids 1024..8192, 2k..16k packets, eps 1/1024..1/256, fp32"}
+
+
 def serving_bench(args, device_index: int):
     """Continuous-batching server under a Poisson stream (the serving workload):
-    packet sets with d in {1, 2}, eps log-uniform in [1/1024, 1/64], M log-uniform
-    in [4k, cap], propagated once to t = 0.5 on the GPU and kept resident;
-    requests pick a set, a grid (1-D: 1024..32768 points, 2-D: 256^2..1024^2)
+    a pool of packet sets with d in {1, 2}, eps log-uniform in [1/1024, 1/64],
+    M = 2^L with L uniform in [12, log2(max packets)] (WKB data on a q x p mesh),
+    propagated once to t = 0.5 on the GPU and kept resident; each request picks
+    a set, a grid (1-D: 1024..32768 points, 2-D: 256^2..1024^2, powers of two)
     and a method (direct / FGGC) uniformly; FP32.  Capacity = 1 / mean isolated
-    service time; p50/p99 of submit-to-done latency at 0.5x and 0.9x capacity."""
+    service time; p50/p99 of submit-to-done latency and packets/s at 0.5x, 0.8x
+    and 1.0x capacity."""
     import numpy as np
     import torch
 
@@ -379,13 +518,15 @@ def serving_bench(args, device_index: int):
     sets = []
     pot1 = fgr.make_potential("cossum", c0=1.0, amp=-1.0, k=1.0)
     pot2 = fgr.make_potential("cossum", c0=2.0, amp=1.0, k=1.0)
+    lmax = int(round(math.log2(args.serve_max_packets)))
+    t_setup = time.perf_counter()
     for i in range(args.serve_sets):
         d = 1 + (i % 2)
         eps = float(2.0 ** -rng.uniform(6, 10))
-        m_target = float(np.exp(rng.uniform(np.log(4096), np.log(args.serve_max_packets))))
-        per_dim = m_target ** (1.0 / d)
-        n = max(8, int(2 ** round(np.log2(np.sqrt(per_dim)))))
-        pk = wkb_packets(d, eps, n, n, WKB_TANH)
+        L = int(rng.integers(12, lmax + 1))
+        half = L // d                       # log2 of nq * np per dimension
+        nq, np_ = 2 ** ((half + 1) // 2), 2 ** (half // 2)
+        pk = wkb_packets(d, eps, nq, np_, WKB_TANH)
         arrs = [torch.tensor(np.ascontiguousarray(pk[k]), dtype=torch.float64, device="cuda") for k in "qpsa"]
         grid0 = dict(d=d, n=[16] * d, lo=[-3.0] * d, hi=[3.0] * d)
         with fgr.Context(d, grid0, eps) as c:
@@ -394,6 +535,7 @@ def serving_bench(args, device_index: int):
         sid = fgr.fgr_register_packets(srv, d, fgr.make_packets(*arrs))
         sets.append((sid, d, eps, int(pk["s"].size)))
         del arrs
+    t_setup = time.perf_counter() - t_setup
     opt = fgr.make_options(precision=fgr.FGR_FP32)
 
     def draw():
@@ -413,6 +555,7 @@ def serving_bench(args, device_index: int):
         t = fgr.fgr_submit(srv, fgr.make_request(method, grid, eps, opt, sid, u))
         r = fgr.fgr_poll(srv, t, -1)
         iso.append(r.t_done_ms - r.t_start_ms)
+    capacity = 1e3 / float(np.mean(iso))
     # saturated throughput: a burst submitted at once, all slots busy
     burst = [draw() for _ in range(args.serve_probe)]
     bouts = [torch.zeros(tuple(g["n"]), dtype=torch.complex64, device="cuda") for (_, _, _, _, g, _) in burst]
@@ -421,9 +564,10 @@ def serving_bench(args, device_index: int):
           for (sid, d, e, m, g, mth), u in zip(burst, bouts)]
     for t in bt:
         fgr.fgr_poll(srv, t, -1)
-    capacity = len(burst) / (time.perf_counter() - tb0)  # requests/s with every slot busy
+    burst_rate = len(burst) / (time.perf_counter() - tb0)
+    del bouts
     levels = {}
-    for frac in (0.5, 0.9):
+    for frac in (0.5, 0.8, 1.0):
         lam = frac * capacity
         reqs = [draw() for _ in range(args.serve_requests)]
         outs = [torch.zeros(tuple(g["n"]), dtype=torch.complex64, device="cuda") for (_, _, _, _, g, _) in reqs]
@@ -444,11 +588,13 @@ def serving_bench(args, device_index: int):
         levels["%.1fx" % frac] = {"lambda_req_per_s": lam, "p50_ms": float(np.percentile(lat, 50)),
                                   "p99_ms": float(np.percentile(lat, 99)), "packets_per_s": packets / (t1 - t0),
                                   "requests": len(reqs), "all_ok": ok}
+        del outs
     fgr.fgr_server_destroy(srv)
-    return {"sets": [{"d": d, "eps": eps, "packets": m} for (_, d, eps, m) in sets],
-            "inflight": args.serve_inflight, "isolated_service_ms_mean": float(np.mean(iso)),
+    ms = [m for (_, _, _, m) in sets]
+    return {"sets": len(sets), "packets_min": min(ms), "packets_max": max(ms), "setup_s_untimed": t_setup,
+            "inflight": args.serve_inflight, "max_batch": 16, "isolated_service_ms_mean": float(np.mean(iso)),
             "isolated_service_ms_p50": float(np.percentile(iso, 50)),
-            "capacity_req_per_s": capacity, "levels": levels,
+            "capacity_req_per_s": capacity, "burst_req_per_s": burst_rate, "levels": levels,
             "mix": "d in {1,2}; grids 1-D 1024..32768, 2-D 256^2..1024^2; direct/fggc 50/50; fp32"}
 
 
@@ -506,7 +652,8 @@ def run_reference(args):
 def run_profile_case(args):
     """One short pass of every kernel on the benchmark workload, for ncu:
     propagate to t = 0.01 (100 RK4 steps), then one FGGC and one direct
-    reconstruction of the propagated packets."""
+    reconstruction of the propagated packets, and one batched direct sum of
+    eight copies of that request (FGGC only for 3-D workloads)."""
     import numpy as np
     import torch
 
@@ -523,7 +670,10 @@ def run_profile_case(args):
         cdt = torch.complex64 if prec == fgr.FGR_FP32 else torch.complex128
         u = torch.zeros(tuple(grid["n"][:d]), dtype=cdt, device="cuda")
         fgr.fgr_reconstruct_fggc(ctx.handle, pk, u)
-        fgr.fgr_reconstruct_direct(ctx.handle, pk, u)
+        if d < 3:  # the 3-D direct sum takes seconds: FGGC only there
+            fgr.fgr_reconstruct_direct(ctx.handle, pk, u)
+            outs = [torch.zeros_like(u) for _ in range(8)]
+            fgr.fgr_reconstruct_direct_batch([ctx] * 8, [pk] * 8, outs)
         torch.cuda.synchronize()
     print(json.dumps({"profile_case": "config %d" % args.config, "ok": True}))
 
@@ -540,9 +690,10 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=512)
     ap.add_argument("--extra", default="3", help="other workloads to reconstruct, e.g. 3,4 ('' for none)")
     ap.add_argument("--no-serving", dest="serving", action="store_false")
-    ap.add_argument("--serve-sets", type=int, default=8)
-    ap.add_argument("--serve-max-packets", type=int, default=1 << 19)
-    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--no-batch", dest="batch", action="store_false")
+    ap.add_argument("--serve-sets", type=int, default=32)
+    ap.add_argument("--serve-max-packets", type=int, default=1 << 22)
+    ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-probe", type=int, default=40)
     ap.add_argument("--serve-inflight", type=int, default=4)
     ap.add_argument("--profile", action="store_true",

@@ -513,6 +513,10 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
         }
     }
     c.row_len = (int64_t)c.A[D - 1] * c.B[D - 1];
+    for (int l = 0; l < D - 1; ++l) {
+        c.ra[l] = c.sa[l] / c.row_len;
+        c.rb[l] = c.sb[l] / c.row_len;
+    }
     const int64_t rows0 = cells / c.row_len;
     ctx->timing.last.nodes = cells;
 
@@ -544,7 +548,8 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
     int2 *brange = (int2 *)scratch.get(sizeof(int2) * (size_t)max_lines);
     if (!W || !flags || !brange || (D > 1 && (!buf1 || !buf2))) return FGR_E_NOMEM;
     FGR_CUDA_TRY(cudaMemsetAsync(W, 0, eb * (size_t)cells, st));
-    FGR_CUDA_TRY(cudaMemsetAsync(flags, 0, (size_t)rows0, st));
+    // the scatter marks the rows it reaches; the single row of d = 1 is marked here
+    FGR_CUDA_TRY(cudaMemsetAsync(flags, D == 1 ? 1 : 0, (size_t)rows0, st));
     timer.mark(&ctx->timing.last.prep_ms);
 
     if (fp64) {
@@ -793,9 +798,9 @@ extern "C" fgr_status fgr_reconstruct_fggc_noalloc(fgr_ctx *ctx, const fgr_packe
     c.sb[0] = 1;
     c.sa[0] = c.B[0];
     c.row_len = cells;
-    // the node array and the row flag accumulate: clear them
+    // the node array accumulates: clear it; the single row is marked non-empty
     FGR_CUDA_TRY(cudaMemsetAsync(W, 0, eb * (size_t)cells, st));
-    FGR_CUDA_TRY(cudaMemsetAsync(flags, 0, 1, st));
+    FGR_CUDA_TRY(cudaMemsetAsync(flags, 1, 1, st));
     if (fp64) {
         Params64 P{};
         P.c = c;

@@ -170,11 +170,11 @@ __global__ void __launch_bounds__(128) coeff_scatter_kernel(
             coeff_dim32<N1>(P, q[l * m + j], p[l * m + j], a0[l], b0[l], cr[l], ci[l]);
     }
     C2 *W = reinterpret_cast<C2 *>(W_v);
-    // tensor product over dimensions, innermost dimension last
+    // tensor product over dimensions, innermost dimension last; the rows of
+    // the first grid pass (the last dimension's [a][b] plane) that receive a
+    // contribution are marked once per row, before its contributions
     auto emit = [&](int64_t idx, bool in, Real vr, Real vi) {
-        if (!in) return;
-        atomic_add_c(W + idx, vr, vi);
-        row_flag[idx / c.row_len] = 1;
+        if (in) atomic_add_c(W + idx, vr, vi);
     };
 #pragma unroll(N1 <= 8 ? N1 : 1)
     for (int k0 = 0; k0 < N1; ++k0) {
@@ -184,8 +184,10 @@ __global__ void __launch_bounds__(128) coeff_scatter_kernel(
         Real p0r, p0i;
         cmul(wr, wi, cr[0][k0], ci[0][k0], p0r, p0i);
         if constexpr (D == 1) {
-            emit(idx0, in0, p0r, p0i);
+            emit(idx0, in0, p0r, p0i);  // the single row is marked by the host
         } else {
+            const int64_t row0 = ia0 * c.ra[0] + ib0 * c.rb[0];
+            if (D == 2 && in0) row_flag[row0] = 1;
 #pragma unroll(N1 <= 8 ? N1 : 1)
             for (int k1 = 0; k1 < N1; ++k1) {
                 const int ia1 = a0[1] + c.dq[k1] - c.amin[1], ib1 = b0[1] + c.dp[k1] - c.bmin[1];
@@ -196,6 +198,7 @@ __global__ void __launch_bounds__(128) coeff_scatter_kernel(
                 if constexpr (D == 2) {
                     emit(idx1, in1, p1r, p1i);
                 } else {
+                    if (in1) row_flag[row0 + ia1 * c.ra[1] + ib1 * c.rb[1]] = 1;
 #pragma unroll
                     for (int k2 = 0; k2 < N1; ++k2) {
                         const int ia2 = a0[2] + c.dq[k2] - c.amin[2], ib2 = b0[2] + c.dp[k2] - c.bmin[2];

@@ -17,6 +17,7 @@ struct Common {
     int amin[kMaxDim], A[kMaxDim], bmin[kMaxDim], B[kMaxDim];
     int64_t sa[kMaxDim], sb[kMaxDim];  // W strides of a_l and b_l
     int64_t row_len;                   // cells per row of the first grid pass
+    int64_t ra[kMaxDim], rb[kMaxDim];  // sa / row_len, sb / row_len (dimensions before the last)
 };
 
 struct Params64 {

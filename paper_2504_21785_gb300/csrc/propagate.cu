@@ -16,10 +16,15 @@
 // RK4 integration of eq. 2.6 to the RK4 truncation error, O(dt^4).
 //
 // Trigonometry (cosine potential).  sin and cos of k Q are evaluated once per
-// step; the three later stages rotate them by the stage offset
-// d = k (Q_stage - Q), |d| <= k h (|P| + h |amp| k), with cos d and sin d from
-// their Taylor series.  When that bound exceeds 0.02 (large steps or momenta)
-// the step evaluates sincos at every stage instead.
+// step; stages 2 and 4 rotate them by the stage offset d = k (Q_stage - Q),
+// |d| <= k h (|P| + h |amp| k), with cos d and sin d from their Taylor series:
+// to d^4 / d^5 while that bound is below 2e-3 (first omitted terms below
+// 1e-19), to d^6 / d^7 below 0.02, and by sincos at every stage above it
+// (large steps or momenta).  Stage 3 sits at the same time as stage 2 and its
+// position differs from stage 2's by (h/2)^2 |V'| <= k h^2 |amp k| / 4; where
+// that is below 1e-6 for every packet (a property of h, k and amp, checked
+// once per launch), stage 3 rotates stage 2's values with cos d = 1 - d^2/2
+// and sin d = d (omitted terms below 2e-19).
 //
 // One thread integrates one packet with the whole state in registers.
 #include "internal.h"
@@ -46,6 +51,26 @@ __device__ __forceinline__ void rotate_small(double s0, double c0, double d, dou
     s = s0 * cd + c0 * sd;
     c = c0 * cd - s0 * sd;
 }
+
+// The same to d^4 and d^5 (for |d| <= 2e-3 the first omitted term is below
+// 1e-19).
+__device__ __forceinline__ void rotate_tiny(double s0, double c0, double d, double &s, double &c) {
+    const double d2 = d * d;
+    const double cd = 1.0 + d2 * (-0.5 + d2 * (1.0 / 24.0));
+    const double sd = d * (1.0 + d2 * (-1.0 / 6.0 + d2 * (1.0 / 120.0)));
+    s = s0 * cd + c0 * sd;
+    c = c0 * cd - s0 * sd;
+}
+
+// For |d| <= 1e-6: cos d = 1 - d^2/2, sin d = d (omitted terms below 2e-19).
+__device__ __forceinline__ void rotate_micro(double s0, double c0, double d, double &s, double &c) {
+    const double cd = fma(-0.5 * d, d, 1.0);
+    s = fma(c0, d, s0 * cd);
+    c = fma(-s0, d, c0 * cd);
+}
+
+// per-dimension choice of the stage trigonometry for one step
+enum Trig : unsigned char { kTiny = 0, kSmall = 1, kFull = 2 };
 
 // right-hand side; sn/cs = sin/cos(k Q_l) (cosine potential only)
 template <int D, int KIND>
@@ -109,17 +134,37 @@ __device__ __forceinline__ void accum(State<D> &acc, double w, const State<D> &k
     acc.S += w * k.S;
 }
 
+// sin/cos of k Q at a stage from their values at the step start (Q0)
 template <int D, int KIND>
-__device__ __forceinline__ void stage_trig(const Pot &v, const State<D> &y, const State<D> &tmp,
-                                           const double *s0, const double *c0, const bool *big, double *sn,
+__device__ __forceinline__ void stage_trig(const Pot &v, const double *Q0, const State<D> &tmp,
+                                           const double *s0, const double *c0, const Trig *how, double *sn,
                                            double *cs) {
     if (KIND == FGR_V_COSSUM) {
 #pragma unroll
         for (int l = 0; l < D; ++l) {
-            if (big[l])
-                sincos(v.k * tmp.Q[l], &sn[l], &cs[l]);
+            if (how[l] == kTiny)
+                rotate_tiny(s0[l], c0[l], v.k * (tmp.Q[l] - Q0[l]), sn[l], cs[l]);
+            else if (how[l] == kSmall)
+                rotate_small(s0[l], c0[l], v.k * (tmp.Q[l] - Q0[l]), sn[l], cs[l]);
             else
-                rotate_small(s0[l], c0[l], v.k * (tmp.Q[l] - y.Q[l]), sn[l], cs[l]);
+                sincos(v.k * tmp.Q[l], &sn[l], &cs[l]);
+        }
+    }
+}
+
+// stage 3 from stage 2 (same time, positions (h/2)^2 |V'| apart)
+template <int D, int KIND>
+__device__ __forceinline__ void stage3_trig(const Pot &v, bool micro, const double *Q0, const double *Q2,
+                                            const State<D> &tmp, const double *s0, const double *c0,
+                                            const Trig *how, double *sn, double *cs) {
+    if (KIND == FGR_V_COSSUM) {
+        if (micro) {
+#pragma unroll
+            for (int l = 0; l < D; ++l)
+                if (how[l] != kFull) rotate_micro(sn[l], cs[l], v.k * (tmp.Q[l] - Q2[l]), sn[l], cs[l]);
+                else sincos(v.k * tmp.Q[l], &sn[l], &cs[l]);
+        } else {
+            stage_trig<D, KIND>(v, Q0, tmp, s0, c0, how, sn, cs);
         }
     }
 }
@@ -145,30 +190,35 @@ __global__ void __launch_bounds__(128) rk4_kernel(double *__restrict__ q, double
     }
     y.S = s[j];
     const double h2 = 0.5 * h, h6 = h / 6.0;
-    double s0[D], c0[D], sn[D], cs[D];
-    bool big[D];
+    double s0[D], c0[D], sn[D], cs[D], Q0[D], Q2[D];
+    Trig how[D];
     const double kh = fabs(v.k) * h, kh_margin = kh * h * fabs(v.ampk);
+    const bool micro = 0.25 * kh_margin <= 1e-6;  // stage 3 from stage 2
     for (int64_t it = 0; it < nsteps; ++it) {
         if (KIND == FGR_V_COSSUM) {
 #pragma unroll
             for (int l = 0; l < D; ++l) {
                 sincos(v.k * y.Q[l], &s0[l], &c0[l]);
-                big[l] = fabs(y.P[l]) * kh + kh_margin > 0.02;
+                const double bound = fabs(y.P[l]) * kh + kh_margin;
+                how[l] = bound <= 2e-3 ? kTiny : (bound <= 0.02 ? kSmall : kFull);
+                Q0[l] = y.Q[l];
             }
         }
         State<D> k, tmp, acc;
         rhs<D, KIND>(v, y, s0, c0, k);
         acc = k;
         axpy<D>(tmp, y, h2, k);
-        stage_trig<D, KIND>(v, y, tmp, s0, c0, big, sn, cs);
+        stage_trig<D, KIND>(v, Q0, tmp, s0, c0, how, sn, cs);
+#pragma unroll
+        for (int l = 0; l < D; ++l) Q2[l] = tmp.Q[l];
         rhs<D, KIND>(v, tmp, sn, cs, k);
         accum<D>(acc, 2.0, k);
         axpy<D>(tmp, y, h2, k);
-        stage_trig<D, KIND>(v, y, tmp, s0, c0, big, sn, cs);
+        stage3_trig<D, KIND>(v, micro, Q0, Q2, tmp, s0, c0, how, sn, cs);
         rhs<D, KIND>(v, tmp, sn, cs, k);
         accum<D>(acc, 2.0, k);
         axpy<D>(tmp, y, h, k);
-        stage_trig<D, KIND>(v, y, tmp, s0, c0, big, sn, cs);
+        stage_trig<D, KIND>(v, Q0, tmp, s0, c0, how, sn, cs);
         rhs<D, KIND>(v, tmp, sn, cs, k);
         accum<D>(acc, 1.0, k);
         axpy<D>(y, y, h6, acc);

@@ -83,6 +83,21 @@ def test_propagate_large_steps():
     assert np.max(np.abs(A - Ar) / np.abs(Ar)) <= 1e-5
 
 
+@pytest.mark.parametrize("dt,p_max", [(4e-3, 6.0), (1e-3, 25.0)])
+def test_propagate_stage_trigonometry_paths(dt, p_max):
+    # the stage trigonometry of the cosine potential depends on k h |P|: short
+    # series (|P| small), long series, sincos per stage (|P| large), and stage 3
+    # rotated from stage 2 only while k h^2 |amp k| / 4 <= 1e-6 (dt = 1e-3 yes,
+    # 4e-3 no); every path must give the oracle's RK4 for Q, P, S
+    pk = random_packets(32, 1, 600, q_range=(-2, 2), p_range=(-p_max, p_max), s_range=(0, 0))
+    ref = tr.propagate(pk, POTS["cos"], 0.5, dt)
+    got = _gpu.propagate(pk, 1, POTS["cos"], 0.5, dt)
+    for k in ("q", "p", "s"):
+        assert np.max(np.abs(got[k] - ref[k])) <= 1e-12 * max(1.0, np.max(np.abs(ref[k])))
+    A, Ar = got["a"][0] + 1j * got["a"][1], ref["a"][0] + 1j * ref["a"][1]
+    assert np.max(np.abs(A - Ar) / np.abs(Ar)) <= 1e-7
+
+
 def test_propagate_host_buffers_and_empty():
     pk = random_packets(7, 2, 257, s_range=(0, 0))
     ref = tr.propagate(pk, POTS["cos"], 0.2, 1e-4)
