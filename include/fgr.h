@@ -141,8 +141,11 @@ fgr_status fgr_propagate(fgr_ctx *ctx, fgr_packets *inout, const fgr_potential *
 
 /* Eq. 2.10 over the box window: u(x_m) = pref * sum_j A_j exp(i/eps (S_j +
  * P_j.(x_m - Q_j)) - |x_m - Q_j|^2/(2 eps)).  FP64: every term in FP64.
- * FP32: the phase is reduced in FP64 per packet and evaluated per point in
- * FP32 turns; exp, sin and cos per packet-point pair in FP32; complex64 out. */
+ * FP32: the phase is reduced in FP64 per packet and evaluated in FP32 turns;
+ * of every 4 consecutive grid points along the last dimension the first term
+ * is evaluated with exp, sin and cos in FP32 and the next three by the exact
+ * recurrences of the Gaussian factor and the phase along that dimension (one
+ * complex multiply each); partial sums are folded into FP64; complex64 out. */
 fgr_status fgr_reconstruct_direct(fgr_ctx *ctx, const fgr_packets *pk, void *u_out,
                                   void *cuda_stream);
 

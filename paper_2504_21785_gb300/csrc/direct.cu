@@ -30,14 +30,18 @@ namespace fgr {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kTpt = 2;                        // points per thread
+constexpr int kTpt = 4;                        // consecutive points per thread (last dimension)
 constexpr int kMaxSeg = 1024;                  // segments per tile list
 
-// Output tile extent per dimension (kThreads * kTpt = 512 points per tile).
+// Output tile extent per dimension (kThreads * kTpt = 1024 points per tile);
+// the last dimension's extent is a multiple of kTpt.
 template <int D>
 __host__ __device__ constexpr int tileT(int l) {
-    return D == 1 ? 512 : (D == 2 ? (l == 0 ? 16 : 32) : 8);
+    return D == 1 ? 1024 : (D == 2 ? (l == 0 ? 16 : 64) : (l < 2 ? 8 : 16));
 }
+static_assert(tileT<1>(0) == kThreads * kTpt && tileT<2>(0) * tileT<2>(1) == kThreads * kTpt &&
+                  tileT<3>(0) * tileT<3>(1) * tileT<3>(2) == kThreads * kTpt,
+              "tiles hold kThreads * kTpt points");
 
 template <int D>
 struct __align__(16) RecF {
@@ -46,8 +50,9 @@ struct __align__(16) RecF {
     float delta[D];  // x_{mlo} - Q per dimension
     float nuhi[D];   // turns per grid step, coarse part
     float nulo[D];   // remainder
-    float tau0;      // phase at the window start, in turns, in [-0.5, 0.5)
-    float ar, ai;    // pref * A
+    float tau0;      // phase of pref * A * e^{i theta} at the window start, turns in [-0.5, 0.5)
+    float la;        // log2 |pref * A| (-inf for A = 0)
+    float spare;
 };
 
 template <int D>
@@ -183,11 +188,14 @@ __global__ void bin_scatter_kernel(const double *__restrict__ q, const double *_
             r.nuhi[l] = (float)nuhi;
             r.nulo[l] = (float)(nu - nuhi);
         }
+        // the amplitude's argument joins the phase, its modulus the Gaussian's exponent
         double tau = phase * inv_2pi_eps;
         tau -= rint(tau);
+        tau += atan2(ai, ar) * 0.15915494309189535;
+        tau -= rint(tau);
         r.tau0 = (float)tau;
-        r.ar = (float)ar;
-        r.ai = (float)ai;
+        r.la = (float)log2(hypot(ar, ai));
+        r.spare = 0.f;
         reinterpret_cast<RecF<D> *>(recs)[pos] = r;
     }
 }
@@ -196,6 +204,8 @@ struct DirectParams {
     GridDev g;
     float hf[3];         // grid steps (FP32 path)
     float ce;            // -log2(e) / (2 eps)
+    float ce_h;          // ce * h of the last dimension
+    float q_last;        // e^{-h^2 / eps} of the last dimension (Gaussian ratio step)
     double inv_eps;      // FP64 path
     double neg_half_inv_eps;
     int splits;
@@ -263,32 +273,37 @@ __device__ __forceinline__ void direct_tile(const void *__restrict__ recs_v, con
     const int nseg = nseg_s;
     const int64_t L = seg_cum[nseg];
 
-    // this thread's points
+    // this thread's points: kTpt consecutive points along the last dimension
+    constexpr int kLane = tileT<D>(D - 1) / kTpt;  // threads along the last dimension
     int mi[kTpt][D];
     bool valid[kTpt];
     int64_t lin_out[kTpt];
+    {
+        int base[D];
+        int i = threadIdx.x / kLane;
+        base[D - 1] = t[D - 1] * tileT<D>(D - 1) + (threadIdx.x % kLane) * kTpt;
 #pragma unroll
-    for (int r = 0; r < kTpt; ++r) {
-        int i = threadIdx.x + r * kThreads;
-        bool ok = true;
-        int64_t lin = 0;
-#pragma unroll
-        for (int l = D - 1; l >= 0; --l) {
-            const int il = i % tileT<D>(l);
+        for (int l = D - 2; l >= 0; --l) {
+            base[l] = t[l] * tileT<D>(l) + i % tileT<D>(l);
             i /= tileT<D>(l);
-            mi[r][l] = t[l] * tileT<D>(l) + il;
-            ok = ok && mi[r][l] < g.n[l];
         }
 #pragma unroll
-        for (int l = 0; l < D; ++l) lin = lin * g.n[l] + mi[r][l];
-        valid[r] = ok;
-        lin_out[r] = lin;
+        for (int r = 0; r < kTpt; ++r) {
+            bool ok = true;
+            int64_t lin = 0;
+#pragma unroll
+            for (int l = 0; l < D; ++l) {
+                mi[r][l] = base[l] + (l == D - 1 ? r : 0);
+                ok = ok && mi[r][l] < g.n[l];
+                lin = lin * g.n[l] + mi[r][l];
+            }
+            valid[r] = ok;
+            lin_out[r] = lin;
+        }
     }
-    float mf[kTpt][D];
+    float mf[D];  // first point (FP32 path)
 #pragma unroll
-    for (int r = 0; r < kTpt; ++r)
-#pragma unroll
-        for (int l = 0; l < D; ++l) mf[r][l] = (float)mi[r][l];
+    for (int l = 0; l < D; ++l) mf[l] = (float)mi[0][l];
     double xd[kTpt][D];
     if (FP64) {
 #pragma unroll
@@ -296,6 +311,7 @@ __device__ __forceinline__ void direct_tile(const void *__restrict__ recs_v, con
 #pragma unroll
             for (int l = 0; l < D; ++l) xd[r][l] = grid_x(g.lo[l], g.h[l], mi[r][l]);
     }
+    __shared__ float2 srot[kThreads];  // FP32: e^{2 pi i nu} of the last dimension per staged record
 
     float accf[kTpt][2];
     double accd[kTpt][2];
@@ -322,16 +338,22 @@ __device__ __forceinline__ void direct_tile(const void *__restrict__ recs_v, con
             for (int w = 0; w < kWords; w += 4)
                 *reinterpret_cast<int4 *>(&srec[threadIdx.x * kWords + w]) =
                     *reinterpret_cast<const int4 *>(src + w);
+            if (!FP64) {  // the rotation by one grid step along the last dimension
+                const RecF<D> &mine = *reinterpret_cast<const RecF<D> *>(&srec[threadIdx.x * kWords]);
+                float sn, cs;
+                sincospif(2.f * (mine.nuhi[D - 1] + mine.nulo[D - 1]), &sn, &cs);
+                srot[threadIdx.x] = make_float2(cs, sn);
+            }
         }
         __syncthreads();
         const int64_t left = L - c * kThreads;
         const int nrec = left < kThreads ? (int)left : kThreads;
         for (int jr = 0; jr < nrec; ++jr) {
             const Rec &R = *reinterpret_cast<const Rec *>(&srec[jr * kWords]);
+            if (FP64) {
+                const RecD<D> &Rd = reinterpret_cast<const RecD<D> &>(R);
 #pragma unroll
-            for (int r = 0; r < kTpt; ++r) {
-                if (FP64) {
-                    const RecD<D> &Rd = reinterpret_cast<const RecD<D> &>(R);
+                for (int r = 0; r < kTpt; ++r) {
                     bool in = valid[r];
 #pragma unroll
                     for (int l = 0; l < D; ++l) {
@@ -352,33 +374,57 @@ __device__ __forceinline__ void direct_tile(const void *__restrict__ recs_v, con
                     const double gr = ga * cs, gi = ga * sn;
                     accd[r][0] += Rd.ar * gr - Rd.ai * gi;
                     accd[r][1] += Rd.ar * gi + Rd.ai * gr;
-                } else {
-                    const RecF<D> &Rf = reinterpret_cast<const RecF<D> &>(R);
-                    float kk[D];
-                    bool in = valid[r];
+                }
+            } else {
+                // the first point evaluated in full, the next kTpt - 1 along
+                // the last dimension by the exact recurrences of the Gaussian
+                // (ratio rho, itself multiplied by e^{-h^2/eps} per step) and of
+                // the phase (rotation by e^{2 pi i nu})
+                const RecF<D> &Rf = reinterpret_cast<const RecF<D> &>(R);
+                float kk[D];
+                bool in = true;
 #pragma unroll
-                    for (int l = 0; l < D; ++l) {
-                        kk[l] = mf[r][l] - Rf.mlo[l];
-                        in = in && kk[l] >= 0.f && kk[l] < Rf.wlen[l];
-                    }
-                    if (!in) continue;
-                    float e = 0.f, tau = Rf.tau0;
+                for (int l = 0; l < D - 1; ++l) {
+                    kk[l] = mf[l] - Rf.mlo[l];
+                    in = in && kk[l] >= 0.f && kk[l] < Rf.wlen[l];
+                }
+                kk[D - 1] = mf[D - 1] - Rf.mlo[D - 1];
+                const float wl = Rf.wlen[D - 1];
+                in = in && kk[D - 1] > -(float)kTpt && kk[D - 1] < wl;
+                if (!in) continue;
+                float e = 0.f, tau = Rf.tau0, dxl = 0.f;
 #pragma unroll
-                    for (int l = 0; l < D; ++l) {
-                        const float kf = kk[l];
-                        const float dx = fmaf(kf, P.hf[l], Rf.delta[l]);
-                        e = fmaf(dx, dx, e);
-                        float f = kf * Rf.nuhi[l];
-                        f -= rint_fast(f);
-                        tau += fmaf(kf, Rf.nulo[l], f);
+                for (int l = 0; l < D; ++l) {
+                    const float kf = kk[l];
+                    const float dx = fmaf(kf, P.hf[l], Rf.delta[l]);
+                    e = fmaf(dx, dx, e);
+                    float f = kf * Rf.nuhi[l];
+                    f -= rint_fast(f);
+                    tau += fmaf(kf, Rf.nulo[l], f);
+                    dxl = dx;
+                }
+                tau -= rint_fast(tau);
+                float sn, cs;
+                __sincosf(6.283185307179586f * tau, &sn, &cs);
+                const float ga = ex2_approx(fmaf(e, P.ce, Rf.la));
+                float vr = ga * cs, vi = ga * sn;
+                const float rho = ex2_approx(P.ce_h * fmaf(2.f, dxl, P.hf[D - 1]));
+                const float2 rot = srot[jr];
+                float wr = rho * rot.x, wi = rho * rot.y;
+#pragma unroll
+                for (int r = 0; r < kTpt; ++r) {
+                    const float k = kk[D - 1] + (float)r;
+                    if (k >= 0.f && k < wl) {
+                        accf[r][0] += vr;
+                        accf[r][1] += vi;
                     }
-                    tau -= rint_fast(tau);
-                    float sn, cs;
-                    __sincosf(6.283185307179586f * tau, &sn, &cs);
-                    const float ga = ex2_approx(e * P.ce);
-                    const float gr = ga * cs, gi = ga * sn;
-                    accf[r][0] = fmaf(Rf.ar, gr, fmaf(-Rf.ai, gi, accf[r][0]));
-                    accf[r][1] = fmaf(Rf.ar, gi, fmaf(Rf.ai, gr, accf[r][1]));
+                    if (r + 1 < kTpt) {
+                        const float nr = vr * wr - vi * wi;
+                        vi = vr * wi + vi * wr;
+                        vr = nr;
+                        wr *= P.q_last;
+                        wi *= P.q_last;
+                    }
                 }
             }
         }
@@ -527,6 +573,8 @@ fgr_status prepare(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t
     P.g = g;
     for (int l = 0; l < D; ++l) P.hf[l] = (float)g.h[l];
     P.ce = (float)(-1.4426950408889634 / (2.0 * M.eps));
+    P.ce_h = (float)(-1.4426950408889634 / (2.0 * M.eps) * g.h[D - 1]);
+    P.q_last = (float)std::exp(-g.h[D - 1] * g.h[D - 1] / M.eps);
     P.inv_eps = 1.0 / M.eps;
     P.neg_half_inv_eps = -0.5 / M.eps;
     const int target = ctx->num_sms * ctx->tune.direct_ctas_per_sm;

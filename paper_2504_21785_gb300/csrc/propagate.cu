@@ -24,7 +24,11 @@
 // position differs from stage 2's by (h/2)^2 |V'| <= k h^2 |amp k| / 4; where
 // that is below 1e-6 for every packet (a property of h, k and amp, checked
 // once per launch), stage 3 rotates stage 2's values with cos d = 1 - d^2/2
-// and sin d = d (omitted terms below 2e-19).
+// and sin d = d (omitted terms below 2e-19).  Under the same kind of bound,
+// k h^2 |amp k| <= 1e-6, the next step's sin and cos come from stage 4's the
+// same way (Q(t+h) - Q_stage4 = h (P1 + 2 P2 + 2 P3 + P4)/6 - h P3, at most
+// h^2 |amp k| in size), and sincos is evaluated afresh every 32nd step so that
+// the rounding of the chained rotations stays below 1e-14.
 //
 // One thread integrates one packet with the whole state in registers.
 #include "internal.h"
@@ -190,15 +194,20 @@ __global__ void __launch_bounds__(128) rk4_kernel(double *__restrict__ q, double
     }
     y.S = s[j];
     const double h2 = 0.5 * h, h6 = h / 6.0;
-    double s0[D], c0[D], sn[D], cs[D], Q0[D], Q2[D];
+    double s0[D], c0[D], sn[D], cs[D], Q0[D], Q2[D], Q4[D];
     Trig how[D];
     const double kh = fabs(v.k) * h, kh_margin = kh * h * fabs(v.ampk);
     const bool micro = 0.25 * kh_margin <= 1e-6;  // stage 3 from stage 2
+    const bool carry = kh_margin <= 1e-6;         // next step from stage 4
     for (int64_t it = 0; it < nsteps; ++it) {
         if (KIND == FGR_V_COSSUM) {
+            const bool fresh = !carry || (it & 31) == 0;
 #pragma unroll
             for (int l = 0; l < D; ++l) {
-                sincos(v.k * y.Q[l], &s0[l], &c0[l]);
+                if (fresh)
+                    sincos(v.k * y.Q[l], &s0[l], &c0[l]);
+                else
+                    rotate_micro(sn[l], cs[l], v.k * (y.Q[l] - Q4[l]), s0[l], c0[l]);
                 const double bound = fabs(y.P[l]) * kh + kh_margin;
                 how[l] = bound <= 2e-3 ? kTiny : (bound <= 0.02 ? kSmall : kFull);
                 Q0[l] = y.Q[l];
@@ -219,6 +228,8 @@ __global__ void __launch_bounds__(128) rk4_kernel(double *__restrict__ q, double
         accum<D>(acc, 2.0, k);
         axpy<D>(tmp, y, h, k);
         stage_trig<D, KIND>(v, Q0, tmp, s0, c0, how, sn, cs);
+#pragma unroll
+        for (int l = 0; l < D; ++l) Q4[l] = tmp.Q[l];
         rhs<D, KIND>(v, tmp, sn, cs, k);
         accum<D>(acc, 1.0, k);
         axpy<D>(y, y, h6, acc);

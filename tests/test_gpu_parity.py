@@ -83,12 +83,14 @@ def test_propagate_large_steps():
     assert np.max(np.abs(A - Ar) / np.abs(Ar)) <= 1e-5
 
 
-@pytest.mark.parametrize("dt,p_max", [(4e-3, 6.0), (1e-3, 25.0)])
+@pytest.mark.parametrize("dt,p_max", [(4e-3, 6.0), (1e-3, 25.0), (5e-4, 50.0)])
 def test_propagate_stage_trigonometry_paths(dt, p_max):
     # the stage trigonometry of the cosine potential depends on k h |P|: short
-    # series (|P| small), long series, sincos per stage (|P| large), and stage 3
-    # rotated from stage 2 only while k h^2 |amp k| / 4 <= 1e-6 (dt = 1e-3 yes,
-    # 4e-3 no); every path must give the oracle's RK4 for Q, P, S
+    # series (|P| small), long series, sincos per stage (|P| large); stage 3
+    # is rotated from stage 2 while k h^2 |amp k| / 4 <= 1e-6 (dt = 1e-3 and
+    # 5e-4 yes, 4e-3 no) and the next step from stage 4 while k h^2 |amp k|
+    # <= 1e-6 (5e-4 yes, 4e-3 no); every path must give the oracle's RK4 for
+    # Q, P, S
     pk = random_packets(32, 1, 600, q_range=(-2, 2), p_range=(-p_max, p_max), s_range=(0, 0))
     ref = tr.propagate(pk, POTS["cos"], 0.5, dt)
     got = _gpu.propagate(pk, 1, POTS["cos"], 0.5, dt)
