@@ -124,10 +124,12 @@ struct PassParams {
     double dp_over_eps;
 };
 
-constexpr int kPassThreads = 64;
+constexpr int kPassThreads = 128;
 constexpr int kCB = 32;
 
-constexpr int kPassPts = 2;                         // grid points per thread
+// one grid point per thread keeps the Gaussian factors of the band (MAXBAND
+// registers) small enough for several CTAs per SM
+constexpr int kPassPts = 1;                         // grid points per thread
 constexpr int kPassTile = kPassThreads * kPassPts;  // grid points per CTA
 
 template <bool FP64, int MAXBAND>

@@ -128,15 +128,43 @@ __device__ __forceinline__ void coeff_dim32(const Params32 &P, double Q, double 
     }
 }
 
+// The last dimension's N1 contributions of one row of outer neighbours,
+// scaled by (pr, pi): cell idx + (a0 + dq_k - amin) sa + (b0 + dp_k - bmin) sb.
+template <int L, int N1, class Real, class C2>
+__device__ __forceinline__ void emit_row(C2 *__restrict__ W, const Common &c, int a0, int b0, const Real *cl_r,
+                                         const Real *cl_i, int64_t idx, Real pr, Real pi) {
+#pragma unroll
+    for (int k = 0; k < N1; ++k) {
+        const int ia = a0 + c.dq[k] - c.amin[L], ib = b0 + c.dp[k] - c.bmin[L];
+        if ((unsigned)ia < (unsigned)c.A[L] && (unsigned)ib < (unsigned)c.B[L]) {
+            Real vr, vi;
+            cmul(pr, pi, cl_r[k], cl_i[k], vr, vi);
+            atomic_add_c(W + idx + ia * c.sa[L] + ib * c.sb[L], vr, vi);
+        }
+    }
+}
+
+// Threads per CTA of the scatter kernel: the coefficients of all dimensions
+// but the last wait in shared memory ([dim][neighbour][thread], at most 32 KB).
+template <bool FP64, int N1>
+__host__ __device__ constexpr int coeff_threads() {
+    return (FP64 && N1 == 16) ? 64 : 128;
+}
+
+template <bool FP64>
+using ParamsT = typename std::conditional<FP64, Params64, Params32>::type;
+
 template <int D, bool FP64, int N1>
-__global__ void __launch_bounds__(128) coeff_scatter_kernel(
-    const double *__restrict__ q, const double *__restrict__ p, const double *__restrict__ s,
-    const double *__restrict__ a, int64_t m,
-    const __grid_constant__ typename std::conditional<FP64, Params64, Params32>::type P,
-    void *__restrict__ W_v, uint8_t *__restrict__ row_flag) {
+__device__ __forceinline__ void coeff_scatter_body(const double *__restrict__ q, const double *__restrict__ p,
+                                                   const double *__restrict__ s, const double *__restrict__ a,
+                                                   int64_t m, const ParamsT<FP64> &P, void *__restrict__ W_v,
+                                                   uint8_t *__restrict__ row_flag) {
     using Real = typename std::conditional<FP64, double, float>::type;
     using C2 = typename std::conditional<FP64, double2, float2>::type;
-    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    constexpr int kT = coeff_threads<FP64, N1>();
+    __shared__ C2 scoef[D > 1 ? D - 1 : 1][N1][kT];
+    const int tid = threadIdx.x;
+    const int64_t j = blockIdx.x * (int64_t)kT + tid;
     if (j >= m) return;
     const Common &c = P.c;
     const double ar = a[j], ai = a[m + j];
@@ -160,69 +188,113 @@ __global__ void __launch_bounds__(128) coeff_scatter_kernel(
         wr = (Real)xr;
         wi = (Real)xi;
     }
-    Real cr[D][N1], ci[D][N1];
+    // per-dimension coefficients: the last dimension's stay in registers, the
+    // others go to this thread's column of shared memory (read back only by
+    // this thread, so no barrier is needed)
+    Real cl_r[N1], cl_i[N1];
     int a0[D], b0[D];
-#pragma unroll
+    // one dimension at a time (for d = 3 not unrolled: three unrolled copies
+    // of the coefficient evaluation do not fit the register file)
+#pragma unroll(D == 3 ? 1 : D)
     for (int l = 0; l < D; ++l) {
+        Real cr[N1], ci[N1];
         if constexpr (FP64)
-            coeff_dim64<N1>(P, q[l * m + j], p[l * m + j], a0[l], b0[l], cr[l], ci[l]);
+            coeff_dim64<N1>(P, q[l * m + j], p[l * m + j], a0[l], b0[l], cr, ci);
         else
-            coeff_dim32<N1>(P, q[l * m + j], p[l * m + j], a0[l], b0[l], cr[l], ci[l]);
+            coeff_dim32<N1>(P, q[l * m + j], p[l * m + j], a0[l], b0[l], cr, ci);
+        if (l < D - 1) {
+#pragma unroll
+            for (int k = 0; k < N1; ++k) {
+                C2 v;
+                v.x = cr[k];
+                v.y = ci[k];
+                scoef[l][k][tid] = v;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < N1; ++k) {
+                cl_r[k] = cr[k];
+                cl_i[k] = ci[k];
+            }
+        }
     }
     C2 *W = reinterpret_cast<C2 *>(W_v);
     // tensor product over dimensions, innermost dimension last; the rows of
     // the first grid pass (the last dimension's [a][b] plane) that receive a
-    // contribution are marked once per row, before its contributions
-    auto emit = [&](int64_t idx, bool in, Real vr, Real vi) {
-        if (in) atomic_add_c(W + idx, vr, vi);
-    };
-#pragma unroll(N1 <= 8 ? N1 : 1)
-    for (int k0 = 0; k0 < N1; ++k0) {
-        const int ia0 = a0[0] + c.dq[k0] - c.amin[0], ib0 = b0[0] + c.dp[k0] - c.bmin[0];
-        const bool in0 = (unsigned)ia0 < (unsigned)c.A[0] && (unsigned)ib0 < (unsigned)c.B[0];
-        const int64_t idx0 = ia0 * c.sa[0] + ib0 * c.sb[0];
-        Real p0r, p0i;
-        cmul(wr, wi, cr[0][k0], ci[0][k0], p0r, p0i);
-        if constexpr (D == 1) {
-            emit(idx0, in0, p0r, p0i);  // the single row is marked by the host
-        } else {
+    // contribution are marked once per row (the single row of d = 1 is marked
+    // by the host)
+    if constexpr (D == 1) {
+        emit_row<D - 1, N1>(W, c, a0[D - 1], b0[D - 1], cl_r, cl_i, 0, wr, wi);
+    } else {
+#pragma unroll 1
+        for (int k0 = 0; k0 < N1; ++k0) {
+            const int ia0 = a0[0] + c.dq[k0] - c.amin[0], ib0 = b0[0] + c.dp[k0] - c.bmin[0];
+            const bool in0 = (unsigned)ia0 < (unsigned)c.A[0] && (unsigned)ib0 < (unsigned)c.B[0];
+            if (!in0) continue;
+            const int64_t idx0 = ia0 * c.sa[0] + ib0 * c.sb[0];
             const int64_t row0 = ia0 * c.ra[0] + ib0 * c.rb[0];
-            if (D == 2 && in0) row_flag[row0] = 1;
-#pragma unroll(N1 <= 8 ? N1 : 1)
-            for (int k1 = 0; k1 < N1; ++k1) {
-                const int ia1 = a0[1] + c.dq[k1] - c.amin[1], ib1 = b0[1] + c.dp[k1] - c.bmin[1];
-                const bool in1 = in0 && (unsigned)ia1 < (unsigned)c.A[1] && (unsigned)ib1 < (unsigned)c.B[1];
-                const int64_t idx1 = idx0 + ia1 * c.sa[1] + ib1 * c.sb[1];
-                Real p1r, p1i;
-                cmul(p0r, p0i, cr[1][k1], ci[1][k1], p1r, p1i);
-                if constexpr (D == 2) {
-                    emit(idx1, in1, p1r, p1i);
-                } else {
-                    if (in1) row_flag[row0 + ia1 * c.ra[1] + ib1 * c.rb[1]] = 1;
-#pragma unroll
-                    for (int k2 = 0; k2 < N1; ++k2) {
-                        const int ia2 = a0[2] + c.dq[k2] - c.amin[2], ib2 = b0[2] + c.dp[k2] - c.bmin[2];
-                        const bool in2 = in1 && (unsigned)ia2 < (unsigned)c.A[2] && (unsigned)ib2 < (unsigned)c.B[2];
-                        Real p2r, p2i;
-                        cmul(p1r, p1i, cr[2][k2], ci[2][k2], p2r, p2i);
-                        emit(idx1 + ia2 * c.sa[2] + ib2 * c.sb[2], in2, p2r, p2i);
-                    }
+            const C2 c0 = scoef[0][k0][tid];
+            Real p0r, p0i;
+            cmul(wr, wi, c0.x, c0.y, p0r, p0i);
+            if constexpr (D == 2) {
+                row_flag[row0] = 1;
+                emit_row<D - 1, N1>(W, c, a0[D - 1], b0[D - 1], cl_r, cl_i, idx0, p0r, p0i);
+            } else {
+#pragma unroll 1
+                for (int k1 = 0; k1 < N1; ++k1) {
+                    const int ia1 = a0[1] + c.dq[k1] - c.amin[1], ib1 = b0[1] + c.dp[k1] - c.bmin[1];
+                    if ((unsigned)ia1 >= (unsigned)c.A[1] || (unsigned)ib1 >= (unsigned)c.B[1]) continue;
+                    const C2 c1 = scoef[1][k1][tid];
+                    Real p1r, p1i;
+                    cmul(p0r, p0i, c1.x, c1.y, p1r, p1i);
+                    row_flag[row0 + ia1 * c.ra[1] + ib1 * c.rb[1]] = 1;
+                    emit_row<D - 1, N1>(W, c, a0[D - 1], b0[D - 1], cl_r, cl_i, idx0 + ia1 * c.sa[1] + ib1 * c.sb[1],
+                                        p1r, p1i);
                 }
             }
         }
     }
 }
 
+// d = 1, 2: the compiler's own register budget; d = 3: at most 128
+// registers (4 CTAs per SM), which the three-dimensional emit loops need
+template <int D, bool FP64, int N1>
+__global__ void __launch_bounds__(coeff_threads<FP64, N1>()) coeff_scatter_kernel(
+    const double *__restrict__ q, const double *__restrict__ p, const double *__restrict__ s,
+    const double *__restrict__ a, int64_t m, const __grid_constant__ ParamsT<FP64> P, void *__restrict__ W_v,
+    uint8_t *__restrict__ row_flag) {
+    coeff_scatter_body<D, FP64, N1>(q, p, s, a, m, P, W_v, row_flag);
+}
+
+template <int D, bool FP64, int N1>
+__global__ void __launch_bounds__(coeff_threads<FP64, N1>(), 4) coeff_scatter3_kernel(
+    const double *__restrict__ q, const double *__restrict__ p, const double *__restrict__ s,
+    const double *__restrict__ a, int64_t m, const __grid_constant__ ParamsT<FP64> P, void *__restrict__ W_v,
+    uint8_t *__restrict__ row_flag) {
+    coeff_scatter_body<D, FP64, N1>(q, p, s, a, m, P, W_v, row_flag);
+}
+
+template <int D, bool FP64, int N1>
+void launch_coeff_kernel(unsigned blocks, cudaStream_t st, const PacketsDev &pk, const ParamsT<FP64> &P, void *W,
+                         uint8_t *flags) {
+    constexpr int T = coeff_threads<FP64, N1>();
+    if constexpr (D == 3)
+        coeff_scatter3_kernel<D, FP64, N1><<<blocks, T, 0, st>>>(pk.q, pk.p, pk.s, pk.a, pk.m, P, W, flags);
+    else
+        coeff_scatter_kernel<D, FP64, N1><<<blocks, T, 0, st>>>(pk.q, pk.p, pk.s, pk.a, pk.m, P, W, flags);
+}
+
 template <int D>
 fgr_status launch_coeff_d(int n1, cudaStream_t st, const PacketsDev &pk, const Params64 *p64, const Params32 *p32,
                           void *W, uint8_t *flags) {
-    const unsigned blocks = (unsigned)((pk.m + 127) / 128);
     if (pk.m == 0) return FGR_OK;
 #define FGR_COEFF(N)                                                                                        \
     if (p64)                                                                                                \
-        coeff_scatter_kernel<D, true, N><<<blocks, 128, 0, st>>>(pk.q, pk.p, pk.s, pk.a, pk.m, *p64, W, flags); \
+        launch_coeff_kernel<D, true, N>((unsigned)((pk.m + coeff_threads<true, N>() - 1) /                  \
+                                                   coeff_threads<true, N>()), st, pk, *p64, W, flags);      \
     else                                                                                                    \
-        coeff_scatter_kernel<D, false, N><<<blocks, 128, 0, st>>>(pk.q, pk.p, pk.s, pk.a, pk.m, *p32, W, flags);
+        launch_coeff_kernel<D, false, N>((unsigned)((pk.m + coeff_threads<false, N>() - 1) /                \
+                                                    coeff_threads<false, N>()), st, pk, *p32, W, flags);
     switch (n1) {
     case 4: FGR_COEFF(4); break;
     case 8: FGR_COEFF(8); break;
