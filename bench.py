@@ -272,7 +272,8 @@ def run_ours(args):
                        "t": t_final, "dt": dt, "strategy": "Q4P2 cq=1/2 cp=pi/8",
                        "step": "propagate (A1) + fggc reconstruct (A3-A5)",
                        "l2": "flushed (512 MiB write) between timed steps", "parallelism": "replicas",
-                       "autotuned_ctas_per_sm": {"direct": tuning[0], "grid_pass": tuning[1]}},
+                       "autotuned": {"direct_ctas_per_sm": tuning[0], "grid_pass_ctas_per_sm": tuning[1],
+                                     "grid_pass_tile": tuning[2]}},
             "stages": {
                 "propagate_ms": ms_prop,
                 "fggc_reconstruct_ms": ms_fggc,
@@ -413,13 +414,15 @@ def reconstruct_bench(cfg: int, args, flush):
             "runs": spread, "fggc_q2p2_ms": res["fggc_q2p2"], "rel_l2_fggc_q2p2_vs_direct": rel_q2,
             "fggc_q2p2_over_direct": (res["direct"] / res["fggc_q2p2"] if rel_q2 <= 1e-5
                                       else "not at equal accuracy (rel L2 > 1e-5)"),
-            "fggc_nodes": int(st.nodes), "autotuned_ctas_per_sm": tuned,
+            "fggc_nodes": int(st.nodes), "autotuned_ctas_per_sm_and_tile": tuned,
             "fggc_stage_split_ms": {"bounds_alloc": st.prep_ms, "coeff_scatter": st.scatter_ms, "grid": st.grid_ms}}
 
 
 def batch_bench(args, flush):
-    """Many small direct-sum requests: one fgr_reconstruct_direct call each on
-    one stream, against one fgr_reconstruct_direct_batch call, eager and replayed
+    """Many small reconstructions: direct sums as one fgr_reconstruct_direct call
+    each on one stream, against one fgr_reconstruct_direct_batch call, eager and
+    replayed from a CUDA graph; FGGC as one fgr_reconstruct_fggc call each
+    against planned calls (fgr_reconstruct_fggc_planned), eager and replayed
     from a CUDA graph.  64 1-D requests, grids 1024..8192 points, 2k..16k
     uniformly placed packets, eps in [1/1024, 1/256], FP32; L2 flushed before
     each timed run."""
@@ -489,12 +492,47 @@ def batch_bench(args, flush):
         t_single = timed(single)
         t_batch = timed(batched)
         t_graph = timed(g.replay)
+
+    # the same requests by FGGC: one fgr_reconstruct_fggc each (each waits for
+    # its node bounds) against planned calls, eager and replayed from a graph
+    plans = [fgr.fgr_fggc_plan_create(c.handle, p, 2) for c, p in zip(ctxs, pks)]
+
+    def fggc_single():
+        for c, p, u in zip(ctxs, pks, outs):
+            fgr.fgr_reconstruct_fggc(c.handle, p, u, s)
+
+    def fggc_planned():
+        for c, pl, p, u in zip(ctxs, plans, pks, outs):
+            fgr.fgr_reconstruct_fggc_planned(c.handle, pl, p, u, s)
+
+    fggc_single()
+    torch.cuda.synchronize()
+    ref_f = [u.clone() for u in outs]
+    fggc_planned()
+    torch.cuda.synchronize()
+    worst_f = max(float(torch.linalg.norm(a - b) / max(float(torch.linalg.norm(b)), 1e-30))
+                  for a, b in zip(outs, ref_f))
+    gf = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        gf.capture_begin()
+        fggc_planned()
+        gf.capture_end()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        tf_single = timed(fggc_single)
+        tf_planned = timed(fggc_planned)
+        tf_graph = timed(gf.replay)
+    for pl in plans:
+        fgr.fgr_fggc_plan_destroy(pl)
     for c in ctxs:
         c.close()
     return {"requests": len(outs), "packets": packets, "single_calls_ms": t_single, "batch_ms": t_batch,
             "graph_replay_ms": t_graph, "requests_per_s_graph": len(outs) / (t_graph * 1e-3),
             "speedup_batch_vs_single": t_single / t_batch, "speedup_graph_vs_single": t_single / t_graph,
             "max_rel_l2_batch_vs_single": worst,
+            "fggc_single_calls_ms": tf_single, "fggc_planned_ms": tf_planned, "fggc_graph_replay_ms": tf_graph,
+            "fggc_requests_per_s_graph": len(outs) / (tf_graph * 1e-3),
+            "max_rel_l2_fggc_planned_vs_single": worst_f,
             "mix": "64 x 1-D, grids 1024..8192, 2k..16k packets, eps 1/1024..1/256, fp32"}
 
 

@@ -201,19 +201,56 @@ fgr_status fgr_reconstruct_fggc(fgr_ctx *ctx, const fgr_packets *pk, void *u_out
 fgr_status fgr_reconstruct_fggc_noalloc(fgr_ctx *ctx, const fgr_packets *pk, void *u_out,
                                         void *cuda_stream);
 
+/* FGGC plans (not in the paper: a serving and graph-capture aid).  A plan
+ * fixes, for one context and one packet set, the node box of the FGGC
+ * reconstruction (the packets' node ranges widened by margin nodes on every
+ * side) and owns its working memory (device memory allocated here, freed by
+ * fgr_fggc_plan_destroy).  fgr_fggc_plan_create waits for the packets' node
+ * bounds, like fgr_reconstruct_fggc; packets may be host or device memory.
+ * FGR_E_INVALID for margin outside 0..4096; FGR_E_NOMEM / FGR_E_CAPACITY when
+ * the box cannot be allocated. */
+typedef struct fgr_fggc_plan fgr_fggc_plan;
+fgr_status fgr_fggc_plan_create(fgr_ctx *ctx, const fgr_packets *pk, int32_t margin, fgr_fggc_plan **out,
+                                void *cuda_stream);
+/* FGGC reconstruction through a plan: the same arithmetic as
+ * fgr_reconstruct_fggc on the plan's box, with only stream-ordered work (no
+ * allocation, no host wait: it can be captured into a CUDA graph and replayed
+ * with new packet values in the same buffers).  Packets (device memory) may
+ * differ from the plan's; their node bounds are recomputed on the device, and
+ * if they leave the box the plan's overflow flag is set (contributions
+ * outside the box are then missing from u_out; re-plan).  Calls that share a
+ * plan share its memory and must not overlap on the device.  FGR_E_INVALID if
+ * the plan belongs to another dimension, precision, grid, eps or neighbour
+ * set, or if packets or u_out are not device memory. */
+fgr_status fgr_reconstruct_fggc_planned(fgr_ctx *ctx, fgr_fggc_plan *plan, const fgr_packets *pk, void *u_out,
+                                        void *cuda_stream);
+/* 1 if the packets of the plan's last completed call left its box (waits for
+ * the device). */
+fgr_status fgr_fggc_plan_overflow(fgr_fggc_plan *plan, int32_t *overflowed);
+/* Node cells of the plan's box; empty = 1 if no packet reached the grid. */
+fgr_status fgr_fggc_plan_info(const fgr_fggc_plan *plan, int64_t *nodes, int32_t *empty);
+void fgr_fggc_plan_destroy(fgr_fggc_plan *plan);
+
 /* Autotuner of the launch shapes (not in the paper: it serves the batching and
- * serving side of the library).  Times, with CUDA events on the given
- * stream, the candidate CTA-per-SM targets of the direct sum (methods & 1:
- * 2, 4, 8, 16, 32) and of the FGGC grid passes (methods & 2: 4, 8, 16, 32, 64)
- * on these packets and this context's grid (u_out receives the last result),
- * keeps the fastest in the context and in a process-wide table keyed by
- * (d, precision, packets and grid points rounded to powers of two) that seeds
- * later contexts; with FGR_TUNE_FILE set, the table is loaded from and appended
- * to that file.  Waits for its own timing runs. */
+ * serving side of the library).  Times, with CUDA events on the given stream,
+ * the candidate CTA-per-SM targets of the direct sum (methods & 1: 2, 4, 8, 16,
+ * 32) and, for the FGGC grid passes (methods & 2), the tile width (128 or 32
+ * grid points per CTA) with each CTA-per-SM target (4, 8, 16, 32, 64) on these
+ * packets and this context's grid (u_out receives the last result), keeps the
+ * fastest in the context and in a process-wide table keyed by (d, precision,
+ * packets and grid points rounded to powers of two) that seeds later contexts;
+ * with FGR_TUNE_FILE set, the table is loaded from and appended to that file.
+ * Waits for its own timing runs. */
 fgr_status fgr_autotune(fgr_ctx *ctx, const fgr_packets *pk, void *u_out, int32_t methods,
                         void *cuda_stream);
-fgr_status fgr_get_tuning(const fgr_ctx *ctx, int32_t *direct_ctas_per_sm, int32_t *pass_ctas_per_sm);
-fgr_status fgr_set_tuning(fgr_ctx *ctx, int32_t direct_ctas_per_sm, int32_t pass_ctas_per_sm);
+/* The context's launch shapes: CTA-per-SM targets (1..256) of the direct sum
+ * and of the grid passes, and the grid-pass tile (32 or 128 grid points per
+ * CTA; 0 = chosen from the node band width, the default).  FGR_E_INVALID for
+ * values outside those ranges. */
+fgr_status fgr_get_tuning(const fgr_ctx *ctx, int32_t *direct_ctas_per_sm, int32_t *pass_ctas_per_sm,
+                          int32_t *pass_tile);
+fgr_status fgr_set_tuning(fgr_ctx *ctx, int32_t direct_ctas_per_sm, int32_t pass_ctas_per_sm,
+                          int32_t pass_tile);
 
 /* Read-only facts about a context. */
 typedef struct {

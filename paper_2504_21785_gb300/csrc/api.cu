@@ -12,6 +12,7 @@
 #include <tuple>
 #include <vector>
 
+#include "fggc_params.h"
 #include "internal.h"
 
 namespace fgr {
@@ -579,6 +580,170 @@ fgr_status fgr_reconstruct_direct_batch(int32_t n, fgr_ctx *const *ctxs, const f
 
 fgr_status fgr_reconstruct_fggc(fgr_ctx *ctx, const fgr_packets *pk, void *u_out, void *stream) {
     return reconstruct(ctx, pk, u_out, stream, true);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// FGGC plans: the node box and the working memory of one (context, packet
+// set) fixed once, so that later reconstructions wait for nothing on the host
+// and can be captured into a CUDA graph.
+// ---------------------------------------------------------------------------
+struct fgr_fggc_plan {
+    int d = 0, precision = 0, device = 0;
+    Grid grid;
+    Mesh mesh;
+    fgr_options opt{};
+    FggcBox box;
+    FggcBuffers buf;
+    int *bnd = nullptr;       // device: the packets' node bounds of the last call
+    int *overflow = nullptr;  // device: set when they left the box
+    void release() {
+        void *ptrs[] = {buf.W, buf.buf1, buf.buf2, buf.flags, buf.brange, bnd, overflow};
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
+        buf = FggcBuffers{};
+        bnd = overflow = nullptr;
+    }
+};
+
+namespace {
+
+bool plan_matches(const fgr_ctx *ctx, const fgr_fggc_plan *pl) {
+    if (ctx->d != pl->d || ctx->opt.precision != pl->precision || ctx->device != pl->device) return false;
+    if (ctx->mesh.eps != pl->mesh.eps || ctx->mesh.dq != pl->mesh.dq || ctx->mesh.dp != pl->mesh.dp ||
+        ctx->mesh.rs != pl->mesh.rs || ctx->opt.nq != pl->opt.nq || ctx->opt.np != pl->opt.np)
+        return false;
+    for (int l = 0; l < ctx->d; ++l)
+        if (ctx->grid.n[l] != pl->grid.n[l] || ctx->grid.lo[l] != pl->grid.lo[l] || ctx->grid.h[l] != pl->grid.h[l])
+            return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+fgr_status fgr_fggc_plan_create(fgr_ctx *ctx, const fgr_packets *pk, int32_t margin, fgr_fggc_plan **out,
+                                void *stream) {
+    clear_error();
+    if (!ctx || !out || margin < 0 || margin > 4096) {
+        set_error("plan: need ctx, out and 0 <= margin <= 4096");
+        return FGR_E_INVALID;
+    }
+    *out = nullptr;
+    fgr_status rc = check_packets(ctx, pk);
+    if (rc != FGR_OK) return rc;
+    return guarded([&]() -> fgr_status {
+        FGR_CUDA_TRY(cudaSetDevice(ctx->device));
+        cudaStream_t st = (cudaStream_t)stream;
+        Scratch scratch(ctx, st);
+        PacketsDev dev;
+        double *q, *p, *s, *a;
+        fgr_status r = stage_packets(ctx, pk, st, scratch, &dev, &q, &p, &s, &a);
+        if (r != FGR_OK) return r;
+        std::unique_ptr<fgr_fggc_plan> pl(new fgr_fggc_plan());
+        pl->d = ctx->d;
+        pl->precision = ctx->opt.precision;
+        pl->device = ctx->device;
+        pl->grid = ctx->grid;
+        pl->mesh = ctx->mesh;
+        pl->opt = ctx->opt;
+        auto fail = [&](cudaError_t e) {
+            cudaGetLastError();
+            pl->release();
+            set_error("plan: device allocation failed: %s", cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? FGR_E_NOMEM : FGR_E_CUDA;
+        };
+        cudaError_t e = cudaMalloc(&pl->bnd, sizeof(int) * 12);
+        if (e == cudaSuccess) e = cudaMalloc(&pl->overflow, sizeof(int));
+        if (e != cudaSuccess) return fail(e);
+        int hb[12];
+        r = compute_node_bounds(ctx, dev, pl->bnd, hb, st);
+        if (r != FGR_OK) {
+            pl->release();
+            return r;
+        }
+        r = make_box(ctx, hb, margin, &pl->box);
+        if (r != FGR_OK) {
+            pl->release();
+            return r;
+        }
+        if (!pl->box.empty) {
+            const size_t eb = elem_bytes(ctx->opt.precision);
+            const FggcBox &b = pl->box;
+            e = cudaMalloc(&pl->buf.W, eb * (size_t)b.cells);
+            if (e == cudaSuccess && ctx->d > 1) e = cudaMalloc(&pl->buf.buf1, eb * (size_t)b.maxbuf);
+            if (e == cudaSuccess && ctx->d > 1) e = cudaMalloc(&pl->buf.buf2, eb * (size_t)b.maxbuf);
+            if (e == cudaSuccess) e = cudaMalloc((void **)&pl->buf.flags, (size_t)b.rows0);
+            if (e == cudaSuccess) e = cudaMalloc((void **)&pl->buf.brange, sizeof(int2) * (size_t)b.max_lines);
+            if (e != cudaSuccess) return fail(e);
+        }
+        *out = pl.release();
+        return FGR_OK;
+    });
+}
+
+fgr_status fgr_reconstruct_fggc_planned(fgr_ctx *ctx, fgr_fggc_plan *plan, const fgr_packets *pk, void *u_out,
+                                        void *stream) {
+    clear_error();
+    if (!ctx || !plan || !u_out) {
+        set_error("planned: need ctx, plan and u_out");
+        return FGR_E_INVALID;
+    }
+    if (!plan_matches(ctx, plan)) {
+        set_error("planned: the plan was made for another dimension, precision, grid, eps or neighbour set");
+        return FGR_E_INVALID;
+    }
+    fgr_status rc = check_packets(ctx, pk);
+    if (rc != FGR_OK) return rc;
+    if (pk->m > 0 && pk->on_device != 1) {
+        set_error("planned: packets must be device memory");
+        return FGR_E_INVALID;
+    }
+    if (!is_device_ptr(u_out)) {
+        set_error("planned: u_out must be device memory");
+        return FGR_E_INVALID;
+    }
+    return guarded([&]() -> fgr_status {
+        FGR_CUDA_TRY(cudaSetDevice(ctx->device));
+        cudaStream_t st = (cudaStream_t)stream;
+        const PacketsDev dev{pk->m, pk->q, pk->p, pk->s, pk->a};
+        fgr_status r = run_fggc_planned(ctx, dev, plan->box, plan->buf, plan->bnd, plan->overflow, u_out, st);
+        if (r != FGR_OK) return r;
+        FGR_CUDA_TRY(cudaGetLastError());
+        if (!stream) FGR_CUDA_TRY(cudaStreamSynchronize(st));
+        return FGR_OK;
+    });
+}
+
+fgr_status fgr_fggc_plan_overflow(fgr_fggc_plan *plan, int32_t *overflowed) {
+    clear_error();
+    if (!plan || !overflowed) return FGR_E_INVALID;
+    int v = 0;
+    cudaError_t e = cudaSetDevice(plan->device);
+    if (e == cudaSuccess) e = cudaMemcpy(&v, plan->overflow, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("plan: %s", cudaGetErrorString(e));
+        return FGR_E_CUDA;
+    }
+    *overflowed = v;
+    return FGR_OK;
+}
+
+fgr_status fgr_fggc_plan_info(const fgr_fggc_plan *plan, int64_t *nodes, int32_t *empty) {
+    if (!plan || !nodes || !empty) return FGR_E_INVALID;
+    *nodes = plan->box.cells;
+    *empty = plan->box.empty ? 1 : 0;
+    return FGR_OK;
+}
+
+void fgr_fggc_plan_destroy(fgr_fggc_plan *plan) {
+    if (!plan) return;
+    cudaSetDevice(plan->device);
+    plan->release();
+    delete plan;
 }
 
 }  // extern "C"

@@ -2,13 +2,14 @@
 //
 // fgr_autotune times, with CUDA events on the caller's stream, each candidate
 // of (a) the number of CTAs per SM the direct sum aims for when it splits the
-// packet lists of its output tiles and (b) the number of CTAs per SM the grid
-// passes aim for when they split the node range, on the caller's packets and
-// grid.  The fastest of each is kept in the context and in a process-wide table
-// keyed by the problem class (dimension, precision, packets and grid points
-// rounded to powers of two), from which new contexts of the same class start.
-// With FGR_TUNE_FILE set, the table is read from and appended to that file
-// (one line per class: d precision log2(M) log2(points) direct pass).
+// packet lists of its output tiles and (b) the grid passes' tile width (32 or
+// 128 grid points per CTA) together with the number of CTAs per SM they aim
+// for when they split the node range, on the caller's packets and grid.  The
+// fastest of each is kept in the context and in a process-wide table keyed by
+// the problem class (dimension, precision, packets and grid points rounded to
+// powers of two), from which new contexts of the same class start.  With
+// FGR_TUNE_FILE set, the table is read from and appended to that file (one
+// line per class: d precision log2(M) log2(points) direct pass tile).
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -44,9 +45,12 @@ void load_file_locked() {
     if (!path) return;
     FILE *f = fopen(path, "r");
     if (!f) return;
-    int d, pr, lm, lg, a, b;
-    while (fscanf(f, "%d %d %d %d %d %d", &d, &pr, &lm, &lg, &a, &b) == 6) {
-        if (a > 0 && a <= 256 && b > 0 && b <= 256) g_tuned[ClassKey(d, pr, lm, lg)] = Tuning{a, b};
+    char line[256];
+    while (fgets(line, sizeof(line), f)) {
+        int d, pr, lm, lg, a, b, t = 0;
+        const int n = sscanf(line, "%d %d %d %d %d %d %d", &d, &pr, &lm, &lg, &a, &b, &t);
+        if (n < 6 || a < 1 || a > 256 || b < 1 || b > 256 || (t != 0 && t != 32 && t != 128)) continue;
+        g_tuned[ClassKey(d, pr, lm, lg)] = Tuning{a, b, t};
     }
     fclose(f);
 }
@@ -56,8 +60,8 @@ void save_line(const ClassKey &k, const Tuning &t) {
     if (!path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k),
-            t.direct_ctas_per_sm, t.pass_ctas_per_sm);
+    fprintf(f, "%d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k),
+            t.direct_ctas_per_sm, t.pass_ctas_per_sm, t.pass_tile);
     fclose(f);
 }
 
@@ -133,15 +137,20 @@ fgr_status fgr_autotune(fgr_ctx *ctx, const fgr_packets *pk, void *u_out, int32_
     }
     if (rc == FGR_OK && (methods & 2)) {
         float best_ms = 1e30f;
-        for (int c : {4, 8, 16, 32, 64}) {
-            ctx->tune.pass_ctas_per_sm = c;
-            float ms;
-            rc = time_call(true, &ms);
-            if (rc != FGR_OK) break;
-            if (ms < best_ms) {
-                best_ms = ms;
-                best.pass_ctas_per_sm = c;
+        for (int tile : {128, 32}) {
+            for (int c : {4, 8, 16, 32, 64}) {
+                ctx->tune.pass_tile = tile;
+                ctx->tune.pass_ctas_per_sm = c;
+                float ms;
+                rc = time_call(true, &ms);
+                if (rc != FGR_OK) break;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best.pass_ctas_per_sm = c;
+                    best.pass_tile = tile;
+                }
             }
+            if (rc != FGR_OK) break;
         }
     }
     cudaEventDestroy(e0);
@@ -159,21 +168,24 @@ fgr_status fgr_autotune(fgr_ctx *ctx, const fgr_packets *pk, void *u_out, int32_
     return FGR_OK;
 }
 
-fgr_status fgr_get_tuning(const fgr_ctx *ctx, int32_t *direct_ctas_per_sm, int32_t *pass_ctas_per_sm) {
-    if (!ctx || !direct_ctas_per_sm || !pass_ctas_per_sm) return FGR_E_INVALID;
+fgr_status fgr_get_tuning(const fgr_ctx *ctx, int32_t *direct_ctas_per_sm, int32_t *pass_ctas_per_sm,
+                          int32_t *pass_tile) {
+    if (!ctx || !direct_ctas_per_sm || !pass_ctas_per_sm || !pass_tile) return FGR_E_INVALID;
     *direct_ctas_per_sm = ctx->tune.direct_ctas_per_sm;
     *pass_ctas_per_sm = ctx->tune.pass_ctas_per_sm;
+    *pass_tile = ctx->tune.pass_tile;
     return FGR_OK;
 }
 
-fgr_status fgr_set_tuning(fgr_ctx *ctx, int32_t direct_ctas_per_sm, int32_t pass_ctas_per_sm) {
+fgr_status fgr_set_tuning(fgr_ctx *ctx, int32_t direct_ctas_per_sm, int32_t pass_ctas_per_sm, int32_t pass_tile) {
     if (!ctx || direct_ctas_per_sm < 1 || direct_ctas_per_sm > 256 || pass_ctas_per_sm < 1 ||
-        pass_ctas_per_sm > 256) {
-        set_error("set_tuning: values must lie in 1..256");
+        pass_ctas_per_sm > 256 || (pass_tile != 0 && pass_tile != 32 && pass_tile != 128)) {
+        set_error("set_tuning: CTA targets must lie in 1..256 and the pass tile be 0, 32 or 128");
         return FGR_E_INVALID;
     }
     ctx->tune.direct_ctas_per_sm = direct_ctas_per_sm;
     ctx->tune.pass_ctas_per_sm = pass_ctas_per_sm;
+    ctx->tune.pass_tile = pass_tile;
     return FGR_OK;
 }
 

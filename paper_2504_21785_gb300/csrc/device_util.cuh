@@ -34,6 +34,21 @@ __device__ __forceinline__ double quotient_for_floor(double x, double step, doub
     return r;
 }
 
+// floor(fl(x / step)) as an int, mostly without FP64 arithmetic: the FP32
+// product (float)x * (float)inv_step has a relative error below 2e-7, so when
+// it lies more than 1e-6 (relative) away from an integer its floor is the
+// floor of the exact quotient; otherwise (and for |x/step| >= 1e6) the FP64
+// path above decides.
+__device__ __forceinline__ int floor_div_int(double x, double step, double inv_step) {
+    const float rf = (float)x * (float)inv_step;
+    const float fl = floorf(rf);
+    const float fr = rf - fl;
+    const float tol = 1e-6f * fmaxf(1.f, fabsf(rf));
+    if (fabsf(rf) < 1e6f && fr > tol && fr < 1.f - tol) return (int)fl;
+    const double r = floor(quotient_for_floor(x, step, inv_step));
+    return (int)fmin(fmax(r, -1e9), 1e9);
+}
+
 // Grid coordinate x_m = lo + m*h without contraction.
 __device__ __forceinline__ double grid_x(double lo, double h, int64_t m) {
     return __dadd_rn(lo, __dmul_rn((double)m, h));

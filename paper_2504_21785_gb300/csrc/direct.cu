@@ -211,6 +211,99 @@ struct DirectParams {
     int splits;
 };
 
+// FP32, d >= 2: the term of a packet factorises over dimensions,
+//   pref A e^{i S/eps} prod_l exp(-(x_l - Q_l)^2 / (2 eps) + i P_l (x_l - Q_l) / eps),
+// with each factor zero outside the packet's window in that dimension.  For a
+// sub-chunk of kSub staged records the CTA tabulates every record's factors
+// on the tile's grid lines (sum of the tile extents per record; the amplitude
+// and the phase at the window start go into the first dimension's factor),
+// then each thread accumulates the products over its 4 points: one complex
+// multiply-add per packet-point pair.
+template <int D>
+__host__ __device__ constexpr int kSumT() {
+    return D == 1 ? tileT<1>(0) : (D == 2 ? tileT<2>(0) + tileT<2>(1) : tileT<3>(0) + tileT<3>(1) + tileT<3>(2));
+}
+template <int D>
+__host__ __device__ constexpr int kSub() {
+    return D == 3 ? 64 : 32;  // records per factor table (20 KB for d = 2, 16 KB for d = 3)
+}
+
+template <int D>
+__device__ __forceinline__ void separable_chunk(const int *__restrict__ srec, const int nrec, const DirectParams &P,
+                                                const int *t, const int (*mi)[D], float2 *__restrict__ sfac,
+                                                float (*accf)[2]) {
+    constexpr int kWords = sizeof(RecF<D>) / 4;
+    constexpr int kS = kSub<D>(), kT = kSumT<D>();
+    int loc[D];  // this thread's first point within the tile
+#pragma unroll
+    for (int l = 0; l < D; ++l) loc[l] = mi[0][l] - t[l] * tileT<D>(l);
+    int foff_last = 0;
+#pragma unroll
+    for (int l = 0; l < D - 1; ++l) foff_last += tileT<D>(l);
+    for (int s0 = 0; s0 < nrec; s0 += kS) {
+        const int ns = min(kS, nrec - s0);
+        // factor tables of records s0 .. s0 + ns - 1
+        for (int e = threadIdx.x; e < ns * kT; e += kThreads) {
+            const int jr = s0 + e / kT;
+            int qd = e % kT, l = 0;
+#pragma unroll
+            for (int j = 0; j < D - 1; ++j)
+                if (l == j && qd >= tileT<D>(j)) {
+                    qd -= tileT<D>(j);
+                    l = j + 1;
+                }
+            const RecF<D> &R = *reinterpret_cast<const RecF<D> *>(&srec[jr * kWords]);
+            const float kf = (float)(t[l] * tileT<D>(l) + qd) - R.mlo[l];
+            float2 f = make_float2(0.f, 0.f);
+            if (kf >= 0.f && kf < R.wlen[l]) {
+                const float dx = fmaf(kf, P.hf[l], R.delta[l]);
+                float ex = dx * dx * P.ce;
+                float fr = kf * R.nuhi[l];
+                fr -= rint_fast(fr);
+                float tau = fmaf(kf, R.nulo[l], fr);
+                if (l == 0) {
+                    ex += R.la;
+                    tau += R.tau0;
+                }
+                tau -= rint_fast(tau);
+                float sn, cs;
+                __sincosf(6.283185307179586f * tau, &sn, &cs);
+                const float ga = ex2_approx(ex);
+                f = make_float2(ga * cs, ga * sn);
+            }
+            sfac[e] = f;
+        }
+        __syncthreads();
+        for (int jj = 0; jj < ns; ++jj) {
+            const RecF<D> &R = *reinterpret_cast<const RecF<D> *>(&srec[(s0 + jj) * kWords]);
+            bool in = true;  // skip packets whose window misses this thread's points
+#pragma unroll
+            for (int l = 0; l < D - 1; ++l) {
+                const float k = (float)mi[0][l] - R.mlo[l];
+                in = in && k >= 0.f && k < R.wlen[l];
+            }
+            const float kl = (float)mi[0][D - 1] - R.mlo[D - 1];
+            in = in && kl > -(float)kTpt && kl < R.wlen[D - 1];
+            if (!in) continue;
+            const float2 *F = sfac + jj * kT;
+            float2 pre = F[loc[0]];
+            if (D == 3) {
+                const float2 f1 = F[tileT<D>(0) + loc[1]];
+                pre = make_float2(pre.x * f1.x - pre.y * f1.y, pre.x * f1.y + pre.y * f1.x);
+            }
+            const float4 a01 = *reinterpret_cast<const float4 *>(F + foff_last + loc[D - 1]);
+            const float4 a23 = *reinterpret_cast<const float4 *>(F + foff_last + loc[D - 1] + 2);
+            const float fr[4] = {a01.x, a01.z, a23.x, a23.z}, fi[4] = {a01.y, a01.w, a23.y, a23.w};
+#pragma unroll
+            for (int r = 0; r < kTpt; ++r) {
+                accf[r][0] = fmaf(pre.x, fr[r], fmaf(-pre.y, fi[r], accf[r][0]));
+                accf[r][1] = fmaf(pre.x, fi[r], fmaf(pre.y, fr[r], accf[r][1]));
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // One (output tile, packet slice) work item of the direct sum, executed by the
 // whole CTA; shared by the one-request kernel and the batched persistent kernel.
 template <int D, bool FP64>
@@ -220,8 +313,9 @@ __device__ __forceinline__ void direct_tile(const void *__restrict__ recs_v, con
     using Rec = typename std::conditional<FP64, RecD<D>, RecF<D>>::type;
     constexpr int kWords = sizeof(Rec) / 4;
     __shared__ __align__(16) int srec[kThreads * kWords];
-    __shared__ int64_t seg_start[kMaxSeg];
-    __shared__ int64_t seg_cum[kMaxSeg + 1];
+    // record offsets fit 32 bits (at most 2^31 packets per call)
+    __shared__ uint32_t seg_start[kMaxSeg];
+    __shared__ uint32_t seg_cum[kMaxSeg + 1];
     __shared__ int nseg_s;
 
     const GridDev &g = P.g;
@@ -260,18 +354,18 @@ __device__ __forceinline__ void direct_tile(const void *__restrict__ recs_v, con
             const int last = first + cnt[D - 1] - 1;
             const int64_t a0 = off[first], a1 = off[last + 1];
             if (a1 > a0) {
-                seg_start[ns] = a0;
-                seg_cum[ns] = cum;
+                seg_start[ns] = (uint32_t)a0;
+                seg_cum[ns] = (uint32_t)cum;
                 cum += a1 - a0;
                 ++ns;
             }
         }
-        seg_cum[ns] = cum;
+        seg_cum[ns] = (uint32_t)cum;
         nseg_s = ns;
     }
     __syncthreads();
     const int nseg = nseg_s;
-    const int64_t L = seg_cum[nseg];
+    const int64_t L = (int64_t)seg_cum[nseg];
 
     // this thread's points: kTpt consecutive points along the last dimension
     constexpr int kLane = tileT<D>(D - 1) / kTpt;  // threads along the last dimension
@@ -311,7 +405,8 @@ __device__ __forceinline__ void direct_tile(const void *__restrict__ recs_v, con
 #pragma unroll
             for (int l = 0; l < D; ++l) xd[r][l] = grid_x(g.lo[l], g.h[l], mi[r][l]);
     }
-    __shared__ float2 srot[kThreads];  // FP32: e^{2 pi i nu} of the last dimension per staged record
+    __shared__ float2 srot[(!FP64 && D == 1) ? kThreads : 1];  // FP32, 1-D: e^{2 pi i nu} per staged record
+    __shared__ __align__(16) float2 sfac[(!FP64 && D >= 2) ? kSub<D>() * kSumT<D>() : 2];  // FP32, d >= 2
 
     float accf[kTpt][2];
     double accd[kTpt][2];
@@ -329,16 +424,16 @@ __device__ __forceinline__ void direct_tile(const void *__restrict__ recs_v, con
             int lo = 0, hi = nseg - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (seg_cum[mid] <= v) lo = mid;
+                if ((int64_t)seg_cum[mid] <= v) lo = mid;
                 else hi = mid - 1;
             }
-            const int64_t idx = seg_start[lo] + (v - seg_cum[lo]);
+            const int64_t idx = (int64_t)seg_start[lo] + (v - (int64_t)seg_cum[lo]);
             const int *src = reinterpret_cast<const int *>(recs + idx);
 #pragma unroll
             for (int w = 0; w < kWords; w += 4)
                 *reinterpret_cast<int4 *>(&srec[threadIdx.x * kWords + w]) =
                     *reinterpret_cast<const int4 *>(src + w);
-            if (!FP64) {  // the rotation by one grid step along the last dimension
+            if (!FP64 && D == 1) {  // the rotation by one grid step along the last dimension
                 const RecF<D> &mine = *reinterpret_cast<const RecF<D> *>(&srec[threadIdx.x * kWords]);
                 float sn, cs;
                 sincospif(2.f * (mine.nuhi[D - 1] + mine.nulo[D - 1]), &sn, &cs);
@@ -348,6 +443,9 @@ __device__ __forceinline__ void direct_tile(const void *__restrict__ recs_v, con
         __syncthreads();
         const int64_t left = L - c * kThreads;
         const int nrec = left < kThreads ? (int)left : kThreads;
+        if constexpr (!FP64 && D >= 2)
+            separable_chunk<D>(srec, nrec, P, t, mi, sfac, accf);
+        else
         for (int jr = 0; jr < nrec; ++jr) {
             const Rec &R = *reinterpret_cast<const Rec *>(&srec[jr * kWords]);
             if (FP64) {

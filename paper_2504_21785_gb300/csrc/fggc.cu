@@ -22,9 +22,10 @@
 // K5 (separable grid stage).  u(x_m) = sum_{a,b} W'[a,b] prod_l g(x_{m_l} - a_l dq)
 // e^{i b_l dp x_{m_l}/eps} is contracted one dimension at a time: a pass maps
 // rows [a_l][b_l] to [m_l]; a transpose brings the next dimension innermost.
-// Each CTA owns 64 grid points of one row: the band of nodes a whose window
-// covers them, g in registers, W staged through shared memory in chunks of b,
-// and e^{i b dp x/eps} generated per (m, b) from a phase reduced in FP64.
+// Each CTA owns 32 or 128 grid points of one row (one per thread): the band of
+// nodes a whose window covers them, g in registers, W staged through shared
+// memory in chunks of b, and e^{i b dp x/eps} generated per (m, b) from a
+// phase reduced in FP64.
 #include <climits>
 #include <cmath>
 
@@ -42,7 +43,6 @@ template <int D>
 __global__ void bounds_kernel(const double *__restrict__ q, const double *__restrict__ p,
                               const double *__restrict__ a, int64_t m, Common c, int aglo0, int aghi0,
                               int aglo1, int aghi1, int aglo2, int aghi2, int *__restrict__ out) {
-    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int aglo[3] = {aglo0, aglo1, aglo2}, aghi[3] = {aghi0, aghi1, aghi2};
     int dqmin = INT_MAX, dqmax = INT_MIN, dpmin = INT_MAX, dpmax = INT_MIN;
     for (int k = 0; k < c.n1; ++k) {
@@ -51,9 +51,9 @@ __global__ void bounds_kernel(const double *__restrict__ q, const double *__rest
         dpmin = min(dpmin, c.dp[k]);
         dpmax = max(dpmax, c.dp[k]);
     }
-    bool use = j < m;
+    // grid-stride: each thread folds its packets into running bounds, so the
+    // atomics below are one set per CTA (a few thousand in all)
     int lo_a[D], hi_a[D], lo_b[D], hi_b[D];
-    if (use) use = !(a[j] == 0.0 && a[m + j] == 0.0);
 #pragma unroll
     for (int l = 0; l < D; ++l) {
         lo_a[l] = INT_MAX;
@@ -61,19 +61,27 @@ __global__ void bounds_kernel(const double *__restrict__ q, const double *__rest
         lo_b[l] = INT_MAX;
         hi_b[l] = INT_MIN;
     }
-    if (use) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        if (a[j] == 0.0 && a[m + j] == 0.0) continue;
+        int pa_lo[D], pa_hi[D], pb_lo[D], pb_hi[D];
+        bool use = true;
 #pragma unroll
         for (int l = 0; l < D; ++l) {
-            const double ra = floor(quotient_for_floor(q[l * m + j], c.dqv, c.inv_dq));
-            const double rb = floor(quotient_for_floor(p[l * m + j], c.dpv, c.inv_dp));
-            const double lim = 1e9;
-            const int a0 = (int)fmin(fmax(ra, -lim), lim), b0 = (int)fmin(fmax(rb, -lim), lim);
-            const int alo = max(a0 + dqmin, aglo[l]), ahi = min(a0 + dqmax, aghi[l]);
-            if (alo > ahi) use = false;
-            lo_a[l] = alo;
-            hi_a[l] = ahi;
-            lo_b[l] = b0 + dpmin;
-            hi_b[l] = b0 + dpmax;
+            const int a0 = floor_div_int(q[l * m + j], c.dqv, c.inv_dq);
+            const int b0 = floor_div_int(p[l * m + j], c.dpv, c.inv_dp);
+            pa_lo[l] = max(a0 + dqmin, aglo[l]);
+            pa_hi[l] = min(a0 + dqmax, aghi[l]);
+            if (pa_lo[l] > pa_hi[l]) use = false;  // no node of this packet reaches the grid
+            pb_lo[l] = b0 + dpmin;
+            pb_hi[l] = b0 + dpmax;
+        }
+        if (!use) continue;
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+            lo_a[l] = min(lo_a[l], pa_lo[l]);
+            hi_a[l] = max(hi_a[l], pa_hi[l]);
+            lo_b[l] = min(lo_b[l], pb_lo[l]);
+            hi_b[l] = max(hi_b[l], pb_hi[l]);
         }
     }
     // warp, then block reduction; one atomic per block and value
@@ -81,10 +89,10 @@ __global__ void bounds_kernel(const double *__restrict__ q, const double *__rest
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 #pragma unroll
     for (int l = 0; l < D; ++l) {
-        const int v0 = __reduce_min_sync(0xffffffffu, use ? lo_a[l] : INT_MAX);
-        const int v1 = __reduce_max_sync(0xffffffffu, use ? hi_a[l] : INT_MIN);
-        const int v2 = __reduce_min_sync(0xffffffffu, use ? lo_b[l] : INT_MAX);
-        const int v3 = __reduce_max_sync(0xffffffffu, use ? hi_b[l] : INT_MIN);
+        const int v0 = __reduce_min_sync(0xffffffffu, lo_a[l]);
+        const int v1 = __reduce_max_sync(0xffffffffu, hi_a[l]);
+        const int v2 = __reduce_min_sync(0xffffffffu, lo_b[l]);
+        const int v3 = __reduce_max_sync(0xffffffffu, hi_b[l]);
         if ((threadIdx.x & 31) == 0) {
             red[warp][l * 4 + 0] = v0;
             red[warp][l * 4 + 1] = v1;
@@ -103,6 +111,12 @@ __global__ void bounds_kernel(const double *__restrict__ q, const double *__rest
             else atomicMax(&out[k], v);
         }
     }
+}
+
+// CTAs of the bounds kernel: enough to fill the GPU, few enough that the
+// per-CTA atomics stay negligible
+inline unsigned bounds_blocks(const fgr_ctx *ctx, int64_t m) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, (int64_t)ctx->num_sms * 8));
 }
 
 __device__ __forceinline__ void cmul(double ar, double ai, double br, double bi, double &cr, double &ci) {
@@ -124,16 +138,22 @@ struct PassParams {
     double dp_over_eps;
 };
 
-constexpr int kPassThreads = 128;
 constexpr int kCB = 32;
 
-// one grid point per thread keeps the Gaussian factors of the band (MAXBAND
-// registers) small enough for several CTAs per SM
-constexpr int kPassPts = 1;                         // grid points per thread
-constexpr int kPassTile = kPassThreads * kPassPts;  // grid points per CTA
+// One grid point per thread keeps the Gaussian factors of the band (MAXBAND
+// registers) small enough for several CTAs per SM.  A CTA covers TP = 128 or
+// 32 consecutive points (TP threads): the node band of a tile spans its width
+// plus one window, so on coarse grids (tile width comparable to the window)
+// the narrow tile wastes fewer zero Gaussian factors.
+constexpr int kPassPts = 1;  // grid points per thread
 
-template <bool FP64, int MAXBAND>
-__global__ void __launch_bounds__(kPassThreads) grid_pass_kernel(const void *__restrict__ in_v,
+// node band of a tile of tp points (nodes whose window can reach it, + margin)
+inline int pass_band(int tp, double h, double rs, double dq) {
+    return (int)std::ceil(((tp - 1) * h + 2 * rs) / dq) + 3;
+}
+
+template <bool FP64, int MAXBAND, int TP>
+__global__ void __launch_bounds__(TP) grid_pass_kernel(const void *__restrict__ in_v,
                                                                  void *__restrict__ out_v, PassParams pp,
                                                                  const uint8_t *__restrict__ flags,
                                                                  const int2 *__restrict__ brange) {
@@ -143,12 +163,12 @@ __global__ void __launch_bounds__(kPassThreads) grid_pass_kernel(const void *__r
     __shared__ int swlo[MAXBAND], swhi[MAXBAND];
     __shared__ int s_blo, s_bhi;
     const int64_t row = blockIdx.x;
-    const int64_t m0 = (int64_t)blockIdx.y * kPassTile;
+    const int64_t m0 = (int64_t)blockIdx.y * TP;
     int64_t mm[kPassPts];
     bool valid[kPassPts];
 #pragma unroll
     for (int r = 0; r < kPassPts; ++r) {
-        mm[r] = m0 + threadIdx.x + r * kPassThreads;
+        mm[r] = m0 + threadIdx.x + r * TP;
         valid[r] = mm[r] < pp.N;
     }
     C2 *out = reinterpret_cast<C2 *>(out_v) + row * pp.N;
@@ -157,7 +177,7 @@ __global__ void __launch_bounds__(kPassThreads) grid_pass_kernel(const void *__r
     zero.x = 0;
     zero.y = 0;
     const bool split = gridDim.z > 1;  // slices add into a zeroed output
-    const int64_t m1 = min(m0 + kPassTile - 1, pp.N - 1);
+    const int64_t m1 = min(m0 + TP - 1, pp.N - 1);
     const double x0 = grid_x(pp.lo, pp.h, m0), x1 = grid_x(pp.lo, pp.h, m1);
     const int a_lo = max(pp.amin, (int)ceil((x0 - pp.rs) / pp.dq) - 1);
     const int a_hi = min(pp.amin + pp.A - 1, (int)floor((x1 + pp.rs) / pp.dq) + 1);
@@ -171,7 +191,7 @@ __global__ void __launch_bounds__(kPassThreads) grid_pass_kernel(const void *__r
         }
         __syncthreads();
         int lo = INT_MAX, hi = INT_MIN;
-        for (int i = threadIdx.x; i < nb_total; i += kPassThreads) {
+        for (int i = threadIdx.x; i < nb_total; i += TP) {
             const int2 r = brange[row * (int64_t)pp.A + (a_lo - pp.amin) + i];
             lo = min(lo, r.x);
             hi = max(hi, r.y);
@@ -223,7 +243,7 @@ __global__ void __launch_bounds__(kPassThreads) grid_pass_kernel(const void *__r
         const int a_first = a_lo + c0;
         // each node's window once per CTA (FP64, the rule of include/fgr.h)
         __syncthreads();
-        for (int i = threadIdx.x; i < nb; i += kPassThreads) {
+        for (int i = threadIdx.x; i < nb; i += TP) {
             int64_t wlo, whi;
             window_bounds((double)(a_first + i) * pp.dq, pp.rs, pp.lo, pp.h, pp.N, &wlo, &whi);
             swlo[i] = (int)wlo;
@@ -251,7 +271,7 @@ __global__ void __launch_bounds__(kPassThreads) grid_pass_kernel(const void *__r
         const int ia0 = a_first - pp.amin;
         for (int b0 = bs; b0 < be; b0 += kCB) {
             const int nbb = min(kCB, be - b0);
-            for (int e = threadIdx.x; e < nb * kCB; e += kPassThreads) {
+            for (int e = threadIdx.x; e < nb * kCB; e += TP) {
                 const int i = e / kCB, bb = e % kCB;
                 sw[i][bb] = bb < nbb ? in[(int64_t)(ia0 + i) * pp.B + b0 + bb] : zero;
             }
@@ -369,31 +389,61 @@ __global__ void brange_kernel(const C2 *__restrict__ in, int64_t lines, int B, i
     if (lane == 0) out[line] = make_int2(lo == INT_MAX ? B : lo, hi);
 }
 
+// The same for short lines (B <= 64): one thread per line, so a warp streams
+// 32 consecutive lines instead of leaving most of its lanes idle.
+template <class C2>
+__global__ void brange_short_kernel(const C2 *__restrict__ in, int64_t lines, int B, int2 *__restrict__ out) {
+    const int64_t line = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (line >= lines) return;
+    const C2 *p = in + line * (int64_t)B;
+    int lo = B, hi = -1;
+    for (int b = 0; b < B; ++b) {
+        const C2 v = p[b];
+        if (v.x != 0 || v.y != 0) {
+            lo = min(lo, b);
+            hi = b;
+        }
+    }
+    out[line] = make_int2(lo, hi);
+}
+
 template <bool FP64>
 fgr_status launch_brange(const void *in, int64_t rows, int A, int B, int2 *out, cudaStream_t st) {
     const int64_t lines = rows * (int64_t)A;
     if (lines == 0) return FGR_OK;
-    const unsigned blocks = (unsigned)((lines + 7) / 8);
-    if (FP64)
-        brange_kernel<double2><<<blocks, 256, 0, st>>>((const double2 *)in, lines, B, out);
-    else
-        brange_kernel<float2><<<blocks, 256, 0, st>>>((const float2 *)in, lines, B, out);
+    if (B <= 64) {
+        const unsigned blocks = (unsigned)((lines + 255) / 256);
+        if (FP64)
+            brange_short_kernel<double2><<<blocks, 256, 0, st>>>((const double2 *)in, lines, B, out);
+        else
+            brange_short_kernel<float2><<<blocks, 256, 0, st>>>((const float2 *)in, lines, B, out);
+    } else {
+        const unsigned blocks = (unsigned)((lines + 7) / 8);
+        if (FP64)
+            brange_kernel<double2><<<blocks, 256, 0, st>>>((const double2 *)in, lines, B, out);
+        else
+            brange_kernel<float2><<<blocks, 256, 0, st>>>((const float2 *)in, lines, B, out);
+    }
     FGR_CUDA_TRY(cudaGetLastError());
     return FGR_OK;
 }
 
 template <bool FP64>
 fgr_status launch_pass(const void *in, void *out, const PassParams &pp, const uint8_t *flags,
-                       const int2 *brange, int band, int64_t target_ctas, cudaStream_t st) {
+                       const int2 *brange, int64_t target_ctas, int tile_pref, cudaStream_t st) {
     if (pp.rows == 0 || pp.N == 0) return FGR_OK;
     if (pp.rows > INT_MAX) {
         set_error("fggc: too many rows in a grid pass");
         return FGR_E_CAPACITY;
     }
-    const int64_t mtiles = (pp.N + kPassTile - 1) / kPassTile;
+    // narrow tiles where they cut the band (the work per grid point) by more
+    // than a quarter, unless the autotuner or the caller fixed the tile
+    const int band128 = pass_band(128, pp.h, pp.rs, pp.dq), band32 = pass_band(32, pp.h, pp.rs, pp.dq);
+    const int tp = tile_pref == 32 || tile_pref == 128 ? tile_pref : (4 * band32 < 3 * band128 ? 32 : 128);
+    const int band = tp == 32 ? band32 : band128;
+    const int64_t mtiles = (pp.N + tp - 1) / tp;
     if (mtiles > 65535) {
-        set_error("fggc: %lld points per grid dimension; at most %d supported", (long long)pp.N,
-                  65535 * kPassTile);
+        set_error("fggc: %lld points per grid dimension; at most %d supported", (long long)pp.N, 65535 * tp);
         return FGR_E_INVALID;
     }
     // split the b-range when rows x tiles alone cannot fill the device
@@ -405,11 +455,18 @@ fgr_status launch_pass(const void *in, void *out, const PassParams &pp, const ui
         FGR_CUDA_TRY(cudaMemsetAsync(out, 0, (FP64 ? 16 : 8) * (size_t)pp.rows * (size_t)pp.N, st));
     }
     dim3 grid((unsigned)pp.rows, (unsigned)mtiles, (unsigned)splits);
-#define FGR_PASS(MB) grid_pass_kernel<FP64, MB><<<grid, kPassThreads, 0, st>>>(in, out, pp, flags, brange)
-    if (band <= 16) FGR_PASS(16);
-    else if (band <= 32) FGR_PASS(32);
-    else if (band <= 48) FGR_PASS(48);
-    else FGR_PASS(64);  // wider bands are processed in chunks of 64
+#define FGR_PASS(MB, TPV) grid_pass_kernel<FP64, MB, TPV><<<grid, TPV, 0, st>>>(in, out, pp, flags, brange)
+#define FGR_PASS_TP(TPV)                                                                                    \
+    if (band <= 16) FGR_PASS(16, TPV);                                                                      \
+    else if (band <= 32) FGR_PASS(32, TPV);                                                                 \
+    else if (band <= 48) FGR_PASS(48, TPV);                                                                 \
+    else FGR_PASS(64, TPV);  // wider bands are processed in chunks of 64
+    if (tp == 32) {
+        FGR_PASS_TP(32)
+    } else {
+        FGR_PASS_TP(128)
+    }
+#undef FGR_PASS_TP
 #undef FGR_PASS
     FGR_CUDA_TRY(cudaGetLastError());
     return FGR_OK;
@@ -428,16 +485,26 @@ fgr_status launch_transpose(const void *in, void *out, int64_t R, int64_t Cc, cu
     return FGR_OK;
 }
 
-template <int D>
-fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t st, Scratch &scratch) {
-    const bool fp64 = ctx->opt.precision == FGR_FP64;
-    const Mesh &M = ctx->mesh;
-    const Grid &G = ctx->grid;
-    const Lsa &L = ctx->lsa;
-    const size_t eb = elem_bytes(ctx->opt.precision);
-    StageTimer timer(ctx, st);
-    int64_t launches = 0;
+__global__ void bounds_init_kernel(int *__restrict__ b) {
+    if (threadIdx.x < 12) b[threadIdx.x] = (threadIdx.x & 1) ? INT_MIN : INT_MAX;
+}
 
+// Sets *overflow when the packets' node bounds b[] leave the planned box.
+__global__ void box_check_kernel(const int *__restrict__ b, int d, Common c, int *__restrict__ overflow) {
+    if (threadIdx.x != 0) return;
+    bool out = false;
+    for (int l = 0; l < d; ++l) {
+        if (b[l * 4] == INT_MAX) continue;  // no packet reaches the grid
+        out = out || b[l * 4 + 0] < c.amin[l] || b[l * 4 + 1] > c.amin[l] + c.A[l] - 1 ||
+              b[l * 4 + 2] < c.bmin[l] || b[l * 4 + 3] > c.bmin[l] + c.B[l] - 1;
+    }
+    if (out) *overflow = 1;
+}
+
+// LSA and mesh constants of a context (the node box is filled in by make_box).
+Common base_common(const fgr_ctx *ctx) {
+    const Mesh &M = ctx->mesh;
+    const Lsa &L = ctx->lsa;
     Common c{};
     c.n1 = L.n1;
     for (int k = 0; k < L.n1; ++k) {
@@ -454,51 +521,71 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
     c.cc = M.cqcp / (2 * M_PI);
     c.inv_2pi_eps = 1.0 / (2 * M_PI * M.eps);
     c.pref = M.pref;
+    return c;
+}
 
-    // grid-relevant node range per dimension (other nodes have empty windows)
-    int aglo[3] = {0, 0, 0}, aghi[3] = {-1, -1, -1};
-    for (int l = 0; l < D; ++l) {
+// Grid-relevant node range per dimension (other nodes have empty windows).
+void grid_node_range(const fgr_ctx *ctx, int *aglo, int *aghi) {
+    const Grid &G = ctx->grid;
+    const Mesh &M = ctx->mesh;
+    for (int l = 0; l < 3; ++l) {
+        aglo[l] = 0;
+        aghi[l] = -1;
+    }
+    for (int l = 0; l < ctx->d; ++l) {
         const double xlast = G.lo[l] + (double)(G.n[l] - 1) * G.h[l];
         aglo[l] = (int)std::max(-1e9, std::ceil((G.lo[l] - M.rs) / M.dq) - 1);
         aghi[l] = (int)std::min(1e9, std::floor((xlast + M.rs) / M.dq) + 1);
     }
-    int *bnd = (int *)scratch.get(sizeof(int) * 12);
-    if (!bnd) return FGR_E_NOMEM;
-    {
-        int init[12];
-        for (int l = 0; l < 3; ++l) {
-            init[l * 4 + 0] = INT_MAX;
-            init[l * 4 + 1] = INT_MIN;
-            init[l * 4 + 2] = INT_MAX;
-            init[l * 4 + 3] = INT_MIN;
+}
+
+// Launches the node-bounds reduction of the packets into b[12] (device).
+fgr_status launch_bounds_reduction(const fgr_ctx *ctx, const PacketsDev &pk, const Common &c, const int *aglo,
+                                   const int *aghi, int *b, cudaStream_t st) {
+    bounds_init_kernel<<<1, 32, 0, st>>>(b);
+    if (pk.m > 0) {
+        const unsigned blocks = bounds_blocks(ctx, pk.m);
+        switch (ctx->d) {
+        case 1:
+            bounds_kernel<1><<<blocks, 256, 0, st>>>(pk.q, pk.p, pk.a, pk.m, c, aglo[0], aghi[0], aglo[1], aghi[1],
+                                                     aglo[2], aghi[2], b);
+            break;
+        case 2:
+            bounds_kernel<2><<<blocks, 256, 0, st>>>(pk.q, pk.p, pk.a, pk.m, c, aglo[0], aghi[0], aglo[1], aghi[1],
+                                                     aglo[2], aghi[2], b);
+            break;
+        default:
+            bounds_kernel<3><<<blocks, 256, 0, st>>>(pk.q, pk.p, pk.a, pk.m, c, aglo[0], aghi[0], aglo[1], aghi[1],
+                                                     aglo[2], aghi[2], b);
         }
-        memcpy(ctx->host_pinned, init, sizeof(init));
-        FGR_CUDA_TRY(cudaMemcpyAsync(bnd, ctx->host_pinned, sizeof(init), cudaMemcpyHostToDevice, st));
     }
-    const int64_t m = pk.m;
-    if (m > 0) {
-        bounds_kernel<D><<<(unsigned)((m + 255) / 256), 256, 0, st>>>(
-            pk.q, pk.p, pk.a, m, c, aglo[0], aghi[0], aglo[1], aghi[1], aglo[2], aghi[2], bnd);
-        FGR_CUDA_TRY(cudaGetLastError());
-        ++launches;
-    }
-    FGR_CUDA_TRY(cudaMemcpyAsync(ctx->host_pinned, bnd, sizeof(int) * 12, cudaMemcpyDeviceToHost, st));
-    FGR_CUDA_TRY(cudaStreamSynchronize(st));
-    int hb[12];
-    memcpy(hb, ctx->host_pinned, sizeof(hb));
-    const size_t out_bytes = eb * (size_t)G.total;
-    if (m == 0 || hb[0] == INT_MAX) {  // nothing reaches the grid
-        FGR_CUDA_TRY(cudaMemsetAsync(u_dev, 0, out_bytes, st));
-        timer.finish();
-        ctx->timing.last.launches = launches;
-        return FGR_OK;
-    }
+    FGR_CUDA_TRY(cudaGetLastError());
+    return FGR_OK;
+}
+
+}  // namespace
+
+// Node box from the packets' bounds hb[12], widened by margin nodes on every
+// side (a-ranges clipped to the grid-relevant range), and the sizes of the
+// buffers of one reconstruction.
+fgr_status make_box(const fgr_ctx *ctx, const int *hb, int margin, FggcBox *box) {
+    const int D = ctx->d;
+    const Grid &G = ctx->grid;
+    int aglo[3], aghi[3];
+    grid_node_range(ctx, aglo, aghi);
+    FggcBox &x = *box;
+    x = FggcBox{};
+    x.c = base_common(ctx);
+    Common &c = x.c;
+    x.empty = hb[0] == INT_MAX;
+    if (x.empty) return FGR_OK;
     int64_t cells = 1;
     for (int l = 0; l < D; ++l) {
-        c.amin[l] = hb[l * 4 + 0];
-        c.A[l] = hb[l * 4 + 1] - hb[l * 4 + 0] + 1;
-        c.bmin[l] = hb[l * 4 + 2];
-        c.B[l] = hb[l * 4 + 3] - hb[l * 4 + 2] + 1;
+        const int alo = std::max(aglo[l], hb[l * 4 + 0] - margin), ahi = std::min(aghi[l], hb[l * 4 + 1] + margin);
+        c.amin[l] = alo;
+        c.A[l] = ahi - alo + 1;
+        c.bmin[l] = hb[l * 4 + 2] - margin;
+        c.B[l] = hb[l * 4 + 3] - hb[l * 4 + 2] + 1 + 2 * margin;
         cells *= (int64_t)c.A[l] * c.B[l];
         if (cells > (int64_t(1) << 36)) {
             set_error("fggc: node array of more than 2^36 cells");
@@ -519,40 +606,38 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
         c.ra[l] = c.sa[l] / c.row_len;
         c.rb[l] = c.sb[l] / c.row_len;
     }
-    const int64_t rows0 = cells / c.row_len;
-    ctx->timing.last.nodes = cells;
+    x.cells = cells;
+    x.rows0 = cells / c.row_len;
+    // intermediate sizes of the passes (the node box itself is only read)
+    int64_t prodN = 1;
+    for (int l = D - 1; l >= 0; --l) {
+        int64_t pre = 1;
+        for (int j = 0; j < l; ++j) pre *= (int64_t)c.A[j] * c.B[j];
+        x.max_lines = std::max(x.max_lines, pre * prodN * c.A[l]);
+        prodN *= G.n[l];
+        x.maxbuf = std::max(x.maxbuf, prodN * pre);
+    }
+    if (D == 1) x.maxbuf = 0;
+    return FGR_OK;
+}
 
-    // intermediate sizes of the passes
-    int64_t maxbuf = cells;
-    {
-        int64_t prodN = 1;
-        for (int l = D - 1; l >= 0; --l) {
-            prodN *= G.n[l];
-            int64_t pre = 1;
-            for (int j = 0; j < l; ++j) pre *= (int64_t)c.A[j] * c.B[j];
-            maxbuf = std::max(maxbuf, prodN * pre);
-        }
-    }
-    void *W = scratch.get(eb * (size_t)cells);
-    void *buf1 = D > 1 ? scratch.get(eb * (size_t)maxbuf) : nullptr;
-    void *buf2 = D > 1 ? scratch.get(eb * (size_t)maxbuf) : nullptr;
-    uint8_t *flags = (uint8_t *)scratch.get((size_t)rows0);
-    int64_t max_lines = 0;
-    {
-        int64_t prodN = 1;
-        for (int l = D - 1; l >= 0; --l) {
-            int64_t pre = 1;
-            for (int j = 0; j < l; ++j) pre *= (int64_t)c.A[j] * c.B[j];
-            max_lines = std::max(max_lines, pre * prodN * c.A[l]);
-            prodN *= G.n[l];
-        }
-    }
-    int2 *brange = (int2 *)scratch.get(sizeof(int2) * (size_t)max_lines);
-    if (!W || !flags || !brange || (D > 1 && (!buf1 || !buf2))) return FGR_E_NOMEM;
-    FGR_CUDA_TRY(cudaMemsetAsync(W, 0, eb * (size_t)cells, st));
+namespace {
+
+// Clears the node box and runs the coefficient scatter and the grid passes
+// into u_dev (all stream-ordered: no allocation, no host synchronisation).
+template <int D>
+fgr_status enqueue_fggc(fgr_ctx *ctx, const PacketsDev &pk, const FggcBox &box, const FggcBuffers &b, void *u_dev,
+                        cudaStream_t st, StageTimer *timer, int64_t *launches) {
+    const bool fp64 = ctx->opt.precision == FGR_FP64;
+    const Mesh &M = ctx->mesh;
+    const Grid &G = ctx->grid;
+    const Lsa &L = ctx->lsa;
+    const size_t eb = elem_bytes(ctx->opt.precision);
+    const Common &c = box.c;
+    FGR_CUDA_TRY(cudaMemsetAsync(b.W, 0, eb * (size_t)box.cells, st));
     // the scatter marks the rows it reaches; the single row of d = 1 is marked here
-    FGR_CUDA_TRY(cudaMemsetAsync(flags, D == 1 ? 1 : 0, (size_t)rows0, st));
-    timer.mark(&ctx->timing.last.prep_ms);
+    FGR_CUDA_TRY(cudaMemsetAsync(b.flags, D == 1 ? 1 : 0, (size_t)box.rows0, st));
+    if (timer) timer->mark(&ctx->timing.last.prep_ms);
 
     if (fp64) {
         Params64 P{};
@@ -560,7 +645,7 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
         memcpy(P.vr, L.vr, sizeof(P.vr));
         memcpy(P.vi, L.vi, sizeof(P.vi));
         memcpy(P.inv_lam, L.inv_lam, sizeof(P.inv_lam));
-        fgr_status r = launch_coeff_scatter(D, L.n1, st, pk, &P, nullptr, W, flags);
+        fgr_status r = launch_coeff_scatter(D, L.n1, st, pk, &P, nullptr, b.W, b.flags);
         if (r != FGR_OK) return r;
     } else {
         Params32 P{};
@@ -571,14 +656,14 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
                     P.cre[(k * kCheb + i) * kCheb + jj] = L.cheb_re[k][i][jj];
                     P.cim[(k * kCheb + i) * kCheb + jj] = L.cheb_im[k][i][jj];
                 }
-        fgr_status r = launch_coeff_scatter(D, L.n1, st, pk, nullptr, &P, W, flags);
+        fgr_status r = launch_coeff_scatter(D, L.n1, st, pk, nullptr, &P, b.W, b.flags);
         if (r != FGR_OK) return r;
     }
-    ++launches;
-    timer.mark(&ctx->timing.last.scatter_ms);
+    ++*launches;
+    if (timer) timer->mark(&ctx->timing.last.scatter_ms);
 
     // separable passes, last dimension first
-    const void *cur = W;
+    const void *cur = b.W;
     int64_t prodN_after = 1;  // product of N of contracted dimensions
     for (int l = D - 1; l >= 0; --l) {
         PassParams pp{};
@@ -602,29 +687,69 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
         while ((1 << lb) < bmax_abs + 1) ++lb;
         pp.two_pow_b = std::ldexp(1.0, std::max(1, 23 - lb));
         pp.inv_two_pow_b = 1.0 / pp.two_pow_b;
-        const int band = (int)std::ceil(((kPassTile - 1) * G.h[l] + 2 * M.rs) / M.dq) + 3;
         const bool last = l == 0;
-        void *dst = (D == 1) ? u_dev : (cur == buf1 ? buf2 : buf1);
-        fgr_status r = fp64 ? launch_brange<true>(cur, pp.rows, pp.A, pp.B, brange, st)
-                            : launch_brange<false>(cur, pp.rows, pp.A, pp.B, brange, st);
+        void *dst = (D == 1) ? u_dev : (cur == b.buf1 ? b.buf2 : b.buf1);
+        fgr_status r = fp64 ? launch_brange<true>(cur, pp.rows, pp.A, pp.B, b.brange, st)
+                            : launch_brange<false>(cur, pp.rows, pp.A, pp.B, b.brange, st);
         if (r != FGR_OK) return r;
-        ++launches;
+        ++*launches;
         const int64_t target = (int64_t)ctx->num_sms * ctx->tune.pass_ctas_per_sm;
-        r = fp64 ? launch_pass<true>(cur, dst, pp, l == D - 1 ? flags : nullptr, brange, band, target, st)
-                 : launch_pass<false>(cur, dst, pp, l == D - 1 ? flags : nullptr, brange, band, target, st);
+        r = fp64 ? launch_pass<true>(cur, dst, pp, l == D - 1 ? b.flags : nullptr, b.brange, target,
+                                     ctx->tune.pass_tile, st)
+                 : launch_pass<false>(cur, dst, pp, l == D - 1 ? b.flags : nullptr, b.brange, target,
+                                      ctx->tune.pass_tile, st);
         if (r != FGR_OK) return r;
-        ++launches;
+        ++*launches;
         if (D > 1) {
-            void *tdst = last ? u_dev : (dst == buf1 ? buf2 : buf1);
+            void *tdst = last ? u_dev : (dst == b.buf1 ? b.buf2 : b.buf1);
             r = fp64 ? launch_transpose<double2>(dst, tdst, pp.rows, pp.N, st)
                      : launch_transpose<float2>(dst, tdst, pp.rows, pp.N, st);
             if (r != FGR_OK) return r;
-            ++launches;
+            ++*launches;
             cur = tdst;
         }
         prodN_after *= G.n[l];
     }
-    timer.mark(&ctx->timing.last.grid_ms);
+    if (timer) timer->mark(&ctx->timing.last.grid_ms);
+    return FGR_OK;
+}
+
+template <int D>
+fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t st, Scratch &scratch) {
+    const size_t eb = elem_bytes(ctx->opt.precision);
+    StageTimer timer(ctx, st);
+    int64_t launches = 0;
+    const Common c = base_common(ctx);
+    int aglo[3], aghi[3];
+    grid_node_range(ctx, aglo, aghi);
+    int *bnd = (int *)scratch.get(sizeof(int) * 12);
+    if (!bnd) return FGR_E_NOMEM;
+    fgr_status r = launch_bounds_reduction(ctx, pk, c, aglo, aghi, bnd, st);
+    if (r != FGR_OK) return r;
+    launches += pk.m > 0 ? 2 : 1;
+    FGR_CUDA_TRY(cudaMemcpyAsync(ctx->host_pinned, bnd, sizeof(int) * 12, cudaMemcpyDeviceToHost, st));
+    FGR_CUDA_TRY(cudaStreamSynchronize(st));
+    int hb[12];
+    memcpy(hb, ctx->host_pinned, sizeof(hb));
+    FggcBox box;
+    r = make_box(ctx, hb, 0, &box);
+    if (r != FGR_OK) return r;
+    if (box.empty) {  // nothing reaches the grid
+        FGR_CUDA_TRY(cudaMemsetAsync(u_dev, 0, eb * (size_t)ctx->grid.total, st));
+        timer.finish();
+        ctx->timing.last.launches = launches;
+        return FGR_OK;
+    }
+    ctx->timing.last.nodes = box.cells;
+    FggcBuffers b{};
+    b.W = scratch.get(eb * (size_t)box.cells);
+    b.buf1 = D > 1 ? scratch.get(eb * (size_t)box.maxbuf) : nullptr;
+    b.buf2 = D > 1 ? scratch.get(eb * (size_t)box.maxbuf) : nullptr;
+    b.flags = (uint8_t *)scratch.get((size_t)box.rows0);
+    b.brange = (int2 *)scratch.get(sizeof(int2) * (size_t)box.max_lines);
+    if (!b.W || !b.flags || !b.brange || (D > 1 && (!b.buf1 || !b.buf2))) return FGR_E_NOMEM;
+    r = enqueue_fggc<D>(ctx, pk, box, b, u_dev, st, &timer, &launches);
+    if (r != FGR_OK) return r;
     ctx->timing.last.launches = launches;
     timer.finish();
     return FGR_OK;
@@ -646,6 +771,45 @@ fgr_status run_fggc(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_
     case 1: return launch<1>(ctx, pk, u_dev, st, scratch);
     case 2: return launch<2>(ctx, pk, u_dev, st, scratch);
     default: return launch<3>(ctx, pk, u_dev, st, scratch);
+    }
+}
+
+// Node bounds of the packets (per dimension: a min, a max, b min, b max; a
+// clipped to the grid-relevant range) into hb on the host; waits for them.
+fgr_status compute_node_bounds(fgr_ctx *ctx, const PacketsDev &pk, int *bnd_dev, int *hb, cudaStream_t st) {
+    const Common c = base_common(ctx);
+    int aglo[3], aghi[3];
+    grid_node_range(ctx, aglo, aghi);
+    fgr_status r = launch_bounds_reduction(ctx, pk, c, aglo, aghi, bnd_dev, st);
+    if (r != FGR_OK) return r;
+    FGR_CUDA_TRY(cudaMemcpyAsync(ctx->host_pinned, bnd_dev, sizeof(int) * 12, cudaMemcpyDeviceToHost, st));
+    FGR_CUDA_TRY(cudaStreamSynchronize(st));
+    memcpy(hb, ctx->host_pinned, sizeof(int) * 12);
+    return FGR_OK;
+}
+
+// Planned reconstruction: the node box and the buffers come from a plan; the
+// packets' bounds are recomputed on the device and compared with the box
+// (overflow flag), so nothing waits for the host.
+fgr_status run_fggc_planned(fgr_ctx *ctx, const PacketsDev &pk, const FggcBox &box, const FggcBuffers &b,
+                            int *bnd, int *overflow, void *u_dev, cudaStream_t st) {
+    const Common c = base_common(ctx);
+    int aglo[3], aghi[3];
+    grid_node_range(ctx, aglo, aghi);
+    FGR_CUDA_TRY(cudaMemsetAsync(overflow, 0, sizeof(int), st));
+    fgr_status r = launch_bounds_reduction(ctx, pk, c, aglo, aghi, bnd, st);
+    if (r != FGR_OK) return r;
+    if (box.empty) {
+        FGR_CUDA_TRY(cudaMemsetAsync(u_dev, 0, elem_bytes(ctx->opt.precision) * (size_t)ctx->grid.total, st));
+        return FGR_OK;
+    }
+    box_check_kernel<<<1, 32, 0, st>>>(bnd, ctx->d, box.c, overflow);
+    FGR_CUDA_TRY(cudaGetLastError());
+    int64_t launches = 0;
+    switch (ctx->d) {
+    case 1: return enqueue_fggc<1>(ctx, pk, box, b, u_dev, st, nullptr, &launches);
+    case 2: return enqueue_fggc<2>(ctx, pk, box, b, u_dev, st, nullptr, &launches);
+    default: return enqueue_fggc<3>(ctx, pk, box, b, u_dev, st, nullptr, &launches);
     }
 }
 
@@ -773,7 +937,7 @@ extern "C" fgr_status fgr_reconstruct_fggc_noalloc(fgr_ctx *ctx, const fgr_packe
     FGR_CUDA_TRY(cudaMemcpyAsync(bnd, ctx->host_pinned, sizeof(init), cudaMemcpyHostToDevice, st));
     const int64_t m = pk->m;
     if (m > 0) {
-        bounds_kernel<1><<<(unsigned)((m + 255) / 256), 256, 0, st>>>(pk->q, pk->p, pk->a, m, c, aglo, aghi,
+        bounds_kernel<1><<<bounds_blocks(ctx, m), 256, 0, st>>>(pk->q, pk->p, pk->a, m, c, aglo, aghi,
                                                                      0, -1, 0, -1, bnd);
         FGR_CUDA_TRY(cudaGetLastError());
     }
@@ -842,10 +1006,9 @@ extern "C" fgr_status fgr_reconstruct_fggc_noalloc(fgr_ctx *ctx, const fgr_packe
     while ((1 << lb) < bmax_abs + 1) ++lb;
     pp.two_pow_b = std::ldexp(1.0, std::max(1, 23 - lb));
     pp.inv_two_pow_b = 1.0 / pp.two_pow_b;
-    const int band = (int)std::ceil(((kPassTile - 1) * G.h[0] + 2 * M.rs) / M.dq) + 3;
     const int64_t target = (int64_t)ctx->num_sms * ctx->tune.pass_ctas_per_sm;
-    rc = fp64 ? launch_pass<true>(W, u_out, pp, flags, nullptr, band, target, st)
-              : launch_pass<false>(W, u_out, pp, flags, nullptr, band, target, st);
+    rc = fp64 ? launch_pass<true>(W, u_out, pp, flags, nullptr, target, ctx->tune.pass_tile, st)
+              : launch_pass<false>(W, u_out, pp, flags, nullptr, target, ctx->tune.pass_tile, st);
     if (rc != FGR_OK) return rc;
     if (!stream) FGR_CUDA_TRY(cudaStreamSynchronize(st));
     return FGR_OK;

@@ -30,6 +30,35 @@ struct Params32 {
     float cre[kMaxN1 * kCheb * kCheb], cim[kMaxN1 * kCheb * kCheb];
 };
 
+// Node box of one FGGC reconstruction and the sizes of its buffers.
+struct FggcBox {
+    Common c;               // constants and box (amin, A, bmin, B, strides)
+    int64_t cells = 0;      // node cells
+    int64_t rows0 = 0;      // rows of the first grid pass
+    int64_t maxbuf = 0;     // elements of each pass buffer (d > 1)
+    int64_t max_lines = 0;  // (row, a) lines of the b-range scan
+    bool empty = true;      // no packet reaches the grid
+};
+
+struct FggcBuffers {
+    void *W = nullptr, *buf1 = nullptr, *buf2 = nullptr;
+    uint8_t *flags = nullptr;
+    int2 *brange = nullptr;
+};
+
+// Box from the packets' node bounds hb[12] (per dimension: a min, a max, b min,
+// b max), widened by margin nodes on every side.
+fgr_status make_box(const fgr_ctx *ctx, const int *hb, int margin, FggcBox *box);
+
+// Node bounds of the packets into hb[12] on the host (waits for them).
+fgr_status compute_node_bounds(fgr_ctx *ctx, const PacketsDev &pk, int *bnd_dev, int *hb, cudaStream_t st);
+
+// FGGC into u_dev with a planned box and buffers: stream-ordered only; sets
+// *overflow (device) when the packets' nodes leave the box (their
+// contributions outside it are then missing).  bnd: 12 device ints.
+fgr_status run_fggc_planned(fgr_ctx *ctx, const PacketsDev &pk, const FggcBox &box, const FggcBuffers &b,
+                            int *bnd, int *overflow, void *u_dev, cudaStream_t st);
+
 // Launches the coefficient + scatter kernel (K3+K4) for dimension d, one
 // thread per packet; exactly one of p64 / p32 is non-NULL.
 fgr_status launch_coeff_scatter(int d, int n1, cudaStream_t st, const PacketsDev &pk, const Params64 *p64,

@@ -54,6 +54,7 @@ struct Timing {
 struct Tuning {
     int direct_ctas_per_sm = 8;  // direct sum: tiles x slices >= this x SMs
     int pass_ctas_per_sm = 16;   // grid passes: rows x tiles x b-slices >= this x SMs
+    int pass_tile = 0;           // grid points per grid-pass CTA: 32, 128, or 0 (by the band width)
 };
 
 // Seeds a new context's tuning from the process-wide table (autotune.cu).

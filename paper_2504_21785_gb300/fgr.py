@@ -93,10 +93,15 @@ SIGNATURES = {
     "fgr_reconstruct_fggc": (ctypes.c_int, [vp, P(fgr_packets), vp, vp]),
     "fgr_reconstruct_fggc_noalloc": (ctypes.c_int, [vp, P(fgr_packets), vp, vp]),
     "fgr_reconstruct_direct_batch": (ctypes.c_int, [ctypes.c_int32, P(vp), P(P(fgr_packets)), P(vp), vp]),
+    "fgr_fggc_plan_create": (ctypes.c_int, [vp, P(fgr_packets), ctypes.c_int32, P(vp), vp]),
+    "fgr_reconstruct_fggc_planned": (ctypes.c_int, [vp, vp, P(fgr_packets), vp, vp]),
+    "fgr_fggc_plan_overflow": (ctypes.c_int, [vp, P(ctypes.c_int32)]),
+    "fgr_fggc_plan_info": (ctypes.c_int, [vp, P(ctypes.c_int64), P(ctypes.c_int32)]),
+    "fgr_fggc_plan_destroy": (None, [vp]),
     "fgr_get_info": (ctypes.c_int, [vp, P(fgr_info)]),
     "fgr_autotune": (ctypes.c_int, [vp, P(fgr_packets), vp, ctypes.c_int32, vp]),
-    "fgr_get_tuning": (ctypes.c_int, [vp, P(ctypes.c_int32), P(ctypes.c_int32)]),
-    "fgr_set_tuning": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.c_int32]),
+    "fgr_get_tuning": (ctypes.c_int, [vp, P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32)]),
+    "fgr_set_tuning": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "fgr_set_timing": (ctypes.c_int, [vp, ctypes.c_int32]),
     "fgr_get_stats": (ctypes.c_int, [vp, P(fgr_stats)]),
     "fgr_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int32, P(vp)]),
@@ -158,7 +163,7 @@ def _ptr(x):
 def make_packets(q, p, s, a) -> fgr_packets:
     """fgr_packets view of q (d,M), p (d,M), s (M,), a (2,M) float64 arrays/tensors.
 
-    The caller keeps the arrays alive for the duration of the call."""
+    The view holds references to the arrays, so they live as long as it does."""
     pq, dq = _ptr(q)
     pp, dp = _ptr(p)
     ps, ds = _ptr(s)
@@ -166,7 +171,9 @@ def make_packets(q, p, s, a) -> fgr_packets:
     if len({dq, dp, ds, da}) != 1:
         raise ValueError("packet arrays must all live on the host or all on the device")
     m = int(s.shape[0])
-    return fgr_packets(m, pq, pp, ps, pa, dq, 0)
+    view = fgr_packets(m, pq, pp, ps, pa, dq, 0)
+    view._arrays = (q, p, s, a)
+    return view
 
 
 def make_grid(grid: dict) -> fgr_grid:
@@ -242,6 +249,37 @@ def fgr_reconstruct_direct_batch(ctxs, packets, u_outs, stream=None):
     return _check(load().fgr_reconstruct_direct_batch(n, c_ctx, c_pk, c_u, _stream_handle(stream)))
 
 
+def fgr_fggc_plan_create(ctx, packets: fgr_packets, margin: int = 2, stream=None):
+    """Plan handle (free with fgr_fggc_plan_destroy)."""
+    out = vp()
+    _check(load().fgr_fggc_plan_create(ctx, ctypes.byref(packets), int(margin), ctypes.byref(out),
+                                       _stream_handle(stream)))
+    return out.value
+
+
+def fgr_reconstruct_fggc_planned(ctx, plan, packets: fgr_packets, u_out, stream=None):
+    return _check(load().fgr_reconstruct_fggc_planned(ctx, plan, ctypes.byref(packets), _ptr(u_out)[0],
+                                                      _stream_handle(stream)))
+
+
+def fgr_fggc_plan_overflow(plan) -> bool:
+    v = ctypes.c_int32()
+    _check(load().fgr_fggc_plan_overflow(plan, ctypes.byref(v)))
+    return bool(v.value)
+
+
+def fgr_fggc_plan_info(plan):
+    """(node cells, empty)."""
+    n, e = ctypes.c_int64(), ctypes.c_int32()
+    _check(load().fgr_fggc_plan_info(plan, ctypes.byref(n), ctypes.byref(e)))
+    return n.value, bool(e.value)
+
+
+def fgr_fggc_plan_destroy(plan):
+    if plan:
+        load().fgr_fggc_plan_destroy(plan)
+
+
 def fgr_reconstruct_fggc(ctx, packets: fgr_packets, u_out, stream=None):
     return _check(load().fgr_reconstruct_fggc(ctx, ctypes.byref(packets), _ptr(u_out)[0],
                                               _stream_handle(stream)))
@@ -258,13 +296,14 @@ def fgr_autotune(ctx, packets: fgr_packets, u_out, methods: int = 3, stream=None
 
 
 def fgr_get_tuning(ctx):
-    a, b = ctypes.c_int32(), ctypes.c_int32()
-    _check(load().fgr_get_tuning(ctx, ctypes.byref(a), ctypes.byref(b)))
-    return a.value, b.value
+    """(direct CTAs per SM, grid-pass CTAs per SM, grid-pass tile)."""
+    a, b, t = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().fgr_get_tuning(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(t)))
+    return a.value, b.value, t.value
 
 
-def fgr_set_tuning(ctx, direct_ctas_per_sm: int, pass_ctas_per_sm: int):
-    return _check(load().fgr_set_tuning(ctx, int(direct_ctas_per_sm), int(pass_ctas_per_sm)))
+def fgr_set_tuning(ctx, direct_ctas_per_sm: int, pass_ctas_per_sm: int, pass_tile: int = 0):
+    return _check(load().fgr_set_tuning(ctx, int(direct_ctas_per_sm), int(pass_ctas_per_sm), int(pass_tile)))
 
 
 def fgr_get_info(ctx) -> fgr_info:

@@ -40,8 +40,8 @@ def test_autotune_picks_candidates_and_keeps_results(fgr):
         fgr.fgr_reconstruct_fggc(ctx.handle, packets, ref_f)
         scratch = torch.zeros_like(ref_d)
         fgr.fgr_autotune(ctx.handle, packets, scratch, 3)
-        a, b = fgr.fgr_get_tuning(ctx.handle)
-        assert a in (2, 4, 8, 16, 32) and b in (4, 8, 16, 32, 64)
+        a, b, t = fgr.fgr_get_tuning(ctx.handle)
+        assert a in (2, 4, 8, 16, 32) and b in (4, 8, 16, 32, 64) and t in (32, 128)
         got_d = torch.zeros_like(ref_d)
         got_f = torch.zeros_like(ref_d)
         fgr.fgr_reconstruct_direct(ctx.handle, packets, got_d)
@@ -52,11 +52,21 @@ def test_autotune_picks_candidates_and_keeps_results(fgr):
             assert np.linalg.norm(g - r) <= 1e-5 * np.linalg.norm(r)
         # a new context of the same class starts from the tuned values
         with fgr.Context(1, grid, 1 / 512, fgr.make_options(precision=fgr.FGR_FP32)) as ctx2:
-            assert fgr.fgr_get_tuning(ctx2.handle) == (a, b)
+            assert fgr.fgr_get_tuning(ctx2.handle) == (a, b, t)
         with pytest.raises(fgr.FgrError):
             fgr.fgr_set_tuning(ctx.handle, 0, 16)
-        fgr.fgr_set_tuning(ctx.handle, 3, 5)
-        assert fgr.fgr_get_tuning(ctx.handle) == (3, 5)
+        with pytest.raises(fgr.FgrError):
+            fgr.fgr_set_tuning(ctx.handle, 4, 16, 64)
+        fgr.fgr_set_tuning(ctx.handle, 3, 5, 32)
+        assert fgr.fgr_get_tuning(ctx.handle) == (3, 5, 32)
+        # both tile widths give the same result
+        for tile in (32, 128):
+            fgr.fgr_set_tuning(ctx.handle, 8, 16, tile)
+            got = torch.zeros_like(ref_d)
+            fgr.fgr_reconstruct_fggc(ctx.handle, packets, got)
+            torch.cuda.synchronize()
+            g, r = got.cpu().numpy(), ref_f.cpu().numpy()
+            assert np.linalg.norm(g - r) <= 1e-5 * np.linalg.norm(r)
 
 
 def test_tuning_file_persists_across_processes(tmp_path):
@@ -81,5 +91,5 @@ def test_tuning_file_persists_across_processes(tmp_path):
                            capture_output=True, text=True, timeout=300)
         assert r.returncode == 0, r.stderr
         outs.append([line for line in r.stdout.splitlines() if line.startswith("TUNING")][0])
-    assert path.exists() and len(path.read_text().split()) == 6
+    assert path.exists() and len(path.read_text().split()) == 7
     assert outs[0] == outs[1]
