@@ -275,15 +275,6 @@ __device__ __forceinline__ void rk4_body(double *__restrict__ q, double *__restr
     a[m + j] = ar * wi + ai * wr;
 }
 
-// 1-D: at most 80 registers, so that 6 CTAs (24 warps) share an SM and hide
-// the FP64 pipe's latency; 2-D and 3-D keep the compiler's register budget.
-template <int D, int KIND>
-__global__ void __launch_bounds__(128, 6) rk4_kernel_1d(double *__restrict__ q, double *__restrict__ p,
-                                                        double *__restrict__ s, double *__restrict__ a,
-                                                        int64_t m, Pot v, int64_t nsteps, double h) {
-    rk4_body<D, KIND>(q, p, s, a, m, v, nsteps, h);
-}
-
 template <int D, int KIND>
 __global__ void __launch_bounds__(128) rk4_kernel(double *__restrict__ q, double *__restrict__ p,
                                                   double *__restrict__ s, double *__restrict__ a, int64_t m,
@@ -291,13 +282,12 @@ __global__ void __launch_bounds__(128) rk4_kernel(double *__restrict__ q, double
     rk4_body<D, KIND>(q, p, s, a, m, v, nsteps, h);
 }
 
+// (A 1-D variant capped at 80 registers for 6 CTAs per SM ran 4% slower: the
+// FP64 pipe stays 86% busy and the cap adds recomputation.)
 template <int D, int KIND>
 void launch_rk4(unsigned blocks, int threads, cudaStream_t st, double *q, double *p, double *s, double *a,
                 int64_t m, const Pot &v, int64_t nsteps, double h) {
-    if constexpr (D == 1)
-        rk4_kernel_1d<D, KIND><<<blocks, threads, 0, st>>>(q, p, s, a, m, v, nsteps, h);
-    else
-        rk4_kernel<D, KIND><<<blocks, threads, 0, st>>>(q, p, s, a, m, v, nsteps, h);
+    rk4_kernel<D, KIND><<<blocks, threads, 0, st>>>(q, p, s, a, m, v, nsteps, h);
 }
 
 template <int D>
