@@ -167,6 +167,10 @@ def run_ours(args):
         stats_launches()
         if ev:
             ev[2].record(stream)
+        fgr.fgr_reconstruct_direct(ctx.handle, packets, u_d, stream)
+        stats_launches()
+        if ev:
+            ev[3].record(stream)
 
     for _ in range(args.warmup):
         step()
@@ -175,7 +179,7 @@ def run_ours(args):
     fgr.fgr_autotune(ctx.handle, packets, u_d, 3, stream)
     tuning = fgr.fgr_get_tuning(ctx.handle)
     launches["n"] = 0
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -188,20 +192,9 @@ def run_ours(args):
         torch.distributed.barrier()
     prop_ms = [e[0].elapsed_time(e[1]) for e in evs]
     fggc_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    step_ms = [a + b for a, b in zip(prop_ms, fggc_ms)]
+    direct_ms = [e[2].elapsed_time(e[3]) for e in evs]
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
     gpu_launches = launches["n"]
-
-    # direct sum on the same propagated batch (A2), same stream, L2 flushed between runs
-    dev_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
-    for _ in range(max(1, args.warmup)):
-        fgr.fgr_reconstruct_direct(ctx.handle, packets, u_d, stream)
-    for i in range(args.steps):
-        flush.zero_()
-        dev_ev[i][0].record(stream)
-        fgr.fgr_reconstruct_direct(ctx.handle, packets, u_d, stream)
-        dev_ev[i][1].record(stream)
-    torch.cuda.synchronize()
-    direct_ms = [e[0].elapsed_time(e[1]) for e in dev_ev]
     ud, uf = u_d.cpu().numpy(), u_f.cpu().numpy()
     rel = float(np.linalg.norm(uf - ud) / max(np.linalg.norm(ud), 1e-300))
 
@@ -224,6 +217,7 @@ def run_ours(args):
     host = {k: np.ascontiguousarray(pk[k]) for k in "qpsa"}
     hwork = {k: np.empty_like(v) for k, v in host.items()}
     hu = np.zeros(shape, dtype=np.complex64 if prec == fgr.FGR_FP32 else np.complex128)
+    hu_d = np.zeros_like(hu)
     e2e_ms = []
     for i in range(args.warmup + args.steps):
         for k in "qpsa":
@@ -233,12 +227,13 @@ def run_ours(args):
         t0 = time.perf_counter()
         fgr.fgr_propagate(ctx.handle, hp, pot, t_final, dt)       # H2D, RK4, D2H of the packets
         fgr.fgr_reconstruct_fggc(ctx.handle, hp, hu)               # H2D of the packets, D2H of u
+        fgr.fgr_reconstruct_direct(ctx.handle, hp, hu_d)           # H2D of the packets, D2H of u
         t1 = time.perf_counter()
         if i >= args.warmup:
             e2e_ms.append((t1 - t0) * 1e3)
     pbytes = sum(v.nbytes for v in host.values())
-    h2d = 2 * pbytes
-    d2h = pbytes + hu.nbytes
+    h2d = 3 * pbytes
+    d2h = pbytes + hu.nbytes + hu_d.nbytes
 
     def agg(xs):
         return max_over_ranks(statistics.mean(xs), world)
@@ -270,7 +265,7 @@ def run_ours(args):
             "data": "synthetic (seeded analytic WKB data, cut-off FFT initial decomposition)",
             "config": {"workload": WORKLOAD, "packets_per_gpu": M, "grid": list(shape), "eps": eps,
                        "t": t_final, "dt": dt, "strategy": "Q4P2 cq=1/2 cp=pi/8",
-                       "step": "propagate (A1) + fggc reconstruct (A3-A5)",
+                       "step": "propagate (A1) + fggc reconstruct (A3-A5) + direct sum (A2), same batch",
                        "l2": "flushed (512 MiB write) between timed steps", "parallelism": "replicas",
                        "autotuned": {"direct_ctas_per_sm": tuning[0], "grid_pass_ctas_per_sm": tuning[1],
                                      "grid_pass_tile": tuning[2]}},
@@ -639,10 +634,10 @@ def serving_bench(args, device_index: int):
 def cpu_baseline(w, sample: int):
     """The FP64 oracle, as it stands, on a bounded sample of the workload:
     `sample` packets propagated (C RK4, OpenMP) and reconstructed by the
-    oracle's FGGC on the full output grid."""
+    oracle's FGGC and by its direct sum on the full output grid."""
     import numpy as np
 
-    from oracle import fggc, lsa, trajectories
+    from oracle import fga, fggc, lsa, trajectories
     pk = w["packets"]
     M = pk["s"].size
     rng = np.random.default_rng(0)
@@ -652,14 +647,16 @@ def cpu_baseline(w, sample: int):
     t0 = time.perf_counter()
     prop = trajectories.propagate(sub, w["potential"], w["t"], w["dt"])
     t1 = time.perf_counter()
-    fggc.reconstruct(prop, w["grid"], w["eps"], mesh.dq, mesh.dp, lsa.Strategy(nq=4, np_=2),
-                     R=6 if w["precision"] == "fp32" else 8)
+    R = 6 if w["precision"] == "fp32" else 8
+    fggc.reconstruct(prop, w["grid"], w["eps"], mesh.dq, mesh.dp, lsa.Strategy(nq=4, np_=2), R=R)
     t2 = time.perf_counter()
+    fga.direct_sum(prop, w["grid"], w["eps"], mesh.dq, mesh.dp, R=R)
+    t3 = time.perf_counter()
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": idx.size / (t2 - t0), "unit": "packets/s", "cores": cores, "kind": "oracle",
+    return {"value": idx.size / (t3 - t0), "unit": "packets/s", "cores": cores, "kind": "oracle",
             "sample": "%d of %d packets (uniform sample, seed 0): propagate %.2f s (C RK4, OpenMP %d threads) "
-                      "+ FGGC reconstruct %.2f s (numpy, 1 thread) on the full grid"
-                      % (idx.size, M, t1 - t0, cores, t2 - t1)}
+                      "+ FGGC reconstruct %.2f s + direct sum %.2f s (numpy, 1 thread) on the full grid"
+                      % (idx.size, M, t1 - t0, cores, t2 - t1, t3 - t2)}
 
 
 def run_reference(args):
@@ -681,7 +678,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "packets_per_step": args.ref_sample,
-                       "step": "propagate + fggc reconstruct of a packet sample (oracle)"},
+                       "step": "propagate + fggc reconstruct + direct sum of a packet sample (oracle)"},
             "cpu_baseline": {"value": value, "unit": "packets/s", "cores": last["cores"],
                              "kind": "oracle", "sample": last["sample"]},
             "e2e": {"value": value, "unit": "packets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
