@@ -218,3 +218,44 @@ def m_lsa(strat: Strategy, n_scan: int = 41, refine: bool = True) -> float:
                          bounds=[(0.0, 1.0), (0.0, 1.0)], method="L-BFGS-B")
             best = max(best, -float(r.fun))
     return best
+
+
+def e_h1(s, t, strat: Strategy, eps: float, npts: int = 8001) -> float:
+    """The H1 error ratio of Remark 3 (eq. 3.add8), 1-D, at (Q, P) = (s dq, t dp):
+    ||d/dx (G - sum_k c_k G_k)||_L2 / ||G||_H1 with the LSA coefficients c_k of
+    coefficients_1d (the L2 optimum), by trapezoid quadrature of the definition
+    at the given eps (||G||_H1^2 = ||G||^2 + ||G'||^2)."""
+    sig = math.sqrt(eps)
+    dq, dp = strat.cq * sig, strat.cp * sig
+    Q, P = s * dq, t * dp
+    a0, b0, c = coefficients_1d(np.array([Q]), np.array([P]), dq, dp, strat)
+    x = np.linspace(Q - 14 * sig - 2 * dq, Q + 14 * sig + 3 * dq, npts)
+    w = x[1] - x[0]
+
+    def G(Qc, Pc):
+        return np.exp(1j * Pc * (x - Qc) / eps - (x - Qc) ** 2 / (2 * eps))
+
+    def dG(Qc, Pc):  # d/dx of G(x; Qc, Pc)
+        return (1j * Pc - (x - Qc)) / eps * G(Qc, Pc)
+
+    r = dG(Q, P)
+    for k, (da, db) in enumerate(strat.shifts):
+        r = r - c[0, k] * dG((a0[0] + da) * dq, (b0[0] + db) * dp)
+    h1 = math.sqrt(w * (np.sum(np.abs(G(Q, P)) ** 2) + np.sum(np.abs(dG(Q, P)) ** 2)))
+    return math.sqrt(w * np.sum(np.abs(r) ** 2)) / h1
+
+
+def m_lsa_h1(strat: Strategy, eps: float, n_scan: int = 11, refine: bool = True) -> float:
+    """sup of e_h1 over the cell (Q, P) in [0, dq] x [0, dp] (eq. 3.add8): grid
+    scan, then a bounded local maximisation from the best scan points."""
+    g = np.linspace(0.0, 1.0, n_scan)
+    vals = np.array([[e_h1(a, b, strat, eps) for b in g] for a in g])
+    best = float(vals.max())
+    if refine:
+        from scipy.optimize import minimize
+        for idx in np.argsort(vals.ravel())[::-1][:3]:
+            i, j = np.unravel_index(idx, vals.shape)
+            r = minimize(lambda z: -e_h1(z[0], z[1], strat, eps), np.array([g[i], g[j]]),
+                         bounds=[(0.0, 1.0), (0.0, 1.0)], method="L-BFGS-B")
+            best = max(best, -float(r.fun))
+    return best

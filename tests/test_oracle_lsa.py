@@ -299,3 +299,35 @@ def test_factored_pseudo_inverse_is_at_the_conditioning_floor():
         worst_m = max(worst_m, math.sqrt(max(e_mat ** 2 - e_opt ** 2, 0)))
     assert worst_f <= 1e3 * floor
     assert worst_m > 10 * worst_f
+
+
+def _golden_h1():
+    rows = []
+    with open(os.path.join(GOLDEN, "m_lsa_h1_table.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                k, *vals = line.split()
+                rows.append((int(k), [float(v) for v in vals]))
+    return rows
+
+
+def test_table_mlsa1_h1_error():
+    # eq. 3.add8 by quadrature of its definition with the oracle's coefficients.
+    # Q2P2 (a well-conditioned Gram) reproduces the printed column to 1% at
+    # every eps, which also pins the phase conventions of the coefficients (a
+    # wrong conjugation or shift-back sign leaves an O(1) gradient residual);
+    # for the larger sets (Gram condition numbers >= 1e9) the printed values
+    # carry the rounding of the paper's solve and bound the oracle's from above.
+    rows = _golden_h1()
+    assert len(rows) == 6
+    q2p2 = lsa.Strategy(nq=2, np_=2)
+    mine = []
+    for k, vals in rows:
+        m = lsa.m_lsa_h1(q2p2, 2.0 ** -k)
+        mine.append(m)
+        assert abs(m / vals[0] - 1) <= 0.01, (k, m, vals[0])
+    assert max(mine) / min(mine) - 1 <= 0.02  # eps-independent
+    k, vals = rows[0]
+    for (nq, np_), printed in zip(((4, 2), (2, 4), (4, 4)), vals[1:]):
+        m = lsa.m_lsa_h1(lsa.Strategy(nq=nq, np_=np_), 2.0 ** -k, n_scan=6, refine=False)
+        assert 0 < m <= printed, (nq, np_, m, printed)
