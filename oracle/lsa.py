@@ -221,7 +221,7 @@ def m_lsa(strat: Strategy, n_scan: int = 41, refine: bool = True) -> float:
 
 
 def e_h1(s, t, strat: Strategy, eps: float, npts: int = 8001) -> float:
-    """The H1 error ratio of Remark 3 (eq. 3.add8), 1-D, at (Q, P) = (s dq, t dp):
+    """The H1 error ratio of Remark 5 (eq. 3.add8), 1-D, at (Q, P) = (s dq, t dp):
     ||d/dx (G - sum_k c_k G_k)||_L2 / ||G||_H1 with the LSA coefficients c_k of
     coefficients_1d (the L2 optimum), by trapezoid quadrature of the definition
     at the given eps (||G||_H1^2 = ||G||^2 + ||G'||^2)."""
