@@ -189,9 +189,10 @@ fgr_status fgr_reconstruct_fggc(fgr_ctx *ctx, const fgr_packets *pk, void *u_out
  * flag and node array) in one static device array of 8 MiB that the library
  * reserves on every device that loads it, for as long as the process lives.
  * Limits: 1-D contexts only; packets and u_out must be device memory; the node
- * array may hold at most (8 MiB - 512 B) / 16 complex128 or / 8 complex64
- * cells; larger problems return FGR_E_CAPACITY with the required size in
- * fgr_last_error() (use fgr_reconstruct_fggc for them).
+ * array (16 bytes per complex128 or 8 per complex64 cell) and the grid pass's
+ * tables (8 bytes per node of the box's a-range and per grid point) must fit
+ * in 8 MiB - 512 B together; larger problems return FGR_E_CAPACITY with the
+ * required sizes in fgr_last_error() (use fgr_reconstruct_fggc for them).
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * Every call clears and reuses the same array, so calls whose work overlaps on

@@ -599,7 +599,7 @@ struct fgr_fggc_plan {
     int *bnd = nullptr;       // device: the packets' node bounds of the last call
     int *overflow = nullptr;  // device: set when they left the box
     void release() {
-        void *ptrs[] = {buf.W, buf.buf1, buf.buf2, buf.flags, buf.brange, bnd, overflow};
+        void *ptrs[] = {buf.W, buf.buf1, buf.buf2, buf.flags, buf.brange, buf.tables, bnd, overflow};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         buf = FggcBuffers{};
@@ -677,6 +677,7 @@ fgr_status fgr_fggc_plan_create(fgr_ctx *ctx, const fgr_packets *pk, int32_t mar
             if (e == cudaSuccess && ctx->d > 1) e = cudaMalloc(&pl->buf.buf2, eb * (size_t)b.maxbuf);
             if (e == cudaSuccess) e = cudaMalloc((void **)&pl->buf.flags, (size_t)b.rows0);
             if (e == cudaSuccess) e = cudaMalloc((void **)&pl->buf.brange, sizeof(int2) * (size_t)b.max_lines);
+            if (e == cudaSuccess) e = cudaMalloc(&pl->buf.tables, 8 * (size_t)b.table_entries);
             if (e != cudaSuccess) return fail(e);
         }
         *out = pl.release();

@@ -152,11 +152,45 @@ inline int pass_band(int tp, double h, double rs, double dq) {
     return (int)std::ceil(((tp - 1) * h + 2 * rs) / dq) + 3;
 }
 
+// Per-pass tables shared by all rows: the grid window of every node a (FP64
+// rule of include/fgr.h), the FP64-reduced phase increment of every grid point
+// m split into an exact FP32 pair, and the node band of every tile of TP
+// points.  They replace per-CTA FP64 divisions and reductions.
+struct PassTables {
+    int2 *win;     // [A]: (first, last) grid point of node amin + i
+    float2 *ph;    // [N]: (hi, lo) turns of e^{i dp x_m / eps} per unit b
+    int2 *band;    // [tiles]: (a_lo, a_hi) of tile t (a_lo > a_hi: empty)
+};
+
+__global__ void pass_tables_kernel(PassParams pp, int tp, int64_t tiles, PassTables t) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < pp.A) {
+        int64_t wlo, whi;
+        window_bounds((double)(pp.amin + i) * pp.dq, pp.rs, pp.lo, pp.h, pp.N, &wlo, &whi);
+        t.win[i] = make_int2((int)wlo, (int)whi);
+    }
+    if (i < pp.N) {
+        const double xm = grid_x(pp.lo, pp.h, i);
+        double phi = pp.phi_scale * xm;
+        phi -= rint(phi);
+        const double phi_hi = rint(phi * pp.two_pow_b) * pp.inv_two_pow_b;
+        t.ph[i] = make_float2((float)phi_hi, (float)(phi - phi_hi));
+    }
+    if (i < tiles) {
+        const int64_t m0 = i * tp, m1 = min(m0 + tp - 1, pp.N - 1);
+        const double x0 = grid_x(pp.lo, pp.h, m0), x1 = grid_x(pp.lo, pp.h, m1);
+        const int a_lo = max(pp.amin, (int)ceil((x0 - pp.rs) / pp.dq) - 1);
+        const int a_hi = min(pp.amin + pp.A - 1, (int)floor((x1 + pp.rs) / pp.dq) + 1);
+        t.band[i] = make_int2(a_lo, a_hi);
+    }
+}
+
 template <bool FP64, int MAXBAND, int TP>
 __global__ void __launch_bounds__(TP) grid_pass_kernel(const void *__restrict__ in_v,
                                                                  void *__restrict__ out_v, PassParams pp,
                                                                  const uint8_t *__restrict__ flags,
-                                                                 const int2 *__restrict__ brange) {
+                                                                 const int2 *__restrict__ brange,
+                                                                 const PassTables tab) {
     using Real = typename std::conditional<FP64, double, float>::type;
     using C2 = typename std::conditional<FP64, double2, float2>::type;
     __shared__ __align__(16) C2 sw[MAXBAND][kCB];
@@ -177,10 +211,8 @@ __global__ void __launch_bounds__(TP) grid_pass_kernel(const void *__restrict__ 
     zero.x = 0;
     zero.y = 0;
     const bool split = gridDim.z > 1;  // slices add into a zeroed output
-    const int64_t m1 = min(m0 + TP - 1, pp.N - 1);
-    const double x0 = grid_x(pp.lo, pp.h, m0), x1 = grid_x(pp.lo, pp.h, m1);
-    const int a_lo = max(pp.amin, (int)ceil((x0 - pp.rs) / pp.dq) - 1);
-    const int a_hi = min(pp.amin + pp.A - 1, (int)floor((x1 + pp.rs) / pp.dq) + 1);
+    const int2 bnd = tab.band[blockIdx.y];
+    const int a_lo = bnd.x, a_hi = bnd.y;
     const int nb_total = a_hi - a_lo + 1;
     // occupied b-range: the union over the band of the per-node ranges
     int ulo = 0, uhi = pp.B - 1;
@@ -218,14 +250,13 @@ __global__ void __launch_bounds__(TP) grid_pass_kernel(const void *__restrict__ 
     float phf[kPassPts], plf[kPassPts];
 #pragma unroll
     for (int r = 0; r < kPassPts; ++r) {
-        xm[r] = grid_x(pp.lo, pp.h, valid[r] ? mm[r] : m0);
-        // e^{i b dp x_m / eps}: turns per unit b, reduced in FP64
-        double phi = pp.phi_scale * xm[r];
-        phi -= rint(phi);
-        const double phi_hi = rint(phi * pp.two_pow_b) * pp.inv_two_pow_b;
-        phf[r] = (float)phi_hi;
-        plf[r] = (float)(phi - phi_hi);
-        th64[r] = pp.dp_over_eps * xm[r];
+        const int64_t mr = valid[r] ? mm[r] : m0;
+        xm[r] = grid_x(pp.lo, pp.h, mr);
+        // e^{i b dp x_m / eps}: turns per unit b, reduced in FP64 (pass table)
+        const float2 ph = tab.ph[mr];
+        phf[r] = ph.x;
+        plf[r] = ph.y;
+        th64[r] = FP64 ? pp.dp_over_eps * xm[r] : 0.0;
     }
     const float cef = (float)(pp.neg_half_inv_eps * 1.4426950408889634);  // log2(e) / (-2 eps)
     const float dqf = (float)pp.dq;
@@ -244,10 +275,9 @@ __global__ void __launch_bounds__(TP) grid_pass_kernel(const void *__restrict__ 
         // each node's window once per CTA (FP64, the rule of include/fgr.h)
         __syncthreads();
         for (int i = threadIdx.x; i < nb; i += TP) {
-            int64_t wlo, whi;
-            window_bounds((double)(a_first + i) * pp.dq, pp.rs, pp.lo, pp.h, pp.N, &wlo, &whi);
-            swlo[i] = (int)wlo;
-            swhi[i] = (int)whi;
+            const int2 w = tab.win[a_first - pp.amin + i];
+            swlo[i] = w.x;
+            swhi[i] = w.y;
         }
         __syncthreads();
         Real g[kPassPts][MAXBAND];
@@ -428,9 +458,14 @@ fgr_status launch_brange(const void *in, int64_t rows, int A, int B, int2 *out, 
     return FGR_OK;
 }
 
+// Entries of the pass tables for a pass over N points and A nodes (int2 /
+// float2 units): node windows, point phases and tile bands (at most N / 32 + 1).
+inline int64_t pass_table_entries(int64_t A, int64_t N) { return A + N + N / 32 + 1; }
+
 template <bool FP64>
 fgr_status launch_pass(const void *in, void *out, const PassParams &pp, const uint8_t *flags,
-                       const int2 *brange, int64_t target_ctas, int tile_pref, cudaStream_t st) {
+                       const int2 *brange, int64_t target_ctas, int tile_pref, void *tables,
+                       cudaStream_t st) {
     if (pp.rows == 0 || pp.N == 0) return FGR_OK;
     if (pp.rows > INT_MAX) {
         set_error("fggc: too many rows in a grid pass");
@@ -454,8 +489,16 @@ fgr_status launch_pass(const void *in, void *out, const PassParams &pp, const ui
     if (splits > 1) {
         FGR_CUDA_TRY(cudaMemsetAsync(out, 0, (FP64 ? 16 : 8) * (size_t)pp.rows * (size_t)pp.N, st));
     }
+    PassTables tab;
+    tab.win = reinterpret_cast<int2 *>(tables);
+    tab.ph = reinterpret_cast<float2 *>(tab.win + pp.A);
+    tab.band = reinterpret_cast<int2 *>(tab.ph + pp.N);
+    {
+        const int64_t n = std::max<int64_t>(std::max<int64_t>(pp.A, pp.N), mtiles);
+        pass_tables_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pp, tp, mtiles, tab);
+    }
     dim3 grid((unsigned)pp.rows, (unsigned)mtiles, (unsigned)splits);
-#define FGR_PASS(MB, TPV) grid_pass_kernel<FP64, MB, TPV><<<grid, TPV, 0, st>>>(in, out, pp, flags, brange)
+#define FGR_PASS(MB, TPV) grid_pass_kernel<FP64, MB, TPV><<<grid, TPV, 0, st>>>(in, out, pp, flags, brange, tab)
 #define FGR_PASS_TP(TPV)                                                                                    \
     if (band <= 16) FGR_PASS(16, TPV);                                                                      \
     else if (band <= 32) FGR_PASS(32, TPV);                                                                 \
@@ -618,6 +661,7 @@ fgr_status make_box(const fgr_ctx *ctx, const int *hb, int margin, FggcBox *box)
         x.maxbuf = std::max(x.maxbuf, prodN * pre);
     }
     if (D == 1) x.maxbuf = 0;
+    for (int l = 0; l < D; ++l) x.table_entries = std::max(x.table_entries, pass_table_entries(c.A[l], G.n[l]));
     return FGR_OK;
 }
 
@@ -695,11 +739,11 @@ fgr_status enqueue_fggc(fgr_ctx *ctx, const PacketsDev &pk, const FggcBox &box, 
         ++*launches;
         const int64_t target = (int64_t)ctx->num_sms * ctx->tune.pass_ctas_per_sm;
         r = fp64 ? launch_pass<true>(cur, dst, pp, l == D - 1 ? b.flags : nullptr, b.brange, target,
-                                     ctx->tune.pass_tile, st)
+                                     ctx->tune.pass_tile, b.tables, st)
                  : launch_pass<false>(cur, dst, pp, l == D - 1 ? b.flags : nullptr, b.brange, target,
-                                      ctx->tune.pass_tile, st);
+                                      ctx->tune.pass_tile, b.tables, st);
         if (r != FGR_OK) return r;
-        ++*launches;
+        *launches += 2;  // tables + pass
         if (D > 1) {
             void *tdst = last ? u_dev : (dst == b.buf1 ? b.buf2 : b.buf1);
             r = fp64 ? launch_transpose<double2>(dst, tdst, pp.rows, pp.N, st)
@@ -747,7 +791,8 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
     b.buf2 = D > 1 ? scratch.get(eb * (size_t)box.maxbuf) : nullptr;
     b.flags = (uint8_t *)scratch.get((size_t)box.rows0);
     b.brange = (int2 *)scratch.get(sizeof(int2) * (size_t)box.max_lines);
-    if (!b.W || !b.flags || !b.brange || (D > 1 && (!b.buf1 || !b.buf2))) return FGR_E_NOMEM;
+    b.tables = scratch.get(8 * (size_t)box.table_entries);
+    if (!b.W || !b.flags || !b.brange || !b.tables || (D > 1 && (!b.buf1 || !b.buf2))) return FGR_E_NOMEM;
     r = enqueue_fggc<D>(ctx, pk, box, b, u_dev, st, &timer, &launches);
     if (r != FGR_OK) return r;
     ctx->timing.last.launches = launches;
@@ -955,12 +1000,17 @@ extern "C" fgr_status fgr_reconstruct_fggc_noalloc(fgr_ctx *ctx, const fgr_packe
     c.bmin[0] = hb[2];
     c.B[0] = hb[3] - hb[2] + 1;
     const int64_t cells = (int64_t)c.A[0] * c.B[0];
-    if ((size_t)cells > (kNoAllocBytes - kNoAllocNodesOffset) / eb) {
-        set_error("noalloc: the node array needs %lld cells (%zu bytes); this entry point holds at most "
-                  "%zu bytes; use fgr_reconstruct_fggc",
-                  (long long)cells, (size_t)cells * eb, kNoAllocBytes - kNoAllocNodesOffset);
+    // node array, then the grid pass's tables (8 bytes per node and per grid point)
+    const size_t node_bytes = ((size_t)cells * eb + 15) / 16 * 16;
+    const size_t table_bytes = 8 * (size_t)pass_table_entries(c.A[0], G.n[0]);
+    if ((size_t)cells > (kNoAllocBytes - kNoAllocNodesOffset) / eb ||
+        node_bytes + table_bytes > kNoAllocBytes - kNoAllocNodesOffset) {
+        set_error("noalloc: the node array needs %lld cells (%zu bytes) and the pass tables %zu bytes; this entry "
+                  "point holds at most %zu bytes; use fgr_reconstruct_fggc",
+                  (long long)cells, (size_t)cells * eb, table_bytes, kNoAllocBytes - kNoAllocNodesOffset);
         return FGR_E_CAPACITY;
     }
+    void *tables = static_cast<unsigned char *>(W) + node_bytes;
     c.sb[0] = 1;
     c.sa[0] = c.B[0];
     c.row_len = cells;
@@ -1007,8 +1057,8 @@ extern "C" fgr_status fgr_reconstruct_fggc_noalloc(fgr_ctx *ctx, const fgr_packe
     pp.two_pow_b = std::ldexp(1.0, std::max(1, 23 - lb));
     pp.inv_two_pow_b = 1.0 / pp.two_pow_b;
     const int64_t target = (int64_t)ctx->num_sms * ctx->tune.pass_ctas_per_sm;
-    rc = fp64 ? launch_pass<true>(W, u_out, pp, flags, nullptr, target, ctx->tune.pass_tile, st)
-              : launch_pass<false>(W, u_out, pp, flags, nullptr, target, ctx->tune.pass_tile, st);
+    rc = fp64 ? launch_pass<true>(W, u_out, pp, flags, nullptr, target, ctx->tune.pass_tile, tables, st)
+              : launch_pass<false>(W, u_out, pp, flags, nullptr, target, ctx->tune.pass_tile, tables, st);
     if (rc != FGR_OK) return rc;
     if (!stream) FGR_CUDA_TRY(cudaStreamSynchronize(st));
     return FGR_OK;

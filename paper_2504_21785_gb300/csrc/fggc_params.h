@@ -37,6 +37,7 @@ struct FggcBox {
     int64_t rows0 = 0;      // rows of the first grid pass
     int64_t maxbuf = 0;     // elements of each pass buffer (d > 1)
     int64_t max_lines = 0;  // (row, a) lines of the b-range scan
+    int64_t table_entries = 0;  // 8-byte entries of the largest pass table
     bool empty = true;      // no packet reaches the grid
 };
 
@@ -44,6 +45,7 @@ struct FggcBuffers {
     void *W = nullptr, *buf1 = nullptr, *buf2 = nullptr;
     uint8_t *flags = nullptr;
     int2 *brange = nullptr;
+    void *tables = nullptr;  // per-pass tables (node windows, point phases, tile bands)
 };
 
 // Box from the packets' node bounds hb[12] (per dimension: a min, a max, b min,
