@@ -607,6 +607,18 @@ struct fgr_fggc_plan {
     }
 };
 
+namespace fgr {
+size_t plan_device_bytes(const fgr_fggc_plan *pl) {
+    const size_t eb = elem_bytes(pl->precision);
+    const FggcBox &b = pl->box;
+    size_t n = 64;  // bounds and overflow flag
+    if (!b.empty)
+        n += eb * (size_t)b.cells + (pl->d > 1 ? 2 * eb * (size_t)b.maxbuf : 0) + (size_t)b.rows0 +
+             sizeof(int2) * (size_t)b.max_lines + 8 * (size_t)b.table_entries;
+    return n;
+}
+}  // namespace fgr
+
 namespace {
 
 bool plan_matches(const fgr_ctx *ctx, const fgr_fggc_plan *pl) {

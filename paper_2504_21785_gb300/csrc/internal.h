@@ -120,6 +120,9 @@ fgr_status run_direct(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStrea
                       Scratch &scratch);
 fgr_status run_fggc(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t st,
                     Scratch &scratch);
+// Device bytes owned by an FGGC plan (api.cu).
+size_t plan_device_bytes(const fgr_fggc_plan *plan);
+
 // n <= 64 requests of one dimension and precision; scratch[r] belongs to request r
 fgr_status run_direct_batch(int n, fgr_ctx *const *ctxs, const PacketsDev *pks, void *const *us,
                             cudaStream_t st, Scratch **scratch, Scratch &shared);

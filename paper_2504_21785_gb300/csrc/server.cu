@@ -6,12 +6,16 @@
 // requests stay within the memory budget.  Each worker owns a CUDA stream and
 // a small cache of contexts, so the kernels of admitted requests overlap on the
 // device; a request that arrives while others run starts as soon as a slot and
-// memory free up.  Direct-sum requests of one dimension and precision that
-// wait together (device outputs) are admitted as one group of up to max_batch
-// and run as a single persistent launch (fgr_reconstruct_direct_batch); a
-// group that the batched call rejects is retried request by request, so each
-// request gets its own status.  Completion is reported through fgr_poll with
-// host timestamps (submit, start, done).
+// memory free up.  Requests of one method, dimension and precision that wait
+// together (device outputs) are admitted as one group of up to max_batch:
+// direct sums run as a single persistent launch (fgr_reconstruct_direct_batch),
+// FGGC reconstructions back to back on the worker's stream through plans
+// (fgr_reconstruct_fggc_planned) with one wait for the group.  Plans are
+// cached per (packet set, grid, eps, options): registered sets never change,
+// so a plan's node box stays valid until the set is released, and its device
+// memory counts as resident within the budget.  A group that fails is retried
+// request by request, so each request gets its own status.  Completion is
+// reported through fgr_poll with host timestamps (submit, start, done).
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -62,6 +66,29 @@ struct CtxKey {
     bool operator==(const CtxKey &o) const { return memcmp(this, &o, sizeof(CtxKey)) == 0; }
 };
 
+CtxKey key_of(const fgr_request &r) {
+    CtxKey key;
+    memset(&key, 0, sizeof(key));
+    key.d = r.d;
+    key.grid = r.grid;
+    key.eps = r.eps;
+    key.opt = r.opt;
+    return key;
+}
+
+// FGGC plan of one (packet set, context key); its bytes count as resident.
+struct PlanKey {
+    uint64_t set_id;
+    CtxKey key;
+    bool operator<(const PlanKey &o) const { return memcmp(this, &o, sizeof(PlanKey)) < 0; }
+};
+
+struct PlanEntry {
+    fgr_fggc_plan *plan = nullptr;
+    size_t bytes = 0;
+    bool busy = false;
+};
+
 }  // namespace
 
 struct fgr_server {
@@ -75,6 +102,7 @@ struct fgr_server {
     std::deque<Group> admitted;                  // waiting for a worker
     std::map<uint64_t, std::shared_ptr<Job>> jobs;
     std::map<uint64_t, PacketSet> sets;
+    std::map<PlanKey, PlanEntry> plans;
     size_t resident = 0, reserved = 0;
     int running = 0;
     uint64_t next_ticket = 1, next_set = 1;
@@ -101,10 +129,10 @@ size_t footprint(const fgr_request &r, const PacketSet &ps) {
     return f + (size_t)total * eb;  // staging of a host output
 }
 
-bool batchable(const Job &j) { return j.req.method == 0 && j.dev_out; }
+bool batchable(const Job &j) { return j.dev_out; }
 
 bool same_batch(const Job &a, const Job &b) {
-    return a.req.d == b.req.d && a.req.opt.precision == b.req.opt.precision;
+    return a.req.method == b.req.method && a.req.d == b.req.d && a.req.opt.precision == b.req.opt.precision;
 }
 
 fgr_packets packets_of(const PacketSet &ps) {
@@ -126,12 +154,7 @@ class CtxCache {
         for (auto &c : items_) fgr_destroy(c.second);
     }
     fgr_status get(const fgr_request &r, fgr_ctx **out) {
-        CtxKey key;
-        memset(&key, 0, sizeof(key));
-        key.d = r.d;
-        key.grid = r.grid;
-        key.eps = r.eps;
-        key.opt = r.opt;
+        const CtxKey key = key_of(r);
         for (size_t i = 0; i < items_.size(); ++i)
             if (items_[i].first == key) {
                 std::rotate(items_.begin(), items_.begin() + i, items_.begin() + i + 1);
@@ -154,17 +177,99 @@ class CtxCache {
     std::vector<std::pair<CtxKey, fgr_ctx *>> items_;
 };
 
-fgr_status run_one(const Job &job, const PacketSet &ps, CtxCache &cache, cudaStream_t stream) {
+// The cached plan of (set, request), created on first use if it fits the
+// budget; marked busy until release_plan.  nullptr: run without a plan.
+fgr_fggc_plan *acquire_plan(fgr_server *S, const Job &job, fgr_ctx *ctx, const fgr_packets &pk,
+                            cudaStream_t stream) {
+    if (!S || !job.dev_out) return nullptr;
+    const PlanKey k{job.req.set_id, key_of(job.req)};
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->plans.find(k);
+        if (it != S->plans.end()) {
+            if (it->second.busy) return nullptr;
+            it->second.busy = true;
+            return it->second.plan;
+        }
+    }
+    fgr_fggc_plan *plan = nullptr;
+    if (fgr_fggc_plan_create(ctx, &pk, 1, &plan, stream) != FGR_OK) return nullptr;
+    const size_t bytes = fgr::plan_device_bytes(plan);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto set = S->sets.find(job.req.set_id);
+        const bool fits = S->resident + S->reserved + bytes <= S->budget;
+        if (fits && set != S->sets.end() && !set->second.released && !S->plans.count(k)) {
+            S->plans[k] = PlanEntry{plan, bytes, true};
+            S->resident += bytes;
+            return plan;
+        }
+    }
+    fgr_fggc_plan_destroy(plan);
+    return nullptr;
+}
+
+void release_plan(fgr_server *S, const Job &job) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->plans.find(PlanKey{job.req.set_id, key_of(job.req)});
+    if (it != S->plans.end()) it->second.busy = false;
+}
+
+// Enqueues one request (FGGC through its plan when there is one); *planned is
+// the plan to release once the stream has finished.
+fgr_status enqueue_one(fgr_server *S, const Job &job, const PacketSet &ps, CtxCache &cache, cudaStream_t stream,
+                       fgr_fggc_plan **planned) {
     const fgr_request &r = job.req;
+    *planned = nullptr;
     fgr_ctx *ctx = nullptr;
     fgr_status st = cache.get(r, &ctx);
     if (st != FGR_OK) return st;
     fgr_packets pk = packets_of(ps);
-    st = r.method == 0 ? fgr_reconstruct_direct(ctx, &pk, r.u_out, stream)
-                       : fgr_reconstruct_fggc(ctx, &pk, r.u_out, stream);
+    if (r.method == 0) return fgr_reconstruct_direct(ctx, &pk, r.u_out, stream);
+    fgr_fggc_plan *plan = acquire_plan(S, job, ctx, pk, stream);
+    if (!plan) return fgr_reconstruct_fggc(ctx, &pk, r.u_out, stream);
+    *planned = plan;
+    return fgr_reconstruct_fggc_planned(ctx, plan, &pk, r.u_out, stream);
+}
+
+// After the stream has finished: a planned request whose packets left the
+// box (they cannot, for an unchanged set) is redone without the plan.
+fgr_status finish_one(fgr_server *S, const Job &job, const PacketSet &ps, CtxCache &cache, cudaStream_t stream,
+                      fgr_fggc_plan *planned, fgr_status st) {
+    if (!planned) return st;
+    int32_t over = 0;
+    if (st == FGR_OK && fgr_fggc_plan_overflow(planned, &over) == FGR_OK && over) {
+        fgr_ctx *ctx = nullptr;
+        st = cache.get(job.req, &ctx);
+        if (st == FGR_OK) {
+            fgr_packets pk = packets_of(ps);
+            st = fgr_reconstruct_fggc(ctx, &pk, job.req.u_out, stream);
+            if (cudaStreamSynchronize(stream) != cudaSuccess && st == FGR_OK) st = FGR_E_CUDA;
+        }
+    }
+    release_plan(S, job);
+    return st;
+}
+
+fgr_status run_one(fgr_server *S, const Job &job, const PacketSet &ps, CtxCache &cache, cudaStream_t stream) {
+    fgr_fggc_plan *planned = nullptr;
+    fgr_status st = enqueue_one(S, job, ps, cache, stream, &planned);
     cudaError_t e = cudaStreamSynchronize(stream);
     if (st == FGR_OK && e != cudaSuccess) st = FGR_E_CUDA;
-    return st;
+    return finish_one(S, job, ps, cache, stream, planned, st);
+}
+
+// FGGC group: the requests back to back on the stream, one wait.
+void run_fggc_group(fgr_server *S, const Group &g, const std::vector<PacketSet> &ps, CtxCache &cache,
+                    cudaStream_t stream, std::vector<fgr_status> &st) {
+    const size_t n = g.size();
+    std::vector<fgr_fggc_plan *> planned(n, nullptr);
+    for (size_t i = 0; i < n; ++i) st[i] = enqueue_one(S, *g[i], ps[i], cache, stream, &planned[i]);
+    const cudaError_t e = cudaStreamSynchronize(stream);
+    for (size_t i = 0; i < n; ++i) {
+        if (st[i] == FGR_OK && e != cudaSuccess) st[i] = FGR_E_CUDA;
+        st[i] = finish_one(S, *g[i], ps[i], cache, stream, planned[i], st[i]);
+    }
 }
 
 // One persistent launch for the whole group; on failure the requests are
@@ -192,7 +297,7 @@ void run_group(const Group &g, const std::vector<PacketSet> &ps, CtxCache &cache
         std::fill(st.begin(), st.end(), FGR_OK);
         return;
     }
-    for (size_t i = 0; i < n; ++i) st[i] = run_one(*g[i], ps[i], cache, stream);
+    for (size_t i = 0; i < n; ++i) st[i] = run_one(nullptr, *g[i], ps[i], cache, stream);
 }
 
 void worker_main(fgr_server *S) {
@@ -218,9 +323,11 @@ void worker_main(fgr_server *S) {
         }
         std::vector<fgr_status> st(group.size(), FGR_OK);
         if (group.size() == 1)
-            st[0] = run_one(*group[0], ps[0], cache, stream);
-        else
+            st[0] = run_one(S, *group[0], ps[0], cache, stream);
+        else if (group[0]->req.method == 0)
             run_group(group, ps, cache, stream, st);
+        else
+            run_fggc_group(S, group, ps, cache, stream, st);
         cache.trim(std::max<size_t>(8, 2 * (size_t)S->max_batch));
         {
             std::lock_guard<std::mutex> lk(S->mu);
@@ -340,6 +447,7 @@ void fgr_server_destroy(fgr_server *S) {
     S->sched.join();
     for (auto &w : S->workers) w.join();  // admitted jobs finish first
     cudaSetDevice(S->device);
+    for (auto &kv : S->plans) fgr_fggc_plan_destroy(kv.second.plan);
     for (auto &kv : S->sets) cudaFree(kv.second.buf);
     delete S;
 }
@@ -413,6 +521,16 @@ fgr_status fgr_release_packets(fgr_server *S, uint64_t set_id) {
     it->second.released = true;
     S->cv_done.wait(lk, [&] { return S->sets[set_id].users == 0; });
     cudaSetDevice(S->device);
+    // the set's plans (none busy: no request of the set is running)
+    for (auto pl = S->plans.begin(); pl != S->plans.end();) {
+        if (pl->first.set_id == set_id) {
+            fgr_fggc_plan_destroy(pl->second.plan);
+            S->resident -= pl->second.bytes;
+            pl = S->plans.erase(pl);
+        } else {
+            ++pl;
+        }
+    }
     cudaFree(it->second.buf);
     S->resident -= it->second.bytes;
     S->sets.erase(it);

@@ -211,3 +211,42 @@ def test_direct_requests_waiting_together_run_as_one_batch(fgr):
             assert np.linalg.norm(got - ref) <= 1e-6 * max(np.linalg.norm(ref), 1e-300)
     finally:
         fgr.fgr_server_destroy(srv)
+
+
+def test_fggc_requests_through_cached_plans_and_release(fgr):
+    import torch
+    from . import _gpu
+    pk = random_packets(80, 1, 6000, q_range=(-2.5, 2.5), p_range=(-2, 2), s_range=(-1, 1))
+    big = random_packets(81, 2, 200000, q_range=(-2.5, 2.5), p_range=(-2, 2))
+    srv = fgr.fgr_server_create(8 << 30, 1)
+    try:
+        sid = fgr.fgr_register_packets(srv, 1, fgr.make_packets(*[np.ascontiguousarray(pk[k]) for k in "qpsa"]))
+        big_id = fgr.fgr_register_packets(srv, 2, fgr.make_packets(*[np.ascontiguousarray(big[k]) for k in "qpsa"]))
+        opt = fgr.make_options(precision=fgr.FGR_FP32)
+        ub = torch.zeros((1024, 1024), dtype=torch.complex64, device="cuda")
+        tickets = [fgr.fgr_submit(srv, fgr.make_request(1, _grid(2, 1024), 1 / 1024, opt, big_id, ub))]
+        # two grids, each asked for several times: the second and later requests
+        # of a (set, grid) reuse its plan; requests that wait together form groups
+        reqs, outs = [], []
+        for i in range(24):
+            n = 2048 if i % 2 else 4096
+            u = torch.full((n,), 9.0, dtype=torch.complex64, device="cuda")
+            reqs.append(n)
+            outs.append(u)
+            tickets.append(fgr.fgr_submit(srv, fgr.make_request(1, _grid(1, n), 1 / 512, opt, sid, u)))
+        res = [fgr.fgr_poll(srv, t, -1) for t in tickets]
+        assert all(x.status == 0 for x in res)
+        for n, u in zip(reqs, outs):
+            ref = _gpu.reconstruct("fggc", pk, _grid(1, n), 1 / 512, opt)
+            got = u.cpu().numpy()
+            assert np.linalg.norm(got - ref) <= 1e-6 * np.linalg.norm(ref)
+        # releasing the set frees its plans; new sets and requests still work
+        fgr.fgr_release_packets(srv, sid)
+        sid2 = fgr.fgr_register_packets(srv, 1, fgr.make_packets(*[np.ascontiguousarray(pk[k]) for k in "qpsa"]))
+        u = torch.zeros(4096, dtype=torch.complex64, device="cuda")
+        r = fgr.fgr_poll(srv, fgr.fgr_submit(srv, fgr.make_request(1, _grid(1, 4096), 1 / 512, opt, sid2, u)), -1)
+        assert r.status == 0
+        ref = _gpu.reconstruct("fggc", pk, _grid(1, 4096), 1 / 512, opt)
+        assert np.linalg.norm(u.cpu().numpy() - ref) <= 1e-6 * np.linalg.norm(ref)
+    finally:
+        fgr.fgr_server_destroy(srv)
