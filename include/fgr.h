@@ -278,16 +278,21 @@ fgr_status fgr_get_stats(const fgr_ctx *ctx, fgr_stats *out);
 
 /* Starts a server on the current device with a scheduler thread and
  * max_inflight worker streams.  Requests are admitted while the resident packet
- * sets plus the footprints of the admitted requests stay within
- * hbm_budget_bytes; others wait in arrival order.  Free with fgr_server_destroy,
- * which cancels what has not started and waits for what has. */
+ * sets (and the FGGC plans the server keeps for them) plus the footprints of
+ * the admitted requests stay within hbm_budget_bytes; others wait in arrival
+ * order.  Requests of one method, dimension and precision with device outputs
+ * that wait together run as one group (see fgr_server_set_max_batch); FGGC
+ * requests go through a plan cached per (packet set, grid, eps, options) when
+ * the budget allows, freed with the set.  Free with fgr_server_destroy, which
+ * cancels what has not started and waits for what has. */
 fgr_status fgr_server_create(size_t hbm_budget_bytes, int32_t max_inflight, fgr_server **out);
 void fgr_server_destroy(fgr_server *srv);
 
-/* Largest group of direct-sum requests (same d and precision, device outputs)
- * that one worker runs as a single fgr_reconstruct_direct_batch launch
- * (default 16; 1 turns grouping off; at most 64).  Applies to requests
- * admitted after the call.  Not in the paper: a serving policy. */
+/* Largest group of waiting requests (same method, d and precision, device
+ * outputs) that one worker takes at once: direct sums run as a single
+ * fgr_reconstruct_direct_batch launch, FGGC reconstructions back to back with
+ * one wait (default 16; 1 turns grouping off; at most 64).  Applies to
+ * requests admitted after the call.  Not in the paper: a serving policy. */
 fgr_status fgr_server_set_max_batch(fgr_server *srv, int32_t max_batch);
 
 /* Copies a packet set (host or device, see fgr_packets) into device memory owned
