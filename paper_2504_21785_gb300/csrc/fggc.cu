@@ -11,7 +11,7 @@
 // coefficients c~_k(s,t) = conj(A~^+ f~(s,t))_k come from
 //   FP64: f~ of eq. 3.23 in FP64 and A~^+ applied through its eigen factors;
 //   FP32: a Chebyshev surrogate of c~(s,t) built on the host in long double
-//         from the same factors (error below 1e-10), evaluated in FP32.
+//         from the same factors (truncation error below 1e-9), evaluated in FP32.
 // The shift back of eq. 3.13 and the node phase of the on-grid packet are
 // folded into one phase per coefficient: G(x; a dq, b dp) =
 // g(x - a dq) e^{i b dp x/eps} e^{-i cq cp a b}, and with r = a0 + s,

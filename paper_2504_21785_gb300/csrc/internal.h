@@ -16,6 +16,11 @@ constexpr int kMaxN1 = 16;  // 1-D neighbours per packet: nq * np <= 16
 
 // Eigen-factored eps-free Gram matrix of eq. 3.22 (paper convention).
 // The Gram A~ is Hermitian PSD: A~ = V diag(lam) V^H, A~^+ = V diag(inv_lam) V^H.
+// Degree of the FP32 coefficient surrogate per variable: its truncation error
+// (3e-10 for Q4P2 at 10, 4e-13 at 12) lies far below the FP32 rounding of its
+// stored coefficients and of its evaluation.
+constexpr int kCheb = 10;
+
 struct Lsa {
     int nq = 4, np = 2, n1 = 8, rank = 0;
     double cq = 0.5, cp = 0.0;
@@ -26,10 +31,9 @@ struct Lsa {
     double vi[kMaxN1 * kMaxN1] = {};
     // Chebyshev surrogate of the true coefficients c~_k(s,t) = conj(A~^+ f~(s,t))_k
     // on [0,1]^2: c~_k ~= sum_{i,j<kCheb} cheb[k][i][j] T_i(2s-1) T_j(2t-1).
-    float cheb_re[kMaxN1][12][12] = {};
-    float cheb_im[kMaxN1][12][12] = {};
+    float cheb_re[kMaxN1][kCheb][kCheb] = {};
+    float cheb_im[kMaxN1][kCheb][kCheb] = {};
 };
-constexpr int kCheb = 12;
 
 // Builds Lsa (host, long double Jacobi).  Returns false on bad input.
 bool build_lsa(double cq, double cp, int nq, int np, double rcond, Lsa *out);
