@@ -7,13 +7,17 @@
 // K_l = ceil((Wmax_l - 1) / T_l) and Wmax_l the largest window length.  In
 // row-major tile order that box is (K+1)^(d-1) contiguous segments.
 //
-// Evaluation.  Each CTA owns one output tile (TPT points per thread) and one of
-// S interleaved slices of the tile's packet list; packet records are staged in
-// shared memory 256 at a time and every thread evaluates exp and sincos for each
-// (packet, point) pair inside the packet's window.  FP32 sums run over one
-// chunk of 256 records and are folded into FP64 totals (a point can collect
-// 10^4-10^5 packets: a single FP32 running sum would drift by ~sqrt(N) ulps).
-// Slices are combined with atomic adds into the zeroed output.
+// Evaluation.  Each CTA owns one output tile (4 consecutive points of the last
+// dimension per thread) and one of S interleaved slices of the tile's packet
+// list; packet records are staged in shared memory 256 at a time.  FP32, 1-D:
+// a thread evaluates exp and sincos for the first of its points and reaches the
+// other three by the exact recurrences of the Gaussian ratio and the phase
+// rotation.  FP32, 2-D and 3-D: the CTA tabulates each record's per-dimension
+// factors on its tile and every pair costs one complex multiply-add.  FP64:
+// every pair is evaluated in full.  FP32 sums run over one chunk of 256
+// records and are folded into FP64 totals (a point can collect 10^4-10^5
+// packets: a single FP32 running sum would drift by ~sqrt(N) ulps).  Slices
+// are combined with atomic adds into the zeroed output.
 //
 // FP32 records carry the per-packet phase reduced in FP64 to turns at the
 // window start (tau0) and the per-grid-step increment nu split into a coarse
