@@ -13,7 +13,8 @@ Modules
 fga           eq. 2.10 / 2.15 / 2.16: packets, inner product, windowed direct sum
 lsa           Sec. 2.2-3.2: neighbour map, eps-free Gram and right-hand side,
               SVD pseudo-inverse, Algorithms 1 and 2 coefficients, E_LSA, M_LSA
-fggc          eq. 2.24-2.25: aggregation onto grid nodes and on-grid sum
+fggc          eq. 2.24-2.25: aggregation onto grid nodes and on-grid sum;
+              Algorithm 3 (multi-step FGGC with a fixed mesh and learned flow)
 decompose     eq. 2.6 / 2.8: initial decomposition of a wave given on the grid
 trajectories  eq. 2.3-2.7: classical RK4 of Q, P, S, A with the Jacobians
               (plain C in c/rk4.c, compiled on first use)

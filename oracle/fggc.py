@@ -68,3 +68,25 @@ def reconstruct(packets: dict, grid: dict, eps: float, dq: float, dp: float,
     node_a, node_b, W = aggregate(packets, eps, dq, dp, strat)
     cells = on_grid_packets(node_a, node_b, W, dq, dp)
     return fga.direct_sum(cells, grid, eps, dq, dp, R=R, points=points)
+
+
+def multistep(u0, grid: dict, mesh: dict, flow: dict, eps: float, dq: float, dp: float,
+              strat: lsa.Strategy, steps: int, R: float = 8.0):
+    """Algorithm 3 (multi-step FGGC) with a fixed phase-space mesh.
+
+    mesh: packets at the mesh positions (q, p) onto which every step decomposes
+    the current wave (Step 1, eq. 2.8); flow: the same packets propagated over
+    one step T_evo from unit amplitude (Step 2, the map learned once: Q, P, S
+    and the amplitude factor, since eq. 2.6 is linear in A).  Each step
+    decomposes u, multiplies the amplitudes by the factors and reconstructs by
+    FGGC (Step 3); returns u after `steps` steps.
+    """
+    from . import decompose as dec
+    factor = flow["a"][0] + 1j * flow["a"][1]
+    u = np.asarray(u0, dtype=np.complex128)
+    for _ in range(steps):
+        a0 = dec.decompose(u, grid, mesh["q"], mesh["p"], eps, R=R)
+        a = (a0[0] + 1j * a0[1]) * factor
+        packets = {"q": flow["q"], "p": flow["p"], "s": flow["s"], "a": np.stack([a.real, a.imag])}
+        u = reconstruct(packets, grid, eps, dq, dp, strat, R=R)
+    return u
