@@ -139,6 +139,34 @@ const char *fgr_last_error(void);
 fgr_status fgr_propagate(fgr_ctx *ctx, fgr_packets *inout, const fgr_potential *v, double t,
                          double dt, void *cuda_stream);
 
+/* Eq. 2.6 and 2.8 (Step 1 of Algorithms 1-3): the initial decomposition of a
+ * wave u given on the context's grid (complex128 for FP64 contexts, complex64
+ * for FP32, row-major, last dimension fastest; host or device memory).  For
+ * every packet j of inout, whose q and p are read, it writes
+ *   a_j = 2^{d/2} prod_l h_l sum_m u(x_m) exp(-i p_j.(x_m - q_j)/eps - |x_m - q_j|^2/(2 eps))
+ * (the rectangle rule of eq. 2.8 on the grid) over the same box window
+ * |x_l - q_l| <= R sqrt(eps) as the reconstructions, and s_j = 0; packets
+ * whose window misses the grid get a_j = 0.  FP64: every term in FP64.  FP32:
+ * the phase is reduced in FP64 per packet, each term evaluated in FP32, sums
+ * folded into FP64.  Host packets are copied back before the call returns.
+ * FGR_E_INVALID for NULL arguments or non-finite host packet data. */
+fgr_status fgr_decompose(fgr_ctx *ctx, const void *u_in, fgr_packets *inout, void *cuda_stream);
+
+/* Algorithm 3 (multi-step FGGC) with a fixed phase-space mesh and the flow
+ * learned once.  mesh: packets at the mesh positions (q, p) onto which every
+ * step decomposes the current wave (only q and p are read); flow: the same
+ * packets, in the same order, propagated over one step from unit amplitude
+ * (fgr_propagate with a = 1): their Q, P, S and amplitude factor A(T_evo)
+ * (eq. 2.6 is linear in A).  Each of the `steps` steps decomposes u (as
+ * fgr_decompose), multiplies the amplitudes by the factors and reconstructs by
+ * FGGC (as fgr_reconstruct_fggc); u_out receives the wave after the last step
+ * (u_in itself when steps = 0).  u_in and u_out: the context's grid and
+ * complex type, host or device.  Waits like fgr_reconstruct_fggc (once per
+ * step).  FGR_E_INVALID if mesh and flow hold different numbers of packets,
+ * steps < 0 or an argument is NULL. */
+fgr_status fgr_fggc_multistep(fgr_ctx *ctx, const fgr_packets *mesh, const fgr_packets *flow, const void *u_in,
+                              void *u_out, int32_t steps, void *cuda_stream);
+
 /* Eq. 2.10 over the box window: u(x_m) = pref * sum_j A_j exp(i/eps (S_j +
  * P_j.(x_m - Q_j)) - |x_m - Q_j|^2/(2 eps)).  FP64: every term in FP64.
  * FP32: the phase is reduced in FP64 per packet and evaluated in FP32 turns;

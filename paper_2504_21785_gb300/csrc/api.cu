@@ -569,6 +569,96 @@ fgr_status fgr_propagate(fgr_ctx *ctx, fgr_packets *pk, const fgr_potential *v, 
     });
 }
 
+fgr_status fgr_decompose(fgr_ctx *ctx, const void *u_in, fgr_packets *pk, void *stream) {
+    clear_error();
+    if (!ctx || !u_in) {
+        set_error("decompose: ctx and u_in must be non-NULL");
+        return FGR_E_INVALID;
+    }
+    fgr_status rc = check_packets(ctx, pk);
+    if (rc != FGR_OK) return rc;
+    return guarded([&]() -> fgr_status {
+        FGR_CUDA_TRY(cudaSetDevice(ctx->device));
+        cudaStream_t st = (cudaStream_t)stream;
+        memset(&ctx->timing.last, 0, sizeof(ctx->timing.last));
+        Scratch scratch(ctx, st);
+        PacketsDev dev;
+        double *q, *p, *s, *a;
+        fgr_status r = stage_packets(ctx, pk, st, scratch, &dev, &q, &p, &s, &a);
+        if (r != FGR_OK) return r;
+        const void *u_dev = u_in;
+        if (!is_device_ptr(u_in) && pk->m > 0) {
+            const size_t bytes = elem_bytes(ctx->opt.precision) * (size_t)ctx->grid.total;
+            void *buf = scratch.get(bytes);
+            if (!buf) return FGR_E_NOMEM;
+            FGR_CUDA_TRY(cudaMemcpyAsync(buf, u_in, bytes, cudaMemcpyHostToDevice, st));
+            u_dev = buf;
+        }
+        r = run_decompose(ctx, u_dev, q, p, s, a, pk->m, st);
+        if (r != FGR_OK) return r;
+        const int64_t m = pk->m;
+        if (!pk->on_device && m > 0) {
+            FGR_CUDA_TRY(cudaMemcpyAsync(pk->s, s, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+            FGR_CUDA_TRY(cudaMemcpyAsync(pk->a, a, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost, st));
+            FGR_CUDA_TRY(cudaStreamSynchronize(st));
+        } else if (!stream) {
+            FGR_CUDA_TRY(cudaStreamSynchronize(st));
+        }
+        return FGR_OK;
+    });
+}
+
+fgr_status fgr_fggc_multistep(fgr_ctx *ctx, const fgr_packets *mesh, const fgr_packets *flow, const void *u_in,
+                              void *u_out, int32_t steps, void *stream) {
+    clear_error();
+    if (!ctx || !u_in || !u_out || steps < 0) {
+        set_error("multistep: need ctx, u_in, u_out and steps >= 0");
+        return FGR_E_INVALID;
+    }
+    fgr_status rc = check_packets(ctx, mesh);
+    if (rc == FGR_OK) rc = check_packets(ctx, flow);
+    if (rc != FGR_OK) return rc;
+    if (mesh->m != flow->m) {
+        set_error("multistep: mesh and flow must hold the same packets (%lld vs %lld)", (long long)mesh->m,
+                  (long long)flow->m);
+        return FGR_E_INVALID;
+    }
+    return guarded([&]() -> fgr_status {
+        FGR_CUDA_TRY(cudaSetDevice(ctx->device));
+        cudaStream_t st = (cudaStream_t)stream;
+        const int64_t m = mesh->m;
+        const size_t bytes = elem_bytes(ctx->opt.precision) * (size_t)ctx->grid.total;
+        Scratch scratch(ctx, st);
+        PacketsDev dm, df;
+        double *q, *p, *s, *a;
+        fgr_status r = stage_packets(ctx, mesh, st, scratch, &dm, &q, &p, &s, &a);
+        if (r == FGR_OK) r = stage_packets(ctx, flow, st, scratch, &df, &q, &p, &s, &a);
+        if (r != FGR_OK) return r;
+        const size_t mm = (size_t)std::max<int64_t>(m, 1);
+        void *ua = scratch.get(bytes), *ub = scratch.get(bytes);
+        double *a0 = (double *)scratch.get(sizeof(double) * 2 * mm);
+        double *aw = (double *)scratch.get(sizeof(double) * 2 * mm);
+        double *s0 = (double *)scratch.get(sizeof(double) * mm);
+        if (!ua || !ub || !a0 || !aw || !s0) return FGR_E_NOMEM;
+        FGR_CUDA_TRY(cudaMemcpyAsync(ua, u_in, bytes, cudaMemcpyDefault, st));
+        void *cur = ua;
+        for (int32_t it = 0; it < steps; ++it) {
+            r = run_decompose(ctx, cur, dm.q, dm.p, s0, a0, m, st);         // Step 1 (eq. 2.8)
+            if (r == FGR_OK) r = run_scale_amplitudes(a0, df.a, aw, m, st);  // Step 2: learned flow
+            if (r != FGR_OK) return r;
+            void *dst = cur == ua ? ub : ua;
+            Scratch step_scratch(ctx, st);
+            r = run_fggc(ctx, PacketsDev{m, df.q, df.p, df.s, aw}, dst, st, step_scratch);  // Step 3
+            if (r != FGR_OK) return r;
+            cur = dst;
+        }
+        FGR_CUDA_TRY(cudaMemcpyAsync(u_out, cur, bytes, cudaMemcpyDefault, st));
+        FGR_CUDA_TRY(cudaGetLastError());
+        if (!stream || !is_device_ptr(u_out)) FGR_CUDA_TRY(cudaStreamSynchronize(st));
+        return FGR_OK;
+    });
+}
+
 fgr_status fgr_reconstruct_direct(fgr_ctx *ctx, const fgr_packets *pk, void *u_out, void *stream) {
     return reconstruct(ctx, pk, u_out, stream, false);
 }

@@ -120,6 +120,12 @@ class Scratch {
 // Kernel-stage launchers (return FGR_OK or an error with the message set).
 fgr_status run_propagate(fgr_ctx *ctx, double *q, double *p, double *s, double *a, int64_t m,
                          const fgr_potential *v, double t, double dt, cudaStream_t st);
+// Eq. 2.6 / 2.8 on the grid: a (2 x m) and s (m) of the packets at (q, p) from
+// the wave u_dev (complex, the context's precision).
+fgr_status run_decompose(fgr_ctx *ctx, const void *u_dev, const double *q, const double *p, double *s, double *a,
+                         int64_t m, cudaStream_t st);
+// out = a0 * f, complex, planes [re][m] then [im][m].
+fgr_status run_scale_amplitudes(const double *a0, const double *f, double *out, int64_t m, cudaStream_t st);
 fgr_status run_direct(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t st,
                       Scratch &scratch);
 fgr_status run_fggc(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t st,

@@ -89,6 +89,8 @@ SIGNATURES = {
     "fgr_last_error": (ctypes.c_char_p, []),
     "fgr_propagate": (ctypes.c_int, [vp, P(fgr_packets), P(fgr_potential), ctypes.c_double,
                                      ctypes.c_double, vp]),
+    "fgr_decompose": (ctypes.c_int, [vp, vp, P(fgr_packets), vp]),
+    "fgr_fggc_multistep": (ctypes.c_int, [vp, P(fgr_packets), P(fgr_packets), vp, vp, ctypes.c_int32, vp]),
     "fgr_reconstruct_direct": (ctypes.c_int, [vp, P(fgr_packets), vp, vp]),
     "fgr_reconstruct_fggc": (ctypes.c_int, [vp, P(fgr_packets), vp, vp]),
     "fgr_reconstruct_fggc_noalloc": (ctypes.c_int, [vp, P(fgr_packets), vp, vp]),
@@ -231,6 +233,17 @@ def fgr_propagate(ctx, packets: fgr_packets, potential: fgr_potential, t: float,
                   stream=None):
     return _check(load().fgr_propagate(ctx, ctypes.byref(packets), ctypes.byref(potential), t, dt,
                                        _stream_handle(stream)))
+
+
+def fgr_decompose(ctx, u_in, packets: fgr_packets, stream=None):
+    """Writes the packets' amplitudes (a) and zero actions (s) from the wave u_in."""
+    return _check(load().fgr_decompose(ctx, _ptr(u_in)[0], ctypes.byref(packets), _stream_handle(stream)))
+
+
+def fgr_fggc_multistep(ctx, mesh: fgr_packets, flow: fgr_packets, u_in, u_out, steps: int, stream=None):
+    """`steps` multi-step FGGC steps from u_in into u_out (mesh positions, learned flow)."""
+    return _check(load().fgr_fggc_multistep(ctx, ctypes.byref(mesh), ctypes.byref(flow), _ptr(u_in)[0],
+                                            _ptr(u_out)[0], int(steps), _stream_handle(stream)))
 
 
 def fgr_reconstruct_direct(ctx, packets: fgr_packets, u_out, stream=None):
