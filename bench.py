@@ -201,6 +201,9 @@ def run_ours(args):
     # reconstruction alone on the propagated batch: median, min and max of 20
     # runs each (L2 flushed before every run), FGGC with Q4P2 and Q2P2
     recon = reconstruct_runs(fgr, ctx, packets, u_d, grid, d, eps, prec, flush, stream, ud, runs=20)
+    # initial decomposition of u0 onto the t = 0 packet positions, and one step
+    # of multi-step FGGC with the flow learned from them (outside the timed region)
+    decomp = decompose_runs(fgr, ctx, w, init, pot, stream, flush, runs=20)
 
     # stage split of FGGC (context timing on; outside the timed region)
     fgr.fgr_set_timing(ctx.handle, True)
@@ -279,6 +282,7 @@ def run_ours(args):
                 "fggc_over_direct_pipeline": (ms_prop + ms_direct) / (ms_prop + ms_fggc),
                 "rel_l2_fggc_vs_direct": rel,
                 "reconstruct_20_runs": recon,
+                "decompose_20_runs": decomp,
                 "fggc_stage_split": fggc_stages,
                 "direct_stage_split": direct_stages,
             },
@@ -343,6 +347,61 @@ def reconstruct_runs(fgr, ctx, packets, u_ref, grid, d, eps, prec, flush, stream
         ok = out[k]["rel_l2_vs_direct"] <= 1e-5
         out[k]["speedup_vs_direct_at_equal_accuracy"] = (
             out["direct"]["median_ms"] / out[k]["median_ms"] if ok else "not at equal accuracy")
+    return out
+
+
+def decompose_runs(fgr, ctx, w, init, pot, stream, flush, runs=20):
+    """Median/min/max ms of `runs` initial decompositions (eq. 2.8) of the
+    workload's u0 onto its t = 0 packet positions, and of one multi-step FGGC
+    step (Algorithm 3: decompose, apply the learned flow, FGGC) whose flow is
+    those positions propagated over the workload's time from unit amplitude."""
+    import math
+    import numpy as np
+    import torch
+    from workloads.wkb import _FAMILIES
+
+    d, eps, grid = w["d"], w["eps"], w["grid"]
+    m = int(init[2].numel())
+    axes = [np.linspace(grid["lo"][l], grid["hi"][l], grid["n"][l], endpoint=False) for l in range(d)]
+    x = np.stack(np.meshgrid(*axes, indexing="ij"))
+    cdt = torch.complex64 if w["precision"] == "fp32" else torch.complex128
+    u0 = torch.tensor(_FAMILIES[w["family"]].u0(x, eps), dtype=cdt, device=init[0].device)
+    q, p = init[0].clone(), init[1].clone()
+    s, a = torch.empty_like(init[2]), torch.empty_like(init[3])
+    mesh = fgr.make_packets(q, p, s, a)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        ms = []
+        for _ in range(runs):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        med = statistics.median(ms)
+        return {"median_ms": med, "min_ms": min(ms), "max_ms": max(ms), "packets_per_s": m / (med * 1e-3)}
+
+    out = {"decompose": timed(lambda: fgr.fgr_decompose(ctx.handle, u0, mesh, stream))}
+    # window points per packet: (2 R sqrt(eps) / h + 1)^d with the context's R
+    R = 6.0 if w["precision"] == "fp32" else 8.0
+    pts = math.prod(2 * R * math.sqrt(eps) / ((grid["hi"][l] - grid["lo"][l]) / grid["n"][l]) + 1
+                    for l in range(d))
+    out["decompose"]["window_points_per_packet"] = pts
+    out["decompose"]["gpoints_per_s"] = m * pts / (out["decompose"]["median_ms"] * 1e-3) / 1e9
+    if d < 3:
+        fq, fp = init[0].clone(), init[1].clone()
+        fs = torch.zeros_like(init[2])
+        fa = torch.zeros_like(init[3])
+        fa[0] = 1.0
+        flow = fgr.make_packets(fq, fp, fs, fa)
+        fgr.fgr_propagate(ctx.handle, flow, pot, w["t"], w["dt"], stream)
+        u1 = torch.empty_like(u0)
+        out["multistep_1_step"] = timed(lambda: fgr.fgr_fggc_multistep(ctx.handle, mesh, flow, u0, u1, 1, stream))
+        out["multistep_1_step"]["note"] = "decompose + flow amplitudes + FGGC; RK4 of the flow learned once, untimed"
     return out
 
 
@@ -687,8 +746,10 @@ def run_reference(args):
 def run_profile_case(args):
     """One short pass of every kernel on the benchmark workload, for ncu:
     propagate to t = 0.01 (100 RK4 steps), then one FGGC and one direct
-    reconstruction of the propagated packets, and one batched direct sum of
-    eight copies of that request (FGGC only for 3-D workloads)."""
+    reconstruction of the propagated packets, one batched direct sum of
+    eight copies of that request and one initial decomposition of the
+    reconstructed wave onto the propagated positions (FGGC only for 3-D
+    workloads)."""
     import numpy as np
     import torch
 
@@ -715,6 +776,7 @@ def run_profile_case(args):
             fgr.fgr_reconstruct_direct(ctx.handle, pk, u)
             outs = [torch.zeros_like(u) for _ in range(8)]
             fgr.fgr_reconstruct_direct_batch([ctx] * 8, [pk] * 8, outs)
+            fgr.fgr_decompose(ctx.handle, u, pk)
         torch.cuda.synchronize()
     print(json.dumps({"profile_case": "config %d" % args.config, "ok": True}))
 
