@@ -350,7 +350,7 @@ def reconstruct_runs(fgr, ctx, packets, u_ref, grid, d, eps, prec, flush, stream
     return out
 
 
-def decompose_runs(fgr, ctx, w, init, pot, stream, flush, runs=20):
+def decompose_runs(fgr, ctx, w, init, pot, stream, flush, runs=20, multistep=True):
     """Median/min/max ms of `runs` initial decompositions (eq. 2.8) of the
     workload's u0 onto its t = 0 packet positions, and of one multi-step FGGC
     step (Algorithm 3: decompose, apply the learned flow, FGGC) whose flow is
@@ -371,10 +371,14 @@ def decompose_runs(fgr, ctx, w, init, pot, stream, flush, runs=20):
     mesh = fgr.make_packets(q, p, s, a)
 
     def timed(fn):
-        for _ in range(3):
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        n = runs if time.perf_counter() - t0 < 1.0 else 3
+        for _ in range(2):
             fn()
         ms = []
-        for _ in range(runs):
+        for _ in range(n):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -383,7 +387,7 @@ def decompose_runs(fgr, ctx, w, init, pot, stream, flush, runs=20):
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
         med = statistics.median(ms)
-        return {"median_ms": med, "min_ms": min(ms), "max_ms": max(ms), "packets_per_s": m / (med * 1e-3)}
+        return {"runs": n, "median_ms": med, "min_ms": min(ms), "max_ms": max(ms), "packets_per_s": m / (med * 1e-3)}
 
     out = {"decompose": timed(lambda: fgr.fgr_decompose(ctx.handle, u0, mesh, stream))}
     # window points per packet: (2 R sqrt(eps) / h + 1)^d with the context's R
@@ -392,7 +396,7 @@ def decompose_runs(fgr, ctx, w, init, pot, stream, flush, runs=20):
                     for l in range(d))
     out["decompose"]["window_points_per_packet"] = pts
     out["decompose"]["gpoints_per_s"] = m * pts / (out["decompose"]["median_ms"] * 1e-3) / 1e9
-    if d < 3:
+    if multistep:
         fq, fp = init[0].clone(), init[1].clone()
         fs = torch.zeros_like(init[2])
         fa = torch.zeros_like(init[3])
@@ -421,6 +425,7 @@ def reconstruct_bench(cfg: int, args, flush):
     ctx = fgr.Context(d, grid, eps, fgr.make_options(precision=prec))
     arrs = [torch.tensor(np.ascontiguousarray(w["packets"][k]), dtype=torch.float64, device="cuda") for k in "qpsa"]
     pk = fgr.make_packets(*arrs)
+    init = [x.clone() for x in arrs]
     t0 = time.perf_counter()
     fgr.fgr_propagate(ctx.handle, pk, fgr.make_potential(**w["potential"]), w["t"], w["dt"])
     torch.cuda.synchronize()
@@ -460,6 +465,8 @@ def reconstruct_bench(cfg: int, args, flush):
     fgr.fgr_reconstruct_fggc(ctx.handle, pk, uf, stream)
     st = fgr.fgr_get_stats(ctx.handle)
     tuned = list(fgr.fgr_get_tuning(ctx.handle))
+    decomp = decompose_runs(fgr, ctx, w, init, None, stream, flush, multistep=False)
+    del init
     ctx.close()
     return {"workload": w["name"], "packets": M, "propagate_s_untimed": t_prop,
             "fggc_ms": res["fggc"], "direct_ms": res["direct"],
@@ -469,6 +476,7 @@ def reconstruct_bench(cfg: int, args, flush):
             "fggc_q2p2_over_direct": (res["direct"] / res["fggc_q2p2"] if rel_q2 <= 1e-5
                                       else "not at equal accuracy (rel L2 > 1e-5)"),
             "fggc_nodes": int(st.nodes), "autotuned_ctas_per_sm_and_tile": tuned,
+            "decompose": decomp["decompose"],
             "fggc_stage_split_ms": {"bounds_alloc": st.prep_ms, "coeff_scatter": st.scatter_ms, "grid": st.grid_ms}}
 
 

@@ -108,3 +108,37 @@ def test_decompose_empty_and_invalid(fgr):
         with pytest.raises(fgr.FgrError):
             fgr.fgr_decompose(ctx.handle, np.zeros(64, np.complex128),
                               fgr.make_packets(*[np.ascontiguousarray(bad[k]) for k in "qpsa"]))
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_decompose_grouped_packets_ragged_tail(fgr, d):
+    # enough packets that every warp takes 32 of them (the last group ragged);
+    # the oracle evaluates a seeded sample, the first and the last packets
+    n = (70, 101) if d == 2 else (20, 17, 23)
+    m = 200003
+    grid = dict(d=d, n=list(n), lo=[-math.pi] * d, hi=[math.pi] * d)
+    eps = 1 / 64
+    rng = np.random.default_rng(70 + d)
+    u = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    pk = random_packets(80 + d, d, m, q_range=(-3.6, 3.6), p_range=(-4, 4))
+    for prec, tol in (("fp32", 1e-5), ("fp64", 1e-12)):
+        a, s = _run(fgr, grid, eps, u, pk, prec)
+        sel = np.unique(np.concatenate([rng.choice(m, 1500, replace=False), np.arange(40), np.arange(m - 40, m)]))
+        ref = decompose.decompose(u, grid, pk["q"][:, sel], pk["p"][:, sel], eps, R=8 if prec == "fp64" else 6)
+        assert _rel(a[:, sel], ref) <= tol, prec
+        assert np.all(s == 0)
+
+
+@pytest.mark.parametrize("shape", [(40, 300), (40, 600), (24, 1500), (12, 10, 400)])
+def test_decompose_long_last_dimension(fgr, shape):
+    # windows of about 70, 140 and 360 points along the last dimension: the
+    # FP32 kernel keeps them in 2, 4 or 8 registers per lane, or reads the table
+    d = len(shape)
+    grid = dict(d=d, n=list(shape), lo=[-math.pi] * d, hi=[math.pi] * d)
+    eps = 1 / 64
+    rng = np.random.default_rng(sum(shape))
+    u = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    pk = random_packets(len(shape) * 7 + shape[-1], d, 300, q_range=(-3.6, 3.6), p_range=(-4, 4))
+    ref = decompose.decompose(u, grid, pk["q"], pk["p"], eps, R=6)
+    a, _ = _run(fgr, grid, eps, u, pk, "fp32")
+    assert _rel(a, ref) <= 1e-5
