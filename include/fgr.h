@@ -147,10 +147,45 @@ fgr_status fgr_propagate(fgr_ctx *ctx, fgr_packets *inout, const fgr_potential *
  * (the rectangle rule of eq. 2.8 on the grid) over the same box window
  * |x_l - q_l| <= R sqrt(eps) as the reconstructions, and s_j = 0; packets
  * whose window misses the grid get a_j = 0.  FP64: every term in FP64.  FP32:
- * the phase is reduced in FP64 per packet, each term evaluated in FP32, sums
- * folded into FP64.  Host packets are copied back before the call returns.
- * FGR_E_INVALID for NULL arguments or non-finite host packet data. */
+ * the phase is reduced in FP64 per packet, each term evaluated in FP32 (d = 1:
+ * every fourth point along the lane's stride by ex2 and sincos, the others by
+ * the exact recurrences of the Gaussian and the phase; d = 2, 3: per-dimension
+ * factors, since the term factorises), compensated FP32 sums.  Host packets
+ * are copied back before the call returns.  FGR_E_INVALID for NULL arguments
+ * or non-finite host packet data. */
 fgr_status fgr_decompose(fgr_ctx *ctx, const void *u_in, fgr_packets *inout, void *cuda_stream);
+
+/* One dimension of a tensor-product packet mesh: n (q, p) pairs. */
+typedef struct {
+    int64_t n;          /* entries, >= 1 */
+    const double *q;    /* [n] centres along this dimension */
+    const double *p;    /* [n] momenta along this dimension */
+    int32_t on_device;  /* 1: device pointers, 0: host pointers */
+    int32_t reserved;
+} fgr_axis;
+
+/* Eq. 2.8, as fgr_decompose, for packets on a tensor-product mesh (the
+ * phase-space meshes of Sec. 2.1 and Algorithm 3 are of this form).  Packet
+ * (i_0, ..., i_{d-1}) sits at Q_l = axes[l].q[i_l], P_l = axes[l].p[i_l]; its
+ * index is row-major, ((i_0 n_1 + i_1) n_2 + i_2) for d = 3.  For j < m,
+ * a_out[j] and a_out[m + j] receive the real and imaginary parts of A(0) of
+ * the packet with index sel[j] (sel NULL: index j, and m must equal
+ * n_0 ... n_{d-1}).  The kernel of eq. 2.8 factorises over dimensions, so for
+ * d >= 2 the sum runs as d banded contractions, last dimension first (work
+ * proportional to the grid and list sizes times the window length, not to the
+ * packets times the window volume); d = 1 runs fgr_decompose's kernel on the
+ * listed packets.  The results equal fgr_decompose's on the same packets to
+ * rounding.  Axes sorted by q keep each block of 64 consecutive entries
+ * within about one window (unsorted axes are correct but slower).  u_in, sel
+ * and a_out: host or device memory (detected).  The library allocates two
+ * intermediate arrays of at most the largest partial product of grid and list
+ * extents (complex, the context's precision).  FGR_E_INVALID for NULL
+ * arguments, an axis with n < 1, a product of more than 2^40 packets, m < 0 or
+ * m > 2^31, sel NULL with m != n_0 ... n_{d-1}, non-finite host axis data, or
+ * a sel entry outside [0, n_0 ... n_{d-1}) (a device sel is checked on the
+ * device, and that check waits for the stream). */
+fgr_status fgr_decompose_tensor(fgr_ctx *ctx, const fgr_axis *axes, const void *u_in, int64_t m,
+                                const int64_t *sel, double *a_out, void *cuda_stream);
 
 /* Algorithm 3 (multi-step FGGC) with a fixed phase-space mesh and the flow
  * learned once.  mesh: packets at the mesh positions (q, p) onto which every
@@ -166,6 +201,15 @@ fgr_status fgr_decompose(fgr_ctx *ctx, const void *u_in, fgr_packets *inout, voi
  * steps < 0 or an argument is NULL. */
 fgr_status fgr_fggc_multistep(fgr_ctx *ctx, const fgr_packets *mesh, const fgr_packets *flow, const void *u_in,
                               void *u_out, int32_t steps, void *cuda_stream);
+
+/* Algorithm 3 as fgr_fggc_multistep, with the fixed mesh given as a tensor
+ * product (axes and sel as in fgr_decompose_tensor, m = flow->m): each step
+ * decomposes by fgr_decompose_tensor's contractions.  flow packet j is mesh
+ * packet sel[j] (j without sel) propagated over one step from unit
+ * amplitude.  Errors as fgr_decompose_tensor and fgr_fggc_multistep. */
+fgr_status fgr_fggc_multistep_tensor(fgr_ctx *ctx, const fgr_axis *axes, const int64_t *sel,
+                                     const fgr_packets *flow, const void *u_in, void *u_out, int32_t steps,
+                                     void *cuda_stream);
 
 /* Eq. 2.10 over the box window: u(x_m) = pref * sum_j A_j exp(i/eps (S_j +
  * P_j.(x_m - Q_j)) - |x_m - Q_j|^2/(2 eps)).  FP64: every term in FP64.

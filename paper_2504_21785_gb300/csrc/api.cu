@@ -309,6 +309,85 @@ fgr_status stage_packets(fgr_ctx *ctx, const fgr_packets *pk, cudaStream_t st, S
     return FGR_OK;
 }
 
+// Tensor-product mesh arguments (fgr_decompose_tensor): every axis present
+// with n >= 1 and finite host data, a product of at most 2^40 packets, m in
+// [0, 2^31], and a host selection inside the product.
+fgr_status check_axes(const fgr_ctx *ctx, const fgr_axis *axes, int64_t m, const int64_t *sel, int64_t *total) {
+    if (!axes) {
+        set_error("axes: NULL");
+        return FGR_E_INVALID;
+    }
+    int64_t tot = 1;
+    for (int l = 0; l < ctx->d; ++l) {
+        const fgr_axis &A = axes[l];
+        if (A.n < 1 || !A.q || !A.p || (A.on_device != 0 && A.on_device != 1)) {
+            set_error("axes: axis %d needs n >= 1, non-NULL q and p, on_device 0 or 1", l);
+            return FGR_E_INVALID;
+        }
+        if (A.n > (int64_t(1) << 40) / tot) {
+            set_error("axes: more than 2^40 packets in the product");
+            return FGR_E_INVALID;
+        }
+        tot *= A.n;
+        if (!A.on_device)
+            for (int64_t i = 0; i < A.n; ++i)
+                if (!is_finite(A.q[i]) || !is_finite(A.p[i])) {
+                    set_error("axes: non-finite q or p at axis %d entry %lld", l, (long long)i);
+                    return FGR_E_INVALID;
+                }
+    }
+    if (m < 0 || m > (int64_t(1) << 31)) {
+        set_error("decompose_tensor: m must lie in [0, 2^31]");
+        return FGR_E_INVALID;
+    }
+    if (!sel && m != tot) {
+        set_error("decompose_tensor: without sel, m (%lld) must equal the product of the axis lengths (%lld)",
+                  (long long)m, (long long)tot);
+        return FGR_E_INVALID;
+    }
+    if (sel && m > 0 && !is_device_ptr(sel))
+        for (int64_t j = 0; j < m; ++j)
+            if (sel[j] < 0 || sel[j] >= tot) {
+                set_error("decompose_tensor: sel[%lld] = %lld outside [0, %lld)", (long long)j, (long long)sel[j],
+                          (long long)tot);
+                return FGR_E_INVALID;
+            }
+    *total = tot;
+    return FGR_OK;
+}
+
+// Device views of the axis lists and the selection (host data copied in; a
+// device selection range-checked on the device).
+fgr_status stage_axes(fgr_ctx *ctx, const fgr_axis *axes, int64_t m, const int64_t *sel, int64_t total,
+                      cudaStream_t st, Scratch &scratch, AxisDev *out, const int64_t **sel_dev) {
+    for (int l = 0; l < ctx->d; ++l) {
+        const fgr_axis &A = axes[l];
+        out[l].L = A.n;
+        if (A.on_device) {
+            out[l].q = A.q;
+            out[l].p = A.p;
+            continue;
+        }
+        double *buf = (double *)scratch.get(sizeof(double) * 2 * (size_t)A.n);
+        if (!buf) return FGR_E_NOMEM;
+        FGR_CUDA_TRY(cudaMemcpyAsync(buf, A.q, sizeof(double) * A.n, cudaMemcpyHostToDevice, st));
+        FGR_CUDA_TRY(cudaMemcpyAsync(buf + A.n, A.p, sizeof(double) * A.n, cudaMemcpyHostToDevice, st));
+        out[l].q = buf;
+        out[l].p = buf + A.n;
+    }
+    *sel_dev = nullptr;
+    if (!sel || m == 0) return FGR_OK;
+    if (is_device_ptr(sel)) {
+        *sel_dev = sel;
+        return check_selection_device(ctx, sel, m, total, st, scratch);
+    }
+    int64_t *buf = (int64_t *)scratch.get(sizeof(int64_t) * (size_t)m);
+    if (!buf) return FGR_E_NOMEM;
+    FGR_CUDA_TRY(cudaMemcpyAsync(buf, sel, sizeof(int64_t) * m, cudaMemcpyHostToDevice, st));
+    *sel_dev = buf;
+    return FGR_OK;
+}
+
 template <class F>
 fgr_status guarded(F f) {
     try {
@@ -409,6 +488,36 @@ fgr_status reconstruct_direct_batch(int32_t n, fgr_ctx *const *ctxs, const fgr_p
 }  // namespace fgr
 
 using namespace fgr;
+
+// Steps of Algorithm 3 shared by both mesh forms: decompose(u, a0) writes the
+// amplitudes of the mesh packets, then the learned factors and FGGC.
+template <class Decompose>
+fgr_status multistep_loop(fgr_ctx *ctx, const PacketsDev &df, const void *u_in, void *u_out, int32_t steps,
+                          cudaStream_t st, Scratch &scratch, void *stream, Decompose decompose) {
+    const int64_t m = df.m;
+    const size_t bytes = elem_bytes(ctx->opt.precision) * (size_t)ctx->grid.total;
+    const size_t mm = (size_t)std::max<int64_t>(m, 1);
+    void *ua = scratch.get(bytes), *ub = scratch.get(bytes);
+    double *a0 = (double *)scratch.get(sizeof(double) * 2 * mm);
+    double *aw = (double *)scratch.get(sizeof(double) * 2 * mm);
+    if (!ua || !ub || !a0 || !aw) return FGR_E_NOMEM;
+    FGR_CUDA_TRY(cudaMemcpyAsync(ua, u_in, bytes, cudaMemcpyDefault, st));
+    void *cur = ua;
+    for (int32_t it = 0; it < steps; ++it) {
+        Scratch step_scratch(ctx, st);
+        fgr_status r = decompose(cur, a0, step_scratch);                    // Step 1 (eq. 2.8)
+        if (r == FGR_OK) r = run_scale_amplitudes(a0, df.a, aw, m, st);      // Step 2: learned flow
+        if (r != FGR_OK) return r;
+        void *dst = cur == ua ? ub : ua;
+        r = run_fggc(ctx, PacketsDev{m, df.q, df.p, df.s, aw}, dst, st, step_scratch);  // Step 3
+        if (r != FGR_OK) return r;
+        cur = dst;
+    }
+    FGR_CUDA_TRY(cudaMemcpyAsync(u_out, cur, bytes, cudaMemcpyDefault, st));
+    FGR_CUDA_TRY(cudaGetLastError());
+    if (!stream || !is_device_ptr(u_out)) FGR_CUDA_TRY(cudaStreamSynchronize(st));
+    return FGR_OK;
+}
 
 extern "C" {
 
@@ -608,6 +717,52 @@ fgr_status fgr_decompose(fgr_ctx *ctx, const void *u_in, fgr_packets *pk, void *
     });
 }
 
+fgr_status fgr_decompose_tensor(fgr_ctx *ctx, const fgr_axis *axes, const void *u_in, int64_t m, const int64_t *sel,
+                                double *a_out, void *stream) {
+    clear_error();
+    if (!ctx || !u_in || (m > 0 && !a_out)) {
+        set_error("decompose_tensor: ctx, u_in and a_out must be non-NULL");
+        return FGR_E_INVALID;
+    }
+    int64_t total = 0;
+    fgr_status rc = check_axes(ctx, axes, m, sel, &total);
+    if (rc != FGR_OK) return rc;
+    return guarded([&]() -> fgr_status {
+        FGR_CUDA_TRY(cudaSetDevice(ctx->device));
+        cudaStream_t st = (cudaStream_t)stream;
+        memset(&ctx->timing.last, 0, sizeof(ctx->timing.last));
+        Scratch scratch(ctx, st);
+        AxisDev ax[FGR_MAX_DIM];
+        const int64_t *sel_dev = nullptr;
+        fgr_status r = stage_axes(ctx, axes, m, sel, total, st, scratch, ax, &sel_dev);
+        if (r != FGR_OK || m == 0) return r;
+        const void *u_dev = u_in;
+        if (!is_device_ptr(u_in)) {
+            const size_t bytes = elem_bytes(ctx->opt.precision) * (size_t)ctx->grid.total;
+            void *buf = scratch.get(bytes);
+            if (!buf) return FGR_E_NOMEM;
+            FGR_CUDA_TRY(cudaMemcpyAsync(buf, u_in, bytes, cudaMemcpyHostToDevice, st));
+            u_dev = buf;
+        }
+        const bool dev_out = is_device_ptr(a_out);
+        double *a = a_out;
+        if (!dev_out) {
+            a = (double *)scratch.get(sizeof(double) * 2 * (size_t)m);
+            if (!a) return FGR_E_NOMEM;
+        }
+        r = run_decompose_tensor(ctx, ax, u_dev, m, sel_dev, a, st, scratch);
+        if (r != FGR_OK) return r;
+        if (!dev_out) {
+            FGR_CUDA_TRY(cudaMemcpyAsync(a_out, a, sizeof(double) * 2 * (size_t)m, cudaMemcpyDeviceToHost, st));
+            FGR_CUDA_TRY(cudaStreamSynchronize(st));
+        } else if (!stream) {
+            FGR_CUDA_TRY(cudaStreamSynchronize(st));
+        }
+        return FGR_OK;
+    });
+}
+
+
 fgr_status fgr_fggc_multistep(fgr_ctx *ctx, const fgr_packets *mesh, const fgr_packets *flow, const void *u_in,
                               void *u_out, int32_t steps, void *stream) {
     clear_error();
@@ -626,36 +781,50 @@ fgr_status fgr_fggc_multistep(fgr_ctx *ctx, const fgr_packets *mesh, const fgr_p
     return guarded([&]() -> fgr_status {
         FGR_CUDA_TRY(cudaSetDevice(ctx->device));
         cudaStream_t st = (cudaStream_t)stream;
-        const int64_t m = mesh->m;
-        const size_t bytes = elem_bytes(ctx->opt.precision) * (size_t)ctx->grid.total;
         Scratch scratch(ctx, st);
         PacketsDev dm, df;
         double *q, *p, *s, *a;
         fgr_status r = stage_packets(ctx, mesh, st, scratch, &dm, &q, &p, &s, &a);
         if (r == FGR_OK) r = stage_packets(ctx, flow, st, scratch, &df, &q, &p, &s, &a);
         if (r != FGR_OK) return r;
-        const size_t mm = (size_t)std::max<int64_t>(m, 1);
-        void *ua = scratch.get(bytes), *ub = scratch.get(bytes);
-        double *a0 = (double *)scratch.get(sizeof(double) * 2 * mm);
-        double *aw = (double *)scratch.get(sizeof(double) * 2 * mm);
-        double *s0 = (double *)scratch.get(sizeof(double) * mm);
-        if (!ua || !ub || !a0 || !aw || !s0) return FGR_E_NOMEM;
-        FGR_CUDA_TRY(cudaMemcpyAsync(ua, u_in, bytes, cudaMemcpyDefault, st));
-        void *cur = ua;
-        for (int32_t it = 0; it < steps; ++it) {
-            r = run_decompose(ctx, cur, dm.q, dm.p, s0, a0, m, st);         // Step 1 (eq. 2.8)
-            if (r == FGR_OK) r = run_scale_amplitudes(a0, df.a, aw, m, st);  // Step 2: learned flow
-            if (r != FGR_OK) return r;
-            void *dst = cur == ua ? ub : ua;
-            Scratch step_scratch(ctx, st);
-            r = run_fggc(ctx, PacketsDev{m, df.q, df.p, df.s, aw}, dst, st, step_scratch);  // Step 3
-            if (r != FGR_OK) return r;
-            cur = dst;
-        }
-        FGR_CUDA_TRY(cudaMemcpyAsync(u_out, cur, bytes, cudaMemcpyDefault, st));
-        FGR_CUDA_TRY(cudaGetLastError());
-        if (!stream || !is_device_ptr(u_out)) FGR_CUDA_TRY(cudaStreamSynchronize(st));
-        return FGR_OK;
+        double *s0 = (double *)scratch.get(sizeof(double) * (size_t)std::max<int64_t>(mesh->m, 1));
+        if (!s0) return FGR_E_NOMEM;
+        return multistep_loop(ctx, df, u_in, u_out, steps, st, scratch, stream,
+                              [&](const void *u, double *a0, Scratch &) {
+                                  return run_decompose(ctx, u, dm.q, dm.p, s0, a0, dm.m, st);
+                              });
+    });
+}
+
+fgr_status fgr_fggc_multistep_tensor(fgr_ctx *ctx, const fgr_axis *axes, const int64_t *sel,
+                                     const fgr_packets *flow, const void *u_in, void *u_out, int32_t steps,
+                                     void *stream) {
+    clear_error();
+    if (!ctx || !u_in || !u_out || steps < 0) {
+        set_error("multistep: need ctx, u_in, u_out and steps >= 0");
+        return FGR_E_INVALID;
+    }
+    fgr_status rc = check_packets(ctx, flow);
+    if (rc != FGR_OK) return rc;
+    int64_t total = 0;
+    rc = check_axes(ctx, axes, flow->m, sel, &total);
+    if (rc != FGR_OK) return rc;
+    return guarded([&]() -> fgr_status {
+        FGR_CUDA_TRY(cudaSetDevice(ctx->device));
+        cudaStream_t st = (cudaStream_t)stream;
+        Scratch scratch(ctx, st);
+        PacketsDev df;
+        double *q, *p, *s, *a;
+        fgr_status r = stage_packets(ctx, flow, st, scratch, &df, &q, &p, &s, &a);
+        if (r != FGR_OK) return r;
+        AxisDev ax[FGR_MAX_DIM];
+        const int64_t *sel_dev = nullptr;
+        r = stage_axes(ctx, axes, flow->m, sel, total, st, scratch, ax, &sel_dev);
+        if (r != FGR_OK) return r;
+        return multistep_loop(ctx, df, u_in, u_out, steps, st, scratch, stream,
+                              [&](const void *u, double *a0, Scratch &step_scratch) {
+                                  return run_decompose_tensor(ctx, ax, u, df.m, sel_dev, a0, st, step_scratch);
+                              });
     });
 }
 

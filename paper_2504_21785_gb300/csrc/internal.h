@@ -124,6 +124,19 @@ fgr_status run_propagate(fgr_ctx *ctx, double *q, double *p, double *s, double *
 // the wave u_dev (complex, the context's precision).
 fgr_status run_decompose(fgr_ctx *ctx, const void *u_dev, const double *q, const double *p, double *s, double *a,
                          int64_t m, cudaStream_t st);
+// One dimension of a tensor-product mesh (device pointers).
+struct AxisDev {
+    int64_t L;
+    const double *q, *p;
+};
+// Eq. 2.8 onto the tensor product of d lists: a (2 x m) of the packets with
+// row-major indices sel[j] (sel NULL: j); d >= 2 by banded contractions.
+fgr_status run_decompose_tensor(fgr_ctx *ctx, const AxisDev *axes, const void *u_dev, int64_t m,
+                                const int64_t *sel, double *a, cudaStream_t st, Scratch &scratch);
+// FGR_E_INVALID unless every sel[j] (device memory) lies in [0, total); waits
+// for the stream.
+fgr_status check_selection_device(fgr_ctx *ctx, const int64_t *sel, int64_t m, int64_t total, cudaStream_t st,
+                                  Scratch &scratch);
 // out = a0 * f, complex, planes [re][m] then [im][m].
 fgr_status run_scale_amplitudes(const double *a0, const double *f, double *out, int64_t m, cudaStream_t st);
 fgr_status run_direct(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t st,

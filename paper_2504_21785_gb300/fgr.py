@@ -47,6 +47,14 @@ class fgr_packets(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+FGR_MAX_DIM = 3
+
+
+class fgr_axis(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("q", ctypes.c_void_p), ("p", ctypes.c_void_p),
+                ("on_device", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class fgr_potential(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("c0", ctypes.c_double),
                 ("amp", ctypes.c_double), ("k", ctypes.c_double), ("omega", ctypes.c_double)]
@@ -91,6 +99,8 @@ SIGNATURES = {
                                      ctypes.c_double, vp]),
     "fgr_decompose": (ctypes.c_int, [vp, vp, P(fgr_packets), vp]),
     "fgr_fggc_multistep": (ctypes.c_int, [vp, P(fgr_packets), P(fgr_packets), vp, vp, ctypes.c_int32, vp]),
+    "fgr_decompose_tensor": (ctypes.c_int, [vp, P(fgr_axis), vp, ctypes.c_int64, vp, vp, vp]),
+    "fgr_fggc_multistep_tensor": (ctypes.c_int, [vp, P(fgr_axis), vp, P(fgr_packets), vp, vp, ctypes.c_int32, vp]),
     "fgr_reconstruct_direct": (ctypes.c_int, [vp, P(fgr_packets), vp, vp]),
     "fgr_reconstruct_fggc": (ctypes.c_int, [vp, P(fgr_packets), vp, vp]),
     "fgr_reconstruct_fggc_noalloc": (ctypes.c_int, [vp, P(fgr_packets), vp, vp]),
@@ -178,6 +188,22 @@ def make_packets(q, p, s, a) -> fgr_packets:
     return view
 
 
+def make_axes(axes):
+    """fgr_axis array from a list of (q, p) pairs of 1-D float64 arrays/tensors,
+    one pair per dimension.  The array holds references to them."""
+    arr = (fgr_axis * FGR_MAX_DIM)()
+    keep = []
+    for l, (q, p) in enumerate(axes):
+        pq, dq = _ptr(q)
+        pp, dp = _ptr(p)
+        if dq != dp:
+            raise ValueError("an axis's q and p must both live on the host or both on the device")
+        arr[l] = fgr_axis(int(q.shape[0]), pq, pp, dq, 0)
+        keep.append((q, p))
+    arr._arrays = keep
+    return arr
+
+
 def make_grid(grid: dict) -> fgr_grid:
     g = fgr_grid()
     g.d = int(grid["d"])
@@ -238,6 +264,18 @@ def fgr_propagate(ctx, packets: fgr_packets, potential: fgr_potential, t: float,
 def fgr_decompose(ctx, u_in, packets: fgr_packets, stream=None):
     """Writes the packets' amplitudes (a) and zero actions (s) from the wave u_in."""
     return _check(load().fgr_decompose(ctx, _ptr(u_in)[0], ctypes.byref(packets), _stream_handle(stream)))
+
+
+def fgr_decompose_tensor(ctx, axes, u_in, m: int, sel, a_out, stream=None):
+    """A(0) of the tensor-product mesh packets sel[j] (or all, in row-major order) into a_out (2, m)."""
+    return _check(load().fgr_decompose_tensor(ctx, axes, _ptr(u_in)[0], int(m), _ptr(sel)[0], _ptr(a_out)[0],
+                                              _stream_handle(stream)))
+
+
+def fgr_fggc_multistep_tensor(ctx, axes, sel, flow: fgr_packets, u_in, u_out, steps: int, stream=None):
+    """Multi-step FGGC with the mesh given as a tensor product (axes from make_axes)."""
+    return _check(load().fgr_fggc_multistep_tensor(ctx, axes, _ptr(sel)[0], ctypes.byref(flow), _ptr(u_in)[0],
+                                                   _ptr(u_out)[0], int(steps), _stream_handle(stream)))
 
 
 def fgr_fggc_multistep(ctx, mesh: fgr_packets, flow: fgr_packets, u_in, u_out, steps: int, stream=None):

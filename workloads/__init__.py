@@ -14,5 +14,5 @@ library implements it.
 
 from .wkb import (  # noqa: F401
     Mesh, WKB_TANH, WKB_LINEAR, config_workload, wkb_packets, mesh_for,
-    random_packets, CONFIGS,
+    random_packets, CONFIGS, mesh_axes, workload_axes,
 )

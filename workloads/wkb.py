@@ -184,6 +184,40 @@ def wkb_packets(d: int, eps: float, nq: int, np_: int, family: _Family = WKB_TAN
     }
 
 
+def mesh_axes(d: int, eps: float, nq: int, np_: int, family: _Family = WKB_TANH,
+              cq: float = 0.5, cp: float = math.pi / 8):
+    """The mesh of wkb_packets as a tensor product of per-dimension lists.
+
+    Returns (axes, sel): axes[l] = (q, p), nq * np_ pairs ordered (a, b)
+    row-major; sel[j] = the row-major tensor-product index of wkb_packets'
+    packet j, so packet j sits at (axes[l][0][i_l], axes[l][1][i_l]).
+    """
+    mesh = Mesh(d=d, eps=eps, cq=cq, cp=cp)
+    axes = []
+    for l in range(d):
+        a = np.arange(nq)
+        q = (a - nq // 2) * mesh.dq
+        centre = np.rint(family.ds0(l, q) / mesh.dp).astype(np.int64)
+        beta = centre[:, None] + (np.arange(np_)[None, :] - np_ // 2)
+        axes.append((np.ascontiguousarray(np.repeat(q, np_)), np.ascontiguousarray((beta * mesh.dp).reshape(-1))))
+    idx = np.indices((nq,) * d + (np_,) * d).reshape(2 * d, -1)
+    L = nq * np_
+    sel = np.zeros(idx.shape[1], dtype=np.int64)
+    for l in range(d):
+        sel = sel * L + idx[l] * np_ + idx[d + l]
+    return axes, sel
+
+
+def workload_axes(w: dict):
+    """(axes, sel) of a config_workload's t = 0 packets (kept ones only where
+    the workload keeps the largest amplitudes)."""
+    axes, sel = mesh_axes(w["d"], w["eps"], w["nq"], w["np_"], _FAMILIES[w["family"]])
+    keep = w["packets"].get("kept_index")
+    if keep is not None:
+        sel = sel[keep]
+    return axes, np.ascontiguousarray(sel)
+
+
 def select_top(packets: dict, pref: float, threshold: float, cap: int) -> dict:
     """Keep packets with pref*|A| > threshold; if more than `cap` remain keep the
     `cap` largest, ties broken towards the lower packet index."""
