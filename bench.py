@@ -350,11 +350,15 @@ def reconstruct_runs(fgr, ctx, packets, u_ref, grid, d, eps, prec, flush, stream
     return out
 
 
-def decompose_runs(fgr, ctx, w, init, pot, stream, flush, runs=20, multistep=True):
+def decompose_runs(fgr, ctx, w, init, pot, stream, flush, runs=20, multistep=True, moved=None):
     """Median/min/max ms of `runs` initial decompositions (eq. 2.8) of the
     workload's u0 onto its t = 0 packet positions, and of one multi-step FGGC
     step (Algorithm 3: decompose, apply the learned flow, FGGC) whose flow is
-    those positions propagated over the workload's time from unit amplitude."""
+    those positions propagated over the workload's time from unit amplitude.
+    For d >= 2 also the tensor-product decomposition of the same mesh
+    (fgr_decompose_tensor) and, given the propagated packets `moved`, one
+    multi-step FGGC step over the tensor mesh whose learned amplitude factors
+    are A(t) / A(0) of the workload (eq. 2.6 is linear in A)."""
     import math
     import numpy as np
     import torch
@@ -396,6 +400,31 @@ def decompose_runs(fgr, ctx, w, init, pot, stream, flush, runs=20, multistep=Tru
                     for l in range(d))
     out["decompose"]["window_points_per_packet"] = pts
     out["decompose"]["gpoints_per_s"] = m * pts / (out["decompose"]["median_ms"] * 1e-3) / 1e9
+    if d >= 2:
+        from workloads import workload_axes
+        axes_np, sel_np = workload_axes(w)
+        dev = init[0].device
+        axes = fgr.make_axes([(torch.tensor(q, device=dev), torch.tensor(p, device=dev)) for q, p in axes_np])
+        sel = torch.tensor(sel_np, device=dev)
+        at = torch.empty((2, m), dtype=torch.float64, device=dev)
+        out["decompose_tensor"] = timed(lambda: fgr.fgr_decompose_tensor(ctx.handle, axes, u0, m, sel, at, stream))
+        ap, aq = torch.complex(a[0], a[1]), torch.complex(at[0], at[1])
+        out["decompose_tensor"]["rel_l2_vs_per_packet_kernel"] = float(torch.linalg.norm(aq - ap) /
+                                                                       torch.linalg.norm(ap))
+        out["decompose_tensor"]["speedup_vs_per_packet_kernel"] = (out["decompose"]["median_ms"] /
+                                                                   out["decompose_tensor"]["median_ms"])
+        out["decompose_tensor"]["mesh"] = "%d-dim tensor product of %d-entry axes, %d packets selected" % (
+            d, axes_np[0][0].size, m)
+        if moved is not None:
+            a0 = torch.complex(init[3][0], init[3][1])
+            at_ = torch.complex(moved[3][0], moved[3][1])
+            fac = torch.where(a0 != 0, at_ / torch.where(a0 != 0, a0, torch.ones_like(a0)), torch.zeros_like(a0))
+            flow = fgr.make_packets(moved[0], moved[1], moved[2], torch.stack([fac.real, fac.imag]).contiguous())
+            u1 = torch.empty_like(u0)
+            out["multistep_tensor_1_step"] = timed(
+                lambda: fgr.fgr_fggc_multistep_tensor(ctx.handle, axes, sel, flow, u0, u1, 1, stream))
+            out["multistep_tensor_1_step"]["note"] = ("tensor decomposition + learned factors + FGGC; "
+                                                      "factors A(t)/A(0) of the workload's propagation, untimed")
     if multistep:
         fq, fp = init[0].clone(), init[1].clone()
         fs = torch.zeros_like(init[2])
@@ -465,7 +494,7 @@ def reconstruct_bench(cfg: int, args, flush):
     fgr.fgr_reconstruct_fggc(ctx.handle, pk, uf, stream)
     st = fgr.fgr_get_stats(ctx.handle)
     tuned = list(fgr.fgr_get_tuning(ctx.handle))
-    decomp = decompose_runs(fgr, ctx, w, init, None, stream, flush, multistep=False)
+    decomp = decompose_runs(fgr, ctx, w, init, None, stream, flush, multistep=False, moved=arrs)
     del init
     ctx.close()
     return {"workload": w["name"], "packets": M, "propagate_s_untimed": t_prop,
@@ -476,7 +505,7 @@ def reconstruct_bench(cfg: int, args, flush):
             "fggc_q2p2_over_direct": (res["direct"] / res["fggc_q2p2"] if rel_q2 <= 1e-5
                                       else "not at equal accuracy (rel L2 > 1e-5)"),
             "fggc_nodes": int(st.nodes), "autotuned_ctas_per_sm_and_tile": tuned,
-            "decompose": decomp["decompose"],
+            "decompose": decomp,
             "fggc_stage_split_ms": {"bounds_alloc": st.prep_ms, "coeff_scatter": st.scatter_ms, "grid": st.grid_ms}}
 
 
@@ -757,7 +786,8 @@ def run_profile_case(args):
     reconstruction of the propagated packets, one batched direct sum of
     eight copies of that request and one initial decomposition of the
     reconstructed wave onto the propagated positions (FGGC only for 3-D
-    workloads)."""
+    workloads); for d >= 2 one tensor-product decomposition of that wave onto
+    the t = 0 mesh."""
     import numpy as np
     import torch
 
@@ -767,11 +797,12 @@ def run_profile_case(args):
     d, eps, grid = w["d"], w["eps"], w["grid"]
     prec = fgr.FGR_FP32 if w["precision"] == "fp32" else fgr.FGR_FP64
     pk = w["packets"]
+    pick = None
     if args.profile_packets and args.profile_packets < pk["s"].size:
         # the largest amplitudes, in their original order (a smaller case of the same shape)
         amp = np.hypot(pk["a"][0], pk["a"][1])
-        sel = np.sort(np.argsort(-amp, kind="stable")[:args.profile_packets])
-        pk = {k: np.ascontiguousarray(pk[k][..., sel]) for k in "qpsa"}
+        pick = np.sort(np.argsort(-amp, kind="stable")[:args.profile_packets])
+        pk = {k: np.ascontiguousarray(pk[k][..., pick]) for k in "qpsa"}
     with fgr.Context(d, grid, eps, fgr.make_options(precision=prec)) as ctx:
         arrs = [torch.tensor(np.ascontiguousarray(pk[k]), dtype=torch.float64, device="cuda")
                 for k in "qpsa"]
@@ -785,6 +816,16 @@ def run_profile_case(args):
             outs = [torch.zeros_like(u) for _ in range(8)]
             fgr.fgr_reconstruct_direct_batch([ctx] * 8, [pk] * 8, outs)
             fgr.fgr_decompose(ctx.handle, u, pk)
+        if d >= 2:  # the same mesh as a tensor product, decomposed by contractions
+            from workloads import workload_axes
+            axes_np, sel_np = workload_axes(w)
+            if pick is not None:
+                sel_np = sel_np[pick]
+            axes = fgr.make_axes([(torch.tensor(q, device="cuda"), torch.tensor(p, device="cuda"))
+                                  for q, p in axes_np])
+            sel = torch.tensor(np.ascontiguousarray(sel_np), device="cuda")
+            at = torch.empty((2, sel.numel()), dtype=torch.float64, device="cuda")
+            fgr.fgr_decompose_tensor(ctx.handle, axes, u, sel.numel(), sel, at)
         torch.cuda.synchronize()
     print(json.dumps({"profile_case": "config %d" % args.config, "ok": True}))
 
