@@ -53,7 +53,7 @@ struct ContractParams {
 constexpr float kTwoPiF = 6.283185307179586f;
 
 template <bool FP64, int RI, int RT>
-__global__ void __launch_bounds__(kNT) axis_contract_kernel(const ContractParams C) {
+__global__ void __launch_bounds__(kNT, 2) axis_contract_kernel(const ContractParams C) {
     using Real = typename std::conditional<FP64, double, float>::type;
     using C2 = typename std::conditional<FP64, double2, float2>::type;
     constexpr int TI = 8 * RI, TS = 32 * RT;

@@ -41,7 +41,7 @@ constexpr int kMaxSeg = 1024;                  // segments per tile list
 // the last dimension's extent is a multiple of kTpt.
 template <int D>
 __host__ __device__ constexpr int tileT(int l) {
-    return D == 1 ? 1024 : (D == 2 ? (l == 0 ? 16 : 64) : (l < 2 ? 8 : 16));
+    return D == 1 ? 1024 : (D == 2 ? 32 : (l < 2 ? 8 : 16));
 }
 static_assert(tileT<1>(0) == kThreads * kTpt && tileT<2>(0) * tileT<2>(1) == kThreads * kTpt &&
                   tileT<3>(0) * tileT<3>(1) * tileT<3>(2) == kThreads * kTpt,
@@ -232,21 +232,38 @@ __host__ __device__ constexpr int kSub() {
     return D == 3 ? 64 : 32;  // records per factor table (20 KB for d = 2, 16 KB for d = 3)
 }
 
+// Points of a thread in the separable path (FP32, d >= 2): a 2 x 2 block of
+// the tile, so that each staged record costs two 16-byte factor loads and four
+// complex multiply-adds.  d = 2 (32 x 32 tile): rows 2 (tid / 16) + {0, 1},
+// columns 2 (tid % 16) + {0, 1}.  d = 3 (8 x 8 x 16 tile): i = tid / 32,
+// j = 2 ((tid / 8) % 4) + {0, 1}, k = 2 (tid % 8) + {0, 1}.  Point r of the
+// block is (second-to-last + r / 2, last + r % 2).
+template <int D>
+__device__ __forceinline__ void separable_local(int tid, int *loc) {
+    if (D == 2) {
+        loc[0] = 2 * (tid / 16);
+        loc[1] = 2 * (tid % 16);
+    } else {
+        loc[0] = tid / 32;
+        loc[1] = 2 * ((tid / 8) % 4);
+        loc[2] = 2 * (tid % 8);
+    }
+}
+
 template <int D>
 __device__ __forceinline__ void separable_chunk(const int *__restrict__ srec, const int nrec, const DirectParams &P,
-                                                const int *t, const int (*mi)[D], float2 *__restrict__ sfac,
-                                                float (*accf)[2]) {
+                                                const int *t, float2 *__restrict__ sfac, float (*accf)[2]) {
     constexpr int kWords = sizeof(RecF<D>) / 4;
     constexpr int kS = kSub<D>(), kT = kSumT<D>();
-    int loc[D];  // this thread's first point within the tile
-#pragma unroll
-    for (int l = 0; l < D; ++l) loc[l] = mi[0][l] - t[l] * tileT<D>(l);
-    int foff_last = 0;
-#pragma unroll
-    for (int l = 0; l < D - 1; ++l) foff_last += tileT<D>(l);
+    int loc[D];
+    separable_local<D>(threadIdx.x, loc);
+    // offsets of this thread's factors in a record's table
+    const int o_a = loc[0];                                  // d = 2: rows; d = 3: i
+    const int o_b = tileT<D>(0) + loc[1];                    // d = 2: columns; d = 3: j
+    const int o_c = D == 3 ? tileT<D>(0) + tileT<D>(1) + loc[2] : 0;  // d = 3: k
     for (int s0 = 0; s0 < nrec; s0 += kS) {
         const int ns = min(kS, nrec - s0);
-        // factor tables of records s0 .. s0 + ns - 1
+        // factor tables of records s0 .. s0 + ns - 1 (zero outside the window)
         for (int e = threadIdx.x; e < ns * kT; e += kThreads) {
             const int jr = s0 + e / kT;
             int qd = e % kT, l = 0;
@@ -278,30 +295,29 @@ __device__ __forceinline__ void separable_chunk(const int *__restrict__ srec, co
             sfac[e] = f;
         }
         __syncthreads();
+#pragma unroll 4
         for (int jj = 0; jj < ns; ++jj) {
-            const RecF<D> &R = *reinterpret_cast<const RecF<D> *>(&srec[(s0 + jj) * kWords]);
-            bool in = true;  // skip packets whose window misses this thread's points
-#pragma unroll
-            for (int l = 0; l < D - 1; ++l) {
-                const float k = (float)mi[0][l] - R.mlo[l];
-                in = in && k >= 0.f && k < R.wlen[l];
-            }
-            const float kl = (float)mi[0][D - 1] - R.mlo[D - 1];
-            in = in && kl > -(float)kTpt && kl < R.wlen[D - 1];
-            if (!in) continue;
             const float2 *F = sfac + jj * kT;
-            float2 pre = F[loc[0]];
-            if (D == 3) {
-                const float2 f1 = F[tileT<D>(0) + loc[1]];
-                pre = make_float2(pre.x * f1.x - pre.y * f1.y, pre.x * f1.y + pre.y * f1.x);
+            float ar[2], ai[2];  // factors of the second-to-last dimension (times the outer one for d = 3)
+            float br[2], bi[2];  // factors of the last dimension
+            if (D == 2) {
+                const float4 a = *reinterpret_cast<const float4 *>(F + o_a);
+                const float4 b = *reinterpret_cast<const float4 *>(F + o_b);
+                ar[0] = a.x; ai[0] = a.y; ar[1] = a.z; ai[1] = a.w;
+                br[0] = b.x; bi[0] = b.y; br[1] = b.z; bi[1] = b.w;
+            } else {
+                const float2 p = F[o_a];
+                const float4 a = *reinterpret_cast<const float4 *>(F + o_b);
+                const float4 b = *reinterpret_cast<const float4 *>(F + o_c);
+                ar[0] = p.x * a.x - p.y * a.y; ai[0] = p.x * a.y + p.y * a.x;
+                ar[1] = p.x * a.z - p.y * a.w; ai[1] = p.x * a.w + p.y * a.z;
+                br[0] = b.x; bi[0] = b.y; br[1] = b.z; bi[1] = b.w;
             }
-            const float4 a01 = *reinterpret_cast<const float4 *>(F + foff_last + loc[D - 1]);
-            const float4 a23 = *reinterpret_cast<const float4 *>(F + foff_last + loc[D - 1] + 2);
-            const float fr[4] = {a01.x, a01.z, a23.x, a23.z}, fi[4] = {a01.y, a01.w, a23.y, a23.w};
 #pragma unroll
-            for (int r = 0; r < kTpt; ++r) {
-                accf[r][0] = fmaf(pre.x, fr[r], fmaf(-pre.y, fi[r], accf[r][0]));
-                accf[r][1] = fmaf(pre.x, fi[r], fmaf(pre.y, fr[r], accf[r][1]));
+            for (int r = 0; r < 4; ++r) {
+                const int ia = r >> 1, ib = r & 1;
+                accf[r][0] = fmaf(ar[ia], br[ib], fmaf(-ai[ia], bi[ib], accf[r][0]));
+                accf[r][1] = fmaf(ar[ia], bi[ib], fmaf(ai[ia], br[ib], accf[r][1]));
             }
         }
         __syncthreads();
@@ -372,18 +388,26 @@ __device__ __forceinline__ void direct_tile(const void *__restrict__ recs_v, con
     const int64_t L = (int64_t)seg_cum[nseg];
 
     // this thread's points: kTpt consecutive points along the last dimension
+    // (FP64 and d = 1), or the 2 x 2 block of separable_local (FP32, d >= 2)
     constexpr int kLane = tileT<D>(D - 1) / kTpt;  // threads along the last dimension
     int mi[kTpt][D];
     bool valid[kTpt];
     int64_t lin_out[kTpt];
     {
         int base[D];
-        int i = threadIdx.x / kLane;
-        base[D - 1] = t[D - 1] * tileT<D>(D - 1) + (threadIdx.x % kLane) * kTpt;
+        if constexpr (!FP64 && D >= 2) {
+            int loc[D];
+            separable_local<D>(threadIdx.x, loc);
 #pragma unroll
-        for (int l = D - 2; l >= 0; --l) {
-            base[l] = t[l] * tileT<D>(l) + i % tileT<D>(l);
-            i /= tileT<D>(l);
+            for (int l = 0; l < D; ++l) base[l] = t[l] * tileT<D>(l) + loc[l];
+        } else {
+            int i = threadIdx.x / kLane;
+            base[D - 1] = t[D - 1] * tileT<D>(D - 1) + (threadIdx.x % kLane) * kTpt;
+#pragma unroll
+            for (int l = D - 2; l >= 0; --l) {
+                base[l] = t[l] * tileT<D>(l) + i % tileT<D>(l);
+                i /= tileT<D>(l);
+            }
         }
 #pragma unroll
         for (int r = 0; r < kTpt; ++r) {
@@ -391,7 +415,12 @@ __device__ __forceinline__ void direct_tile(const void *__restrict__ recs_v, con
             int64_t lin = 0;
 #pragma unroll
             for (int l = 0; l < D; ++l) {
-                mi[r][l] = base[l] + (l == D - 1 ? r : 0);
+                int off = 0;
+                if (!FP64 && D >= 2)
+                    off = l == D - 2 ? (r >> 1) : (l == D - 1 ? (r & 1) : 0);
+                else
+                    off = l == D - 1 ? r : 0;
+                mi[r][l] = base[l] + off;
                 ok = ok && mi[r][l] < g.n[l];
                 lin = lin * g.n[l] + mi[r][l];
             }
@@ -448,7 +477,7 @@ __device__ __forceinline__ void direct_tile(const void *__restrict__ recs_v, con
         const int64_t left = L - c * kThreads;
         const int nrec = left < kThreads ? (int)left : kThreads;
         if constexpr (!FP64 && D >= 2)
-            separable_chunk<D>(srec, nrec, P, t, mi, sfac, accf);
+            separable_chunk<D>(srec, nrec, P, t, sfac, accf);
         else
         for (int jr = 0; jr < nrec; ++jr) {
             const Rec &R = *reinterpret_cast<const Rec *>(&srec[jr * kWords]);
