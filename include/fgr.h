@@ -307,8 +307,11 @@ void fgr_fggc_plan_destroy(fgr_fggc_plan *plan);
 
 /* Autotuner of the launch shapes (not in the paper: it serves the batching and
  * serving side of the library).  Times, with CUDA events on the given stream,
- * the candidate CTA-per-SM targets of the direct sum (methods & 1: 2, 4, 8, 16,
- * 32) and, for the FGGC grid passes (methods & 2), the tile width (128 or 32
+ * the candidate work-item targets per SM of the direct sum (methods & 1: 2, 4,
+ * 8, 16, 32; fgr_reconstruct_direct cuts each output tile's packet list into
+ * slices in proportion to its length so that about that many items per SM
+ * exist, heaviest first, and persistent CTAs pull them; the batched call gives
+ * every tile of a request the same number of slices) and, for the FGGC grid passes (methods & 2), the tile width (128 or 32
  * grid points per CTA) with each CTA-per-SM target (4, 8, 16, 32, 64) on these
  * packets and this context's grid (u_out receives the last result), keeps the
  * fastest in the context and in a process-wide table keyed by (d, precision,
@@ -317,8 +320,8 @@ void fgr_fggc_plan_destroy(fgr_fggc_plan *plan);
  * Waits for its own timing runs. */
 fgr_status fgr_autotune(fgr_ctx *ctx, const fgr_packets *pk, void *u_out, int32_t methods,
                         void *cuda_stream);
-/* The context's launch shapes: CTA-per-SM targets (1..256) of the direct sum
- * and of the grid passes, and the grid-pass tile (32 or 128 grid points per
+/* The context's launch shapes: work-item (direct sum) and CTA (grid passes)
+ * targets per SM (1..256), and the grid-pass tile (32 or 128 grid points per
  * CTA; 0 = chosen from the node band width, the default).  FGR_E_INVALID for
  * values outside those ranges. */
 fgr_status fgr_get_tuning(const fgr_ctx *ctx, int32_t *direct_ctas_per_sm, int32_t *pass_ctas_per_sm,

@@ -329,7 +329,7 @@ __device__ __forceinline__ void separable_chunk(const int *__restrict__ srec, co
 template <int D, bool FP64>
 __device__ __forceinline__ void direct_tile(const void *__restrict__ recs_v, const int64_t *__restrict__ off,
                                             const DirectParams &P, void *__restrict__ u_v, const int tile,
-                                            const int split) {
+                                            const int split, const int nsplit) {
     using Rec = typename std::conditional<FP64, RecD<D>, RecF<D>>::type;
     constexpr int kWords = sizeof(Rec) / 4;
     __shared__ __align__(16) int srec[kThreads * kWords];
@@ -450,7 +450,7 @@ __device__ __forceinline__ void direct_tile(const void *__restrict__ recs_v, con
     }
 
     const int64_t nchunks = (L + kThreads - 1) / kThreads;
-    for (int64_t c = split; c < nchunks; c += P.splits) {
+    for (int64_t c = split; c < nchunks; c += nsplit) {
         const int64_t v = c * kThreads + threadIdx.x;
         if (v < L) {
             // segment holding virtual index v
@@ -584,7 +584,143 @@ template <int D, bool FP64>
 __global__ void __launch_bounds__(kThreads) direct_kernel(const void *__restrict__ recs_v,
                                                           const int64_t *__restrict__ off,
                                                           DirectParams P, void *__restrict__ u_v) {
-    direct_tile<D, FP64>(recs_v, off, P, u_v, blockIdx.x, blockIdx.y);
+    direct_tile<D, FP64>(recs_v, off, P, u_v, blockIdx.x, blockIdx.y, P.splits);
+}
+
+// Records in the list of every tile (the home-tile box of direct_tile).
+template <int D>
+__global__ void tile_load_kernel(const int64_t *__restrict__ off, GridDev g, uint32_t *__restrict__ load) {
+    const int tile = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tile >= g.ntiles) return;
+    int t[D];
+    int rem = tile;
+#pragma unroll
+    for (int l = D - 1; l >= 0; --l) {
+        t[l] = rem % g.nt[l];
+        rem /= g.nt[l];
+    }
+    int lo[D], cnt[D];
+    int rows = 1;
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+        lo[l] = max(0, t[l] - g.K[l]);
+        cnt[l] = t[l] - lo[l] + 1;
+        if (l < D - 1) rows *= cnt[l];
+    }
+    int64_t sum = 0;
+    for (int r = 0; r < rows; ++r) {
+        int h[D];
+        int rr = r;
+#pragma unroll
+        for (int l = D - 2; l >= 0; --l) {
+            h[l] = lo[l] + rr % cnt[l];
+            rr /= cnt[l];
+        }
+        h[D - 1] = lo[D - 1];
+        const int first = tile_linear<D>(g, h);
+        sum += off[first + cnt[D - 1]] - off[first];
+    }
+    load[tile] = (uint32_t)sum;
+}
+
+// Work items of the balanced launch (one CTA): tile t gets s_t slices in
+// proportion to its chunks of 256 records (1 <= s_t <= min(64, chunks)), and
+// the items are listed heaviest tiles first (tiles bucketed by the highest bit
+// of their record count), so that the persistent kernel finishes with light
+// items.  item = (tile, split | nsplit << 8).
+constexpr int kPlanThreads = 1024;
+__global__ void __launch_bounds__(kPlanThreads) plan_items_kernel(const uint32_t *__restrict__ load, int ntiles,
+                                                                   int target, int *__restrict__ rank_tile,
+                                                                   int *__restrict__ rank_splits,
+                                                                   int2 *__restrict__ items,
+                                                                   int *__restrict__ n_items) {
+    __shared__ unsigned long long s_chunks;
+    __shared__ int bucket_cnt[33], bucket_off[33];
+    __shared__ int part[kPlanThreads];
+    __shared__ int carry;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        s_chunks = 0;
+        carry = 0;
+    }
+    if (tid < 33) bucket_cnt[tid] = 0;
+    __syncthreads();
+    unsigned long long mine = 0;
+    for (int t = tid; t < ntiles; t += kPlanThreads) {
+        const uint32_t L = load[t];
+        mine += (L + 255u) / 256u;
+        const int b = L == 0 ? 32 : 31 - __clz((int)L);  // empty tiles last
+        atomicAdd(&bucket_cnt[b], 1);
+    }
+    atomicAdd(&s_chunks, mine);
+    __syncthreads();
+    if (tid == 0) {  // buckets in descending order of size, empty tiles last
+        int acc = 0;
+        for (int b = 31; b >= 0; --b) {
+            bucket_off[b] = acc;
+            acc += bucket_cnt[b];
+        }
+        bucket_off[32] = acc;
+    }
+    __syncthreads();
+    const double total = (double)(s_chunks > 0 ? s_chunks : 1);
+    for (int t = tid; t < ntiles; t += kPlanThreads) {
+        const uint32_t L = load[t];
+        const int b = L == 0 ? 32 : 31 - __clz((int)L);
+        const int r = atomicAdd(&bucket_off[b], 1);
+        const int chunks = (int)((L + 255u) / 256u);
+        int sp = 0;
+        if (chunks > 0) {
+            sp = (int)ceil((double)chunks * (double)target / total);
+            sp = max(1, min(sp, min(64, chunks)));
+        }
+        rank_tile[r] = t;
+        rank_splits[r] = sp;
+    }
+    __syncthreads();
+    // exclusive scan of the slice counts in rank order, items written as we go
+    for (int base = 0; base < ntiles; base += kPlanThreads) {
+        const int i = base + tid;
+        const int v = i < ntiles ? rank_splits[i] : 0;
+        part[tid] = v;
+        __syncthreads();
+        for (int st = 1; st < kPlanThreads; st <<= 1) {
+            const int add = tid >= st ? part[tid - st] : 0;
+            __syncthreads();
+            part[tid] += add;
+            __syncthreads();
+        }
+        if (i < ntiles) {
+            const int start = carry + part[tid] - v;
+            const int tile = rank_tile[i];
+            for (int k = 0; k < v; ++k) items[start + k] = make_int2(tile, k | (v << 8));
+        }
+        __syncthreads();
+        if (tid == kPlanThreads - 1) carry += part[kPlanThreads - 1];
+        __syncthreads();
+    }
+    if (tid == 0) *n_items = carry;
+}
+
+// Balanced direct sum: persistent CTAs pull the planned items in order.
+template <int D, bool FP64>
+__global__ void __launch_bounds__(kThreads) direct_items_kernel(const void *__restrict__ recs_v,
+                                                                const int64_t *__restrict__ off, DirectParams P,
+                                                                void *__restrict__ u_v,
+                                                                const int2 *__restrict__ items,
+                                                                const int *__restrict__ n_items,
+                                                                unsigned long long *__restrict__ counter) {
+    __shared__ long long s_item;
+    const long long total = *n_items;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ULL);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= total) break;
+        const int2 it = items[item];
+        direct_tile<D, FP64>(recs_v, off, P, u_v, it.x, it.y & 0xff, it.y >> 8);
+    }
 }
 
 // Batched direct sum: one persistent launch over the work items of up to
@@ -628,7 +764,7 @@ __global__ void __launch_bounds__(kThreads) direct_batch_kernel(const __grid_con
         }
         const BatchReq &R = B.req[lo];
         const long long j = item - B.item_start[lo];
-        direct_tile<D, FP64>(R.recs, R.off, R.P, R.u, (int)(j / R.P.splits), (int)(j % R.P.splits));
+        direct_tile<D, FP64>(R.recs, R.off, R.P, R.u, (int)(j / R.P.splits), (int)(j % R.P.splits), R.P.splits);
     }
 }
 
@@ -729,14 +865,48 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
         timer.finish();
         return FGR_OK;
     }
-    dim3 grid((unsigned)pr.ntiles, (unsigned)pr.P.splits);
+    if (D == 1) {
+        // 1-D: a few long tiles of similar load; one CTA per (tile, slice)
+        dim3 grid((unsigned)pr.ntiles, (unsigned)pr.P.splits);
+        if (fp64)
+            direct_kernel<D, true><<<grid, kThreads, 0, st>>>(pr.recs, pr.off, pr.P, u_dev);
+        else
+            direct_kernel<D, false><<<grid, kThreads, 0, st>>>(pr.recs, pr.off, pr.P, u_dev);
+        FGR_CUDA_TRY(cudaGetLastError());
+        timer.mark(&ctx->timing.last.direct_ms);
+        ctx->timing.last.launches = 4;
+        timer.finish();
+        return FGR_OK;
+    }
+    // d >= 2, balanced launch: per-tile loads (the dense middle of a wave packet
+    // set holds many times the records of its edges), items heaviest first,
+    // persistent CTAs
+    const int ntiles = pr.ntiles;
+    auto *load = (uint32_t *)scratch.get(sizeof(uint32_t) * (size_t)ntiles);
+    auto *rank = (int *)scratch.get(sizeof(int) * 2 * (size_t)ntiles);
+    auto *items = (int2 *)scratch.get(sizeof(int2) * 64 * (size_t)ntiles);
+    auto *cnt = (unsigned long long *)scratch.get(2 * sizeof(unsigned long long));
+    if (!load || !rank || !items || !cnt) return FGR_E_NOMEM;
+    FGR_CUDA_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st));
+    tile_load_kernel<D><<<(unsigned)((ntiles + 255) / 256), 256, 0, st>>>(pr.off, pr.P.g, load);
+    const int target = ctx->num_sms * ctx->tune.direct_ctas_per_sm;
+    plan_items_kernel<<<1, kPlanThreads, 0, st>>>(load, ntiles, target, rank, rank + ntiles, items,
+                                                  reinterpret_cast<int *>(cnt + 1));
+    int per_sm = 1;
     if (fp64)
-        direct_kernel<D, true><<<grid, kThreads, 0, st>>>(pr.recs, pr.off, pr.P, u_dev);
+        FGR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, direct_items_kernel<D, true>, kThreads, 0));
     else
-        direct_kernel<D, false><<<grid, kThreads, 0, st>>>(pr.recs, pr.off, pr.P, u_dev);
+        FGR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, direct_items_kernel<D, false>, kThreads, 0));
+    const unsigned ctas = (unsigned)(ctx->num_sms * std::max(1, per_sm));
+    if (fp64)
+        direct_items_kernel<D, true><<<ctas, kThreads, 0, st>>>(pr.recs, pr.off, pr.P, u_dev, items,
+                                                                reinterpret_cast<int *>(cnt + 1), cnt);
+    else
+        direct_items_kernel<D, false><<<ctas, kThreads, 0, st>>>(pr.recs, pr.off, pr.P, u_dev, items,
+                                                                 reinterpret_cast<int *>(cnt + 1), cnt);
     FGR_CUDA_TRY(cudaGetLastError());
     timer.mark(&ctx->timing.last.direct_ms);
-    ctx->timing.last.launches = 4;
+    ctx->timing.last.launches = 6;
     timer.finish();
     return FGR_OK;
 }
