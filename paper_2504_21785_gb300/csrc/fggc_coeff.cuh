@@ -84,11 +84,15 @@ template <int N>
 __device__ __forceinline__ void coeff_dim32(const Params32 &P, double Q, double Pm, int &a0, int &b0,
                                             float *cr, float *ci) {
     const Common &c = P.c;
-    const double r = quotient_for_floor(Q, c.dqv, c.inv_dq), rp = quotient_for_floor(Pm, c.dpv, c.inv_dp);
-    const double fa = floor(r), fb = floor(rp);
-    a0 = (int)fmin(fmax(fa, -1e9), 1e9);
-    b0 = (int)fmin(fmax(fb, -1e9), 1e9);
-    const float xs = (float)(2.0 * (r - fa) - 1.0), xt = (float)(2.0 * (rp - fb) - 1.0);
+    // the floors of Q/dq and P/dp as the FP64 division decides them (FP32
+    // estimate, FP64 only near an integer); the fractions from one FP64
+    // product each (within a few ulps of the quotient, which is all the FP32
+    // surrogate below can resolve)
+    a0 = floor_div_int(Q, c.dqv, c.inv_dq);
+    b0 = floor_div_int(Pm, c.dpv, c.inv_dp);
+    const double fa = (double)a0, fb = (double)b0;
+    const double r = Q * c.inv_dq, rp = Pm * c.inv_dp;
+    const float xs = fmaf(2.f, (float)(r - fa), -1.f), xt = fmaf(2.f, (float)(rp - fb), -1.f);
     float Ts[kCheb], Tt[kCheb];
     Ts[0] = 1.f;
     Ts[1] = xs;
