@@ -830,6 +830,99 @@ def run_profile_case(args):
     print(json.dumps({"profile_case": "config %d" % args.config, "ok": True}))
 
 
+def multistep_study(args):
+    """Runtimes of single-step FGA and multi-step FGGC (Algorithm 3, Q2P2) on
+    Examples 4 and 5 of Sec. 4.4 for the T_evo x T_multi splits of Tables 19
+    and 22: per split the learning of the flow (RK4 of the fixed mesh over
+    T / T_multi from unit amplitude) and the T_multi steps (decomposition by
+    tensor-product contractions, learned amplitude factors, FGGC), timed with
+    CUDA events (the second of two runs, or the first where it takes over a
+    second); FGA = decomposition, RK4 over T and the direct sum.  The errors of the same runs against the exact harmonic
+    solution are checked by tests/test_gpu_examples.py."""
+    import torch
+
+    import paper_2504_21785_gb300 as fgr
+    from workloads.examples import EXAMPLES, SPLITS, example_axis, example_grid, example_u0
+
+    prec = fgr.FGR_FP32 if args.study_precision == "fp32" else fgr.FGR_FP64
+    cdt = torch.complex64 if prec == fgr.FGR_FP32 else torch.complex128
+    stream = torch.cuda.current_stream()
+    out = {"study": "multistep (Sec. 4.4, Tables 19 and 22)", "precision": args.study_precision, "cases": []}
+
+    def timed(fn):
+        # the first run is timed too; runs under a second are timed again
+        # (warm memory pool) and the second time is reported
+        ms = 0.0
+        for rep in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            if ms > 1000.0:
+                break
+        return ms
+
+    for ex in (4, 5):
+        e = EXAMPLES[ex]
+        d, eps = e["d"], e["eps"]
+        grid = example_grid(ex)
+        u0 = torch.tensor(example_u0(ex), dtype=cdt, device="cuda")
+        q, p = example_axis(ex)
+        aq, ap = torch.tensor(q, device="cuda"), torch.tensor(p, device="cuda")
+        L = q.size
+        idx = torch.arange(L ** d, device="cuda")
+        Q = torch.stack([aq[(idx // (L ** (d - 1 - l))) % L] for l in range(d)]).contiguous()
+        P = torch.stack([ap[(idx // (L ** (d - 1 - l))) % L] for l in range(d)]).contiguous()
+        m = Q.shape[1]
+        axes = fgr.make_axes([(aq, ap)] * d)
+        with fgr.Context(d, grid, eps, fgr.make_options(precision=prec, nq=2, np_=2)) as ctx:
+            for vname, pot in e["potentials"].items():
+                potv = fgr.make_potential(**pot)
+                case = {"example": ex, "potential": vname, "d": d, "eps": eps, "T": e["T"], "packets": m,
+                        "grid": grid["n"], "splits": {}}
+                # single-step FGA
+                s = torch.zeros(m, dtype=torch.float64, device="cuda")
+                a = torch.zeros((2, m), dtype=torch.float64, device="cuda")
+                Qw, Pw = Q.clone(), P.clone()
+                pk = fgr.make_packets(Qw, Pw, s, a)
+                u = torch.zeros_like(u0)
+
+                def fga():
+                    Qw.copy_(Q)
+                    Pw.copy_(P)
+                    fgr.fgr_decompose_tensor(ctx.handle, axes, u0, m, None, a, stream)
+                    s.zero_()
+                    fgr.fgr_propagate(ctx.handle, pk, potv, e["T"], e["dt"], stream)
+                    fgr.fgr_reconstruct_direct(ctx.handle, pk, u, stream)
+                case["fga_ms"] = timed(fga)
+                for M in SPLITS:
+                    fs = torch.zeros(m, dtype=torch.float64, device="cuda")
+                    fa = torch.zeros((2, m), dtype=torch.float64, device="cuda")
+                    Fq, Fp = Q.clone(), P.clone()
+                    flow = fgr.make_packets(Fq, Fp, fs, fa)
+
+                    def learn():
+                        Fq.copy_(Q)
+                        Fp.copy_(P)
+                        fs.zero_()
+                        fa.zero_()
+                        fa[0] = 1.0
+                        fgr.fgr_propagate(ctx.handle, flow, potv, e["T"] / M, e["dt"], stream)
+                    learn_ms = timed(learn)
+                    steps_ms = timed(lambda: fgr.fgr_fggc_multistep_tensor(ctx.handle, axes, None, flow, u0, u, M,
+                                                                            stream))
+                    case["splits"]["%dx%d" % (round(e["T"] / e["dt"]) // M, M)] = {
+                        "learn_ms": learn_ms, "steps_ms": steps_ms, "total_ms": learn_ms + steps_ms,
+                        "per_step_ms": steps_ms / M}
+                    del flow, Fq, Fp, fs, fa
+                out["cases"].append(case)
+        del Q, P, idx
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -852,9 +945,15 @@ def main():
                     help="with --profile: keep only this many largest-amplitude packets")
     ap.add_argument("--profile", action="store_true",
                     help="run every kernel once on a short case (for ncu) and exit")
+    ap.add_argument("--study", choices=["multistep"], default=None,
+                    help="print the runtimes of the multi-step examples of Sec. 4.4 and exit")
+    ap.add_argument("--study-precision", choices=["fp32", "fp64"], default="fp32")
     args = ap.parse_args()
     if args.profile:
         run_profile_case(args)
+        return
+    if args.study == "multistep":
+        print(json.dumps(multistep_study(args)))
         return
     out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:
