@@ -18,6 +18,8 @@ fggc          eq. 2.24-2.25: aggregation onto grid nodes and on-grid sum;
 decompose     eq. 2.6 / 2.8: initial decomposition of a wave given on the grid
 trajectories  eq. 2.3-2.7: classical RK4 of Q, P, S, A with the Jacobians
               (plain C in c/rk4.c, compiled on first use)
+exact         the exact Gaussian solution for V = |x|^2/2 (reference of the
+              multi-step examples of Sec. 4.4)
 
 Parity status: every function is pinned by a test in tests/test_oracle_*.py
 against a closed form, a brute-force evaluation, an independent quadrature or a
