@@ -2,12 +2,16 @@
 against the closed-form harmonic solution (oracle/exact.py): the L2 error of
 single-step FGA (decompose, propagate over T, direct sum) and of multi-step
 FGGC (Algorithm 3, Q2P2) for the T_evo x T_multi splits of Tables 18 and 20.
-The paper measures these errors against a time-splitting spectral solution;
-its printed values (Table 18: FGA 3.151e-5, FGGC 3.376e-5 .. 2.509e-4 for
-T_multi = 1 .. 32; Table 20: FGA 6.640e-6, FGGC 7.793e-5 .. 3.130e-4) set the
-scale the errors here must stay within (a factor of 3, or 1e-5 absolute where
-the printed value is smaller), and multi-step FGGC must not drift far from
-single-step FGGC as T_multi grows.  FP64 contexts (R = 8)."""
+The paper measures these errors against a time-splitting spectral solution.
+For this potential FGA itself is exact up to the mesh and the window (error
+below 1e-9 here), so the printed FGA error of Example 4 (3.151e-5, Table 18)
+is read as the error of that reference; combined in quadrature with it, the
+single-step error here must reproduce the printed 3.376e-5 to 10 %, and every
+split must stay below 1.2 x its printed value.  In Example 5 (eps = 2^-6) the
+reference error is small (printed FGA error 6.6e-6) and the multi-step errors
+must reproduce Table 20 to 25 % (T_multi = 8, 16, 32; the shorter splits take
+minutes of RK4 on 17M packets and are timed by the bench study instead).
+FP64 contexts (R = 8)."""
 
 import math
 
@@ -113,14 +117,14 @@ def _report(name, errs, table):
 def test_example4_v2_errors_against_the_exact_solution(fgr):
     errs = _run(fgr, 4, (1, 2, 4, 8, 16, 32), with_fga=True)
     _report("Example 4, V2", errs, TABLE18)
-    for k, v in errs.items():
-        assert v <= max(3 * TABLE18[k], 1e-5), (k, v)
-    # restarts add decomposition and least-squares errors, they do not blow up
-    assert errs[32] <= 20 * errs[1]
+    assert errs["FGA"] <= 1e-9
+    assert abs(math.hypot(errs[1], TABLE18["FGA"]) / TABLE18[1] - 1) <= 0.10
+    for k in (1, 2, 4, 8, 16, 32):
+        assert errs[k] <= 1.2 * TABLE18[k], (k, errs[k])
 
 
 def test_example5_v2_errors_against_the_exact_solution(fgr):
     errs = _run(fgr, 5, (8, 16, 32), with_fga=False)
     _report("Example 5, V2", errs, TABLE20)
     for k, v in errs.items():
-        assert v <= max(3 * TABLE20[k], 1e-5), (k, v)
+        assert abs(v / TABLE20[k] - 1) <= 0.25, (k, v)
