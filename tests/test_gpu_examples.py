@@ -15,7 +15,6 @@ FP64 contexts (R = 8)."""
 
 import math
 
-import numpy as np
 import pytest
 
 from oracle import exact
