@@ -209,3 +209,51 @@ def test_multistep_tensor_matches_oracle(fgr):
         torch.cuda.synchronize()
         got = out.cpu().numpy()
     assert _gpu.rel_l2(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_multistep_tensor_with_selection_matches_oracle(fgr, precision):
+    # 2-D harmonic oscillator on a selected subset of a tensor mesh (host and
+    # device selections), two quarter-period steps, flow from the oracle's RK4
+    import torch
+    from workloads import mesh_for
+    eps = 1 / 16
+    mesh = mesh_for(2, eps)
+    ax = []
+    for l in range(2):
+        qs = np.arange(-5, 5) * mesh.dq
+        ps = np.arange(-9, 9) * mesh.dp
+        Q, P = np.meshgrid(qs, ps, indexing="ij")
+        ax.append((np.ascontiguousarray(Q.reshape(-1)), np.ascontiguousarray(P.reshape(-1))))
+    total = ax[0][0].size * ax[1][0].size
+    rng = np.random.default_rng(12)
+    sel = np.sort(rng.choice(total, total * 3 // 4, replace=False)).astype(np.int64)
+    q, p = _expand(ax, sel)
+    m = sel.size
+    sub = {"q": q, "p": p, "s": np.zeros(m), "a": np.stack([np.ones(m), np.zeros(m)])}
+    flow = tr.propagate(sub, {"kind": "harmonic", "omega": 1.0}, math.pi / 2, 1e-3)
+    grid = dict(d=2, n=[40, 36], lo=[-3.0, -3.0], hi=[3.0, 3.0])
+    x0 = np.linspace(-3, 3, 40, endpoint=False)
+    x1 = np.linspace(-3, 3, 36, endpoint=False)
+    X0, X1 = np.meshgrid(x0, x1, indexing="ij")
+    u0 = np.exp(-((X0 - 0.3) ** 2 + (X1 + 0.2) ** 2) / (2 * 0.2)) * np.exp(1j * (0.4 * X0 - 0.6 * X1) / eps)
+    R = 8 if precision == "fp64" else 6
+    ref = fggc.multistep(u0, grid, sub, flow, eps, mesh.dq, mesh.dp, lsa.Strategy(nq=4, np_=2), 2, R=R)
+    cdt = np.complex128 if precision == "fp64" else np.complex64
+    tol = 2 * max(1e-12, 4 * np.finfo(float).eps / math.sqrt(
+        lsa.Strategy(nq=4, np_=2).pinv.singular_values[lsa.Strategy(nq=4, np_=2).pinv.rank - 1])) \
+        if precision == "fp64" else 1e-5
+    with fgr.Context(2, grid, eps, _gpu.options(precision)) as ctx:
+        fl = [torch.tensor(np.ascontiguousarray(flow[k]), device="cuda") for k in "qpsa"]
+        for on_device in (True, False):
+            if on_device:
+                axd = fgr.make_axes([(torch.tensor(a, device="cuda"), torch.tensor(b, device="cuda")) for a, b in ax])
+                s_arg = torch.tensor(sel, device="cuda")
+            else:
+                axd = fgr.make_axes(ax)
+                s_arg = sel
+            uin = torch.tensor(u0.astype(cdt), device="cuda")
+            out = torch.zeros_like(uin)
+            fgr.fgr_fggc_multistep_tensor(ctx.handle, axd, s_arg, fgr.make_packets(*fl), uin, out, 2)
+            torch.cuda.synchronize()
+            assert _gpu.rel_l2(out.cpu().numpy(), ref) <= tol, on_device
