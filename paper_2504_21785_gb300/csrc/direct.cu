@@ -24,6 +24,7 @@
 // part nu_hi (a multiple of 2^-b, so k*nu_hi is exact in FP32 for k < 2^(24-b))
 // and a small remainder nu_lo.  FP64 records carry Q, P, S, A and every pair is
 // evaluated in FP64.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -734,6 +735,7 @@ struct BatchReq {
     const int64_t *off;
     void *u;
     DirectParams P;
+    const int2 *items;  // balanced batches (d >= 2): the request's planned items
 };
 
 struct BatchParams {
@@ -765,6 +767,47 @@ __global__ void __launch_bounds__(kThreads) direct_batch_kernel(const __grid_con
         const BatchReq &R = B.req[lo];
         const long long j = item - B.item_start[lo];
         direct_tile<D, FP64>(R.recs, R.off, R.P, R.u, (int)(j / R.P.splits), (int)(j % R.P.splits), R.P.splits);
+    }
+}
+
+// Balanced batch (d >= 2): request r's items, planned on the device like the
+// single call's, occupy [start[r], start[r+1]) of one list whose prefix
+// start[] is computed on the device from the per-request item counts.
+__global__ void batch_item_start_kernel(const int *__restrict__ nitems, int n, int *__restrict__ start) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int acc = 0;
+        for (int r = 0; r < n; ++r) {
+            start[r] = acc;
+            acc += nitems[r];
+        }
+        start[n] = acc;
+    }
+}
+
+template <int D, bool FP64>
+__global__ void __launch_bounds__(kThreads) direct_batch_items_kernel(const __grid_constant__ BatchParams B,
+                                                                      const int *__restrict__ start,
+                                                                      unsigned long long *__restrict__ counter) {
+    __shared__ int s_start[kBatchMax + 1];
+    __shared__ long long s_item;
+    for (int r = threadIdx.x; r <= B.n; r += blockDim.x) s_start[r] = start[r];
+    __syncthreads();
+    const long long total = s_start[B.n];
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ULL);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= total) break;
+        int lo = 0, hi = B.n - 1;  // request holding this item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_start[mid] <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchReq &R = B.req[lo];
+        const int2 it = R.items[item - s_start[lo]];
+        direct_tile<D, FP64>(R.recs, R.off, R.P, R.u, it.x, it.y & 0xff, it.y >> 8);
     }
 }
 
@@ -919,15 +962,44 @@ fgr_status launch_batch(int n, fgr_ctx *const *ctxs, const PacketsDev *pks, void
     const bool fp64 = ctxs[0]->opt.precision == FGR_FP64;
     BatchParams B;
     memset(&B, 0, sizeof(B));
+    // d >= 2: largest requests first, each cut into items in proportion to
+    // its share of the packets (planned on the device, heaviest tiles first)
+    int order[kBatchMax];
+    for (int r = 0; r < n; ++r) order[r] = r;
+    int64_t msum = 0;
+    for (int r = 0; r < n; ++r) msum += pks[r].m;
+    if (D >= 2)
+        std::stable_sort(order, order + n, [&](int x, int y) { return pks[x].m > pks[y].m; });
+    int *nitems = nullptr;
+    if (D >= 2) {
+        nitems = (int *)shared.get(sizeof(int) * (2 * kBatchMax + 2));
+        if (!nitems) return FGR_E_NOMEM;
+        FGR_CUDA_TRY(cudaMemsetAsync(nitems, 0, sizeof(int) * (2 * kBatchMax + 2), st));
+    }
     int64_t total = 0;
-    for (int r = 0; r < n; ++r) {
+    for (int k = 0; k < n; ++k) {
+        const int r = order[k];
         Prepared pr;
         fgr_status rc = prepare<D>(ctxs[r], pks[r], us[r], st, *scratch[r], &pr);
         if (rc != FGR_OK) return rc;
         if (pr.empty) continue;
-        B.req[B.n] = BatchReq{pr.recs, pr.off, us[r], pr.P};
-        B.item_start[B.n] = total;
-        total += (int64_t)pr.ntiles * pr.P.splits;
+        B.req[B.n] = BatchReq{pr.recs, pr.off, us[r], pr.P, nullptr};
+        if (D >= 2) {
+            const int ntiles = pr.ntiles;
+            auto *load = (uint32_t *)scratch[r]->get(sizeof(uint32_t) * (size_t)ntiles);
+            auto *rank = (int *)scratch[r]->get(sizeof(int) * 2 * (size_t)ntiles);
+            auto *items = (int2 *)scratch[r]->get(sizeof(int2) * 64 * (size_t)ntiles);
+            if (!load || !rank || !items) return FGR_E_NOMEM;
+            tile_load_kernel<D><<<(unsigned)((ntiles + 255) / 256), 256, 0, st>>>(pr.off, pr.P.g, load);
+            const int64_t all = (int64_t)ctxs[0]->num_sms * ctxs[0]->tune.direct_ctas_per_sm;
+            const int target = (int)std::max<int64_t>(1, all * pks[r].m / std::max<int64_t>(msum, 1));
+            plan_items_kernel<<<1, kPlanThreads, 0, st>>>(load, ntiles, target, rank, rank + ntiles, items,
+                                                          nitems + B.n);
+            B.req[B.n].items = items;
+        } else {
+            B.item_start[B.n] = total;
+            total += (int64_t)pr.ntiles * pr.P.splits;
+        }
         ++B.n;
     }
     B.item_start[B.n] = total;
@@ -935,6 +1007,24 @@ fgr_status launch_batch(int n, fgr_ctx *const *ctxs, const PacketsDev *pks, void
     auto *counter = (unsigned long long *)shared.get(sizeof(unsigned long long));
     if (!counter) return FGR_E_NOMEM;
     FGR_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+    if (D >= 2) {
+        int *start = nitems + kBatchMax;
+        batch_item_start_kernel<<<1, 32, 0, st>>>(nitems, B.n, start);
+        int per_sm = 1;
+        if (fp64)
+            FGR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, direct_batch_items_kernel<D, true>,
+                                                                       kThreads, 0));
+        else
+            FGR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, direct_batch_items_kernel<D, false>,
+                                                                       kThreads, 0));
+        const unsigned ctas = (unsigned)(ctxs[0]->num_sms * std::max(1, per_sm));
+        if (fp64)
+            direct_batch_items_kernel<D, true><<<ctas, kThreads, 0, st>>>(B, start, counter);
+        else
+            direct_batch_items_kernel<D, false><<<ctas, kThreads, 0, st>>>(B, start, counter);
+        FGR_CUDA_TRY(cudaGetLastError());
+        return FGR_OK;
+    }
     const int64_t ctas = std::min<int64_t>(total, (int64_t)ctxs[0]->num_sms * 8);
     if (fp64)
         direct_batch_kernel<D, true><<<(unsigned)ctas, kThreads, 0, st>>>(B, counter);

@@ -85,9 +85,11 @@ def test_batch_matches_single_calls_and_oracle(fgr, d, precision):
             r["ctx"].close()
 
 
-def test_batch_replays_from_a_cuda_graph(fgr):
+@pytest.mark.parametrize("d", [1, 2])
+def test_batch_replays_from_a_cuda_graph(fgr, d):
+    # d = 2 runs the balanced batch (items planned on the device)
     import torch
-    eps, mesh, reqs = _make(fgr, 1, "fp32", seed=40)
+    eps, mesh, reqs = _make(fgr, d, "fp32", seed=40 + d)
     try:
         ctxs = [r["ctx"] for r in reqs]
         pks = [r["packets"] for r in reqs]
