@@ -226,7 +226,9 @@ fgr_status fgr_reconstruct_direct(fgr_ctx *ctx, const fgr_packets *pk, void *u_o
  * u_outs[r], exactly as fgr_reconstruct_direct would, but all n requests share
  * one persistent launch of the summation kernel whose CTAs take (request,
  * tile, packet-split) items from a device counter until none remain, so many
- * requests with small grids fill the GPU together.  1 <= n <= 64; all contexts
+ * requests with small grids fill the GPU together (d >= 2: the largest
+ * requests first, each tile's packet list cut on the device into slices in
+ * proportion to its length, heaviest tiles first).  1 <= n <= 64; all contexts
  * must have the same dimension, precision and device; every u_outs[r] must be
  * device memory of its context's output size and the outputs must not
  * overlap.  Packets may be host memory (staged like fgr_reconstruct_direct);
