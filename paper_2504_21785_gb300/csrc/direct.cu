@@ -47,6 +47,9 @@ __host__ __device__ constexpr int tileT(int l) {
 static_assert(tileT<1>(0) == kThreads * kTpt && tileT<2>(0) * tileT<2>(1) == kThreads * kTpt &&
                   tileT<3>(0) * tileT<3>(1) * tileT<3>(2) == kThreads * kTpt,
               "tiles hold kThreads * kTpt points");
+static_assert(tileT<2>(0) % 4 == 0 && tileT<2>(1) % 4 == 0 && tileT<3>(0) % 4 == 0 && tileT<3>(1) % 4 == 0 &&
+                  tileT<3>(2) % 4 == 0,
+              "the factor tables of d >= 2 are filled 4 grid lines at a time");
 
 template <int D>
 struct __align__(16) RecF {
@@ -211,6 +214,7 @@ struct DirectParams {
     float ce;            // -log2(e) / (2 eps)
     float ce_h;          // ce * h of the last dimension
     float q_last;        // e^{-h^2 / eps} of the last dimension (Gaussian ratio step)
+    float q_dim[3];      // e^{-h_l^2 / eps} per dimension (factor tables, d >= 2)
     double inv_eps;      // FP64 path
     double neg_half_inv_eps;
     int splits;
@@ -264,8 +268,13 @@ __device__ __forceinline__ void separable_chunk(const int *__restrict__ srec, co
     const int o_c = D == 3 ? tileT<D>(0) + tileT<D>(1) + loc[2] : 0;  // d = 3: k
     for (int s0 = 0; s0 < nrec; s0 += kS) {
         const int ns = min(kS, nrec - s0);
-        // factor tables of records s0 .. s0 + ns - 1 (zero outside the window)
-        for (int e = threadIdx.x; e < ns * kT; e += kThreads) {
+        // factor tables of records s0 .. s0 + ns - 1 (zero outside the window):
+        // a thread fills 4 consecutive grid lines of one record and dimension
+        // (tile extents are multiples of 4), the first by ex2 and one sincos,
+        // the next three by the exact recurrences of the Gaussian ratio
+        // (rho_{k+1} = rho_k e^{-h^2/eps}) and the phase rotation e^{2 pi i nu}
+        for (int e4 = threadIdx.x; e4 < ns * (kT / 4); e4 += kThreads) {
+            const int e = 4 * e4;
             const int jr = s0 + e / kT;
             int qd = e % kT, l = 0;
 #pragma unroll
@@ -276,8 +285,9 @@ __device__ __forceinline__ void separable_chunk(const int *__restrict__ srec, co
                 }
             const RecF<D> &R = *reinterpret_cast<const RecF<D> *>(&srec[jr * kWords]);
             const float kf = (float)(t[l] * tileT<D>(l) + qd) - R.mlo[l];
-            float2 f = make_float2(0.f, 0.f);
-            if (kf >= 0.f && kf < R.wlen[l]) {
+            const float wl = R.wlen[l];
+            float4 out01 = make_float4(0.f, 0.f, 0.f, 0.f), out23 = out01;
+            if (kf + 3.f >= 0.f && kf < wl) {  // some of the four lines lie in the window
                 const float dx = fmaf(kf, P.hf[l], R.delta[l]);
                 float ex = dx * dx * P.ce;
                 float fr = kf * R.nuhi[l];
@@ -291,9 +301,29 @@ __device__ __forceinline__ void separable_chunk(const int *__restrict__ srec, co
                 float sn, cs;
                 __sincosf(6.283185307179586f * tau, &sn, &cs);
                 const float ga = ex2_approx(ex);
-                f = make_float2(ga * cs, ga * sn);
+                float fr0 = ga * cs, fi0 = ga * sn;
+                float rs_, rc_;
+                __sincosf(6.283185307179586f * (R.nuhi[l] + R.nulo[l]), &rs_, &rc_);
+                float rho = ex2_approx(P.ce * P.hf[l] * fmaf(2.f, dx, P.hf[l]));
+                float v[8];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const bool in = kf + (float)i >= 0.f && kf + (float)i < wl;
+                    v[2 * i] = in ? fr0 : 0.f;
+                    v[2 * i + 1] = in ? fi0 : 0.f;
+                    if (i < 3) {
+                        const float pr = rc_ * rho, pi = rs_ * rho;
+                        const float nr = fr0 * pr - fi0 * pi;
+                        fi0 = fr0 * pi + fi0 * pr;
+                        fr0 = nr;
+                        rho *= P.q_dim[l];
+                    }
+                }
+                out01 = make_float4(v[0], v[1], v[2], v[3]);
+                out23 = make_float4(v[4], v[5], v[6], v[7]);
             }
-            sfac[e] = f;
+            *reinterpret_cast<float4 *>(&sfac[e]) = out01;
+            *reinterpret_cast<float4 *>(&sfac[e + 2]) = out23;
         }
         __syncthreads();
 #pragma unroll 4
@@ -885,6 +915,7 @@ fgr_status prepare(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t
     P.ce = (float)(-1.4426950408889634 / (2.0 * M.eps));
     P.ce_h = (float)(-1.4426950408889634 / (2.0 * M.eps) * g.h[D - 1]);
     P.q_last = (float)std::exp(-g.h[D - 1] * g.h[D - 1] / M.eps);
+    for (int l = 0; l < D; ++l) P.q_dim[l] = (float)std::exp(-g.h[l] * g.h[l] / M.eps);
     P.inv_eps = 1.0 / M.eps;
     P.neg_half_inv_eps = -0.5 / M.eps;
     const int target = ctx->num_sms * ctx->tune.direct_ctas_per_sm;
