@@ -119,11 +119,6 @@ inline unsigned bounds_blocks(const fgr_ctx *ctx, int64_t m) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, (int64_t)ctx->num_sms * 8));
 }
 
-__device__ __forceinline__ void cmul(double ar, double ai, double br, double bi, double &cr, double &ci) {
-    cr = ar * br - ai * bi;
-    ci = ar * bi + ai * br;
-}
-
 // ---------------------------------------------------------------------------
 // grid passes
 // ---------------------------------------------------------------------------
