@@ -17,7 +17,7 @@ import numpy as np
 import pytest
 
 from oracle import fga, fggc, lsa, trajectories as tr
-from workloads import random_packets, mesh_for, wkb_packets, WKB_TANH, WKB_LINEAR
+from workloads import random_packets, mesh_for
 
 from . import _gpu
 

@@ -7,7 +7,7 @@ import threading
 import numpy as np
 import pytest
 
-from workloads import random_packets, mesh_for
+from workloads import random_packets
 
 pytestmark = pytest.mark.gpu
 

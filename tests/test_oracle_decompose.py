@@ -9,8 +9,6 @@
 * Packets whose window misses the grid get zero amplitude.
 """
 
-import math
-
 import numpy as np
 
 from oracle import decompose, fga
