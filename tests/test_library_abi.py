@@ -50,7 +50,7 @@ def test_ctypes_layout_matches_c(tmp_path):
     structs = {"fgr_grid": fgr.fgr_grid, "fgr_options": fgr.fgr_options,
                "fgr_packets": fgr.fgr_packets, "fgr_potential": fgr.fgr_potential,
                "fgr_info": fgr.fgr_info, "fgr_stats": fgr.fgr_stats,
-               "fgr_request": fgr.fgr_request, "fgr_result": fgr.fgr_result}
+               "fgr_request": fgr.fgr_request, "fgr_result": fgr.fgr_result, "fgr_axis": fgr.fgr_axis}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fgr.h"', "int main(void){"]
     for name, cls in structs.items():
         lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
