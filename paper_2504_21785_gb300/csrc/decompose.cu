@@ -16,10 +16,11 @@
 // over the lanes instead of repeated per packet; the warp then takes the
 // group's packets in turn, their parameters broadcast by shuffles.
 //
-// d = 1: the lanes own 4 consecutive window points at a time (coalesced
-// reads of u).  FP32: the first point's Gaussian by one ex2 and its phase by
-// one MUFU sincos, the next three by the exact recurrences
-// g_{k+1} = g_k rho_k, rho_{k+1} = rho_k 2^{2 ce h^2}, e_{k+1} = e_k e^{2 pi i nu}.
+// d = 1: the lanes own the window points lane + 32 i (coalesced reads of u).
+// FP32: of every 8 of a lane's points the first gets its Gaussian by one ex2
+// and its phase by one MUFU sincos, the next seven the exact recurrences
+// over the stride H = 32 h: g_{k+32} = g_k rho, rho <- rho 2^{2 ce H^2},
+// e_{k+32} = e_k e^{2 pi i 32 nu}.
 // d = 2, 3: the kernel factorises over dimensions, so each packet's
 // per-dimension factors f_l(k) = g(dx_l) e^{-i p_l dx_l / eps} are tabulated
 // once in the warp's shared memory and every window point costs one complex
@@ -53,6 +54,7 @@ struct DecParams {
 
 constexpr int kDecMaxWarps = 8;
 constexpr float kTwoPi = 6.283185307179586f;
+constexpr int kDecGroup = 8;  // d = 1: points per full evaluation along a lane's stride
 
 // s + x with the running compensation c (Kahan)
 __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
@@ -275,8 +277,8 @@ __global__ void __launch_bounds__(32 * kDecMaxWarps) decompose_kernel(const void
             float sr = 0.f, si = 0.f, cr = 0.f, ci = 0.f;  // Kahan sums
             const float2 *u = reinterpret_cast<const float2 *>(u_v);
             if constexpr (D == 1) {
-                // lane owns the points k = lane + 32 i; every fourth is
-                // evaluated in full, the next three by the recurrences over
+                // lane owns the points k = lane + 32 i; every eighth is
+                // evaluated in full, the next seven by the recurrences over
                 // the stride H = 32 h (coalesced loads of u)
                 const float h = P.hf[0], ce = P.ce, H = 32.f * h;
                 float nu32 = 32.f * bnh[0];
@@ -287,14 +289,14 @@ __global__ void __launch_bounds__(32 * kDecMaxWarps) decompose_kernel(const void
                 const float c2 = ex2_approx(2.f * ce * H * H);
                 const float2 *ub = u + bb[0];
                 const int w = bw[0];
-                for (int k = lane; k < w; k += 128) {
+                for (int k = lane; k < w; k += 32 * kDecGroup) {
                     const float dx = fmaf((float)k, h, bdl[0]);
                     float rho = ex2_approx(ce * H * fmaf(2.f, dx, H));
                     float2 e = factor32(k, h, bdl[0], bt0[0], bnh[0], bnl[0], ce);
                     float2 uv = ub[k];
                     float tr = uv.x * e.x - uv.y * e.y, ti = uv.x * e.y + uv.y * e.x;
 #pragma unroll
-                    for (int i = 1; i < 4; ++i) {
+                    for (int i = 1; i < kDecGroup; ++i) {
                         if (k + 32 * i < w) {
                             const float pr = rc_ * rho, pi = rs_ * rho;
                             e = make_float2(e.x * pr - e.y * pi, e.x * pi + e.y * pr);

@@ -500,7 +500,10 @@ fgr_status launch_pass(const void *in, void *out, const PassParams &pp, const ui
     else if (band <= 48) FGR_PASS(48, TPV);                                                                 \
     else FGR_PASS(64, TPV);  // wider bands are processed in chunks of 64
     if (tp == 32) {
-        FGR_PASS_TP(32)
+        // narrow tiles: at most 32 band factors in registers (wider bands in
+        // chunks of 32), so that more warps fit an SM
+        if (band <= 16) FGR_PASS(16, 32);
+        else FGR_PASS(32, 32);
     } else {
         FGR_PASS_TP(128)
     }
