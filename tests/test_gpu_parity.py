@@ -217,6 +217,18 @@ def test_fggc_fp32_matches_oracle(d):
     assert _gpu.rel_l2(got, ref) <= 1e-5
 
 
+@pytest.mark.parametrize("d", [1, 2])
+@pytest.mark.parametrize("nq,np_", [(2, 2), (2, 4), (4, 4)])
+def test_fggc_fp32_other_strategies(d, nq, np_):
+    pk, grid, eps, mesh = _case(d, seed=7)
+    strat = lsa.Strategy(nq=nq, np_=np_)
+    ref = fggc.reconstruct(pk, grid, eps, mesh.dq, mesh.dp, strat, R=6)
+    got = _gpu.reconstruct("fggc", pk, grid, eps, _gpu.options("fp32", nq=nq, np_=np_))
+    err = _gpu.rel_l2(got, ref)
+    print("FP32 FGGC Q%dP%d d=%d: rel L2 %.3e" % (nq, np_, d, err))
+    assert err <= 1e-5
+
+
 def test_fggc_on_grid_packets_equal_direct_on_gpu():
     d = 2
     eps = 1 / 64
