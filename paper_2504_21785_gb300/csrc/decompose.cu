@@ -432,10 +432,8 @@ fgr_status run_decompose(fgr_ctx *ctx, const void *u_dev, const double *q, const
     }
     // packets per warp: amortise the FP64 set-up over up to 32 packets while
     // keeping at least 32 warps per SM busy
-    int dev_sms = 152;
-    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device);
     int G = 32;
-    while (G > 1 && (m + G - 1) / G < (int64_t)dev_sms * 32) G /= 2;
+    while (G > 1 && (m + G - 1) / G < (int64_t)ctx->num_sms * 32) G /= 2;
     P.group = G;
     const int64_t nwarps = (m + G - 1) / G;
     const unsigned blocks = (unsigned)((nwarps + warps - 1) / warps);

@@ -733,6 +733,14 @@ __global__ void __launch_bounds__(kPlanThreads) plan_items_kernel(const uint32_t
     if (tid == 0) *n_items = carry;
 }
 
+// Items plan_items_kernel can write: a tile's slice count is at most
+// max(1, ceil(chunks_t * target / chunks)) <= chunks_t * target / chunks + 1,
+// so all tiles together hold at most target + tiles (64 of margin for the
+// rounding of the quotient).
+inline size_t plan_items_capacity(int ntiles, int target) {
+    return std::min<size_t>((size_t)64 * ntiles, (size_t)ntiles + (size_t)target + 64);
+}
+
 // Balanced direct sum: persistent CTAs pull the planned items in order.
 template <int D, bool FP64>
 __global__ void __launch_bounds__(kThreads) direct_items_kernel(const void *__restrict__ recs_v,
@@ -958,12 +966,12 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
     const int ntiles = pr.ntiles;
     auto *load = (uint32_t *)scratch.get(sizeof(uint32_t) * (size_t)ntiles);
     auto *rank = (int *)scratch.get(sizeof(int) * 2 * (size_t)ntiles);
-    auto *items = (int2 *)scratch.get(sizeof(int2) * 64 * (size_t)ntiles);
+    const int target = ctx->num_sms * ctx->tune.direct_ctas_per_sm;
+    auto *items = (int2 *)scratch.get(sizeof(int2) * plan_items_capacity(ntiles, target));
     auto *cnt = (unsigned long long *)scratch.get(2 * sizeof(unsigned long long));
     if (!load || !rank || !items || !cnt) return FGR_E_NOMEM;
     FGR_CUDA_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st));
     tile_load_kernel<D><<<(unsigned)((ntiles + 255) / 256), 256, 0, st>>>(pr.off, pr.P.g, load);
-    const int target = ctx->num_sms * ctx->tune.direct_ctas_per_sm;
     plan_items_kernel<<<1, kPlanThreads, 0, st>>>(load, ntiles, target, rank, rank + ntiles, items,
                                                   reinterpret_cast<int *>(cnt + 1));
     int per_sm = 1;
@@ -1019,11 +1027,11 @@ fgr_status launch_batch(int n, fgr_ctx *const *ctxs, const PacketsDev *pks, void
             const int ntiles = pr.ntiles;
             auto *load = (uint32_t *)scratch[r]->get(sizeof(uint32_t) * (size_t)ntiles);
             auto *rank = (int *)scratch[r]->get(sizeof(int) * 2 * (size_t)ntiles);
-            auto *items = (int2 *)scratch[r]->get(sizeof(int2) * 64 * (size_t)ntiles);
-            if (!load || !rank || !items) return FGR_E_NOMEM;
-            tile_load_kernel<D><<<(unsigned)((ntiles + 255) / 256), 256, 0, st>>>(pr.off, pr.P.g, load);
             const int64_t all = (int64_t)ctxs[0]->num_sms * ctxs[0]->tune.direct_ctas_per_sm;
             const int target = (int)std::max<int64_t>(1, all * pks[r].m / std::max<int64_t>(msum, 1));
+            auto *items = (int2 *)scratch[r]->get(sizeof(int2) * plan_items_capacity(ntiles, target));
+            if (!load || !rank || !items) return FGR_E_NOMEM;
+            tile_load_kernel<D><<<(unsigned)((ntiles + 255) / 256), 256, 0, st>>>(pr.off, pr.P.g, load);
             plan_items_kernel<<<1, kPlanThreads, 0, st>>>(load, ntiles, target, rank, rank + ntiles, items,
                                                           nitems + B.n);
             B.req[B.n].items = items;
