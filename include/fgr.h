@@ -148,7 +148,7 @@ fgr_status fgr_propagate(fgr_ctx *ctx, fgr_packets *inout, const fgr_potential *
  * |x_l - q_l| <= R sqrt(eps) as the reconstructions, and s_j = 0; packets
  * whose window misses the grid get a_j = 0.  FP64: every term in FP64.  FP32:
  * the phase is reduced in FP64 per packet, each term evaluated in FP32 (d = 1:
- * every fourth point along the lane's stride by ex2 and sincos, the others by
+ * every eighth point along the lane's stride by ex2 and sincos, the others by
  * the exact recurrences of the Gaussian and the phase; d = 2, 3: per-dimension
  * factors, since the term factorises), compensated FP32 sums.  Host packets
  * are copied back before the call returns.  FGR_E_INVALID for NULL arguments
