@@ -213,11 +213,17 @@ fgr_status fgr_fggc_multistep_tensor(fgr_ctx *ctx, const fgr_axis *axes, const i
 
 /* Eq. 2.10 over the box window: u(x_m) = pref * sum_j A_j exp(i/eps (S_j +
  * P_j.(x_m - Q_j)) - |x_m - Q_j|^2/(2 eps)).  FP64: every term in FP64.
- * FP32: the phase is reduced in FP64 per packet and evaluated in FP32 turns;
- * of every 4 consecutive grid points along the last dimension the first term
- * is evaluated with exp, sin and cos in FP32 and the next three by the exact
- * recurrences of the Gaussian factor and the phase along that dimension (one
- * complex multiply each); partial sums are folded into FP64; complex64 out. */
+ * FP32: the phase is reduced in FP64 per packet and evaluated in FP32 turns.
+ * d = 1: of every 4 consecutive grid points the first term is evaluated with
+ * exp, sin and cos in FP32 and the next three by the exact recurrences of the
+ * Gaussian factor and the phase (one complex multiply each).  d = 2, 3: the
+ * term factorises over dimensions; each packet's per-dimension factors are
+ * tabulated on an output tile's grid lines (the same recurrences, four lines
+ * at a time) and every packet-point pair costs one complex multiply-add of
+ * those factors.  Partial sums are folded into FP64; complex64 out.  The work
+ * is cut into (output tile, packet slice) items: d = 1 the same number of
+ * slices per tile, d >= 2 slices in proportion to each tile's packet count,
+ * heaviest first, taken by persistent CTAs (no host wait). */
 fgr_status fgr_reconstruct_direct(fgr_ctx *ctx, const fgr_packets *pk, void *u_out,
                                   void *cuda_stream);
 
