@@ -46,3 +46,21 @@ def test_example4_mesh_holds_the_wave():
         core = decompose.decompose(u, grid, QN.reshape(1, -1), PN.reshape(1, -1), eps, R=8)
         amax = np.max(np.hypot(core[0], core[1]))
         assert np.max(np.hypot(out[0], out[1])) <= 1e-9 * amax, t
+
+
+def test_example_inputs_follow_sec_4_4():
+    from workloads.examples import EXAMPLES, SPLITS, example_u0
+    e4, e5 = EXAMPLES[4], EXAMPLES[5]
+    assert (e4["d"], e4["eps"], e4["T"]) == (1, 2.0 ** -12, 0.8)
+    assert (e5["d"], e5["eps"], e5["T"]) == (2, 2.0 ** -6, 1.6)
+    # 8000 and 16000 RK4 steps of 1e-4, split as in Tables 17-22
+    assert round(e4["T"] / e4["dt"]) == 8000 and round(e5["T"] / e5["dt"]) == 16000
+    assert SPLITS == (1, 2, 4, 8, 16, 32)
+    for ex in (4, 5):
+        e = EXAMPLES[ex]
+        g = example_grid(ex)
+        h = [(g["hi"][l] - g["lo"][l]) / g["n"][l] for l in range(g["d"])]
+        assert all(abs(hl - e["eps"]) <= 1e-15 for hl in h)  # dx = eps on [-2, 2)
+        u0 = example_u0(ex)
+        # (64/pi)^{d/4} exp(-32|x|^2): unit L2 norm
+        assert abs(math.sqrt(float(np.prod(h)) * np.sum(np.abs(u0) ** 2)) - 1) <= 1e-12
