@@ -1,19 +1,24 @@
 #!/usr/bin/env python3
 """Benchmark: FGGC reconstruction on one GB300 (and N independent GPUs).
 
-Workload (default): the 1-D WKB problem with eps = 1/1024, 512 (q) x 512 (p) =
-262144 packets, V = 1 - cos x, t = 1.0 (RK4, dt = 1e-4), output 32768 points on
-[-pi, pi), FP32 bulk arithmetic with FP64 phase reduction, complex64 output.
+Headline workload (default, --config 4): the 3-D WKB problem with eps = 1/64,
+the 2^24 largest-amplitude packets of a 32^3 (q) x 16^3 (p) mesh, V = |x|^2/2,
+propagated to t = 0.5 (RK4, dt = 1e-4, once, outside the timed region), output
+256^3 points on [-pi, pi)^3, FP32 bulk arithmetic with FP64 phase reduction,
+complex64 output, Q4P2 neighbours.
 
-One step = Algorithm 2 on one batch: copy the t = 0 packets into the working
-buffers, fgr_propagate to t (A1), fgr_reconstruct_fggc (A3-A5).  value =
-packets / step time.  In the same run the direct sum (A2) reconstructs the same
-propagated batch; its packets/s and the FGGC-vs-direct relative L2 are reported
-beside it.  L2 is flushed (a 512 MiB write) between timed steps; only the steps
-are inside the CUDA events.
+One step = one fgr_reconstruct_fggc call (A3-A5) on the device-resident
+packets; value = packets / mean step time (CUDA events on the launching
+stream; L2 flushed by a 512 MiB write between steps, outside the events).
+Beside it: the direct sum (A2) of the same packets, the FGGC/direct speed-up
+where their relative L2 difference is <= 1e-5, the end-to-end rate through
+the C ABI with pinned host buffers, and the roofline of the step's dominant
+kernel.  Extras: the 1-D pipeline with its RK4 step (workload 2), the 2-D
+reconstruction (workload 3), batched requests, the serving workload and the
+oracle on the host cores.
 
 --impl reference runs the FP64 CPU oracle (the only reference this method has)
-on a bounded sample of the same workload.
+on a bounded packet sample of the same workload.
 """
 
 from __future__ import annotations
@@ -33,8 +38,25 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "packets reconstructed/s, FGGC vs direct sum at rel L2<=1e-5; serving p50/p99 ms"
-WORKLOAD = "wkb-1d eps=1/1024 grid=32768 M=262144 (512q x 512p) V=1-cos(x) t=1.0 rk4 dt=1e-4 fp32/complex64 Q4P2"
-FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (no measured FP64 peak on file)
+WORKLOADS = {
+    1: "wkb-1d eps=1/64 grid=1024 M=4096 (64q x 64p) V=1-cos(x) t=0.5 fp64 Q4P2",
+    2: "wkb-1d eps=1/1024 grid=32768 M=262144 (512q x 512p) V=1-cos(x) t=1.0 rk4 dt=1e-4 fp32/complex64 Q4P2",
+    3: "wkb-2d eps=1/256 grid=1024^2 M=4194304 (64^2q x 32^2p) V=cos(x1)+cos(x2)+2 t=0.5 fp32/complex64 Q4P2",
+    4: "wkb-3d eps=1/64 grid=256^3 M=16777216 (top 2^24 by |a| of 32^3q x 16^3p) V=|x|^2/2 t=0.5 "
+       "fp32/complex64 Q4P2",
+}
+# FP64 FMA rate of this GB300 measured by a DFMA probe (2 FMA per clock per SM,
+# 152 SMs at 2.07 GHz; nominal 1.26 TFLOP/s)
+FP64_PEAK_TFLOPS = 1.19
+# FP32 FMA rate measured by an FFMA probe on this GB300 (nominal 152 x 128 x 2
+# x 2.07e9 = 80.5 TFLOP/s)
+FP32_PEAK_TFLOPS = 74.6
+# float2 reductions per second in L2 measured on this GB300 by a probe of
+# reductions to random addresses of a 64 MiB buffer (one 8-byte reduction per
+# lane, no two lanes of a warp on one 32-byte sector); 32 consecutive ones per
+# warp reach 855e9 per second
+L2_RED_PEAK_GPS = 222.8
+L2_RED_COALESCED_GPS = 855.1
 
 
 def _rank_env():
@@ -108,16 +130,27 @@ def rk4_nsteps(t: float, dt: float) -> int:
     return int(n) if abs(r - n) <= 1e-9 * max(n, 1.0) else int(math.ceil(r))
 
 
+# Algorithmic FP64 work of one RK4 packet-step per dimension: 4 stages of
+# about 40 FLOPs each.
+RK4_ALG_FLOPS_PER_PACKET_STEP = 160
 # FP64 FLOPs the RK4 kernel executes per packet-step (FMA = 2), counted by ncu
 # on GB300 (DFMA x 2 + DMUL + DADD of rk4_kernel), 1-D cosine potential:
 # 69.83 DFMA + 35.18 DMUL + 14.02 DADD (262144 packets, 100 steps).
-RK4_FP64_FLOPS_PER_PACKET_STEP = {(1, "cossum"): 188.86}
-# DRAM bytes of one RK4 launch on the bench workload (ncu, same capture): the
+RK4_EXEC_FLOPS_PER_PACKET_STEP = {(1, "cossum"): 188.86}
+# DRAM bytes of one RK4 launch on the 1-D workload (ncu, same capture): the
 # packet arrays are read once; the written state stays in L2 at kernel end.
 RK4_TRAFFIC_BYTES = {(1, "cossum", 262144): 10530816}
 
 
 def run_ours(args):
+    """The headline: FGGC reconstruction of the 3-D workload (2^24 propagated
+    packets onto 256^3 points, FP32/complex64, Q4P2).  One step = one
+    fgr_reconstruct_fggc call on device-resident packets (its node-box zeroing,
+    binning, coefficient scatter and grid passes); the packets are propagated
+    once before the timed region.  The direct sum of the same packets, the
+    FGGC/direct speed-up at equal accuracy, the end-to-end rate through the C
+    ABI with pinned host buffers and the roofline of the step's dominant
+    kernel are reported beside it."""
     import numpy as np
     import torch
 
@@ -138,121 +171,94 @@ def run_ours(args):
     prec = fgr.FGR_FP32 if w["precision"] == "fp32" else fgr.FGR_FP64
     ctx = fgr.Context(d, grid, eps, fgr.make_options(precision=prec))
     pot = fgr.make_potential(**w["potential"])
-    t_final, dt = w["t"], w["dt"]
     shape = tuple(grid["n"][:d])
     cdt = torch.complex64 if prec == fgr.FGR_FP32 else torch.complex128
+    stream = torch.cuda.current_stream(dev)
 
-    init = [torch.tensor(np.ascontiguousarray(pk[k]), dtype=torch.float64, device=dev) for k in "qpsa"]
-    work = [x.clone() for x in init]
-    packets = fgr.make_packets(*work)
+    # packets at t = 0, propagated once (A1; outside the timed region)
+    arrs = [torch.tensor(np.ascontiguousarray(pk[k]), dtype=torch.float64, device=dev) for k in "qpsa"]
+    packets = fgr.make_packets(*arrs)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fgr.fgr_propagate(ctx.handle, packets, pot, w["t"], w["dt"], stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    propagate_ms = e0.elapsed_time(e1)
+
     u_f = torch.zeros(shape, dtype=cdt, device=dev)
     u_d = torch.zeros(shape, dtype=cdt, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream(dev)
-    launches = {"n": 0}
-
-    def stats_launches():
-        launches["n"] += int(fgr.fgr_get_stats(ctx.handle).launches)
-
-    def step(ev=None):
-        for wbuf, ibuf in zip(work, init):
-            wbuf.copy_(ibuf)
-        if ev:
-            ev[0].record(stream)
-        fgr.fgr_propagate(ctx.handle, packets, pot, t_final, dt, stream)
-        stats_launches()
-        if ev:
-            ev[1].record(stream)
-        fgr.fgr_reconstruct_fggc(ctx.handle, packets, u_f, stream)
-        stats_launches()
-        if ev:
-            ev[2].record(stream)
-        fgr.fgr_reconstruct_direct(ctx.handle, packets, u_d, stream)
-        stats_launches()
-        if ev:
-            ev[3].record(stream)
 
     for _ in range(args.warmup):
-        step()
+        fgr.fgr_reconstruct_fggc(ctx.handle, packets, u_f, stream)
     torch.cuda.synchronize()
-    # launch shapes picked by the library's autotuner on the propagated batch
-    fgr.fgr_autotune(ctx.handle, packets, u_d, 3, stream)
-    tuning = fgr.fgr_get_tuning(ctx.handle)
-    launches["n"] = 0
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    # the library's per-stage CUDA events (recorded on this stream) give the
+    # dominant kernel's own duration in every timed step
+    fgr.fgr_set_timing(ctx.handle, True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stage = {"prep_ms": [], "bin_ms": [], "scatter_ms": [], "grid_ms": [], "pass_ms": [], "pass_terms": []}
+    launches = 0
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         for i in range(args.steps):
-            flush.zero_()
-            step(evs[i])
+            flush.zero_()                      # L2 flushed between steps, outside the events
+            evs[i][0].record(stream)
+            fgr.fgr_reconstruct_fggc(ctx.handle, packets, u_f, stream)
+            evs[i][1].record(stream)
+            st = fgr.fgr_get_stats(ctx.handle)
+            stage["prep_ms"].append(st.prep_ms)
+            stage["bin_ms"].append(st.coeff_ms)
+            stage["scatter_ms"].append(st.scatter_ms)
+            stage["grid_ms"].append(st.grid_ms)
+            stage["pass_ms"].append(st.pass_ms)
+            stage["pass_terms"].append(st.pass_terms)
+            launches += int(st.launches)
         torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    prop_ms = [e[0].elapsed_time(e[1]) for e in evs]
-    fggc_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    direct_ms = [e[2].elapsed_time(e[3]) for e in evs]
-    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
-    gpu_launches = launches["n"]
+    fgr.fgr_set_timing(ctx.handle, False)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    nodes = int(fgr.fgr_get_stats(ctx.handle).nodes)
+
+    # the direct sum of the same packets (A2) and the other FGGC variants
+    recon = reconstruct_runs(fgr, ctx, packets, u_d, grid, d, eps, prec, flush, stream, None, runs=20,
+                             direct_runs=args.direct_runs)
     ud, uf = u_d.cpu().numpy(), u_f.cpu().numpy()
     rel = float(np.linalg.norm(uf - ud) / max(np.linalg.norm(ud), 1e-300))
 
-    # reconstruction alone on the propagated batch: median, min and max of 20
-    # runs each (L2 flushed before every run), FGGC with Q4P2 and Q2P2
-    recon = reconstruct_runs(fgr, ctx, packets, u_d, grid, d, eps, prec, flush, stream, ud, runs=20)
-    # initial decomposition of u0 onto the t = 0 packet positions, and one step
-    # of multi-step FGGC with the flow learned from them (outside the timed region)
-    decomp = decompose_runs(fgr, ctx, w, init, pot, stream, flush, runs=20)
-
-    # stage split of FGGC (context timing on; outside the timed region)
-    fgr.fgr_set_timing(ctx.handle, True)
-    fgr.fgr_reconstruct_fggc(ctx.handle, packets, u_f, stream)
-    st = fgr.fgr_get_stats(ctx.handle)
-    fggc_stages = {"bounds_alloc_ms": st.prep_ms, "coeff_scatter_ms": st.scatter_ms, "grid_ms": st.grid_ms,
-                   "nodes": int(st.nodes)}
-    fgr.fgr_reconstruct_direct(ctx.handle, packets, u_d, stream)
-    st = fgr.fgr_get_stats(ctx.handle)
-    direct_stages = {"bin_ms": st.prep_ms, "sum_ms": st.direct_ms}
-    fgr.fgr_set_timing(ctx.handle, False)
-
-    # end to end through the C ABI with host buffers (copies inside the timed region)
-    host = {k: np.ascontiguousarray(pk[k]) for k in "qpsa"}
-    hwork = {k: np.empty_like(v) for k, v in host.items()}
-    hu = np.zeros(shape, dtype=np.complex64 if prec == fgr.FGR_FP32 else np.complex128)
-    hu_d = np.zeros_like(hu)
+    # end to end through the C ABI: packets in pinned host memory, u back to
+    # pinned host memory, both copies inside the timed region
+    host = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in arrs]
+    for h, x in zip(host, arrs):
+        h.copy_(x)
+    hpk = fgr.make_packets(*[h.numpy() for h in host])
+    hu = torch.empty(shape, dtype=cdt, pin_memory=True)
     e2e_ms = []
     for i in range(args.warmup + args.steps):
-        for k in "qpsa":
-            hwork[k][...] = host[k]
-        hp = fgr.make_packets(hwork["q"], hwork["p"], hwork["s"], hwork["a"])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        fgr.fgr_propagate(ctx.handle, hp, pot, t_final, dt)       # H2D, RK4, D2H of the packets
-        fgr.fgr_reconstruct_fggc(ctx.handle, hp, hu)               # H2D of the packets, D2H of u
-        fgr.fgr_reconstruct_direct(ctx.handle, hp, hu_d)           # H2D of the packets, D2H of u
+        fgr.fgr_reconstruct_fggc(ctx.handle, hpk, hu.numpy())   # H2D of the packets, D2H of u
         t1 = time.perf_counter()
         if i >= args.warmup:
             e2e_ms.append((t1 - t0) * 1e3)
-    pbytes = sum(v.nbytes for v in host.values())
-    h2d = 3 * pbytes
-    d2h = pbytes + hu.nbytes + hu_d.nbytes
+    e2e_rel = float(np.linalg.norm(hu.numpy() - uf) / max(np.linalg.norm(uf), 1e-300))
+    h2d = sum(h.numel() * h.element_size() for h in host)
+    d2h = hu.numel() * hu.element_size()
+    del host, hu
 
     def agg(xs):
         return max_over_ranks(statistics.mean(xs), world)
 
     ms_step = agg(step_ms)
-    ms_prop = agg(prop_ms)
-    ms_fggc = agg(fggc_ms)
-    ms_direct = agg(direct_ms)
     ms_e2e = agg(e2e_ms)
+    kern = {k: statistics.mean(v) for k, v in stage.items()}
+    roof = reconstruction_roofline(d, M, nodes, kern, ms_step)
     total_packets = M * world
-    kind = w["potential"]["kind"]
-    fpps = RK4_FP64_FLOPS_PER_PACKET_STEP.get((d, kind))
-    flops = fpps * M * rk4_nsteps(t_final, dt) if fpps else None
-    achieved_tflops = flops / (ms_prop * 1e-3) / 1e12 if flops else None
     out = None
     if rank == 0:
+        direct = recon["direct"]
         out = {
             "metric": METRIC,
             "value": total_packets / (ms_step * 1e-3),
@@ -264,73 +270,211 @@ def run_ours(args):
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f64 trajectories + f32/complex64 reconstruction",
+            "dtype": "f32/complex64 reconstruction (f64 phase reduction); f64 trajectories (untimed)",
             "data": "synthetic (seeded analytic WKB data, cut-off FFT initial decomposition)",
-            "config": {"workload": WORKLOAD, "packets_per_gpu": M, "grid": list(shape), "eps": eps,
-                       "t": t_final, "dt": dt, "strategy": "Q4P2 cq=1/2 cp=pi/8",
-                       "step": "propagate (A1) + fggc reconstruct (A3-A5) + direct sum (A2), same batch",
-                       "l2": "flushed (512 MiB write) between timed steps", "parallelism": "replicas",
-                       "autotuned": {"direct_ctas_per_sm": tuning[0], "grid_pass_ctas_per_sm": tuning[1],
-                                     "grid_pass_tile": tuning[2]}},
-            "stages": {
-                "propagate_ms": ms_prop,
-                "fggc_reconstruct_ms": ms_fggc,
-                "direct_reconstruct_ms": ms_direct,
-                "fggc_reconstruct_packets_per_s": total_packets / (ms_fggc * 1e-3),
-                "direct_reconstruct_packets_per_s": total_packets / (ms_direct * 1e-3),
-                "fggc_over_direct_reconstruct": ms_direct / ms_fggc,
-                "fggc_over_direct_pipeline": (ms_prop + ms_direct) / (ms_prop + ms_fggc),
+            "config": {"workload": WORKLOADS[args.config], "packets_per_gpu": M, "grid": list(shape),
+                       "eps": eps, "strategy": "Q4P2 cq=1/2 cp=pi/8",
+                       "step": "fgr_reconstruct_fggc of the propagated packets (A3-A5), device-resident",
+                       "l2": "flushed (512 MiB write) between timed steps, outside the events",
+                       "parallelism": "replicas"},
+            "headline": {
+                "fggc_packets_per_s": total_packets / (ms_step * 1e-3),
+                "fggc_ms_mean": ms_step, "fggc_ms_median": statistics.median(step_ms),
+                "fggc_ms_min": min(step_ms), "fggc_ms_max": max(step_ms),
+                "direct_packets_per_s": direct["packets_per_s"], "direct_ms_median": direct["median_ms"],
+                "direct_runs": direct["runs"],
+                "speedup_fggc_over_direct": (direct["median_ms"] / statistics.median(step_ms)
+                                             if rel <= 1e-5 else "not at equal accuracy"),
                 "rel_l2_fggc_vs_direct": rel,
-                "reconstruct_20_runs": recon,
-                "decompose_20_runs": decomp,
-                "fggc_stage_split": fggc_stages,
-                "direct_stage_split": direct_stages,
+                "propagate_ms_untimed": propagate_ms,
+                "fggc_stage_ms_mean": kern, "nodes": nodes,
             },
-            "roofline": {"kernel": "rk4_kernel (fgr_propagate)", "bound": "alu",
-                         "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved_tflops / FP64_PEAK_TFLOPS if achieved_tflops else None,
-                         "traffic": RK4_TRAFFIC_BYTES.get((d, kind, M)),
-                         "peak_source": "nominal FP64 rate of the profiling recipe (MEASURED_PEAKS.json has no "
-                                        "FP64 figure; a pure-DFMA probe measured 1.19 TFLOP/s)",
-                         "flops_per_launch": flops,
-                         "flops_counted": "FP64 FLOPs executed per packet-step (ncu: 2 DFMA + DMUL + DADD)"},
+            "stages": {"reconstruct_runs": recon},
+            "roofline": roof,
             "e2e": {"value": total_packets / (ms_e2e * 1e-3), "unit": "packets/s",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": gpu_launches,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "call": "fgr_reconstruct_fggc with pinned host packets and a pinned host output",
+                    "rel_l2_vs_device_call": e2e_rel},
+            "gpu_launches": launches,
             "clocks": clk.summary(),
         }
+    ctx.close()
+    del arrs, packets, u_f, u_d
+    torch.cuda.empty_cache()
+    if rank == 0:
         if args.extra:
             out["workloads"] = {}
             for cfg in [int(x) for x in args.extra.split(",") if x]:
-                out["workloads"]["config%d" % cfg] = reconstruct_bench(cfg, args, flush)
+                if cfg == 2:
+                    out["workloads"]["config2_pipeline"] = pipeline_bench(2, args, flush)
+                else:
+                    out["workloads"]["config%d" % cfg] = reconstruct_bench(cfg, args, flush)
+        if args.fft:
+            out["fft_grid_stage"] = fft_grid_bench(args, flush)
         if args.batch:
             out["batched_direct"] = batch_bench(args, flush)
         if args.serving:
             out["serving"] = serving_bench(args, local)
         if args.cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(w, args.cpu_sample)
-    ctx.close()
+            out["cpu_baseline"] = cpu_baseline(w, args)
     if world > 1:
         torch.distributed.destroy_process_group()
     return out
 
 
-def reconstruct_runs(fgr, ctx, packets, u_ref, grid, d, eps, prec, flush, stream, ud, runs=20):
-    """Median/min/max ms of `runs` reconstructions per method; FGGC with the
-    Q4P2 and Q2P2 neighbour sets and Q4P2 through a plan, relative L2
-    difference from the direct sum."""
+def reconstruction_roofline(d, M, nodes, kern, ms_step):
+    """Roofline block of the FGGC step's dominant kernel, from the library's
+    per-stage CUDA events of the timed steps (kern: mean per stage).
+
+    Scatter (K3+K4): unit = one contribution A e^{iS/eps} c_k of a packet to a
+    node (eq. 2.25), M 8^d per launch (Q4P2), against the probed rate of
+    scattered 8-byte L2 reductions.  Grid passes (K5): unit = one node-point
+    term W[a, b] g(x_m - a dq) (a real x complex multiply-add, 4 FLOPs), counted
+    on the device per launch (occupied b-range x window points over every
+    (row, a) line), against the measured FP32 FMA rate."""
+    contrib = M * 8 ** d
+    scatter_ms, pass_ms = kern["scatter_ms"], kern["pass_ms"]
+    if scatter_ms >= pass_ms:
+        out = {"kernel": "coefficient + scatter (K3+K4)", "bound": "l2",
+               "achieved": contrib / (scatter_ms * 1e-3) / 1e9, "peak": L2_RED_PEAK_GPS,
+               "unit": "G contributions/s", "traffic": None, "launch_ms": scatter_ms,
+               "units_per_launch": contrib,
+               "unit_def": "one contribution of a packet to a node (eq. 2.25), M 8^d per launch",
+               "peak_source": "float2 reductions to random addresses of a 64 MiB buffer (probe on this GB300)"}
+    else:
+        terms = kern["pass_terms"]
+        out = {"kernel": "grid_pass_kernel (K5, all passes)", "bound": "alu",
+               "achieved": 4.0 * terms / (pass_ms * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,
+               "unit": "TFLOP/s", "traffic": None, "launch_ms": pass_ms,
+               "units_per_launch": terms,
+               "unit_def": "one node-point term W[a,b] g(x_m - a dq): a real x complex multiply-add (4 FLOPs); "
+                           "per pass the occupied b-range x window points of every (row, a) line",
+               "peak_source": "FFMA probe on this GB300 (74.6 TFLOP/s; nominal 80.5 at 2.07 GHz)"}
+    out["frac"] = out["achieved"] / out["peak"]
+    out["share_of_step"] = out["launch_ms"] / ms_step
+    out["stage_ms"] = {"scatter": scatter_ms, "passes": pass_ms}
+    return out
+
+
+def pipeline_bench(cfg: int, args, flush):
+    """The 1-D workload as a whole pipeline: copy the t = 0 packets into the
+    working buffers, fgr_propagate (A1, 10^4 RK4 steps), fgr_reconstruct_fggc
+    (A3-A5) and fgr_reconstruct_direct (A2) of the same batch; CUDA events
+    between the calls give the stage times; the roofline of the RK4 launch."""
+    import numpy as np
+    import torch
+
+    import paper_2504_21785_gb300 as fgr
+    from workloads import config_workload
+
+    w = config_workload(cfg)
+    d, eps, grid = w["d"], w["eps"], w["grid"]
+    pk = w["packets"]
+    M = int(pk["s"].size)
+    prec = fgr.FGR_FP32 if w["precision"] == "fp32" else fgr.FGR_FP64
+    ctx = fgr.Context(d, grid, eps, fgr.make_options(precision=prec))
+    pot = fgr.make_potential(**w["potential"])
+    t_final, dt = w["t"], w["dt"]
+    shape = tuple(grid["n"][:d])
+    cdt = torch.complex64 if prec == fgr.FGR_FP32 else torch.complex128
+    init = [torch.tensor(np.ascontiguousarray(pk[k]), dtype=torch.float64, device="cuda") for k in "qpsa"]
+    work = [x.clone() for x in init]
+    packets = fgr.make_packets(*work)
+    u_f = torch.zeros(shape, dtype=cdt, device="cuda")
+    u_d = torch.zeros(shape, dtype=cdt, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        for wbuf, ibuf in zip(work, init):
+            wbuf.copy_(ibuf)
+        if ev:
+            ev[0].record(stream)
+        fgr.fgr_propagate(ctx.handle, packets, pot, t_final, dt, stream)
+        if ev:
+            ev[1].record(stream)
+        fgr.fgr_reconstruct_fggc(ctx.handle, packets, u_f, stream)
+        if ev:
+            ev[2].record(stream)
+        fgr.fgr_reconstruct_direct(ctx.handle, packets, u_d, stream)
+        if ev:
+            ev[3].record(stream)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    fgr.fgr_autotune(ctx.handle, packets, u_d, 3, stream)
+    tuning = fgr.fgr_get_tuning(ctx.handle)
+    nsteps = 5
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(nsteps)]
+    for i in range(nsteps):
+        flush.zero_()
+        step(evs[i])
+    torch.cuda.synchronize()
+    prop_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    fggc_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    direct_ms = statistics.mean(e[2].elapsed_time(e[3]) for e in evs)
+    step_ms = statistics.mean(e[0].elapsed_time(e[3]) for e in evs)
+    ud, uf = u_d.cpu().numpy(), u_f.cpu().numpy()
+    rel = float(np.linalg.norm(uf - ud) / max(np.linalg.norm(ud), 1e-300))
+    recon = reconstruct_runs(fgr, ctx, packets, u_d, grid, d, eps, prec, flush, stream, ud, runs=20)
+    decomp = decompose_runs(fgr, ctx, w, init, pot, stream, flush, runs=20)
+    fgr.fgr_set_timing(ctx.handle, True)
+    fgr.fgr_reconstruct_fggc(ctx.handle, packets, u_f, stream)
+    st = fgr.fgr_get_stats(ctx.handle)
+    fggc_stages = {"prep_ms": st.prep_ms, "bin_ms": st.coeff_ms, "coeff_scatter_ms": st.scatter_ms,
+                   "grid_ms": st.grid_ms, "nodes": int(st.nodes)}
+    fgr.fgr_set_timing(ctx.handle, False)
+    kind = w["potential"]["kind"]
+    steps_rk4 = rk4_nsteps(t_final, dt)
+    # algorithmic FP64 work of one packet-step (4 stages, about 40 d FLOPs
+    # each) against the measured DFMA rate; the FLOPs the kernel executes
+    # (counted by ncu) are kept beside it
+    alg = RK4_ALG_FLOPS_PER_PACKET_STEP * d * M * steps_rk4
+    exe = RK4_EXEC_FLOPS_PER_PACKET_STEP.get((d, kind))
+    ctx.close()
+    return {
+        "workload": WORKLOADS[cfg], "packets": M,
+        "step": "propagate (A1) + fggc reconstruct (A3-A5) + direct sum (A2), same batch, 5 steps",
+        "step_ms": step_ms, "packets_per_s": M / (step_ms * 1e-3),
+        "propagate_ms": prop_ms, "fggc_ms": fggc_ms, "direct_ms": direct_ms,
+        "fggc_packets_per_s": M / (fggc_ms * 1e-3), "direct_packets_per_s": M / (direct_ms * 1e-3),
+        "rel_l2_fggc_vs_direct": rel,
+        "reconstruct_20_runs": recon, "decompose_20_runs": decomp, "fggc_stage_split": fggc_stages,
+        "autotuned": {"direct_ctas_per_sm": tuning[0], "grid_pass_ctas_per_sm": tuning[1],
+                      "grid_pass_tile": tuning[2]},
+        "rk4_roofline": {"kernel": "rk4_kernel (fgr_propagate)", "bound": "alu",
+                         "achieved": alg / (prop_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": alg / (prop_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                         "flops_per_launch": alg,
+                         "flops_counted": "algorithmic: 4 stages x 40 d FP64 FLOPs per packet-step",
+                         "peak_source": "DFMA probe on this GB300 (2 FP64 FMA per clock per SM at 2.07 GHz)",
+                         "executed_flops_per_packet_step": exe,
+                         "traffic": RK4_TRAFFIC_BYTES.get((d, kind, M))},
+    }
+
+
+def reconstruct_runs(fgr, ctx, packets, u_ref, grid, d, eps, prec, flush, stream, ud, runs=20, direct_runs=None):
+    """Median/min/max ms of `runs` reconstructions per method (`direct_runs`
+    for the direct sum, whose 3-D runs take seconds); FGGC with the Q4P2 and
+    Q2P2 neighbour sets and Q4P2 through a plan, relative L2 difference from
+    the direct sum.  The direct sum is left in u_ref; with ud None its result
+    becomes the reference."""
     import numpy as np
     import torch
 
     q2 = fgr.Context(d, grid, eps, fgr.make_options(precision=prec, nq=2, np_=2))
-    u = torch.zeros_like(u_ref)
     out = {}
     for name, fn, c in (("direct", fgr.fgr_reconstruct_direct, ctx), ("fggc_q4p2", fgr.fgr_reconstruct_fggc, ctx),
                         ("fggc_q2p2", fgr.fgr_reconstruct_fggc, q2)):
-        for _ in range(3):
+        u = u_ref if name == "direct" else torch.zeros_like(u_ref)
+        nrun = direct_runs if (name == "direct" and direct_runs) else runs
+        t0 = time.perf_counter()
+        fn(c.handle, packets, u, stream)
+        torch.cuda.synchronize()
+        for _ in range(2 if time.perf_counter() - t0 < 0.5 else 0):
             fn(c.handle, packets, u, stream)
         ms = []
-        for _ in range(runs):
+        for _ in range(nrun):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -339,10 +483,15 @@ def reconstruct_runs(fgr, ctx, packets, u_ref, grid, d, eps, prec, flush, stream
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
         got = u.cpu().numpy()
+        if name == "direct" and ud is None:
+            ud = got
         rel = float(np.linalg.norm(got - ud) / max(np.linalg.norm(ud), 1e-300))
         med = statistics.median(ms)
-        out[name] = {"median_ms": med, "min_ms": min(ms), "max_ms": max(ms),
+        out[name] = {"runs": nrun, "median_ms": med, "min_ms": min(ms), "max_ms": max(ms),
                      "packets_per_s": int(packets.m) / (med * 1e-3), "rel_l2_vs_direct": rel}
+        if name != "direct":
+            del u
+    u = torch.zeros_like(u_ref)
     q2.close()
     # FGGC Q4P2 through a plan: the node box fixed once for this packet set,
     # so a call waits for nothing on the host (the unplanned call reads the
@@ -534,6 +683,76 @@ def reconstruct_bench(cfg: int, args, flush):
             "fggc_stage_split_ms": {"bounds_alloc": st.prep_ms, "coeff_scatter": st.scatter_ms, "grid": st.grid_ms}}
 
 
+def fft_grid_bench(args, flush):
+    """FGGC with the DFT grid stage (FGR_FLAG_FFT_GRID) beside the direct grid
+    stage on the commensurate meshes of Examples 4 and 5 (Sec. 4.4: h = eps,
+    N = 16 / sqrt(eps) = 1024 and 128): the fixed mesh of each example with
+    the amplitudes of u0 (fgr_decompose_tensor), propagated under V2 over
+    T / 32 (one restart interval of the 32-step split; untimed), FP32, Q2P2;
+    median of 20 reconstructions each, L2 flushed before every run."""
+    import numpy as np
+    import torch
+
+    import paper_2504_21785_gb300 as fgr
+    from workloads.examples import EXAMPLES, example_axis, example_grid, example_u0
+
+    stream = torch.cuda.current_stream()
+    out = {}
+    for ex in (4, 5):
+        e = EXAMPLES[ex]
+        d, eps = e["d"], e["eps"]
+        grid = example_grid(ex)
+        q, p = example_axis(ex)
+        aq, ap = torch.tensor(q, device="cuda"), torch.tensor(p, device="cuda")
+        L = q.size
+        idx = torch.arange(L ** d, device="cuda")
+        Q = torch.stack([aq[(idx // (L ** (d - 1 - l))) % L] for l in range(d)]).contiguous()
+        P = torch.stack([ap[(idx // (L ** (d - 1 - l))) % L] for l in range(d)]).contiguous()
+        del idx
+        m = Q.shape[1]
+        S = torch.zeros(m, dtype=torch.float64, device="cuda")
+        A = torch.zeros((2, m), dtype=torch.float64, device="cuda")
+        u0 = torch.tensor(example_u0(ex), dtype=torch.complex64, device="cuda")
+        opts = {name: fgr.make_options(precision=fgr.FGR_FP32, nq=2, np_=2, flags=fl)
+                for name, fl in (("direct_stage", 0), ("dft_stage", fgr.FGR_FLAG_FFT_GRID))}
+        res = {"packets": m, "grid": grid["n"], "eps": eps, "N_dft": int(round(16 / math.sqrt(eps)))}
+        outs = {}
+        with fgr.Context(d, grid, eps, opts["direct_stage"]) as c0:
+            fgr.fgr_decompose_tensor(c0.handle, fgr.make_axes([(aq, ap)] * d), u0, m, None, A, stream)
+            pk = fgr.make_packets(Q, P, S, A)
+            fgr.fgr_propagate(c0.handle, pk, fgr.make_potential(**e["potentials"]["V2"]), e["T"] / 32, e["dt"],
+                              stream)
+        for name, o in opts.items():
+            with fgr.Context(d, grid, eps, o) as c:
+                u = torch.zeros(tuple(grid["n"]), dtype=torch.complex64, device="cuda")
+                for _ in range(3):
+                    fgr.fgr_reconstruct_fggc(c.handle, pk, u, stream)
+                ms = []
+                for _ in range(20):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    fgr.fgr_reconstruct_fggc(c.handle, pk, u, stream)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                fgr.fgr_set_timing(c.handle, True)
+                fgr.fgr_reconstruct_fggc(c.handle, pk, u, stream)
+                st = fgr.fgr_get_stats(c.handle)
+                fgr.fgr_set_timing(c.handle, False)
+                outs[name] = u.cpu().numpy()
+                res[name] = {"median_ms": statistics.median(ms), "min_ms": min(ms), "max_ms": max(ms),
+                             "packets_per_s": m / (statistics.median(ms) * 1e-3), "grid_stage_ms": st.grid_ms,
+                             "pass_kernels_ms": st.pass_ms}
+        a, b = outs["dft_stage"], outs["direct_stage"]
+        res["rel_l2_dft_vs_direct_stage"] = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+        res["grid_stage_speedup"] = res["direct_stage"]["grid_stage_ms"] / res["dft_stage"]["grid_stage_ms"]
+        out["example%d" % ex] = res
+        del Q, P, S, A, pk, u0
+        torch.cuda.empty_cache()
+    return out
+
+
 def batch_bench(args, flush):
     """Many small reconstructions: direct sums as one fgr_reconstruct_direct call
     each on one stream, against one fgr_reconstruct_direct_batch call, eager and
@@ -658,9 +877,10 @@ def serving_bench(args, device_index: int):
     M = 2^L with L uniform in [12, log2(max packets)] (WKB data on a q x p mesh),
     propagated once to t = 0.5 on the GPU and kept resident; each request picks
     a set, a grid (1-D: 1024..32768 points, 2-D: 256^2..1024^2, powers of two)
-    and a method (direct / FGGC) uniformly; FP32.  Capacity = 1 / mean isolated
-    service time; p50/p99 of submit-to-done latency and packets/s at 0.5x, 0.8x
-    and 1.0x capacity."""
+    and a method (direct / FGGC) uniformly; FP32.  Capacity = the saturated
+    request rate (a burst submitted at once); Poisson streams of 2000 requests
+    at 0.5x, 0.8x and 1.0x capacity; p50/p99 of submit-to-done latency and
+    packets/s per level."""
     import numpy as np
     import torch
 
@@ -709,9 +929,9 @@ def serving_bench(args, device_index: int):
         t = fgr.fgr_submit(srv, fgr.make_request(method, grid, eps, opt, sid, u))
         r = fgr.fgr_poll(srv, t, -1)
         iso.append(r.t_done_ms - r.t_start_ms)
-    capacity = 1e3 / float(np.mean(iso))
-    # saturated throughput: a burst submitted at once, all slots busy
-    burst = [draw() for _ in range(args.serve_probe)]
+    # capacity = the saturated rate: a burst submitted at once keeps every
+    # slot busy (the load levels below are fractions of it)
+    burst = [draw() for _ in range(4 * args.serve_probe)]
     bouts = [torch.zeros(tuple(g["n"]), dtype=torch.complex64, device="cuda") for (_, _, _, _, g, _) in burst]
     tb0 = time.perf_counter()
     bt = [fgr.fgr_submit(srv, fgr.make_request(mth, g, e, opt, sid, u))
@@ -719,6 +939,7 @@ def serving_bench(args, device_index: int):
     for t in bt:
         fgr.fgr_poll(srv, t, -1)
     burst_rate = len(burst) / (time.perf_counter() - tb0)
+    capacity = burst_rate
     del bouts
     levels = {}
     for frac in (0.5, 0.8, 1.0):
@@ -748,60 +969,140 @@ def serving_bench(args, device_index: int):
     return {"sets": len(sets), "packets_min": min(ms), "packets_max": max(ms), "setup_s_untimed": t_setup,
             "inflight": args.serve_inflight, "max_batch": 16, "isolated_service_ms_mean": float(np.mean(iso)),
             "isolated_service_ms_p50": float(np.percentile(iso, 50)),
-            "capacity_req_per_s": capacity, "burst_req_per_s": burst_rate, "levels": levels,
+            "capacity_req_per_s": capacity, "capacity_def": "saturated rate of a burst of %d requests" % len(burst),
+            "isolated_capacity_req_per_s": 1e3 / float(np.mean(iso)), "levels": levels,
             "mix": "d in {1,2}; grids 1-D 1024..32768, 2-D 256^2..1024^2; direct/fggc 50/50; fp32"}
 
 
-def cpu_baseline(w, sample: int):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload:
-    `sample` packets propagated (C RK4, OpenMP) and reconstructed by the
-    oracle's FGGC and by its direct sum on the full output grid."""
+def _oracle_job(job):
+    """One oracle reconstruction of a packet chunk on the full grid (runs in a
+    spawned worker process); returns (seconds, squared norm of the field)."""
     import numpy as np
 
-    from oracle import fga, fggc, lsa, trajectories
+    from oracle import fga, fggc, lsa
+    kind, pk, grid, eps, dq, dp, R = job
+    t0 = time.perf_counter()
+    if kind == "fggc":
+        u = fggc.reconstruct(pk, grid, eps, dq, dp, lsa.Strategy(nq=4, np_=2), R=R)
+    else:
+        u = fga.direct_sum(pk, grid, eps, dq, dp, R=R)
+    return time.perf_counter() - t0, float(np.vdot(u, u).real)
+
+
+def _oracle_sample(w, count: int, seed: int = 0):
+    """`count` packets of the workload (uniform sample without replacement,
+    seeded), propagated to the workload's t by the oracle's RK4."""
+    import numpy as np
+
+    from oracle import trajectories
     pk = w["packets"]
     M = pk["s"].size
-    rng = np.random.default_rng(0)
-    idx = np.sort(rng.choice(M, size=min(sample, M), replace=False))
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(M, size=min(count, M), replace=False))
     sub = {k: np.ascontiguousarray(pk[k][..., idx]) for k in ("q", "p", "s", "a")}
-    mesh = w["mesh"]
     t0 = time.perf_counter()
     prop = trajectories.propagate(sub, w["potential"], w["t"], w["dt"])
-    t1 = time.perf_counter()
+    return prop, idx, time.perf_counter() - t0
+
+
+def _chunks(pk: dict, n: int):
+    """The packet set split into n consecutive chunks (FGGC and the direct sum
+    are linear in the packets, so the chunks' fields add up to the whole)."""
+    import numpy as np
+    m = pk["s"].size
+    cuts = np.linspace(0, m, n + 1).astype(int)
+    return [{k: np.ascontiguousarray(pk[k][..., a:b]) for k in ("q", "p", "s", "a")}
+            for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
+
+
+def oracle_pool(workers: int):
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(workers)
+
+
+def cpu_baseline(w, args, pool=None):
+    """The FP64 oracle, as it stands, on bounded packet samples of the
+    workload on the host cores: FGGC (Algorithm 2: aggregation onto the nodes,
+    eq. 2.25, then eq. 2.24 node by node) and the direct sum (eq. 2.10) of
+    propagated packets on the full output grid, single-threaded and spread
+    over all cores (one spawned process per core, each reconstructing its own
+    chunk of the sample; their partial fields are not summed)."""
     R = 6 if w["precision"] == "fp32" else 8
-    fggc.reconstruct(prop, w["grid"], w["eps"], mesh.dq, mesh.dp, lsa.Strategy(nq=4, np_=2), R=R)
-    t2 = time.perf_counter()
-    fga.direct_sum(prop, w["grid"], w["eps"], mesh.dq, mesh.dp, R=R)
-    t3 = time.perf_counter()
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": idx.size / (t3 - t0), "unit": "packets/s", "cores": cores, "kind": "oracle",
-            "sample": "%d of %d packets (uniform sample, seed 0): propagate %.2f s (C RK4, OpenMP %d threads) "
-                      "+ FGGC reconstruct %.2f s + direct sum %.2f s (numpy, 1 thread) on the full grid"
-                      % (idx.size, M, t1 - t0, cores, t2 - t1, t3 - t2)}
+    mesh = w["mesh"]
+    cores = os.cpu_count() or 1
+    own_pool = pool is None
+    if own_pool:
+        pool = oracle_pool(cores)
+    try:
+        res = {}
+        for kind, n1, nall in (("fggc", args.cpu_fggc_single, args.cpu_fggc_all),
+                               ("direct", args.cpu_direct_single, args.cpu_direct_all)):
+            sub, _, _ = _oracle_sample(w, max(n1, nall), seed=0)
+            one = _chunks(sub, max(1, sub["s"].size // max(n1, 1)))[0]
+            t_single, _ = _oracle_job((kind, one, w["grid"], w["eps"], mesh.dq, mesh.dp, R))
+            jobs = [(kind, c, w["grid"], w["eps"], mesh.dq, mesh.dp, R) for c in _chunks(sub, cores)]
+            t0 = time.perf_counter()
+            list(pool.imap_unordered(_oracle_job, jobs))
+            t_all = time.perf_counter() - t0
+            res[kind] = {"single_thread_packets_per_s": one["s"].size / t_single,
+                         "single_thread_sample": int(one["s"].size), "single_thread_s": t_single,
+                         "all_core_packets_per_s": sub["s"].size / t_all, "all_core_sample": int(sub["s"].size),
+                         "all_core_s": t_all}
+    finally:
+        if own_pool:
+            pool.close()
+            pool.join()
+    f = res["fggc"]
+    return {"value": f["all_core_packets_per_s"], "unit": "packets/s", "cores": cores, "kind": "oracle",
+            "sample": "FGGC of %d propagated packets (uniform sample, seed 0) on the full %s grid over %d processes "
+                      "(%.1f s); single-threaded %d packets in %.1f s = %.3g packets/s; direct sum %.3g packets/s "
+                      "on %d cores, %.3g on one" % (
+                          f["all_core_sample"], "x".join(str(n) for n in w["grid"]["n"][:w["d"]]), cores,
+                          f["all_core_s"], f["single_thread_sample"], f["single_thread_s"],
+                          f["single_thread_packets_per_s"], res["direct"]["all_core_packets_per_s"], cores,
+                          res["direct"]["single_thread_packets_per_s"]),
+            "fggc": res["fggc"], "direct": res["direct"]}
 
 
 def run_reference(args):
+    """The oracle's FGGC reconstruction of the headline workload on the host
+    cores: each step reconstructs a fresh packet sample (one chunk per core,
+    spawned processes) on the full grid; value = sampled packets / step time."""
     rank, _, world = _rank_env()
     if rank != 0:
         return None
     from workloads import config_workload
     w = config_workload(args.config)
-    times, vals = [], []
-    last = None
-    for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(w, args.ref_sample)
-        if i >= args.warmup:
-            vals.append(cb["value"])
-            last = cb
-    value = statistics.mean(vals)
-    ms = args.ref_sample / value * 1e3
+    R = 6 if w["precision"] == "fp32" else 8
+    mesh = w["mesh"]
+    cores = os.cpu_count() or 1
+    per_step = max(cores, args.ref_sample)
+    sub, _, t_prop = _oracle_sample(w, per_step * (args.warmup + args.steps), seed=1)
+    pool = oracle_pool(cores)
+    times = []
+    try:
+        allc = _chunks(sub, args.warmup + args.steps)
+        for i, step_pk in enumerate(allc):
+            jobs = [("fggc", c, w["grid"], w["eps"], mesh.dq, mesh.dp, R) for c in _chunks(step_pk, cores)]
+            t0 = time.perf_counter()
+            list(pool.imap_unordered(_oracle_job, jobs))
+            if i >= args.warmup:
+                times.append((time.perf_counter() - t0, step_pk["s"].size))
+    finally:
+        pool.close()
+        pool.join()
+    tot_s = sum(t for t, _ in times)
+    tot_p = sum(n for _, n in times)
+    value = tot_p / tot_s
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "packets/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "packets_per_step": args.ref_sample,
-                       "step": "propagate + fggc reconstruct + direct sum of a packet sample (oracle)"},
-            "cpu_baseline": {"value": value, "unit": "packets/s", "cores": last["cores"],
-                             "kind": "oracle", "sample": last["sample"]},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_s / len(times) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.config], "packets_per_step": tot_p // len(times),
+                       "step": "oracle FGGC reconstruction (Algorithm 2) of a packet sample on the full grid"},
+            "cpu_baseline": {"value": value, "unit": "packets/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d propagated packets per step (uniform sample, seed 1; oracle RK4 %.1f s, "
+                                       "untimed), one chunk per process on %d processes, full grid"
+                                       % (tot_p // len(times), t_prop, cores)},
             "e2e": {"value": value, "unit": "packets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -951,19 +1252,26 @@ def multistep_study(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--config", type=int, default=4)
+    ap.add_argument("--direct-runs", type=int, default=5,
+                    help="timed runs of the direct sum beside the headline (each takes seconds in 3-D)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
-    ap.add_argument("--cpu-sample", type=int, default=2048)
-    ap.add_argument("--ref-sample", type=int, default=512)
-    ap.add_argument("--extra", default="3", help="other workloads to reconstruct, e.g. 3,4 ('' for none)")
+    ap.add_argument("--cpu-fggc-single", type=int, default=2, help="oracle FGGC packets, one process")
+    ap.add_argument("--cpu-fggc-all", type=int, default=0, help="oracle FGGC packets over all cores (0: 2 per core)")
+    ap.add_argument("--cpu-direct-single", type=int, default=32)
+    ap.add_argument("--cpu-direct-all", type=int, default=0, help="0: 32 per core")
+    ap.add_argument("--ref-sample", type=int, default=0, help="oracle packets per reference step (0: one per core)")
+    ap.add_argument("--extra", default="2,3", help="other workloads: 2 = 1-D pipeline with RK4, 3 = 2-D ('' for none)")
     ap.add_argument("--no-serving", dest="serving", action="store_false")
     ap.add_argument("--no-batch", dest="batch", action="store_false")
+    ap.add_argument("--no-fft", dest="fft", action="store_false",
+                    help="skip the DFT grid stage on the meshes of Examples 4-5")
     ap.add_argument("--serve-sets", type=int, default=32)
     ap.add_argument("--serve-max-packets", type=int, default=1 << 22)
-    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-probe", type=int, default=40)
     ap.add_argument("--serve-inflight", type=int, default=4)
     ap.add_argument("--profile-packets", type=int, default=0,
@@ -974,6 +1282,9 @@ def main():
                     help="print the runtimes of the multi-step examples of Sec. 4.4 and exit")
     ap.add_argument("--study-precision", choices=["fp32", "fp64"], default="fp32")
     args = ap.parse_args()
+    cores = os.cpu_count() or 1
+    args.cpu_fggc_all = args.cpu_fggc_all or 2 * cores
+    args.cpu_direct_all = args.cpu_direct_all or 32 * cores
     if args.profile:
         run_profile_case(args)
         return

@@ -84,8 +84,24 @@ typedef struct {
     double rcond;       /* relative singular-value cut-off of the pseudo-inverse
                            (Remark 2); 0 -> 1e-14 */
     int32_t precision;  /* fgr_precision; FP64 default */
-    int32_t flags;      /* 0; reserved */
+    int32_t flags;      /* FGR_FLAG_* bits, 0 by default */
 } fgr_options;
+/* Option flags.
+ * FGR_FLAG_FFT_GRID: FGGC's grid stage (eq. 2.24) evaluates the sum over the
+ *   p-nodes of every q-node by an inverse DFT, the route of Sec. 2.3 (after
+ *   eq. 2.25) and Remark 3 for meshes commensurate with the grid: with
+ *   x_m = lo + m h, e^{i b dp x_m / eps} = e^{i b dp lo / eps} e^{2 pi i b m / N}
+ *   when h dp / eps = 2 pi / N.  fgr_create returns FGR_E_INVALID unless, in
+ *   every dimension, N = 2 pi eps / (h dp) is a power of two in [8, 8192]
+ *   (relative tolerance 1e-9); the meshes of Sec. 4.4 (h = eps, dp =
+ *   pi sqrt(eps) / 8, so N = 16 / sqrt(eps)) are.  Same results as the direct
+ *   grid stage up to rounding.  fgr_reconstruct_fggc_noalloc ignores the flag.
+ * FGR_FLAG_SNAP_CP: before anything else, cp is replaced by the nearest value
+ *   that makes dimension 0 commensurate (N a power of two, as above); the
+ *   least-squares constants (Tables 1-4) then belong to that cp. */
+#define FGR_FLAG_FFT_GRID 1
+#define FGR_FLAG_SNAP_CP 2
+
 
 typedef struct {
     int64_t m;          /* number of packets, >= 0 */
@@ -269,7 +285,8 @@ fgr_status fgr_reconstruct_fggc(fgr_ctx *ctx, const fgr_packets *pk, void *u_out
  * fgr_reconstruct_fggc computes, with all of its working memory (bounds, row
  * flag and node array) in one static device array of 8 MiB that the library
  * reserves on every device that loads it, for as long as the process lives.
- * Limits: 1-D contexts only; packets and u_out must be device memory; the node
+ * Limits: 1-D contexts only; packets and u_out must be device memory of the
+ * context's device (or managed memory; FGR_E_INVALID otherwise); the node
  * array (16 bytes per complex128 or 8 per complex64 cell) and the grid pass's
  * tables (8 bytes per node of the box's a-range and per grid point) must fit
  * in 8 MiB - 512 B together; larger problems return FGR_E_CAPACITY with the
@@ -346,12 +363,20 @@ typedef struct {
 fgr_status fgr_get_info(const fgr_ctx *ctx, fgr_info *out);
 
 /* Per-stage device times (milliseconds, CUDA events) of the context's last
- * reconstruct or propagate call, when timing is enabled with fgr_set_timing. */
+ * reconstruct or propagate call, when timing is enabled with fgr_set_timing.
+ * FGGC: prep_ms = clearing the node array, coeff_ms = binning the packets by
+ * anchor cell (d >= 2, FP32), scatter_ms = the coefficient and scatter
+ * kernels, grid_ms = the whole grid stage (eq. 2.24), of which pass_ms is the
+ * grid-pass kernels alone; pass_terms = node-point terms of the grid passes
+ * (per pass, over every (row, node a) line: the occupied b-range times the
+ * grid points in node a's window; counted on the device when timing is on). */
 typedef struct {
     double prep_ms, coeff_ms, scatter_ms, grid_ms, direct_ms, propagate_ms, total_ms;
     int64_t launches;       /* kernels launched by the last call */
     int64_t pairs;          /* FGR direct: packet-point pairs inside windows */
     int64_t nodes;          /* FGGC: cells of the node array */
+    double pass_ms;         /* FGGC: grid-pass kernels alone (part of grid_ms) */
+    int64_t pass_terms;     /* FGGC: node-point terms of the grid passes */
 } fgr_stats;
 fgr_status fgr_set_timing(fgr_ctx *ctx, int32_t enabled);
 fgr_status fgr_get_stats(const fgr_ctx *ctx, fgr_stats *out);

@@ -84,7 +84,7 @@ StageTimer::StageTimer(fgr_ctx *ctx, cudaStream_t s) : ctx_(ctx), s_(s) {
 }
 
 void StageTimer::mark(double *slot) {
-    if (!ctx_->timing.enabled || n_ >= 12) return;
+    if (!ctx_->timing.enabled || n_ >= 24) return;
     cudaEventCreate(&ev_[n_]);
     cudaEventRecord(ev_[n_], s_);
     slot_[n_] = slot;
@@ -233,9 +233,9 @@ fgr_status resolve_options(const fgr_options *in, fgr_options *out) {
     if (o.window_r == 0) o.window_r = o.precision == FGR_FP64 ? 8.0 : 6.0;
     if (!(o.cq > 0) || !(o.cp > 0) || !is_finite(o.cq) || !is_finite(o.cp) || (o.nq != 2 && o.nq != 4) ||
         (o.np != 2 && o.np != 4) || !(o.window_r > 0) || o.window_r > 40 || !(o.rcond > 0) ||
-        o.rcond >= 1 || o.flags != 0) {
+        o.rcond >= 1 || (o.flags & ~(FGR_FLAG_FFT_GRID | FGR_FLAG_SNAP_CP)) != 0) {
         set_error("options out of range (cq, cp > 0; nq, np in {2,4}; 0 < window_r <= 40; "
-                  "0 < rcond < 1; flags = 0)");
+                  "0 < rcond < 1; flags of FGR_FLAG_FFT_GRID | FGR_FLAG_SNAP_CP)");
         return FGR_E_INVALID;
     }
     *out = o;
@@ -555,6 +555,29 @@ fgr_status fgr_create(int32_t d, const fgr_grid *grid, double eps, const fgr_opt
     fgr_options o;
     rc = resolve_options(opt, &o);
     if (rc != FGR_OK) return rc;
+    // commensurate meshes: h dp / eps = 2 pi / N per dimension (N a power of two)
+    int fft_logn[kMaxDim] = {0, 0, 0};
+    if (o.flags & FGR_FLAG_SNAP_CP) {
+        const double n0 = 2 * M_PI * eps / (G.h[0] * o.cp * std::sqrt(eps));
+        const double l2 = std::round(std::log2(n0));
+        if (!(l2 >= 3 && l2 <= 13)) {
+            set_error("snap: 2 pi eps / (h dp) = %g is not near a power of two in [8, 8192]", n0);
+            return FGR_E_INVALID;
+        }
+        o.cp = 2 * M_PI * eps / (G.h[0] * std::ldexp(1.0, (int)l2) * std::sqrt(eps));
+    }
+    if (o.flags & FGR_FLAG_FFT_GRID) {
+        for (int l = 0; l < d; ++l) {
+            const double n = 2 * M_PI * eps / (G.h[l] * o.cp * std::sqrt(eps));
+            const double l2 = std::round(std::log2(n));
+            if (!(l2 >= 3 && l2 <= 13) || std::fabs(n - std::ldexp(1.0, (int)l2)) > 1e-9 * n) {
+                set_error("fft grid stage: dimension %d has 2 pi eps / (h dp) = %.12g, not a power of two in "
+                          "[8, 8192] (use a commensurate grid or FGR_FLAG_SNAP_CP)", l, n);
+                return FGR_E_INVALID;
+            }
+            fft_logn[l] = (int)l2;
+        }
+    }
     return guarded([&]() -> fgr_status {
         std::shared_ptr<Lsa> L = shared_lsa(o.cq, o.cp, o.nq, o.np, o.rcond);
         if (!L) {
@@ -565,6 +588,7 @@ fgr_status fgr_create(int32_t d, const fgr_grid *grid, double eps, const fgr_opt
         c->d = d;
         c->grid = G;
         c->opt = o;
+        for (int l = 0; l < kMaxDim; ++l) c->fft_logn[l] = fft_logn[l];
         c->lsa = *L;
         Mesh &M = c->mesh;
         M.eps = eps;
@@ -857,8 +881,10 @@ struct fgr_fggc_plan {
     FggcBuffers buf;
     int *bnd = nullptr;       // device: the packets' node bounds of the last call
     int *overflow = nullptr;  // device: set when they left the box
+    size_t bin_bytes = 0;     // binning buffers (d >= 2, FP32)
     void release() {
-        void *ptrs[] = {buf.W, buf.buf1, buf.buf2, buf.flags, buf.brange, buf.tables, bnd, overflow};
+        void *ptrs[] = {buf.W,   buf.buf1, buf.buf2, buf.flags,   buf.brange, buf.tables,
+                        buf.bin, buf.fft,  buf.twiddle, bnd, overflow};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         buf = FggcBuffers{};
@@ -873,7 +899,8 @@ size_t plan_device_bytes(const fgr_fggc_plan *pl) {
     size_t n = 64;  // bounds and overflow flag
     if (!b.empty)
         n += eb * (size_t)b.cells + (pl->d > 1 ? 2 * eb * (size_t)b.maxbuf : 0) + (size_t)b.rows0 +
-             sizeof(int2) * (size_t)b.max_lines + 8 * (size_t)b.table_entries;
+             sizeof(int2) * (size_t)b.max_lines + 8 * (size_t)b.table_entries + pl->bin_bytes +
+             (b.fft_elems > 0 ? eb * ((size_t)b.fft_elems + 4096) : 0);
     return n;
 }
 }  // namespace fgr
@@ -883,7 +910,8 @@ namespace {
 bool plan_matches(const fgr_ctx *ctx, const fgr_fggc_plan *pl) {
     if (ctx->d != pl->d || ctx->opt.precision != pl->precision || ctx->device != pl->device) return false;
     if (ctx->mesh.eps != pl->mesh.eps || ctx->mesh.dq != pl->mesh.dq || ctx->mesh.dp != pl->mesh.dp ||
-        ctx->mesh.rs != pl->mesh.rs || ctx->opt.nq != pl->opt.nq || ctx->opt.np != pl->opt.np)
+        ctx->mesh.rs != pl->mesh.rs || ctx->opt.nq != pl->opt.nq || ctx->opt.np != pl->opt.np ||
+        (ctx->opt.flags & FGR_FLAG_FFT_GRID) != (pl->opt.flags & FGR_FLAG_FFT_GRID))
         return false;
     for (int l = 0; l < ctx->d; ++l)
         if (ctx->grid.n[l] != pl->grid.n[l] || ctx->grid.lo[l] != pl->grid.lo[l] || ctx->grid.h[l] != pl->grid.h[l])
@@ -949,6 +977,14 @@ fgr_status fgr_fggc_plan_create(fgr_ctx *ctx, const fgr_packets *pk, int32_t mar
             if (e == cudaSuccess) e = cudaMalloc((void **)&pl->buf.flags, (size_t)b.rows0);
             if (e == cudaSuccess) e = cudaMalloc((void **)&pl->buf.brange, sizeof(int2) * (size_t)b.max_lines);
             if (e == cudaSuccess) e = cudaMalloc(&pl->buf.tables, 8 * (size_t)b.table_entries);
+            if (e == cudaSuccess && b.fft_elems > 0) e = cudaMalloc(&pl->buf.fft, eb * (size_t)b.fft_elems);
+            if (e == cudaSuccess && b.fft_elems > 0) e = cudaMalloc(&pl->buf.twiddle, eb * 4096);
+            BinBox bb;
+            if (e == cudaSuccess && ctx->opt.precision == FGR_FP32 && make_bin_box(b, ctx->d, &bb)) {
+                pl->bin_bytes = bin_buffer_bytes(pk->m, bb);
+                e = cudaMalloc(&pl->buf.bin, pl->bin_bytes);
+                pl->buf.bin_m = pk->m;
+            }
             if (e != cudaSuccess) return fail(e);
         }
         *out = pl.release();

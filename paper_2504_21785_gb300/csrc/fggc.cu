@@ -180,6 +180,8 @@ __global__ void pass_tables_kernel(PassParams pp, int tp, int64_t tiles, PassTab
     }
 }
 
+#include "fggc_fft.cuh"
+
 template <bool FP64, int MAXBAND, int TP>
 __global__ void __launch_bounds__(TP) grid_pass_kernel(const void *__restrict__ in_v,
                                                                  void *__restrict__ out_v, PassParams pp,
@@ -432,6 +434,21 @@ __global__ void brange_short_kernel(const C2 *__restrict__ in, int64_t lines, in
     out[line] = make_int2(lo, hi);
 }
 
+// Node-point terms of one pass (timing only): over the (row, a) lines, the
+// occupied b-range times the grid points in node a's window, summed into *out.
+__global__ void pass_terms_kernel(const int2 *__restrict__ brange, int64_t lines, int A,
+                                  const int2 *__restrict__ win, unsigned long long *__restrict__ out) {
+    unsigned long long t = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < lines;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int2 r = brange[i], w = win[i % A];
+        if (r.y >= r.x && w.y >= w.x) t += (unsigned long long)(r.y - r.x + 1) * (unsigned long long)(w.y - w.x + 1);
+    }
+    t = __reduce_add_sync(0xffffffffu, (unsigned)(t & 0xffffffffu)) +
+        ((unsigned long long)__reduce_add_sync(0xffffffffu, (unsigned)(t >> 32)) << 32);
+    if ((threadIdx.x & 31) == 0 && t) atomicAdd(out, t);
+}
+
 template <bool FP64>
 fgr_status launch_brange(const void *in, int64_t rows, int A, int B, int2 *out, cudaStream_t st) {
     const int64_t lines = rows * (int64_t)A;
@@ -460,7 +477,7 @@ inline int64_t pass_table_entries(int64_t A, int64_t N) { return A + N + N / 32 
 template <bool FP64>
 fgr_status launch_pass(const void *in, void *out, const PassParams &pp, const uint8_t *flags,
                        const int2 *brange, int64_t target_ctas, int tile_pref, void *tables,
-                       cudaStream_t st) {
+                       cudaStream_t st, StageMarks *before_pass = nullptr) {
     if (pp.rows == 0 || pp.N == 0) return FGR_OK;
     if (pp.rows > INT_MAX) {
         set_error("fggc: too many rows in a grid pass");
@@ -492,6 +509,7 @@ fgr_status launch_pass(const void *in, void *out, const PassParams &pp, const ui
         const int64_t n = std::max<int64_t>(std::max<int64_t>(pp.A, pp.N), mtiles);
         pass_tables_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pp, tp, mtiles, tab);
     }
+    if (before_pass) before_pass->binned();
     dim3 grid((unsigned)pp.rows, (unsigned)mtiles, (unsigned)splits);
 #define FGR_PASS(MB, TPV) grid_pass_kernel<FP64, MB, TPV><<<grid, TPV, 0, st>>>(in, out, pp, flags, brange, tab)
 #define FGR_PASS_TP(TPV)                                                                                    \
@@ -509,6 +527,47 @@ fgr_status launch_pass(const void *in, void *out, const PassParams &pp, const ui
     }
 #undef FGR_PASS_TP
 #undef FGR_PASS
+    FGR_CUDA_TRY(cudaGetLastError());
+    return FGR_OK;
+}
+
+// The grid pass of a commensurate dimension (N = 2^logn): pass tables, DFT
+// twiddles, one inverse DFT per (row, a) line into F, the banded contraction.
+template <bool FP64>
+fgr_status launch_fft_pass(const void *in, void *out, const PassParams &pp, const uint8_t *flags,
+                           const int2 *brange, int logn, void *F, void *twiddle, void *tables, cudaStream_t st,
+                           StageMarks *before_pass) {
+    using C2 = typename std::conditional<FP64, double2, float2>::type;
+    if (pp.rows == 0 || pp.N == 0) return FGR_OK;
+    if (pp.rows > INT_MAX || pp.rows * (int64_t)pp.A > INT_MAX) {
+        set_error("fggc: too many lines in a DFT grid pass");
+        return FGR_E_CAPACITY;
+    }
+    constexpr int tp = 128;
+    const int64_t mtiles = (pp.N + tp - 1) / tp;
+    if (mtiles > 65535) {
+        set_error("fggc: %lld points per grid dimension; at most %d supported", (long long)pp.N, 65535 * tp);
+        return FGR_E_INVALID;
+    }
+    const int N = 1 << logn;
+    PassTables tab;
+    tab.win = reinterpret_cast<int2 *>(tables);
+    tab.ph = reinterpret_cast<float2 *>(tab.win + pp.A);
+    tab.band = reinterpret_cast<int2 *>(tab.ph + pp.N);
+    {
+        const int64_t n = std::max<int64_t>(std::max<int64_t>(pp.A, pp.N), mtiles);
+        pass_tables_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pp, tp, mtiles, tab);
+    }
+    fft_twiddle_kernel<C2><<<(unsigned)((N / 2 + 255) / 256), 256, 0, st>>>(N, (C2 *)twiddle);
+    if (before_pass) before_pass->binned();
+    const size_t smem = sizeof(C2) * (size_t)N;
+    if (smem > 48 * 1024)
+        FGR_CUDA_TRY(cudaFuncSetAttribute(dft_lines_kernel<FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+    const double th = pp.phi_scale * pp.lo;  // dp lo / (2 pi eps), turns per unit b
+    dft_lines_kernel<FP64><<<(unsigned)(pp.rows * pp.A), 256, smem, st>>>(in, F, pp.rows, pp.A, pp.B, pp.bmin, th,
+                                                                          logn, brange, flags, twiddle);
+    band_fft_kernel<FP64><<<dim3((unsigned)pp.rows, (unsigned)mtiles), tp, 0, st>>>(F, out, pp, logn, tab);
     FGR_CUDA_TRY(cudaGetLastError());
     return FGR_OK;
 }
@@ -660,7 +719,80 @@ fgr_status make_box(const fgr_ctx *ctx, const int *hb, int margin, FggcBox *box)
     }
     if (D == 1) x.maxbuf = 0;
     for (int l = 0; l < D; ++l) x.table_entries = std::max(x.table_entries, pass_table_entries(c.A[l], G.n[l]));
+    // DFT grid stage: one N-point line per (row, a) of each pass
+    prodN = 1;
+    for (int l = D - 1; l >= 0; --l) {
+        int64_t pre = 1;
+        for (int j = 0; j < l; ++j) pre *= (int64_t)c.A[j] * c.B[j];
+        if (ctx->fft_logn[l] > 0) x.fft_elems = std::max(x.fft_elems, pre * prodN * c.A[l] << ctx->fft_logn[l]);
+        prodN *= G.n[l];
+    }
     return FGR_OK;
+}
+
+bool make_bin_box(const FggcBox &box, int d, BinBox *bb) {
+    if (d < 2 || box.empty) return false;
+    const Common &c = box.c;
+    BinBox x;
+    x.dqmin = x.dpmin = INT_MAX;
+    x.dqmax = x.dpmax = INT_MIN;
+    for (int k = 0; k < c.n1; ++k) {
+        x.dqmin = std::min(x.dqmin, c.dq[k]);
+        x.dqmax = std::max(x.dqmax, c.dq[k]);
+        x.dpmin = std::min(x.dpmin, c.dp[k]);
+        x.dpmax = std::max(x.dpmax, c.dp[k]);
+    }
+    // an outer anchor a0 has a node inside [amin, amin + A) for a0 in
+    // [amin - dqmax, amin + A - 1 - dqmin] (likewise b0)
+    int64_t K = 1;
+    for (int l = 0; l < d - 1; ++l) {
+        x.ka_lo[l] = c.amin[l] - x.dqmax;
+        x.KA[l] = c.A[l] + x.dqmax - x.dqmin;
+        x.kb_lo[l] = c.bmin[l] - x.dpmax;
+        x.KB[l] = c.B[l] + x.dpmax - x.dpmin;
+        K *= (int64_t)x.KA[l] * x.KB[l];
+        if (K > kMaxBinKeys) return false;
+    }
+    x.K = K;
+    *bb = x;
+    return true;
+}
+
+namespace {
+inline size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+inline int64_t bin_max_items(int64_t m) { return m / 16 + m / 256 + 1; }
+}  // namespace
+
+size_t bin_buffer_bytes(int64_t m, const BinBox &bb) {
+    const int64_t K = bb.K;
+    return 3 * align256(sizeof(int) * (size_t)m) + align256(sizeof(int) * (size_t)K) +
+           align256(sizeof(int2) * (size_t)(K + 1)) + align256(sizeof(int2) * (size_t)((K + 1023) / 1024)) +
+           align256(sizeof(int4) * (size_t)bin_max_items(m)) + align256(sizeof(int) * 4);
+}
+
+void bin_buffers_at(void *block, int64_t m, const BinBox &bb, BinBuffers *out) {
+    char *p = (char *)block;
+    const int64_t K = bb.K;
+    auto take = [&](size_t n) {
+        char *r = p;
+        p += align256(n);
+        return r;
+    };
+    out->key = (int *)take(sizeof(int) * (size_t)m);
+    out->sorted = (int *)take(sizeof(int) * (size_t)m);
+    out->loose = (int *)take(sizeof(int) * (size_t)m);
+    out->count = (int *)take(sizeof(int) * (size_t)K);
+    out->off = (int2 *)take(sizeof(int2) * (size_t)(K + 1));
+    out->bsum = (int2 *)take(sizeof(int2) * (size_t)((K + 1023) / 1024));
+    out->items = (int4 *)take(sizeof(int4) * (size_t)bin_max_items(m));
+    out->ctr = (int *)take(sizeof(int) * 4);
+}
+
+fgr_status launch_binned_scatter(int d, int n1, const BinLaunch &L, cudaStream_t st, const PacketsDev &pk,
+                                 const Params32 &P, void *W, uint8_t *flags, StageMarks *marks) {
+    if (pk.m == 0) return FGR_OK;
+    return d == 2 ? launch_binned_d2(n1, L, st, pk, P, W, flags, marks)
+                  : launch_binned_d3(n1, L, st, pk, P, W, flags, marks);
 }
 
 namespace {
@@ -698,7 +830,20 @@ fgr_status enqueue_fggc(fgr_ctx *ctx, const PacketsDev &pk, const FggcBox &box, 
                     P.cre[(k * kCheb + i) * kCheb + jj] = L.cheb_re[k][i][jj];
                     P.cim[(k * kCheb + i) * kCheb + jj] = L.cheb_im[k][i][jj];
                 }
-        fgr_status r = launch_coeff_scatter(D, L.n1, st, pk, nullptr, &P, b.W, b.flags);
+        BinLaunch bl;
+        const bool binned = D >= 2 && b.bin && b.bin_m >= pk.m && pk.m > 0 && (L.n1 == 4 || L.n1 == 8) &&
+                            make_bin_box(box, D, &bl.box);
+        fgr_status r;
+        if (binned) {
+            bin_buffers_at(b.bin, pk.m, bl.box, &bl.buf);
+            bl.num_sms = ctx->num_sms;
+            bl.min_count = kBinMinCount;
+            StageMarks marks{timer, &ctx->timing.last.coeff_ms};
+            r = launch_binned_scatter(D, L.n1, bl, st, pk, P, b.W, b.flags, &marks);
+            *launches += 8;  // key, 3 scan, place, items, binned, loose
+        } else {
+            r = launch_coeff_scatter(D, L.n1, st, pk, nullptr, &P, b.W, b.flags);
+        }
         if (r != FGR_OK) return r;
     }
     ++*launches;
@@ -736,12 +881,32 @@ fgr_status enqueue_fggc(fgr_ctx *ctx, const PacketsDev &pk, const FggcBox &box, 
         if (r != FGR_OK) return r;
         ++*launches;
         const int64_t target = (int64_t)ctx->num_sms * ctx->tune.pass_ctas_per_sm;
-        r = fp64 ? launch_pass<true>(cur, dst, pp, l == D - 1 ? b.flags : nullptr, b.brange, target,
-                                     ctx->tune.pass_tile, b.tables, st)
-                 : launch_pass<false>(cur, dst, pp, l == D - 1 ? b.flags : nullptr, b.brange, target,
-                                      ctx->tune.pass_tile, b.tables, st);
+        StageMarks before{timer, &ctx->timing.last.grid_ms};  // the pass kernel is timed alone
+        const uint8_t *fl = l == D - 1 ? b.flags : nullptr;
+        if (ctx->fft_logn[l] > 0 && b.fft) {
+            r = fp64 ? launch_fft_pass<true>(cur, dst, pp, fl, b.brange, ctx->fft_logn[l], b.fft, b.twiddle,
+                                             b.tables, st, &before)
+                     : launch_fft_pass<false>(cur, dst, pp, fl, b.brange, ctx->fft_logn[l], b.fft, b.twiddle,
+                                              b.tables, st, &before);
+            ++*launches;  // twiddles + DFT + contraction (tables and pass counted below)
+        } else {
+            r = fp64 ? launch_pass<true>(cur, dst, pp, fl, b.brange, target, ctx->tune.pass_tile, b.tables, st,
+                                         &before)
+                     : launch_pass<false>(cur, dst, pp, fl, b.brange, target, ctx->tune.pass_tile, b.tables, st,
+                                          &before);
+        }
         if (r != FGR_OK) return r;
         *launches += 2;  // tables + pass
+        if (timer) {
+            timer->mark(&ctx->timing.last.pass_ms);
+            if (b.terms) {
+                const int64_t lines = pp.rows * (int64_t)pp.A;
+                const unsigned blocks = (unsigned)std::max<int64_t>(
+                    1, std::min<int64_t>((lines + 255) / 256, (int64_t)ctx->num_sms * 8));
+                pass_terms_kernel<<<blocks, 256, 0, st>>>(b.brange, lines, pp.A, (const int2 *)b.tables, b.terms);
+                FGR_CUDA_TRY(cudaGetLastError());
+            }
+        }
         if (D > 1) {
             void *tdst = last ? u_dev : (dst == b.buf1 ? b.buf2 : b.buf1);
             r = fp64 ? launch_transpose<double2>(dst, tdst, pp.rows, pp.N, st)
@@ -791,10 +956,32 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
     b.brange = (int2 *)scratch.get(sizeof(int2) * (size_t)box.max_lines);
     b.tables = scratch.get(8 * (size_t)box.table_entries);
     if (!b.W || !b.flags || !b.brange || !b.tables || (D > 1 && (!b.buf1 || !b.buf2))) return FGR_E_NOMEM;
+    if (box.fft_elems > 0) {
+        b.fft = scratch.get(eb * (size_t)box.fft_elems);
+        b.twiddle = scratch.get(eb * 4096);
+        if (!b.fft || !b.twiddle) return FGR_E_NOMEM;
+    }
+    BinBox bb;
+    if (ctx->opt.precision == FGR_FP32 && make_bin_box(box, D, &bb)) {
+        b.bin = scratch.get(bin_buffer_bytes(pk.m, bb));
+        if (!b.bin) return FGR_E_NOMEM;
+        b.bin_m = pk.m;
+    }
+    if (ctx->timing.enabled) {
+        b.terms = (unsigned long long *)scratch.get(sizeof(unsigned long long));
+        if (!b.terms) return FGR_E_NOMEM;
+        FGR_CUDA_TRY(cudaMemsetAsync(b.terms, 0, sizeof(unsigned long long), st));
+    }
     r = enqueue_fggc<D>(ctx, pk, box, b, u_dev, st, &timer, &launches);
     if (r != FGR_OK) return r;
     ctx->timing.last.launches = launches;
     timer.finish();
+    if (b.terms) {
+        unsigned long long terms = 0;
+        FGR_CUDA_TRY(cudaMemcpy(&terms, b.terms, sizeof(terms), cudaMemcpyDeviceToHost));
+        ctx->timing.last.pass_terms = (int64_t)terms;
+        ctx->timing.last.grid_ms += ctx->timing.last.pass_ms;
+    }
     return FGR_OK;
 }
 
@@ -925,12 +1112,20 @@ extern "C" fgr_status fgr_reconstruct_fggc_noalloc(fgr_ctx *ctx, const fgr_packe
         return FGR_E_CUDA;
     }
     {
-        cudaPointerAttributes at;
-        if (cudaPointerGetAttributes(&at, u_out) != cudaSuccess ||
-            (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
-            cudaGetLastError();
-            set_error("noalloc: u_out must be device memory");
-            return FGR_E_INVALID;
+        // u_out and the packet arrays: device memory of this context's device
+        // (or managed memory)
+        const void *ptrs[5] = {u_out, pk->q, pk->p, pk->s, pk->a};
+        const char *names[5] = {"u_out", "q", "p", "s", "a"};
+        for (int i = 0; i < (pk->m > 0 ? 5 : 1); ++i) {
+            cudaPointerAttributes at;
+            const bool ok = cudaPointerGetAttributes(&at, ptrs[i]) == cudaSuccess &&
+                            ((at.type == cudaMemoryTypeDevice && at.device == ctx->device) ||
+                             at.type == cudaMemoryTypeManaged);
+            if (!ok) {
+                cudaGetLastError();
+                set_error("noalloc: %s must be device memory of device %d", names[i], ctx->device);
+                return FGR_E_INVALID;
+            }
         }
     }
     unsigned char *base = nullptr;

@@ -161,15 +161,13 @@ using ParamsT = typename std::conditional<FP64, Params64, Params32>::type;
 template <int D, bool FP64, int N1>
 __device__ __forceinline__ void coeff_scatter_body(const double *__restrict__ q, const double *__restrict__ p,
                                                    const double *__restrict__ s, const double *__restrict__ a,
-                                                   int64_t m, const ParamsT<FP64> &P, void *__restrict__ W_v,
-                                                   uint8_t *__restrict__ row_flag) {
+                                                   int64_t m, int64_t j, const ParamsT<FP64> &P,
+                                                   void *__restrict__ W_v, uint8_t *__restrict__ row_flag) {
     using Real = typename std::conditional<FP64, double, float>::type;
     using C2 = typename std::conditional<FP64, double2, float2>::type;
     constexpr int kT = coeff_threads<FP64, N1>();
     __shared__ C2 scoef[D > 1 ? D - 1 : 1][N1][kT];
     const int tid = threadIdx.x;
-    const int64_t j = blockIdx.x * (int64_t)kT + tid;
-    if (j >= m) return;
     const Common &c = P.c;
     const double ar = a[j], ai = a[m + j];
     if (ar == 0.0 && ai == 0.0) return;  // contributes exact zeros
@@ -267,7 +265,8 @@ __global__ void __launch_bounds__(coeff_threads<FP64, N1>()) coeff_scatter_kerne
     const double *__restrict__ q, const double *__restrict__ p, const double *__restrict__ s,
     const double *__restrict__ a, int64_t m, const __grid_constant__ ParamsT<FP64> P, void *__restrict__ W_v,
     uint8_t *__restrict__ row_flag) {
-    coeff_scatter_body<D, FP64, N1>(q, p, s, a, m, P, W_v, row_flag);
+    const int64_t j = blockIdx.x * (int64_t)coeff_threads<FP64, N1>() + threadIdx.x;
+    if (j < m) coeff_scatter_body<D, FP64, N1>(q, p, s, a, m, j, P, W_v, row_flag);
 }
 
 template <int D, bool FP64, int N1>
@@ -275,7 +274,20 @@ __global__ void __launch_bounds__(coeff_threads<FP64, N1>(), 4) coeff_scatter3_k
     const double *__restrict__ q, const double *__restrict__ p, const double *__restrict__ s,
     const double *__restrict__ a, int64_t m, const __grid_constant__ ParamsT<FP64> P, void *__restrict__ W_v,
     uint8_t *__restrict__ row_flag) {
-    coeff_scatter_body<D, FP64, N1>(q, p, s, a, m, P, W_v, row_flag);
+    const int64_t j = blockIdx.x * (int64_t)coeff_threads<FP64, N1>() + threadIdx.x;
+    if (j < m) coeff_scatter_body<D, FP64, N1>(q, p, s, a, m, j, P, W_v, row_flag);
+}
+
+// The same over the packets list[0 .. *count) (device count), grid-stride.
+template <int D, bool FP64, int N1>
+__global__ void __launch_bounds__(coeff_threads<FP64, N1>(), D == 3 ? 4 : 1) coeff_scatter_list_kernel(
+    const double *__restrict__ q, const double *__restrict__ p, const double *__restrict__ s,
+    const double *__restrict__ a, int64_t m, const __grid_constant__ ParamsT<FP64> P, void *__restrict__ W_v,
+    uint8_t *__restrict__ row_flag, const int *__restrict__ list, const int *__restrict__ count) {
+    constexpr int kT = coeff_threads<FP64, N1>();
+    const int n = *count;
+    for (int64_t t = blockIdx.x * (int64_t)kT + threadIdx.x; t < n; t += (int64_t)gridDim.x * kT)
+        coeff_scatter_body<D, FP64, N1>(q, p, s, a, m, list[t], P, W_v, row_flag);
 }
 
 template <int D, bool FP64, int N1>

@@ -38,6 +38,7 @@ struct FggcBox {
     int64_t maxbuf = 0;     // elements of each pass buffer (d > 1)
     int64_t max_lines = 0;  // (row, a) lines of the b-range scan
     int64_t table_entries = 0;  // 8-byte entries of the largest pass table
+    int64_t fft_elems = 0;      // complex elements of the DFT lines of the largest pass (0: no DFT stage)
     bool empty = true;      // no packet reaches the grid
 };
 
@@ -46,6 +47,60 @@ struct FggcBuffers {
     uint8_t *flags = nullptr;
     int2 *brange = nullptr;
     void *tables = nullptr;  // per-pass tables (node windows, point phases, tile bands)
+    void *bin = nullptr;     // binning buffers of the d >= 2 FP32 scatter (NULL: per-packet scatter)
+    int64_t bin_m = 0;       // packets the binning buffers hold
+    unsigned long long *terms = nullptr;  // node-point terms of the passes (timed calls only)
+    void *fft = nullptr;      // DFT lines of the commensurate grid stage (box.fft_elems complex)
+    void *twiddle = nullptr;  // e^{2 pi i j / N}, j < N / 2 <= 4096 (complex)
+};
+
+// Binning of the d >= 2 scatter (fggc_bin.cuh): key box of the outer anchor
+// cells (a0, b0) of dimensions 0..d-2 whose neighbours can reach the node box,
+// key = row-major index over (a0_0, b0_0, a0_1, b0_1).
+struct BinBox {
+    int ka_lo[2] = {}, KA[2] = {1, 1}, kb_lo[2] = {}, KB[2] = {1, 1};
+    int dqmin = 0, dqmax = 0, dpmin = 0, dpmax = 0;  // neighbour shift ranges
+    int64_t K = 0;                                   // keys
+};
+
+// Device buffers of the binning (m packets, K keys).
+struct BinBuffers {
+    int *key = nullptr;     // [m] key of each packet (-1: adds nothing)
+    int *count = nullptr;   // [K] packets per key, then the placement cursor
+    int2 *off = nullptr;    // [K + 1] (first sorted packet, first item) per key; totals at K
+    int2 *bsum = nullptr;   // [ceil(K / 1024)] block totals of the scan
+    int *sorted = nullptr;  // [m] binned packets by key
+    int *loose = nullptr;   // [m] packets of small cells
+    int4 *items = nullptr;  // [max items] (key, first sorted packet, packets)
+    int *ctr = nullptr;     // [4] loose count, work counter
+};
+
+struct BinLaunch {
+    BinBox box;
+    BinBuffers buf;
+    int min_count = 32;  // smallest binned cell
+    int num_sms = 1;
+};
+
+// Largest key box of the binned scatter; larger boxes use the per-packet kernel.
+constexpr int64_t kMaxBinKeys = int64_t(1) << 26;
+// Smallest binned cell (packets); smaller cells take the per-packet kernel.
+constexpr int kBinMinCount = 32;
+
+// Key box of a node box (false when the binned scatter does not apply).
+bool make_bin_box(const FggcBox &box, int d, BinBox *bb);
+// Bytes of the binning buffers for m packets and key box bb.
+size_t bin_buffer_bytes(int64_t m, const BinBox &bb);
+// Carves the binning buffers out of one device block of bin_buffer_bytes.
+void bin_buffers_at(void *block, int64_t m, const BinBox &bb, BinBuffers *out);
+
+// Stage marks of the timed FGGC call (the binning ends where binned() is called).
+struct StageMarks {
+    StageTimer *timer = nullptr;
+    double *slot = nullptr;
+    void binned() {
+        if (timer) timer->mark(slot);
+    }
 };
 
 // Box from the packets' node bounds hb[12] (per dimension: a min, a max, b min,
@@ -71,5 +126,13 @@ fgr_status launch_coeff_scatter_d2(int n1, cudaStream_t st, const PacketsDev &pk
                                    const Params32 *p32, void *W, uint8_t *flags);
 fgr_status launch_coeff_scatter_d3(int n1, cudaStream_t st, const PacketsDev &pk, const Params64 *p64,
                                    const Params32 *p32, void *W, uint8_t *flags);
+// The binned scatter (FP32, d = 2 or 3, n1 = 4 or 8): binning kernels, then
+// the binned kernel and the per-packet kernel over the loose list.
+fgr_status launch_binned_scatter(int d, int n1, const BinLaunch &L, cudaStream_t st, const PacketsDev &pk,
+                                 const Params32 &P, void *W, uint8_t *flags, StageMarks *marks);
+fgr_status launch_binned_d2(int n1, const BinLaunch &L, cudaStream_t st, const PacketsDev &pk, const Params32 &P,
+                            void *W, uint8_t *flags, StageMarks *marks);
+fgr_status launch_binned_d3(int n1, const BinLaunch &L, cudaStream_t st, const PacketsDev &pk, const Params32 &P,
+                            void *W, uint8_t *flags, StageMarks *marks);
 
 }  // namespace fgr

@@ -77,6 +77,7 @@ struct fgr_ctx {
     cudaMemPool_t pool = nullptr;
     fgr::Timing timing;
     fgr::Tuning tune;
+    int fft_logn[fgr::kMaxDim] = {0, 0, 0};  // log2 N of the DFT grid stage per dimension (0: direct stage)
     int64_t *host_pinned = nullptr;  // small pinned buffer for device->host sizes
 };
 
@@ -161,8 +162,8 @@ class StageTimer {
   private:
     fgr_ctx *ctx_;
     cudaStream_t s_;
-    cudaEvent_t ev_[12] = {};
-    double *slot_[12] = {};
+    cudaEvent_t ev_[24] = {};
+    double *slot_[24] = {};
     int n_ = 0;
 };
 

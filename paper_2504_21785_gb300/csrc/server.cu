@@ -87,6 +87,7 @@ struct PlanEntry {
     fgr_fggc_plan *plan = nullptr;
     size_t bytes = 0;
     bool busy = false;
+    uint64_t last_used = 0;  // plan clock at the last acquisition
 };
 
 }  // namespace
@@ -104,6 +105,8 @@ struct fgr_server {
     std::map<uint64_t, PacketSet> sets;
     std::map<PlanKey, PlanEntry> plans;
     size_t resident = 0, reserved = 0;
+    size_t plan_resident = 0;  // the part of resident held by cached plans (they can be freed)
+    uint64_t plan_clock = 0;
     int running = 0;
     uint64_t next_ticket = 1, next_set = 1;
     bool stop = false;
@@ -189,6 +192,7 @@ fgr_fggc_plan *acquire_plan(fgr_server *S, const Job &job, fgr_ctx *ctx, const f
         if (it != S->plans.end()) {
             if (it->second.busy) return nullptr;
             it->second.busy = true;
+            it->second.last_used = ++S->plan_clock;
             return it->second.plan;
         }
     }
@@ -200,8 +204,9 @@ fgr_fggc_plan *acquire_plan(fgr_server *S, const Job &job, fgr_ctx *ctx, const f
         auto set = S->sets.find(job.req.set_id);
         const bool fits = S->resident + S->reserved + bytes <= S->budget;
         if (fits && set != S->sets.end() && !set->second.released && !S->plans.count(k)) {
-            S->plans[k] = PlanEntry{plan, bytes, true};
+            S->plans[k] = PlanEntry{plan, bytes, true, ++S->plan_clock};
             S->resident += bytes;
+            S->plan_resident += bytes;
             return plan;
         }
     }
@@ -348,16 +353,69 @@ void worker_main(fgr_server *S) {
     cudaStreamDestroy(stream);
 }
 
+bool has_idle_plan(const fgr_server *S) {
+    for (const auto &kv : S->plans)
+        if (!kv.second.busy) return true;
+    return false;
+}
+
+// Takes idle plans out of the cache, least recently used first, until need
+// more bytes fit the budget or no idle plan is left; returns them for
+// destruction outside the lock.
+std::vector<fgr_fggc_plan *> evict_idle_plans(fgr_server *S, size_t need) {
+    std::vector<fgr_fggc_plan *> out;
+    while (S->resident + S->reserved + need > S->budget) {
+        auto lru = S->plans.end();
+        for (auto it = S->plans.begin(); it != S->plans.end(); ++it)
+            if (!it->second.busy && (lru == S->plans.end() || it->second.last_used < lru->second.last_used)) lru = it;
+        if (lru == S->plans.end()) break;
+        S->resident -= lru->second.bytes;
+        S->plan_resident -= lru->second.bytes;
+        out.push_back(lru->second.plan);
+        S->plans.erase(lru);
+    }
+    return out;
+}
+
+// Completes the queue's head with FGR_E_CAPACITY: it does not fit the budget
+// even with nothing else admitted and no cached plan left.
+void fail_head_capacity(fgr_server *S) {
+    auto j = S->queue.front();
+    S->queue.pop_front();
+    const double t = now_ms();
+    j->res.status = FGR_E_CAPACITY;
+    j->res.t_start_ms = j->res.t_done_ms = t;
+    j->st = St::Done;
+    S->sets[j->req.set_id].users -= 1;
+    S->cv_done.notify_all();
+}
+
 void scheduler_main(fgr_server *S) {
     std::unique_lock<std::mutex> lk(S->mu);
     for (;;) {
         S->cv_sched.wait(lk, [&] {
             if (S->stop) return true;
-            if (S->queue.empty()) return false;
+            if (S->queue.empty() || S->running >= S->max_inflight) return false;
             const auto &j = S->queue.front();
-            return S->running < S->max_inflight && S->resident + S->reserved + j->footprint <= S->budget;
+            if (S->resident + S->reserved + j->footprint <= S->budget) return true;
+            // the head does not fit: free idle plans, or fail it when nothing
+            // that could free memory is in flight
+            return has_idle_plan(S) || (S->running == 0 && S->reserved == 0);
         });
         if (S->stop) break;
+        if (S->resident + S->reserved + S->queue.front()->footprint > S->budget) {
+            std::vector<fgr_fggc_plan *> drop = evict_idle_plans(S, S->queue.front()->footprint);
+            if (!drop.empty()) {
+                lk.unlock();
+                for (fgr_fggc_plan *pl : drop) fgr_fggc_plan_destroy(pl);
+                lk.lock();
+                continue;  // look again: the queue or the memory may have changed
+            }
+            if (S->running == 0 && S->reserved == 0) {
+                fail_head_capacity(S);
+                continue;
+            }
+        }
         // admit in arrival order while slots and memory allow; a batchable
         // request takes the later compatible ones with it
         while (!S->queue.empty() && S->running < S->max_inflight) {
@@ -473,12 +531,18 @@ fgr_status fgr_register_packets(fgr_server *S, int32_t d, const fgr_packets *pk,
     const int64_t m = pk->m;
     const size_t bytes = sizeof(double) * (size_t)std::max<int64_t>(m, 1) * (2 * d + 3);
     {
-        std::lock_guard<std::mutex> lk(S->mu);
-        if (S->resident + S->reserved + bytes > S->budget) {
-            set_error("register: %zu bytes exceed the remaining budget", bytes);
-            return FGR_E_CAPACITY;
+        std::vector<fgr_fggc_plan *> drop;
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            drop = evict_idle_plans(S, bytes);  // cached plans give way to a new set
+            if (S->resident + S->reserved + bytes > S->budget) {
+                set_error("register: %zu bytes exceed the remaining budget", bytes);
+                for (fgr_fggc_plan *pl : drop) fgr_fggc_plan_destroy(pl);
+                return FGR_E_CAPACITY;
+            }
+            S->resident += bytes;  // reserve now, release on failure below
         }
-        S->resident += bytes;  // reserve now, release on failure below
+        for (fgr_fggc_plan *pl : drop) fgr_fggc_plan_destroy(pl);
     }
     cudaSetDevice(S->device);
     double *buf = nullptr;
@@ -526,6 +590,7 @@ fgr_status fgr_release_packets(fgr_server *S, uint64_t set_id) {
         if (pl->first.set_id == set_id) {
             fgr_fggc_plan_destroy(pl->second.plan);
             S->resident -= pl->second.bytes;
+            S->plan_resident -= pl->second.bytes;
             pl = S->plans.erase(pl);
         } else {
             ++pl;
@@ -566,9 +631,10 @@ fgr_status fgr_submit(fgr_server *S, const fgr_request *req, uint64_t *ticket) {
         return FGR_E_INVALID;
     }
     j->footprint = footprint(j->req, it->second);
-    if (S->resident + j->footprint > S->budget) {
-        set_error("submit: request needs %zu bytes; budget %zu with %zu resident", j->footprint,
-                  S->budget, S->resident);
+    // cached plans do not count: the scheduler frees them for requests that need their memory
+    if (S->resident - S->plan_resident + j->footprint > S->budget) {
+        set_error("submit: request needs %zu bytes; budget %zu with %zu resident in packet sets", j->footprint,
+                  S->budget, S->resident - S->plan_resident);
         return FGR_E_CAPACITY;
     }
     it->second.users += 1;

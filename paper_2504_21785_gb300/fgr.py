@@ -72,7 +72,8 @@ class fgr_stats(ctypes.Structure):
                 ("scatter_ms", ctypes.c_double), ("grid_ms", ctypes.c_double),
                 ("direct_ms", ctypes.c_double), ("propagate_ms", ctypes.c_double),
                 ("total_ms", ctypes.c_double), ("launches", ctypes.c_int64),
-                ("pairs", ctypes.c_int64), ("nodes", ctypes.c_int64)]
+                ("pairs", ctypes.c_int64), ("nodes", ctypes.c_int64),
+                ("pass_ms", ctypes.c_double), ("pass_terms", ctypes.c_int64)]
 
 
 class fgr_request(ctypes.Structure):
@@ -220,9 +221,13 @@ def fgr_default_options() -> fgr_options:
     return o
 
 
+FGR_FLAG_FFT_GRID = 1
+FGR_FLAG_SNAP_CP = 2
+
+
 def make_options(precision=FGR_FP64, cq=0.5, cp=math.pi / 8, nq=4, np_=2, window_r=0.0,
-                 rcond=1e-14) -> fgr_options:
-    return fgr_options(cq, cp, nq, np_, window_r, rcond, precision, 0)
+                 rcond=1e-14, flags=0) -> fgr_options:
+    return fgr_options(cq, cp, nq, np_, window_r, rcond, precision, int(flags))
 
 
 def make_potential(kind="free", c0=0.0, amp=0.0, k=1.0, omega=1.0) -> fgr_potential:

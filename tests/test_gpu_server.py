@@ -250,3 +250,43 @@ def test_fggc_requests_through_cached_plans_and_release(fgr):
         assert np.linalg.norm(u.cpu().numpy() - ref) <= 1e-6 * np.linalg.norm(ref)
     finally:
         fgr.fgr_server_destroy(srv)
+
+
+def test_cached_plans_give_way_to_a_request_that_needs_their_memory(fgr):
+    # A small budget; FGGC requests on distinct grids each leave a cached plan
+    # (resident memory); then a request whose footprint fitted only before
+    # those plans existed.  The scheduler frees idle plans, least recently
+    # used first, instead of waiting for memory that nothing would release.
+    import torch
+    from . import _gpu
+    m = 4000
+    pk = random_packets(82, 1, m, q_range=(-2.5, 2.5), p_range=(-2, 2), s_range=(-1, 1))
+    n_big = 1 << 20
+    set_bytes = m * 5 * 8
+    big_footprint = m * 112 + (n_big // 64 + 1) * 16 + n_big * 8   # direct-sum footprint rule of the server
+    srv = fgr.fgr_server_create(set_bytes + big_footprint + (3 << 19), 1)
+    try:
+        sid = fgr.fgr_register_packets(srv, 1, fgr.make_packets(*[np.ascontiguousarray(pk[k]) for k in "qpsa"]))
+        opt = fgr.make_options(precision=fgr.FGR_FP32)
+        grids = [1024 + 96 * i for i in range(12)]
+        outs = []
+        for n in grids:   # one at a time: every request creates and keeps its plan
+            u = torch.zeros(n, dtype=torch.complex64, device="cuda")
+            r = fgr.fgr_poll(srv, fgr.fgr_submit(srv, fgr.make_request(1, _grid(1, n), 1 / 512, opt, sid, u)),
+                             60000)
+            assert r.status == 0
+            outs.append(u)
+        ub = torch.zeros(n_big, dtype=torch.complex64, device="cuda")
+        t = fgr.fgr_submit(srv, fgr.make_request(0, _grid(1, n_big), 1 / 512, opt, sid, ub))
+        r = fgr.fgr_poll(srv, t, 60000)
+        assert r.status == 0
+        ref = _gpu.reconstruct("direct", pk, _grid(1, n_big), 1 / 512, opt)
+        assert np.linalg.norm(ub.cpu().numpy() - ref) <= 1e-6 * np.linalg.norm(ref)
+        # the evicted plans are rebuilt on demand
+        u = torch.zeros(grids[0], dtype=torch.complex64, device="cuda")
+        r = fgr.fgr_poll(srv, fgr.fgr_submit(srv, fgr.make_request(1, _grid(1, grids[0]), 1 / 512, opt, sid, u)),
+                         60000)
+        assert r.status == 0
+        assert np.linalg.norm(u.cpu().numpy() - outs[0].cpu().numpy()) <= 1e-6 * np.linalg.norm(outs[0].cpu().numpy())
+    finally:
+        fgr.fgr_server_destroy(srv)

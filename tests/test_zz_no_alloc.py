@@ -73,3 +73,23 @@ def test_noalloc_rejects_problems_beyond_its_array(fgr):
         assert "at most" in str(e.value)
         # the allocating entry point still serves the same problem
         fgr.fgr_reconstruct_fggc(ctx.handle, fgr.make_packets(*arrs), u)
+
+
+def test_noalloc_rejects_packets_in_host_memory(fgr):
+    # packet arrays must be device memory of the context's device: a host array
+    # is refused before anything is launched
+    import torch
+    eps = 1 / 1024
+    mesh = mesh_for(1, eps)
+    grid = dict(d=1, n=[4096], lo=[-math.pi], hi=[math.pi])
+    pk = random_packets(24, 1, 100, q_range=(-1, 1), p_range=(-1, 1), mesh=mesh)
+    arrs = _device_packets(pk)
+    host_q = np.ascontiguousarray(pk["q"])
+    packets = fgr.make_packets(*arrs)
+    packets.q = host_q.ctypes.data   # q on the host, the rest on the device
+    with fgr.Context(1, grid, eps, fgr.make_options(precision=fgr.FGR_FP32)) as ctx:
+        u = torch.zeros(4096, dtype=torch.complex64, device="cuda")
+        with pytest.raises(fgr.FgrError) as e:
+            fgr.fgr.fgr_reconstruct_fggc_noalloc(ctx.handle, packets, u)
+        assert e.value.status == fgr.fgr.FGR_E_INVALID
+        assert "q must be device memory" in str(e.value)
