@@ -130,6 +130,9 @@ def rk4_nsteps(t: float, dt: float) -> int:
     return int(n) if abs(r - n) <= 1e-9 * max(n, 1.0) else int(math.ceil(r))
 
 
+# DRAM bytes (read + written) of one launch of the 3-D scatter stage on the
+# 3-D workload, from ncu (None until captured for the current kernel).
+SCATTER_TRAFFIC_BYTES = {}
 # Algorithmic FP64 work of one RK4 packet-step per dimension: 4 stages of
 # about 40 FLOPs each.
 RK4_ALG_FLOPS_PER_PACKET_STEP = 160
@@ -327,20 +330,25 @@ def reconstruction_roofline(d, M, nodes, kern, ms_step):
     per-stage CUDA events of the timed steps (kern: mean per stage).
 
     Scatter (K3+K4): unit = one contribution A e^{iS/eps} c_k of a packet to a
-    node (eq. 2.25), M 8^d per launch (Q4P2), against the probed rate of
-    scattered 8-byte L2 reductions.  Grid passes (K5): unit = one node-point
+    node (eq. 2.25), an 8-byte reduction in L2 as the method states it, M 8^d
+    per launch (Q4P2), against the best rate at which this GB300's L2 absorbs
+    8-byte reductions (a warp on 32 consecutive cells, probed); the binned 3-D
+    kernel sums a cell's contributions in registers first, so it issues fewer
+    reductions than contributions.  Grid passes (K5): unit = one node-point
     term W[a, b] g(x_m - a dq) (a real x complex multiply-add, 4 FLOPs), counted
     on the device per launch (occupied b-range x window points over every
     (row, a) line), against the measured FP32 FMA rate."""
     contrib = M * 8 ** d
     scatter_ms, pass_ms = kern["scatter_ms"], kern["pass_ms"]
     if scatter_ms >= pass_ms:
-        out = {"kernel": "coefficient + scatter (K3+K4)", "bound": "l2",
-               "achieved": contrib / (scatter_ms * 1e-3) / 1e9, "peak": L2_RED_PEAK_GPS,
-               "unit": "G contributions/s", "traffic": None, "launch_ms": scatter_ms,
-               "units_per_launch": contrib,
-               "unit_def": "one contribution of a packet to a node (eq. 2.25), M 8^d per launch",
-               "peak_source": "float2 reductions to random addresses of a 64 MiB buffer (probe on this GB300)"}
+        out = {"kernel": "coefficient + scatter (K3+K4: binned_scatter_kernel in 3-D)", "bound": "l2",
+               "achieved": contrib / (scatter_ms * 1e-3) / 1e9, "peak": L2_RED_COALESCED_GPS,
+               "unit": "G contributions/s", "traffic": SCATTER_TRAFFIC_BYTES.get((d, M)),
+               "launch_ms": scatter_ms, "units_per_launch": contrib,
+               "unit_def": "one contribution of a packet to a node (eq. 2.25): an 8-byte L2 reduction as the "
+                           "method states it; M 8^d per launch",
+               "peak_source": "float2 reductions by warps on 32 consecutive cells of a 64 MiB buffer, probe on "
+                              "this GB300 (scattered ones: 222.8e9/s)"}
     else:
         terms = kern["pass_terms"]
         out = {"kernel": "grid_pass_kernel (K5, all passes)", "bound": "alu",
@@ -756,9 +764,9 @@ def fft_grid_bench(args, flush):
 def batch_bench(args, flush):
     """Many small reconstructions: direct sums as one fgr_reconstruct_direct call
     each on one stream, against one fgr_reconstruct_direct_batch call, eager and
-    replayed from a CUDA graph; FGGC as one fgr_reconstruct_fggc call each
-    against planned calls (fgr_reconstruct_fggc_planned), eager and replayed
-    from a CUDA graph.  64 1-D requests, grids 1024..8192 points, 2k..16k
+    replayed from a CUDA graph; FGGC as one fgr_reconstruct_fggc call each,
+    as planned calls (fgr_reconstruct_fggc_planned) and as one
+    fgr_reconstruct_fggc_batch call, eager and replayed from CUDA graphs.  64 1-D requests, grids 1024..8192 points, 2k..16k
     uniformly placed packets, eps in [1/1024, 1/256], FP32; L2 flushed before
     each timed run."""
     import numpy as np
@@ -853,10 +861,26 @@ def batch_bench(args, flush):
         fggc_planned()
         gf.capture_end()
     torch.cuda.synchronize()
+
+    def fggc_batched():
+        fgr.fgr_reconstruct_fggc_batch(ctxs, plans, pks, outs, s)
+
+    fggc_batched()
+    torch.cuda.synchronize()
+    worst_b = max(float(torch.linalg.norm(a - b) / max(float(torch.linalg.norm(b)), 1e-30))
+                  for a, b in zip(outs, ref_f))
+    gb = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        gb.capture_begin()
+        fggc_batched()
+        gb.capture_end()
+    torch.cuda.synchronize()
     with torch.cuda.stream(s):
         tf_single = timed(fggc_single)
         tf_planned = timed(fggc_planned)
         tf_graph = timed(gf.replay)
+        tf_batch = timed(fggc_batched)
+        tf_batch_graph = timed(gb.replay)
     for pl in plans:
         fgr.fgr_fggc_plan_destroy(pl)
     for c in ctxs:
@@ -865,9 +889,11 @@ def batch_bench(args, flush):
             "graph_replay_ms": t_graph, "requests_per_s_graph": len(outs) / (t_graph * 1e-3),
             "speedup_batch_vs_single": t_single / t_batch, "speedup_graph_vs_single": t_single / t_graph,
             "max_rel_l2_batch_vs_single": worst,
-            "fggc_single_calls_ms": tf_single, "fggc_planned_ms": tf_planned, "fggc_graph_replay_ms": tf_graph,
-            "fggc_requests_per_s_graph": len(outs) / (tf_graph * 1e-3),
-            "max_rel_l2_fggc_planned_vs_single": worst_f,
+            "fggc_single_calls_ms": tf_single, "fggc_planned_ms": tf_planned,
+            "fggc_planned_graph_replay_ms": tf_graph, "fggc_batch_ms": tf_batch,
+            "fggc_batch_graph_replay_ms": tf_batch_graph,
+            "fggc_requests_per_s_batch_graph": len(outs) / (tf_batch_graph * 1e-3),
+            "max_rel_l2_fggc_planned_vs_single": worst_f, "max_rel_l2_fggc_batch_vs_single": worst_b,
             "mix": "64 x 1-D, grids 1024..8192, 2k..16k packets, eps 1/1024..1/256, fp32"}
 
 

@@ -323,6 +323,24 @@ fgr_status fgr_fggc_plan_create(fgr_ctx *ctx, const fgr_packets *pk, int32_t mar
  * set, or if packets or u_out are not device memory. */
 fgr_status fgr_reconstruct_fggc_planned(fgr_ctx *ctx, fgr_fggc_plan *plan, const fgr_packets *pk, void *u_out,
                                         void *cuda_stream);
+/* Many FGGC reconstructions in one go (not in the paper: a batching and
+ * serving aid).  Request r is fgr_reconstruct_fggc_planned(ctxs[r], plans[r],
+ * pks[r], u_outs[r]): the same arithmetic on the plan's box, with packets and
+ * outputs in device memory.  Requests of one dimension run together, up to 32
+ * per launch: every stage (clearing the node arrays, node bounds and box
+ * checks, coefficients and scatter, b-range scans, pass tables, grid passes,
+ * transposes) is one launch for all of them, whose CTAs find their request by
+ * a prefix over per-request CTA counts; requests of different dimensions may
+ * be mixed (one sequence of launches per dimension).  Only stream-ordered work:
+ * no allocation and no host wait, so a batch can be captured into a CUDA
+ * graph.  Contexts with FGR_FLAG_FFT_GRID run their request alone inside the
+ * call.  Overflow flags are set per plan as for planned calls; calls that
+ * share a plan must not overlap.  FGR_E_INVALID (naming the request) if n is
+ * outside 1..64, an argument is NULL, a plan does not match its context,
+ * packets or u_out are not device memory, or a request's device, precision or
+ * neighbour strategy (cq, cp, nq, np, rcond) differs from request 0's. */
+fgr_status fgr_reconstruct_fggc_batch(int32_t n, fgr_ctx *const *ctxs, fgr_fggc_plan *const *plans,
+                                      const fgr_packets *const *pks, void *const *u_outs, void *cuda_stream);
 /* 1 if the packets of the plan's last completed call left its box (waits for
  * the device). */
 fgr_status fgr_fggc_plan_overflow(fgr_fggc_plan *plan, int32_t *overflowed);
@@ -365,7 +383,7 @@ fgr_status fgr_get_info(const fgr_ctx *ctx, fgr_info *out);
 /* Per-stage device times (milliseconds, CUDA events) of the context's last
  * reconstruct or propagate call, when timing is enabled with fgr_set_timing.
  * FGGC: prep_ms = clearing the node array, coeff_ms = binning the packets by
- * anchor cell (d >= 2, FP32), scatter_ms = the coefficient and scatter
+ * anchor cell (d = 3, FP32), scatter_ms = the coefficient and scatter
  * kernels, grid_ms = the whole grid stage (eq. 2.24), of which pass_ms is the
  * grid-pass kernels alone; pass_terms = node-point terms of the grid passes
  * (per pass, over every (row, node a) line: the occupied b-range times the
@@ -399,8 +417,9 @@ void fgr_server_destroy(fgr_server *srv);
 
 /* Largest group of waiting requests (same method, d and precision, device
  * outputs) that one worker takes at once: direct sums run as a single
- * fgr_reconstruct_direct_batch launch, FGGC reconstructions back to back with
- * one wait (default 16; 1 turns grouping off; at most 64).  Applies to
+ * fgr_reconstruct_direct_batch launch, FGGC reconstructions through their
+ * cached plans as one fgr_reconstruct_fggc_batch call, with one wait
+ * (default 16; 1 turns grouping off; at most 64).  Applies to
  * requests admitted after the call.  Not in the paper: a serving policy. */
 fgr_status fgr_server_set_max_batch(fgr_server *srv, int32_t max_batch);
 

@@ -159,3 +159,57 @@ def direct_sum(packets: dict, grid: dict, eps: float, dq: float, dp: float, R: f
         terms = A[sel] * np.exp(-g2 / (2.0 * eps)) * (np.cos(theta) + 1j * np.sin(theta))
         out[i] = np.sum(terms)
     return pref * out
+
+
+def direct_sum_tensor(axes, amps, actions, sel, grid: dict, eps: float, dq: float, dp: float, points,
+                      R: float = 8.0, phase: complex = 1.0):
+    """Eq. 2.10 at grid multi-indices ``points`` (d, K) for packets that form a
+    selection of a tensor product of per-dimension lists.
+
+    Packet j has the row-major multi-index (i_0, ..., i_{d-1}) = sel[j] and sits
+    at Q_l = axes[l][0][i_l], P_l = axes[l][1][i_l] in dimension l, with
+    amplitude phase * prod_l amps[l][i_l] and action sum_l actions[l][i_l].
+    Its term A exp(i(S + P.(x - Q))/eps - |x - Q|^2/(2 eps)), box window
+    included, is then a product over dimensions of
+        f_l(i_l, x_l) = amps[l][i_l] exp(i (actions[l][i_l] + P_l (x_l - Q_l))/eps
+                        - (x_l - Q_l)^2 / (2 eps)) [x_l in the window of Q_l],
+    so u = pref phase sum over the selected multi-indices of the product of the
+    d factors: a masked contraction over the list entries whose windows hold
+    the point (the first dimension contracted once per distinct first index of
+    the points).  Same sum as ``direct_sum`` on the expanded packets, in
+    another order.
+    """
+    d = int(grid["d"])
+    L = [int(np.asarray(q).size) for q, _ in axes]
+    mask = np.zeros(int(np.prod(L)), dtype=np.float64)
+    mask[np.asarray(sel, dtype=np.int64)] = 1.0
+    mask = mask.reshape(L[0], -1)
+    pref = prefactor(d, eps, dq, dp)
+    xs = [grid_axis(grid, l) for l in range(d)]
+    bounds = [window_bounds(axes[l][0], grid, l, eps, R) for l in range(d)]
+
+    def factor(l, m):
+        lo, hi = bounds[l]
+        inwin = np.nonzero((lo <= m) & (m <= hi))[0]
+        q = np.asarray(axes[l][0])[inwin]
+        p = np.asarray(axes[l][1])[inwin]
+        dx = xs[l][m] - q
+        theta = (np.asarray(actions[l])[inwin] + p * dx) / eps
+        f = np.asarray(amps[l])[inwin] * np.exp(-dx * dx / (2.0 * eps)) * (np.cos(theta) + 1j * np.sin(theta))
+        return inwin, f
+
+    pts = np.asarray(points, dtype=np.int64).reshape(d, -1)
+    out = np.zeros(pts.shape[1], dtype=np.complex128)
+    for m0 in np.unique(pts[0]):
+        i0, f0 = factor(0, m0)
+        # T[i_1, ..., i_{d-1}] = sum over i_0 of f_0(i_0) mask[i_0, ...]
+        T = (f0.real @ mask[i0] + 1j * (f0.imag @ mask[i0])).reshape(L[1:]) if i0.size else None
+        for k in np.nonzero(pts[0] == m0)[0]:
+            if T is None:
+                continue
+            val = T
+            for l in range(1, d):
+                il, fl = factor(l, pts[l, k])
+                val = np.tensordot(fl, val[il], axes=(0, 0)) if il.size else 0.0
+            out[k] = val
+    return pref * phase * out

@@ -10,7 +10,8 @@ from .fgr import (  # noqa: F401
     Context, FgrError, make_grid, make_options, make_packets, make_potential,
     fgr_create, fgr_destroy, fgr_propagate, fgr_decompose, fgr_fggc_multistep, fgr_decompose_tensor,
     fgr_fggc_multistep_tensor, make_axes, fgr_reconstruct_direct, fgr_reconstruct_direct_batch,
-    fgr_reconstruct_fggc, fgr_fggc_plan_create, fgr_reconstruct_fggc_planned, fgr_fggc_plan_overflow,
+    fgr_reconstruct_fggc, fgr_fggc_plan_create, fgr_reconstruct_fggc_planned, fgr_reconstruct_fggc_batch,
+    fgr_fggc_plan_overflow,
     fgr_fggc_plan_info, fgr_fggc_plan_destroy,
     fgr_get_info, fgr_set_timing, fgr_get_stats, fgr_last_error, fgr_autotune, fgr_get_tuning,
     fgr_set_tuning,

@@ -881,7 +881,7 @@ struct fgr_fggc_plan {
     FggcBuffers buf;
     int *bnd = nullptr;       // device: the packets' node bounds of the last call
     int *overflow = nullptr;  // device: set when they left the box
-    size_t bin_bytes = 0;     // binning buffers (d >= 2, FP32)
+    size_t bin_bytes = 0;     // binning buffers (d = 3, FP32)
     void release() {
         void *ptrs[] = {buf.W,   buf.buf1, buf.buf2, buf.flags,   buf.brange, buf.tables,
                         buf.bin, buf.fft,  buf.twiddle, bnd, overflow};
@@ -1019,6 +1019,69 @@ fgr_status fgr_reconstruct_fggc_planned(fgr_ctx *ctx, fgr_fggc_plan *plan, const
         const PacketsDev dev{pk->m, pk->q, pk->p, pk->s, pk->a};
         fgr_status r = run_fggc_planned(ctx, dev, plan->box, plan->buf, plan->bnd, plan->overflow, u_out, st);
         if (r != FGR_OK) return r;
+        FGR_CUDA_TRY(cudaGetLastError());
+        if (!stream) FGR_CUDA_TRY(cudaStreamSynchronize(st));
+        return FGR_OK;
+    });
+}
+
+fgr_status fgr_reconstruct_fggc_batch(int32_t n, fgr_ctx *const *ctxs, fgr_fggc_plan *const *plans,
+                                      const fgr_packets *const *pks, void *const *u_outs, void *stream) {
+    clear_error();
+    if (n < 1 || n > 64 || !ctxs || !plans || !pks || !u_outs) {
+        set_error("fggc batch: need 1 <= n <= 64 and the arrays ctxs, plans, pks, u_outs");
+        return FGR_E_INVALID;
+    }
+    for (int r = 0; r < n; ++r) {
+        fgr_ctx *ctx = ctxs[r];
+        if (!ctx || !plans[r] || !u_outs[r] || !pks[r]) {
+            set_error("fggc batch: request %d: need ctx, plan, packets and u_out", r);
+            return FGR_E_INVALID;
+        }
+        const fgr_ctx *c0 = ctxs[0];
+        if (ctx->device != c0->device || ctx->opt.precision != c0->opt.precision || ctx->opt.nq != c0->opt.nq ||
+            ctx->opt.np != c0->opt.np || ctx->opt.cq != c0->opt.cq || ctx->opt.cp != c0->opt.cp ||
+            ctx->opt.rcond != c0->opt.rcond) {
+            set_error("fggc batch: request %d: device, precision and neighbour strategy (cq, cp, nq, np, rcond) "
+                      "must be those of request 0", r);
+            return FGR_E_INVALID;
+        }
+        if (!plan_matches(ctx, plans[r])) {
+            set_error("fggc batch: request %d: the plan was made for another dimension, precision, grid, eps or "
+                      "neighbour set", r);
+            return FGR_E_INVALID;
+        }
+        fgr_status rc = check_packets(ctx, pks[r]);
+        if (rc != FGR_OK) return rc;
+        if (pks[r]->m > 0 && pks[r]->on_device != 1) {
+            set_error("fggc batch: request %d: packets must be device memory", r);
+            return FGR_E_INVALID;
+        }
+        if (!is_device_ptr(u_outs[r])) {
+            set_error("fggc batch: request %d: u_out must be device memory", r);
+            return FGR_E_INVALID;
+        }
+    }
+    return guarded([&]() -> fgr_status {
+        FGR_CUDA_TRY(cudaSetDevice(ctxs[0]->device));
+        cudaStream_t st = (cudaStream_t)stream;
+        std::vector<FggcRequest> req;
+        for (int r = 0; r < n; ++r) {
+            const fgr_packets *pk = pks[r];
+            const PacketsDev dev{pk->m, pk->q, pk->p, pk->s, pk->a};
+            if (ctxs[r]->fft_logn[0] > 0) {  // the DFT grid stage runs request by request
+                fgr_status e = run_fggc_planned(ctxs[r], dev, plans[r]->box, plans[r]->buf, plans[r]->bnd,
+                                                plans[r]->overflow, u_outs[r], st);
+                if (e != FGR_OK) return e;
+                continue;
+            }
+            req.push_back(FggcRequest{ctxs[r], &plans[r]->box, &plans[r]->buf, plans[r]->bnd, plans[r]->overflow,
+                                      dev, u_outs[r]});
+        }
+        if (!req.empty()) {
+            fgr_status e = run_fggc_batch((int)req.size(), req.data(), st);
+            if (e != FGR_OK) return e;
+        }
         FGR_CUDA_TRY(cudaGetLastError());
         if (!stream) FGR_CUDA_TRY(cudaStreamSynchronize(st));
         return FGR_OK;

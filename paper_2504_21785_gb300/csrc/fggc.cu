@@ -27,6 +27,8 @@
 // memory in chunks of b, and e^{i b dp x/eps} generated per (m, b) from a
 // phase reduced in FP64.
 #include <climits>
+#include <memory>
+#include <vector>
 #include <cmath>
 
 #include "device_util.cuh"
@@ -39,11 +41,13 @@ namespace {
 // ---------------------------------------------------------------------------
 // node box
 // ---------------------------------------------------------------------------
+// Body of the bounds reduction for CTA bid of nblk (a batched launch runs it
+// for the CTAs of each request).
 template <int D>
-__global__ void bounds_kernel(const double *__restrict__ q, const double *__restrict__ p,
-                              const double *__restrict__ a, int64_t m, Common c, int aglo0, int aghi0,
-                              int aglo1, int aghi1, int aglo2, int aghi2, int *__restrict__ out) {
-    const int aglo[3] = {aglo0, aglo1, aglo2}, aghi[3] = {aghi0, aghi1, aghi2};
+__device__ __forceinline__ void bounds_body(const double *__restrict__ q, const double *__restrict__ p,
+                                            const double *__restrict__ a, int64_t m, const Common &c,
+                                            const int *aglo, const int *aghi, int *__restrict__ out, int64_t bid,
+                                            int64_t nblk) {
     int dqmin = INT_MAX, dqmax = INT_MIN, dpmin = INT_MAX, dpmax = INT_MIN;
     for (int k = 0; k < c.n1; ++k) {
         dqmin = min(dqmin, c.dq[k]);
@@ -61,7 +65,7 @@ __global__ void bounds_kernel(const double *__restrict__ q, const double *__rest
         lo_b[l] = INT_MAX;
         hi_b[l] = INT_MIN;
     }
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t j = bid * (int64_t)blockDim.x + threadIdx.x; j < m; j += nblk * blockDim.x) {
         if (a[j] == 0.0 && a[m + j] == 0.0) continue;
         int pa_lo[D], pa_hi[D], pb_lo[D], pb_hi[D];
         bool use = true;
@@ -113,6 +117,14 @@ __global__ void bounds_kernel(const double *__restrict__ q, const double *__rest
     }
 }
 
+template <int D>
+__global__ void bounds_kernel(const double *__restrict__ q, const double *__restrict__ p,
+                              const double *__restrict__ a, int64_t m, Common c, int aglo0, int aghi0,
+                              int aglo1, int aghi1, int aglo2, int aghi2, int *__restrict__ out) {
+    const int aglo[3] = {aglo0, aglo1, aglo2}, aghi[3] = {aghi0, aghi1, aghi2};
+    bounds_body<D>(q, p, a, m, c, aglo, aghi, out, blockIdx.x, gridDim.x);
+}
+
 // CTAs of the bounds kernel: enough to fill the GPU, few enough that the
 // per-CTA atomics stay negligible
 inline unsigned bounds_blocks(const fgr_ctx *ctx, int64_t m) {
@@ -157,8 +169,8 @@ struct PassTables {
     int2 *band;    // [tiles]: (a_lo, a_hi) of tile t (a_lo > a_hi: empty)
 };
 
-__global__ void pass_tables_kernel(PassParams pp, int tp, int64_t tiles, PassTables t) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void pass_tables_body(const PassParams &pp, int tp, int64_t tiles, const PassTables &t,
+                                                 int64_t i) {
     if (i < pp.A) {
         int64_t wlo, whi;
         window_bounds((double)(pp.amin + i) * pp.dq, pp.rs, pp.lo, pp.h, pp.N, &wlo, &whi);
@@ -180,21 +192,25 @@ __global__ void pass_tables_kernel(PassParams pp, int tp, int64_t tiles, PassTab
     }
 }
 
+__global__ void pass_tables_kernel(PassParams pp, int tp, int64_t tiles, PassTables t) {
+    pass_tables_body(pp, tp, tiles, t, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+}
+
 #include "fggc_fft.cuh"
 
+// Body of a grid pass for the CTA (row, tile, b-slice zs of nz); a batched
+// launch runs it for the CTAs of each request.
 template <bool FP64, int MAXBAND, int TP>
-__global__ void __launch_bounds__(TP) grid_pass_kernel(const void *__restrict__ in_v,
-                                                                 void *__restrict__ out_v, PassParams pp,
-                                                                 const uint8_t *__restrict__ flags,
-                                                                 const int2 *__restrict__ brange,
-                                                                 const PassTables tab) {
+__device__ __forceinline__ void grid_pass_body(const void *__restrict__ in_v, void *__restrict__ out_v,
+                                               const PassParams &pp, const uint8_t *__restrict__ flags,
+                                               const int2 *__restrict__ brange, const PassTables &tab,
+                                               int64_t row, int tile, int zs, int nz) {
     using Real = typename std::conditional<FP64, double, float>::type;
     using C2 = typename std::conditional<FP64, double2, float2>::type;
     __shared__ __align__(16) C2 sw[MAXBAND][kCB];
     __shared__ int swlo[MAXBAND], swhi[MAXBAND];
     __shared__ int s_blo, s_bhi;
-    const int64_t row = blockIdx.x;
-    const int64_t m0 = (int64_t)blockIdx.y * TP;
+    const int64_t m0 = (int64_t)tile * TP;
     int64_t mm[kPassPts];
     bool valid[kPassPts];
 #pragma unroll
@@ -207,8 +223,8 @@ __global__ void __launch_bounds__(TP) grid_pass_kernel(const void *__restrict__ 
     C2 zero;
     zero.x = 0;
     zero.y = 0;
-    const bool split = gridDim.z > 1;  // slices add into a zeroed output
-    const int2 bnd = tab.band[blockIdx.y];
+    const bool split = nz > 1;  // slices add into a zeroed output
+    const int2 bnd = tab.band[tile];
     const int a_lo = bnd.x, a_hi = bnd.y;
     const int nb_total = a_hi - a_lo + 1;
     // occupied b-range: the union over the band of the per-node ranges
@@ -231,10 +247,10 @@ __global__ void __launch_bounds__(TP) grid_pass_kernel(const void *__restrict__ 
         ulo = s_blo;
         uhi = s_bhi;
     }
-    // b-slice of this CTA: blockIdx.z of gridDim.z parts of [ulo, uhi], whole chunks
+    // b-slice of this CTA: part zs of nz of [ulo, uhi], whole chunks
     const int nchunk = uhi >= ulo ? (uhi - ulo + kCB) / kCB : 0;
-    const int per = (nchunk + gridDim.z - 1) / gridDim.z;
-    const int bs = ulo + blockIdx.z * per * kCB, be = min(uhi + 1, bs + per * kCB);
+    const int per = (nchunk + nz - 1) / nz;
+    const int bs = ulo + zs * per * kCB, be = min(uhi + 1, bs + per * kCB);
     if ((flags && !flags[row]) || bs >= be || nb_total <= 0) {
         if (!split) {
 #pragma unroll
@@ -380,10 +396,19 @@ __global__ void __launch_bounds__(TP) grid_pass_kernel(const void *__restrict__ 
     }
 }
 
+template <bool FP64, int MAXBAND, int TP>
+__global__ void __launch_bounds__(TP) grid_pass_kernel(const void *__restrict__ in_v, void *__restrict__ out_v,
+                                                       PassParams pp, const uint8_t *__restrict__ flags,
+                                                       const int2 *__restrict__ brange, const PassTables tab) {
+    grid_pass_body<FP64, MAXBAND, TP>(in_v, out_v, pp, flags, brange, tab, blockIdx.x, blockIdx.y, blockIdx.z,
+                                      gridDim.z);
+}
+
 template <class C2>
-__global__ void transpose_kernel(const C2 *__restrict__ in, C2 *__restrict__ out, int64_t R, int64_t Cc) {
+__device__ __forceinline__ void transpose_body(const C2 *__restrict__ in, C2 *__restrict__ out, int64_t R,
+                                               int64_t Cc, int64_t bx, int64_t by) {
     __shared__ C2 tile[32][33];
-    const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+    const int64_t r0 = bx * 32, c0 = by * 32;
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
         const int64_t r = r0 + i, c = c0 + threadIdx.x;
         if (r < R && c < Cc) tile[i][threadIdx.x] = in[r * Cc + c];
@@ -395,11 +420,17 @@ __global__ void transpose_kernel(const C2 *__restrict__ in, C2 *__restrict__ out
     }
 }
 
+template <class C2>
+__global__ void transpose_kernel(const C2 *__restrict__ in, C2 *__restrict__ out, int64_t R, int64_t Cc) {
+    transpose_body<C2>(in, out, R, Cc, blockIdx.x, blockIdx.y);
+}
+
 // Occupied b-range of every line [row][a][0..B): first and last b with a
 // non-zero value ((B, -1) for an empty line).  One warp per line.
 template <class C2>
-__global__ void brange_kernel(const C2 *__restrict__ in, int64_t lines, int B, int2 *__restrict__ out) {
-    const int64_t line = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+__device__ __forceinline__ void brange_body(const C2 *__restrict__ in, int64_t lines, int B,
+                                            int2 *__restrict__ out, int64_t bid) {
+    const int64_t line = bid * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     if (line >= lines) return;
     const int lane = threadIdx.x & 31;
     const C2 *p = in + line * (int64_t)B;
@@ -414,6 +445,11 @@ __global__ void brange_kernel(const C2 *__restrict__ in, int64_t lines, int B, i
     lo = __reduce_min_sync(0xffffffffu, lo);
     hi = __reduce_max_sync(0xffffffffu, hi);
     if (lane == 0) out[line] = make_int2(lo == INT_MAX ? B : lo, hi);
+}
+
+template <class C2>
+__global__ void brange_kernel(const C2 *__restrict__ in, int64_t lines, int B, int2 *__restrict__ out) {
+    brange_body<C2>(in, lines, B, out, blockIdx.x);
 }
 
 // The same for short lines (B <= 64): one thread per line, so a warp streams
@@ -731,7 +767,7 @@ fgr_status make_box(const fgr_ctx *ctx, const int *hb, int margin, FggcBox *box)
 }
 
 bool make_bin_box(const FggcBox &box, int d, BinBox *bb) {
-    if (d < 2 || box.empty) return false;
+    if (d != 3 || box.empty) return false;
     const Common &c = box.c;
     BinBox x;
     x.dqmin = x.dpmin = INT_MAX;
@@ -791,11 +827,164 @@ void bin_buffers_at(void *block, int64_t m, const BinBox &bb, BinBuffers *out) {
 fgr_status launch_binned_scatter(int d, int n1, const BinLaunch &L, cudaStream_t st, const PacketsDev &pk,
                                  const Params32 &P, void *W, uint8_t *flags, StageMarks *marks) {
     if (pk.m == 0) return FGR_OK;
-    return d == 2 ? launch_binned_d2(n1, L, st, pk, P, W, flags, marks)
-                  : launch_binned_d3(n1, L, st, pk, P, W, flags, marks);
+    if (d != 3) {
+        set_error("fggc: the binned scatter serves d = 3");
+        return FGR_E_INTERNAL;
+    }
+    return launch_binned_d3(n1, L, st, pk, P, W, flags, marks);
 }
 
 namespace {
+
+// ---------------------------------------------------------------------------
+// batched FGGC: one launch per stage over the planned requests of one
+// dimension (fgr_reconstruct_fggc_batch)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int batch_request(const int *block0, int n) {
+    int r = 0;
+    while (r + 1 < n && (int)blockIdx.x >= block0[r + 1]) ++r;
+    return r;
+}
+
+// Byte fills of up to 3 segments per request (node array, row flags, output).
+struct FillBatch {
+    int n;  // segments
+    int block0[3 * kBatchMax + 1];
+    unsigned char *ptr[3 * kBatchMax];
+    int64_t bytes[3 * kBatchMax];
+    int value[3 * kBatchMax];
+};
+
+__global__ void __launch_bounds__(256) fill_batch_kernel(const __grid_constant__ FillBatch B) {
+    const int r = batch_request(B.block0, B.n);
+    const int64_t nblk = B.block0[r + 1] - B.block0[r], bid = blockIdx.x - B.block0[r];
+    unsigned char *p = B.ptr[r];
+    const int64_t bytes = B.bytes[r];
+    const unsigned char v = (unsigned char)B.value[r];
+    // 16-byte stores from the first 16-byte boundary, single bytes around them
+    const int64_t head = min(bytes, (int64_t)((16 - ((uintptr_t)p & 15)) & 15));
+    const int64_t n16 = (bytes - head) / 16;
+    const unsigned w = v * 0x01010101u;
+    uint4 *p16 = reinterpret_cast<uint4 *>(p + head);
+    for (int64_t i = bid * 256 + threadIdx.x; i < n16; i += nblk * 256) p16[i] = make_uint4(w, w, w, w);
+    if (bid == 0) {
+        for (int64_t i = threadIdx.x; i < head; i += 256) p[i] = v;
+        for (int64_t i = head + n16 * 16 + threadIdx.x; i < bytes; i += 256) p[i] = v;
+    }
+}
+
+struct BoundsBatch {
+    int n;
+    int block0[kBatchMax + 1];
+    Common c[kBatchMax];
+    const double *q[kBatchMax], *p[kBatchMax], *a[kBatchMax];
+    int64_t m[kBatchMax];
+    int aglo[kBatchMax][3], aghi[kBatchMax][3];
+    int *out[kBatchMax];     // 12 bounds per request
+    int *overflow[kBatchMax];
+};
+
+// Initial bounds and cleared overflow flags of every request (one CTA).
+__global__ void bounds_init_batch_kernel(const __grid_constant__ BoundsBatch B) {
+    for (int i = threadIdx.x; i < B.n * 12; i += blockDim.x) B.out[i / 12][i % 12] = (i & 1) ? INT_MIN : INT_MAX;
+    for (int r = threadIdx.x; r < B.n; r += blockDim.x) *B.overflow[r] = 0;
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) bounds_batch_kernel(const __grid_constant__ BoundsBatch B) {
+    const int r = batch_request(B.block0, B.n);
+    bounds_body<D>(B.q[r], B.p[r], B.a[r], B.m[r], B.c[r], B.aglo[r], B.aghi[r], B.out[r], blockIdx.x - B.block0[r],
+                   B.block0[r + 1] - B.block0[r]);
+}
+
+// Overflow flag of every request whose packets left its planned box (one CTA).
+__global__ void box_check_batch_kernel(const __grid_constant__ BoundsBatch B, int d) {
+    for (int r = threadIdx.x; r < B.n; r += blockDim.x) {
+        const int *b = B.out[r];
+        const Common &c = B.c[r];
+        bool out = false;
+        for (int l = 0; l < d; ++l) {
+            if (b[l * 4] == INT_MAX) continue;
+            out = out || b[l * 4 + 0] < c.amin[l] || b[l * 4 + 1] > c.amin[l] + c.A[l] - 1 ||
+                  b[l * 4 + 2] < c.bmin[l] || b[l * 4 + 3] > c.bmin[l] + c.B[l] - 1;
+        }
+        if (out) *B.overflow[r] = 1;
+    }
+}
+
+// One grid pass (b-range scan, tables, pass or transpose) of every request.
+struct PassBatch {
+    int n;
+    int block0[kBatchMax + 1];
+    PassParams pp[kBatchMax];
+    PassTables tab[kBatchMax];
+    const void *in[kBatchMax];
+    void *out[kBatchMax];
+    const uint8_t *flags[kBatchMax];
+    int2 *brange[kBatchMax];
+    int64_t tiles[kBatchMax];  // pass: grid-point tiles per row; tables: table entries
+    int64_t tx[kBatchMax];     // transpose: 32-row blocks
+};
+
+template <class C2>
+__global__ void __launch_bounds__(256) brange_batch_kernel(const __grid_constant__ PassBatch B) {
+    const int r = batch_request(B.block0, B.n);
+    brange_body<C2>(reinterpret_cast<const C2 *>(B.in[r]), B.pp[r].rows * (int64_t)B.pp[r].A, B.pp[r].B, B.brange[r],
+                    blockIdx.x - B.block0[r]);
+}
+
+__global__ void __launch_bounds__(256) tables_batch_kernel(const __grid_constant__ PassBatch B, int tp) {
+    const int r = batch_request(B.block0, B.n);
+    const int64_t mtiles = (B.pp[r].N + tp - 1) / tp;
+    pass_tables_body(B.pp[r], tp, mtiles, B.tab[r], (int64_t)(blockIdx.x - B.block0[r]) * 256 + threadIdx.x);
+}
+
+template <bool FP64, int MAXBAND, int TP>
+__global__ void __launch_bounds__(TP) grid_pass_batch_kernel(const __grid_constant__ PassBatch B) {
+    const int r = batch_request(B.block0, B.n);
+    const int64_t local = blockIdx.x - B.block0[r];
+    const int64_t row = local / B.tiles[r];
+    const int tile = (int)(local - row * B.tiles[r]);
+    grid_pass_body<FP64, MAXBAND, TP>(B.in[r], B.out[r], B.pp[r], B.flags[r], B.brange[r], B.tab[r], row, tile, 0, 1);
+}
+
+template <class C2>
+__global__ void transpose_batch_kernel(const __grid_constant__ PassBatch B) {
+    const int r = batch_request(B.block0, B.n);
+    const int64_t local = blockIdx.x - B.block0[r];
+    const int64_t bx = local % B.tx[r], by = local / B.tx[r];
+    transpose_body<C2>(reinterpret_cast<const C2 *>(B.in[r]), reinterpret_cast<C2 *>(B.out[r]), B.pp[r].rows,
+                       B.pp[r].N, bx, by);
+}
+
+// Parameters of the grid pass over dimension l of a node box c; prodN_after =
+// product of the grid sizes of the dimensions already contracted.
+PassParams pass_params(const fgr_ctx *ctx, const Common &c, int l, int64_t prodN_after) {
+    const Mesh &M = ctx->mesh;
+    const Grid &G = ctx->grid;
+    PassParams pp{};
+    int64_t pre = 1;
+    for (int j = 0; j < l; ++j) pre *= (int64_t)c.A[j] * c.B[j];
+    pp.rows = pre * prodN_after;
+    pp.A = c.A[l];
+    pp.B = c.B[l];
+    pp.amin = c.amin[l];
+    pp.bmin = c.bmin[l];
+    pp.N = G.n[l];
+    pp.lo = G.lo[l];
+    pp.h = G.h[l];
+    pp.dq = M.dq;
+    pp.rs = M.rs;
+    pp.neg_half_inv_eps = -0.5 / M.eps;
+    pp.phi_scale = M.dp / (2 * M_PI * M.eps);
+    pp.dp_over_eps = M.dp / M.eps;
+    const int bmax_abs = std::max(std::abs(c.bmin[l]), std::abs(c.bmin[l] + c.B[l] - 1));
+    int lb = 1;
+    while ((1 << lb) < bmax_abs + 1) ++lb;
+    pp.two_pow_b = std::ldexp(1.0, std::max(1, 23 - lb));
+    pp.inv_two_pow_b = 1.0 / pp.two_pow_b;
+    return pp;
+}
 
 // Clears the node box and runs the coefficient scatter and the grid passes
 // into u_dev (all stream-ordered: no allocation, no host synchronisation).
@@ -803,7 +992,6 @@ template <int D>
 fgr_status enqueue_fggc(fgr_ctx *ctx, const PacketsDev &pk, const FggcBox &box, const FggcBuffers &b, void *u_dev,
                         cudaStream_t st, StageTimer *timer, int64_t *launches) {
     const bool fp64 = ctx->opt.precision == FGR_FP64;
-    const Mesh &M = ctx->mesh;
     const Grid &G = ctx->grid;
     const Lsa &L = ctx->lsa;
     const size_t eb = elem_bytes(ctx->opt.precision);
@@ -831,7 +1019,7 @@ fgr_status enqueue_fggc(fgr_ctx *ctx, const PacketsDev &pk, const FggcBox &box, 
                     P.cim[(k * kCheb + i) * kCheb + jj] = L.cheb_im[k][i][jj];
                 }
         BinLaunch bl;
-        const bool binned = D >= 2 && b.bin && b.bin_m >= pk.m && pk.m > 0 && (L.n1 == 4 || L.n1 == 8) &&
+        const bool binned = D == 3 && b.bin && b.bin_m >= pk.m && pk.m > 0 && (L.n1 == 4 || L.n1 == 8) &&
                             make_bin_box(box, D, &bl.box);
         fgr_status r;
         if (binned) {
@@ -853,27 +1041,7 @@ fgr_status enqueue_fggc(fgr_ctx *ctx, const PacketsDev &pk, const FggcBox &box, 
     const void *cur = b.W;
     int64_t prodN_after = 1;  // product of N of contracted dimensions
     for (int l = D - 1; l >= 0; --l) {
-        PassParams pp{};
-        int64_t pre = 1;
-        for (int j = 0; j < l; ++j) pre *= (int64_t)c.A[j] * c.B[j];
-        pp.rows = pre * prodN_after;
-        pp.A = c.A[l];
-        pp.B = c.B[l];
-        pp.amin = c.amin[l];
-        pp.bmin = c.bmin[l];
-        pp.N = G.n[l];
-        pp.lo = G.lo[l];
-        pp.h = G.h[l];
-        pp.dq = M.dq;
-        pp.rs = M.rs;
-        pp.neg_half_inv_eps = -0.5 / M.eps;
-        pp.phi_scale = M.dp / (2 * M_PI * M.eps);
-        pp.dp_over_eps = M.dp / M.eps;
-        const int bmax_abs = std::max(std::abs(c.bmin[l]), std::abs(c.bmin[l] + c.B[l] - 1));
-        int lb = 1;
-        while ((1 << lb) < bmax_abs + 1) ++lb;
-        pp.two_pow_b = std::ldexp(1.0, std::max(1, 23 - lb));
-        pp.inv_two_pow_b = 1.0 / pp.two_pow_b;
+        const PassParams pp = pass_params(ctx, c, l, prodN_after);
         const bool last = l == 0;
         void *dst = (D == 1) ? u_dev : (cur == b.buf1 ? b.buf2 : b.buf1);
         fgr_status r = fp64 ? launch_brange<true>(cur, pp.rows, pp.A, pp.B, b.brange, st)
@@ -986,6 +1154,245 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
 }
 
 }  // namespace
+
+namespace {
+
+// Blocks of a batched launch: block0 = prefix of per-request counts.
+template <class Batch>
+bool set_blocks(Batch &B, const std::vector<int64_t> &counts) {
+    int64_t acc = 0;
+    for (size_t r = 0; r < counts.size(); ++r) {
+        B.block0[r] = (int)acc;
+        acc += counts[r];
+        if (acc > INT_MAX) return false;
+    }
+    B.block0[counts.size()] = (int)acc;
+    return true;
+}
+
+// One chunk (<= kBatchMax requests) of one dimension D: fill, bounds, box
+// check, scatter, passes: every stage one launch for the whole chunk.
+template <int D>
+fgr_status enqueue_fggc_batch(int n, const FggcRequest *req, cudaStream_t st) {
+    const fgr_ctx *ctx0 = req[0].ctx;
+    const bool fp64 = ctx0->opt.precision == FGR_FP64;
+    const size_t eb = elem_bytes(ctx0->opt.precision);
+    const int num_sms = ctx0->num_sms;
+    auto too_many = [] {
+        set_error("fggc batch: too many CTAs in one launch");
+        return FGR_E_CAPACITY;
+    };
+    // fills: the node array and row flags of every non-empty box; the output
+    // of an empty one (nothing reaches its grid)
+    {
+        FillBatch fb{};
+        std::vector<int64_t> cnt;
+        auto seg = [&](void *ptr, int64_t bytes, int value) {
+            if (bytes <= 0) return;
+            fb.ptr[fb.n] = (unsigned char *)ptr;
+            fb.bytes[fb.n] = bytes;
+            fb.value[fb.n] = value;
+            cnt.push_back(std::max<int64_t>(1, std::min<int64_t>((bytes + 16383) / 16384, 4 * (int64_t)num_sms)));
+            ++fb.n;
+        };
+        for (int r = 0; r < n; ++r) {
+            const FggcRequest &q = req[r];
+            if (q.box->empty) {
+                seg(q.u, (int64_t)(eb * (size_t)q.ctx->grid.total), 0);
+            } else {
+                seg(q.buf->W, (int64_t)(eb * (size_t)q.box->cells), 0);
+                seg(q.buf->flags, q.box->rows0, D == 1 ? 1 : 0);
+            }
+        }
+        if (fb.n > 0) {
+            if (!set_blocks(fb, cnt)) return too_many();
+            fill_batch_kernel<<<fb.block0[fb.n], 256, 0, st>>>(fb);
+        }
+    }
+    std::vector<int> live;  // requests with a non-empty box
+    for (int r = 0; r < n; ++r)
+        if (!req[r].box->empty) live.push_back(r);
+    if (live.empty()) {
+        FGR_CUDA_TRY(cudaGetLastError());
+        return FGR_OK;
+    }
+    const int nl = (int)live.size();
+    // node bounds of the packets, compared with the planned boxes
+    {
+        BoundsBatch bb{};
+        bb.n = nl;
+        std::vector<int64_t> cnt;
+        for (int i = 0; i < nl; ++i) {
+            const FggcRequest &q = req[live[i]];
+            bb.c[i] = base_common(q.ctx);
+            bb.q[i] = q.pk.q;
+            bb.p[i] = q.pk.p;
+            bb.a[i] = q.pk.a;
+            bb.m[i] = q.pk.m;
+            grid_node_range(q.ctx, bb.aglo[i], bb.aghi[i]);
+            bb.out[i] = q.bnd;
+            bb.overflow[i] = q.overflow;
+            cnt.push_back(std::max<int64_t>(1, std::min<int64_t>((q.pk.m + 255) / 256, 8 * (int64_t)num_sms / nl + 1)));
+        }
+        if (!set_blocks(bb, cnt)) return too_many();
+        bounds_init_batch_kernel<<<1, 256, 0, st>>>(bb);
+        bounds_batch_kernel<D><<<bb.block0[nl], 256, 0, st>>>(bb);
+        for (int i = 0; i < nl; ++i) bb.c[i] = req[live[i]].box->c;  // planned boxes for the check
+        box_check_batch_kernel<<<1, 64, 0, st>>>(bb, D);
+    }
+    // coefficients + scatter (per-packet form)
+    {
+        const Lsa &L = ctx0->lsa;
+        const int T = scatter_threads(fp64, L.n1);
+        std::vector<int64_t> cnt;
+        ScatterBatchBase *base;
+        std::unique_ptr<ScatterBatch64> b64;
+        std::unique_ptr<ScatterBatch32> b32;
+        if (fp64) {
+            b64.reset(new ScatterBatch64());
+            memcpy(b64->vr, L.vr, sizeof(b64->vr));
+            memcpy(b64->vi, L.vi, sizeof(b64->vi));
+            memcpy(b64->inv_lam, L.inv_lam, sizeof(b64->inv_lam));
+            base = b64.get();
+        } else {
+            b32.reset(new ScatterBatch32());
+            for (int k = 0; k < kMaxN1; ++k)
+                for (int i = 0; i < kCheb; ++i)
+                    for (int jj = 0; jj < kCheb; ++jj) {
+                        b32->cre[(k * kCheb + i) * kCheb + jj] = L.cheb_re[k][i][jj];
+                        b32->cim[(k * kCheb + i) * kCheb + jj] = L.cheb_im[k][i][jj];
+                    }
+            base = b32.get();
+        }
+        base->n = nl;
+        for (int i = 0; i < nl; ++i) {
+            const FggcRequest &q = req[live[i]];
+            base->c[i] = q.box->c;
+            base->q[i] = q.pk.q;
+            base->p[i] = q.pk.p;
+            base->s[i] = q.pk.s;
+            base->a[i] = q.pk.a;
+            base->m[i] = q.pk.m;
+            base->W[i] = q.buf->W;
+            base->flags[i] = q.buf->flags;
+            cnt.push_back((q.pk.m + T - 1) / T);
+        }
+        if (!set_blocks(*base, cnt)) return too_many();
+        fgr_status r = launch_scatter_batch(D, L.n1, st, b64.get(), b32.get());
+        if (r != FGR_OK) return r;
+    }
+    // separable passes, last dimension first
+    constexpr int TP = 128;
+    std::vector<const void *> cur(nl);
+    std::vector<int64_t> prodN(nl, 1);
+    for (int i = 0; i < nl; ++i) cur[i] = req[live[i]].buf->W;
+    for (int l = D - 1; l >= 0; --l) {
+        PassBatch pb{};
+        pb.n = nl;
+        int band = 1;
+        std::vector<void *> dst(nl);
+        for (int i = 0; i < nl; ++i) {
+            const FggcRequest &q = req[live[i]];
+            pb.pp[i] = pass_params(q.ctx, q.box->c, l, prodN[i]);
+            const PassParams &pp = pb.pp[i];
+            if (pp.rows > INT_MAX) {
+                set_error("fggc batch: too many rows in a grid pass");
+                return FGR_E_CAPACITY;
+            }
+            const FggcBuffers &b = *q.buf;
+            dst[i] = D == 1 ? q.u : (cur[i] == b.buf1 ? b.buf2 : b.buf1);
+            pb.in[i] = cur[i];
+            pb.out[i] = dst[i];
+            pb.flags[i] = l == D - 1 ? b.flags : nullptr;
+            pb.brange[i] = b.brange;
+            PassTables tab;
+            tab.win = reinterpret_cast<int2 *>(b.tables);
+            tab.ph = reinterpret_cast<float2 *>(tab.win + pp.A);
+            tab.band = reinterpret_cast<int2 *>(tab.ph + pp.N);
+            pb.tab[i] = tab;
+            pb.tiles[i] = (pp.N + TP - 1) / TP;
+            if (pb.tiles[i] > 65535) {
+                set_error("fggc batch: %lld points per grid dimension; at most %d", (long long)pp.N, 65535 * TP);
+                return FGR_E_INVALID;
+            }
+            band = std::max(band, pass_band(TP, pp.h, pp.rs, pp.dq));
+        }
+        std::vector<int64_t> cnt(nl);
+        for (int i = 0; i < nl; ++i) cnt[i] = (pb.pp[i].rows * (int64_t)pb.pp[i].A + 7) / 8;
+        if (!set_blocks(pb, cnt)) return too_many();
+        if (fp64)
+            brange_batch_kernel<double2><<<pb.block0[nl], 256, 0, st>>>(pb);
+        else
+            brange_batch_kernel<float2><<<pb.block0[nl], 256, 0, st>>>(pb);
+        for (int i = 0; i < nl; ++i)
+            cnt[i] = (std::max<int64_t>(std::max<int64_t>(pb.pp[i].A, pb.pp[i].N), pb.tiles[i]) + 255) / 256;
+        if (!set_blocks(pb, cnt)) return too_many();
+        tables_batch_kernel<<<pb.block0[nl], 256, 0, st>>>(pb, TP);
+        for (int i = 0; i < nl; ++i) cnt[i] = pb.pp[i].rows * pb.tiles[i];
+        if (!set_blocks(pb, cnt)) return too_many();
+#define FGR_PB(MB)                                                                                   \
+    if (fp64)                                                                                        \
+        grid_pass_batch_kernel<true, MB, TP><<<pb.block0[nl], TP, 0, st>>>(pb);                      \
+    else                                                                                             \
+        grid_pass_batch_kernel<false, MB, TP><<<pb.block0[nl], TP, 0, st>>>(pb);
+        if (band <= 16) {
+            FGR_PB(16)
+        } else if (band <= 32) {
+            FGR_PB(32)
+        } else if (band <= 48) {
+            FGR_PB(48)
+        } else {
+            FGR_PB(64)
+        }
+#undef FGR_PB
+        if (D > 1) {
+            for (int i = 0; i < nl; ++i) {
+                const FggcRequest &q = req[live[i]];
+                const FggcBuffers &b = *q.buf;
+                pb.in[i] = dst[i];
+                pb.out[i] = l == 0 ? q.u : (dst[i] == b.buf1 ? b.buf2 : b.buf1);
+                pb.tx[i] = (pb.pp[i].rows + 31) / 32;
+                cnt[i] = pb.tx[i] * ((pb.pp[i].N + 31) / 32);
+                cur[i] = pb.out[i];
+            }
+            if (!set_blocks(pb, cnt)) return too_many();
+            if (fp64)
+                transpose_batch_kernel<double2><<<pb.block0[nl], dim3(32, 8), 0, st>>>(pb);
+            else
+                transpose_batch_kernel<float2><<<pb.block0[nl], dim3(32, 8), 0, st>>>(pb);
+        }
+        for (int i = 0; i < nl; ++i) prodN[i] *= req[live[i]].ctx->grid.n[l];
+    }
+    FGR_CUDA_TRY(cudaGetLastError());
+    return FGR_OK;
+}
+
+}  // namespace
+
+fgr_status launch_scatter_batch(int d, int n1, cudaStream_t st, const ScatterBatch64 *b64, const ScatterBatch32 *b32) {
+    switch (d) {
+    case 1: return launch_scatter_batch_d1(n1, st, b64, b32);
+    case 2: return launch_scatter_batch_d2(n1, st, b64, b32);
+    default: return launch_scatter_batch_d3(n1, st, b64, b32);
+    }
+}
+
+fgr_status run_fggc_batch(int n, const FggcRequest *req, cudaStream_t st) {
+    // requests of one dimension together, kBatchMax per launch
+    for (int d = 1; d <= 3; ++d) {
+        std::vector<FggcRequest> group;
+        for (int r = 0; r < n; ++r)
+            if (req[r].ctx->d == d) group.push_back(req[r]);
+        for (size_t i0 = 0; i0 < group.size(); i0 += kBatchMax) {
+            const int k = (int)std::min<size_t>(kBatchMax, group.size() - i0);
+            fgr_status r = d == 1 ? enqueue_fggc_batch<1>(k, group.data() + i0, st)
+                         : d == 2 ? enqueue_fggc_batch<2>(k, group.data() + i0, st)
+                                  : enqueue_fggc_batch<3>(k, group.data() + i0, st);
+            if (r != FGR_OK) return r;
+        }
+    }
+    return FGR_OK;
+}
 
 fgr_status launch_coeff_scatter(int d, int n1, cudaStream_t st, const PacketsDev &pk, const Params64 *p64,
                                 const Params32 *p32, void *W, uint8_t *flags) {

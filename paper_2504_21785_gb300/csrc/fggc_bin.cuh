@@ -1,4 +1,4 @@
-// K4 for d >= 2 (FP32 path): the scatter of eq. 2.25 with the packets binned
+// K4 for d = 3 (FP32 path): the scatter of eq. 2.25 with the packets binned
 // by the anchor cell (a0, b0) of their outer dimensions.
 //
 // A packet's contributions to one row of the node array (the last dimension's
@@ -13,7 +13,8 @@
 // row.  Cells with fewer packets than BinLaunch::min_count go through the
 // per-packet kernel (fggc_coeff.cuh) from a list.
 //
-// Included by fggc_coeff2.cu and fggc_coeff3.cu after fggc_coeff.cuh.
+// Included by fggc_coeff3.cu.  The kernels are written for d >= 2; the
+// library uses them for d = 3, where a packet has 512 contributions.
 #pragma once
 
 #include <climits>
@@ -372,49 +373,65 @@ __global__ void __launch_bounds__(kBinT, 2) binned_scatter_kernel(
             }
             __syncthreads();
             const int nact = s_nact;
-            // --- cells: all rows in registers, then one reduction per row ------
-            for (int i = tid; i < nact; i += kBinT) {
+            // --- cells: rows in registers, then one reduction per row ----------
+            // work unit = (pass kp over NA values of k0, cell); consecutive
+            // threads take consecutive cells of one pass (coalesced reductions)
+            constexpr int NP = N1 / NA;
+            for (int u0 = tid; u0 < nact * NP; u0 += kBinT) {
+                const int kp = u0 / nact, i = u0 - kp * nact;
                 const unsigned cell = act[i];
                 const int ia = (int)(cell >> 16), ib = (int)(cell & 0xffffu);
                 const int e = ia * TB + ib;
                 const int x0 = cstart[e], x1 = cend[e];
                 float2 *Wc = W + (int64_t)(ta0 + wa + ia) * c.sa[D - 1] + tb0 + ib;
-#pragma unroll 1
-                for (int kp = 0; kp < N1 / NA; ++kp) {
-                    float accr[NA][NK1], acci[NA][NK1];
+                float accr[NA][NK1], acci[NA][NK1];
 #pragma unroll
-                    for (int u = 0; u < NA; ++u)
+                for (int u = 0; u < NA; ++u)
 #pragma unroll
-                        for (int v = 0; v < NK1; ++v) accr[u][v] = acci[u][v] = 0.f;
-                    for (int x = x0; x < x1; ++x) {
-                        const float2 ev = eval[x];
-                        const float2 *cp = coef + (int)ejj[x] * D * N1;
+                    for (int v = 0; v < NK1; ++v) accr[u][v] = acci[u][v] = 0.f;
+                for (int x = x0; x < x1; ++x) {
+                    const float2 ev = eval[x];
+                    // the packet's coefficients, 16-byte loads (two neighbours each)
+                    const float4 *cp4 = reinterpret_cast<const float4 *>(coef + (int)ejj[x] * D * N1);
+                    float2 c0v[NA];
 #pragma unroll
-                        for (int u = 0; u < NA; ++u) {
-                            const float2 c0 = cp[kp * NA + u];
-                            float tr, ti;
-                            cmul(ev.x, ev.y, c0.x, c0.y, tr, ti);
-                            if constexpr (D == 3) {
+                    for (int u = 0; u < NA; u += 2) {
+                        const float4 t = cp4[(kp * NA + u) / 2];
+                        c0v[u] = make_float2(t.x, t.y);
+                        c0v[u + 1] = make_float2(t.z, t.w);
+                    }
+                    float2 c1v[NK1];
+                    if constexpr (D == 3) {
 #pragma unroll
-                                for (int v = 0; v < NK1; ++v) {
-                                    const float2 c1 = cp[N1 + v];
-                                    accr[u][v] = fmaf(tr, c1.x, fmaf(-ti, c1.y, accr[u][v]));
-                                    acci[u][v] = fmaf(tr, c1.y, fmaf(ti, c1.x, acci[u][v]));
-                                }
-                            } else {
-                                accr[u][0] += tr;
-                                acci[u][0] += ti;
-                            }
+                        for (int v = 0; v < NK1; v += 2) {
+                            const float4 t = cp4[(N1 + v) / 2];
+                            c1v[v] = make_float2(t.x, t.y);
+                            c1v[v + 1] = make_float2(t.z, t.w);
                         }
                     }
 #pragma unroll
-                    for (int u = 0; u < NA; ++u)
+                    for (int u = 0; u < NA; ++u) {
+                        float tr, ti;
+                        cmul(ev.x, ev.y, c0v[u].x, c0v[u].y, tr, ti);
+                        if constexpr (D == 3) {
 #pragma unroll
-                        for (int v = 0; v < NK1; ++v) {
-                            const int r = (kp * NA + u) * NK1 + v;
-                            if ((rows_in >> r) & 1ull) atomicAdd(Wc + rowoff[r], make_float2(accr[u][v], acci[u][v]));
+                            for (int v = 0; v < NK1; ++v) {
+                                accr[u][v] = fmaf(tr, c1v[v].x, fmaf(-ti, c1v[v].y, accr[u][v]));
+                                acci[u][v] = fmaf(tr, c1v[v].y, fmaf(ti, c1v[v].x, acci[u][v]));
+                            }
+                        } else {
+                            accr[u][0] += tr;
+                            acci[u][0] += ti;
                         }
+                    }
                 }
+#pragma unroll
+                for (int u = 0; u < NA; ++u)
+#pragma unroll
+                    for (int v = 0; v < NK1; ++v) {
+                        const int r = (kp * NA + u) * NK1 + v;
+                        if ((rows_in >> r) & 1ull) atomicAdd(Wc + rowoff[r], make_float2(accr[u][v], acci[u][v]));
+                    }
             }
         }
     }

@@ -22,9 +22,21 @@ __device__ __forceinline__ void cmul(float ar, float ai, float br, float bi, flo
     ci = ar * bi + ai * br;
 }
 
-// FP64: per-dimension coefficients through the eigen factors.
-template <int N>
-__device__ __forceinline__ void coeff_dim64(const Params64 &P, double Q, double Pm, int &a0, int &b0,
+// Parameter views of one request inside a batch: that request's constants
+// with the least-squares tables shared by the batch (same strategy).
+struct Params64View {
+    const Common &c;
+    const double *vr, *vi, *inv_lam;
+};
+struct Params32View {
+    const Common &c;
+    const float *cre, *cim;
+};
+
+// FP64: per-dimension coefficients through the eigen factors (PT: Params64
+// or Params64View).
+template <int N, class PT>
+__device__ __forceinline__ void coeff_dim64(const PT &P, double Q, double Pm, int &a0, int &b0,
                                             double *cr, double *ci) {
     const Common &c = P.c;
     const double r = __ddiv_rn(Q, c.dqv), rp = __ddiv_rn(Pm, c.dpv);
@@ -79,9 +91,10 @@ __device__ __forceinline__ void coeff_dim64(const Params64 &P, double Q, double 
     }
 }
 
-// FP32: per-dimension coefficients through the Chebyshev surrogate.
-template <int N>
-__device__ __forceinline__ void coeff_dim32(const Params32 &P, double Q, double Pm, int &a0, int &b0,
+// FP32: per-dimension coefficients through the Chebyshev surrogate (PT:
+// Params32 or Params32View).
+template <int N, class PT>
+__device__ __forceinline__ void coeff_dim32(const PT &P, double Q, double Pm, int &a0, int &b0,
                                             float *cr, float *ci) {
     const Common &c = P.c;
     // the floors of Q/dq and P/dp as the FP64 division decides them (FP32
@@ -158,10 +171,10 @@ __host__ __device__ constexpr int coeff_threads() {
 template <bool FP64>
 using ParamsT = typename std::conditional<FP64, Params64, Params32>::type;
 
-template <int D, bool FP64, int N1>
+template <int D, bool FP64, int N1, class PT>
 __device__ __forceinline__ void coeff_scatter_body(const double *__restrict__ q, const double *__restrict__ p,
                                                    const double *__restrict__ s, const double *__restrict__ a,
-                                                   int64_t m, int64_t j, const ParamsT<FP64> &P,
+                                                   int64_t m, int64_t j, const PT &P,
                                                    void *__restrict__ W_v, uint8_t *__restrict__ row_flag) {
     using Real = typename std::conditional<FP64, double, float>::type;
     using C2 = typename std::conditional<FP64, double2, float2>::type;
@@ -288,6 +301,44 @@ __global__ void __launch_bounds__(coeff_threads<FP64, N1>(), D == 3 ? 4 : 1) coe
     const int n = *count;
     for (int64_t t = blockIdx.x * (int64_t)kT + threadIdx.x; t < n; t += (int64_t)gridDim.x * kT)
         coeff_scatter_body<D, FP64, N1>(q, p, s, a, m, list[t], P, W_v, row_flag);
+}
+
+// Batched form: the CTAs of every request of a launch (same dimension,
+// precision and neighbour strategy: shared least-squares tables).
+template <int D, bool FP64, int N1>
+__global__ void __launch_bounds__(coeff_threads<FP64, N1>(), D == 3 ? 4 : 1) coeff_scatter_batch_kernel(
+    const __grid_constant__ typename std::conditional<FP64, ScatterBatch64, ScatterBatch32>::type B) {
+    int r = 0;
+    while (r + 1 < B.n && (int)blockIdx.x >= B.block0[r + 1]) ++r;
+    const int64_t j = (int64_t)(blockIdx.x - B.block0[r]) * coeff_threads<FP64, N1>() + threadIdx.x;
+    if (j >= B.m[r]) return;
+    if constexpr (FP64) {
+        const Params64View v{B.c[r], B.vr, B.vi, B.inv_lam};
+        coeff_scatter_body<D, FP64, N1>(B.q[r], B.p[r], B.s[r], B.a[r], B.m[r], j, v, B.W[r], B.flags[r]);
+    } else {
+        const Params32View v{B.c[r], B.cre, B.cim};
+        coeff_scatter_body<D, FP64, N1>(B.q[r], B.p[r], B.s[r], B.a[r], B.m[r], j, v, B.W[r], B.flags[r]);
+    }
+}
+
+template <int D>
+fgr_status launch_scatter_batch_dim(int n1, cudaStream_t st, const ScatterBatch64 *b64, const ScatterBatch32 *b32) {
+    const int nb = b64 ? b64->block0[b64->n] : b32->block0[b32->n];
+    if (nb == 0) return FGR_OK;
+#define FGR_SB(N)                                                                                      \
+    if (b64)                                                                                           \
+        coeff_scatter_batch_kernel<D, true, N><<<nb, coeff_threads<true, N>(), 0, st>>>(*b64);         \
+    else                                                                                               \
+        coeff_scatter_batch_kernel<D, false, N><<<nb, coeff_threads<false, N>(), 0, st>>>(*b32);
+    switch (n1) {
+    case 4: FGR_SB(4); break;
+    case 8: FGR_SB(8); break;
+    case 16: FGR_SB(16); break;
+    default: set_error("fggc: unsupported neighbour count %d", n1); return FGR_E_INVALID;
+    }
+#undef FGR_SB
+    FGR_CUDA_TRY(cudaGetLastError());
+    return FGR_OK;
 }
 
 template <int D, bool FP64, int N1>

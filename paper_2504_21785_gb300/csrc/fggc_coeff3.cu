@@ -14,4 +14,7 @@ fgr_status launch_binned_d3(int n1, const BinLaunch &L, cudaStream_t st, const P
     default: set_error("fggc: no binned scatter for %d neighbours", n1); return FGR_E_INVALID;
     }
 }
+fgr_status launch_scatter_batch_d3(int n1, cudaStream_t st, const ScatterBatch64 *b64, const ScatterBatch32 *b32) {
+    return launch_scatter_batch_dim<3>(n1, st, b64, b32);
+}
 }  // namespace fgr

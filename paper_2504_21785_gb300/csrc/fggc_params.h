@@ -47,14 +47,14 @@ struct FggcBuffers {
     uint8_t *flags = nullptr;
     int2 *brange = nullptr;
     void *tables = nullptr;  // per-pass tables (node windows, point phases, tile bands)
-    void *bin = nullptr;     // binning buffers of the d >= 2 FP32 scatter (NULL: per-packet scatter)
+    void *bin = nullptr;     // binning buffers of the 3-D FP32 scatter (NULL: per-packet scatter)
     int64_t bin_m = 0;       // packets the binning buffers hold
     unsigned long long *terms = nullptr;  // node-point terms of the passes (timed calls only)
     void *fft = nullptr;      // DFT lines of the commensurate grid stage (box.fft_elems complex)
     void *twiddle = nullptr;  // e^{2 pi i j / N}, j < N / 2 <= 4096 (complex)
 };
 
-// Binning of the d >= 2 scatter (fggc_bin.cuh): key box of the outer anchor
+// Binning of the 3-D scatter (fggc_bin.cuh): key box of the outer anchor
 // cells (a0, b0) of dimensions 0..d-2 whose neighbours can reach the node box,
 // key = row-major index over (a0_0, b0_0, a0_1, b0_1).
 struct BinBox {
@@ -103,6 +103,50 @@ struct StageMarks {
     }
 };
 
+// Batched FGGC (fgr_reconstruct_fggc_batch): per-request parameters of one
+// launch over up to kBatchMax requests of one dimension; CTA b of the launch
+// belongs to the request r with block0[r] <= b < block0[r + 1].
+constexpr int kBatchMax = 32;
+
+struct ScatterBatchBase {
+    int n;
+    int block0[kBatchMax + 1];
+    Common c[kBatchMax];
+    const double *q[kBatchMax], *p[kBatchMax], *s[kBatchMax], *a[kBatchMax];
+    int64_t m[kBatchMax];
+    void *W[kBatchMax];
+    uint8_t *flags[kBatchMax];
+};
+struct ScatterBatch64 : ScatterBatchBase {
+    double vr[kMaxN1 * kMaxN1], vi[kMaxN1 * kMaxN1], inv_lam[kMaxN1];
+};
+struct ScatterBatch32 : ScatterBatchBase {
+    float cre[kMaxN1 * kCheb * kCheb], cim[kMaxN1 * kCheb * kCheb];
+};
+
+// One request of a batched FGGC call: its context, planned box and buffers,
+// bounds and overflow flag (device), packets and output (device).
+struct FggcRequest {
+    const fgr_ctx *ctx;
+    const FggcBox *box;
+    const FggcBuffers *buf;
+    int *bnd, *overflow;
+    PacketsDev pk;
+    void *u;
+};
+// Enqueues the requests (any dimensions, one precision and neighbour
+// strategy): per dimension and kBatchMax requests, one launch per stage.
+fgr_status run_fggc_batch(int n, const FggcRequest *req, cudaStream_t st);
+
+// Launches the batched per-packet coefficient + scatter kernel of dimension d
+// (grid: batch.block0[batch.n] CTAs of coeff_threads); exactly one batch is non-NULL.
+fgr_status launch_scatter_batch(int d, int n1, cudaStream_t st, const ScatterBatch64 *b64, const ScatterBatch32 *b32);
+fgr_status launch_scatter_batch_d1(int n1, cudaStream_t st, const ScatterBatch64 *b64, const ScatterBatch32 *b32);
+fgr_status launch_scatter_batch_d2(int n1, cudaStream_t st, const ScatterBatch64 *b64, const ScatterBatch32 *b32);
+fgr_status launch_scatter_batch_d3(int n1, cudaStream_t st, const ScatterBatch64 *b64, const ScatterBatch32 *b32);
+// Threads per CTA of the per-packet scatter kernel.
+int scatter_threads(bool fp64, int n1);
+
 // Box from the packets' node bounds hb[12] (per dimension: a min, a max, b min,
 // b max), widened by margin nodes on every side.
 fgr_status make_box(const fgr_ctx *ctx, const int *hb, int margin, FggcBox *box);
@@ -126,12 +170,12 @@ fgr_status launch_coeff_scatter_d2(int n1, cudaStream_t st, const PacketsDev &pk
                                    const Params32 *p32, void *W, uint8_t *flags);
 fgr_status launch_coeff_scatter_d3(int n1, cudaStream_t st, const PacketsDev &pk, const Params64 *p64,
                                    const Params32 *p32, void *W, uint8_t *flags);
-// The binned scatter (FP32, d = 2 or 3, n1 = 4 or 8): binning kernels, then
-// the binned kernel and the per-packet kernel over the loose list.
+// The binned scatter (FP32, d = 3, n1 = 4 or 8): binning kernels, then the
+// binned kernel and the per-packet kernel over the loose list.  (In 2-D a
+// packet has only 64 contributions and an outer cell reaches 8 rows: the
+// per-packet kernel is faster there, measured on the 2-D workload.)
 fgr_status launch_binned_scatter(int d, int n1, const BinLaunch &L, cudaStream_t st, const PacketsDev &pk,
                                  const Params32 &P, void *W, uint8_t *flags, StageMarks *marks);
-fgr_status launch_binned_d2(int n1, const BinLaunch &L, cudaStream_t st, const PacketsDev &pk, const Params32 &P,
-                            void *W, uint8_t *flags, StageMarks *marks);
 fgr_status launch_binned_d3(int n1, const BinLaunch &L, cudaStream_t st, const PacketsDev &pk, const Params32 &P,
                             void *W, uint8_t *flags, StageMarks *marks);
 

@@ -9,8 +9,8 @@
 // memory free up.  Requests of one method, dimension and precision that wait
 // together (device outputs) are admitted as one group of up to max_batch:
 // direct sums run as a single persistent launch (fgr_reconstruct_direct_batch),
-// FGGC reconstructions back to back on the worker's stream through plans
-// (fgr_reconstruct_fggc_planned) with one wait for the group.  Plans are
+// FGGC reconstructions through their plans in one fgr_reconstruct_fggc_batch
+// call (one launch per stage) with one wait for the group.  Plans are
 // cached per (packet set, grid, eps, options): registered sets never change,
 // so a plan's node box stays valid until the set is released, and its device
 // memory counts as resident within the budget.  A group that fails is retried
@@ -264,12 +264,45 @@ fgr_status run_one(fgr_server *S, const Job &job, const PacketSet &ps, CtxCache 
     return finish_one(S, job, ps, cache, stream, planned, st);
 }
 
-// FGGC group: the requests back to back on the stream, one wait.
+// FGGC group: the requests that have (or get) a plan in one
+// fgr_reconstruct_fggc_batch call, the others alone; one wait.
 void run_fggc_group(fgr_server *S, const Group &g, const std::vector<PacketSet> &ps, CtxCache &cache,
                     cudaStream_t stream, std::vector<fgr_status> &st) {
     const size_t n = g.size();
     std::vector<fgr_fggc_plan *> planned(n, nullptr);
-    for (size_t i = 0; i < n; ++i) st[i] = enqueue_one(S, *g[i], ps[i], cache, stream, &planned[i]);
+    std::vector<fgr_ctx *> bctx;
+    std::vector<fgr_fggc_plan *> bplan;
+    std::vector<fgr_packets> bpk(n);
+    std::vector<const fgr_packets *> bpkp;
+    std::vector<void *> bu;
+    std::vector<size_t> bidx;
+    for (size_t i = 0; i < n; ++i) {
+        fgr_ctx *ctx = nullptr;
+        st[i] = cache.get(g[i]->req, &ctx);
+        if (st[i] != FGR_OK) continue;
+        bpk[i] = packets_of(ps[i]);
+        planned[i] = acquire_plan(S, *g[i], ctx, bpk[i], stream);
+        if (!planned[i]) {
+            st[i] = fgr_reconstruct_fggc(ctx, &bpk[i], g[i]->req.u_out, stream);
+            continue;
+        }
+        const fgr_options &o = g[i]->req.opt, &o0 = bidx.empty() ? o : g[bidx[0]]->req.opt;
+        if (o.cq != o0.cq || o.cp != o0.cp || o.nq != o0.nq || o.np != o0.np || o.rcond != o0.rcond) {
+            // another neighbour strategy: not in this batch
+            st[i] = fgr_reconstruct_fggc_planned(ctx, planned[i], &bpk[i], g[i]->req.u_out, stream);
+            continue;
+        }
+        bctx.push_back(ctx);
+        bplan.push_back(planned[i]);
+        bpkp.push_back(&bpk[i]);
+        bu.push_back(g[i]->req.u_out);
+        bidx.push_back(i);
+    }
+    if (!bidx.empty()) {
+        const fgr_status rb = fgr_reconstruct_fggc_batch((int32_t)bidx.size(), bctx.data(), bplan.data(), bpkp.data(),
+                                                         bu.data(), stream);
+        for (size_t k = 0; k < bidx.size(); ++k) st[bidx[k]] = rb;
+    }
     const cudaError_t e = cudaStreamSynchronize(stream);
     for (size_t i = 0; i < n; ++i) {
         if (st[i] == FGR_OK && e != cudaSuccess) st[i] = FGR_E_CUDA;

@@ -108,6 +108,7 @@ SIGNATURES = {
     "fgr_reconstruct_direct_batch": (ctypes.c_int, [ctypes.c_int32, P(vp), P(P(fgr_packets)), P(vp), vp]),
     "fgr_fggc_plan_create": (ctypes.c_int, [vp, P(fgr_packets), ctypes.c_int32, P(vp), vp]),
     "fgr_reconstruct_fggc_planned": (ctypes.c_int, [vp, vp, P(fgr_packets), vp, vp]),
+    "fgr_reconstruct_fggc_batch": (ctypes.c_int, [ctypes.c_int32, P(vp), P(vp), P(P(fgr_packets)), P(vp), vp]),
     "fgr_fggc_plan_overflow": (ctypes.c_int, [vp, P(ctypes.c_int32)]),
     "fgr_fggc_plan_info": (ctypes.c_int, [vp, P(ctypes.c_int64), P(ctypes.c_int32)]),
     "fgr_fggc_plan_destroy": (None, [vp]),
@@ -316,6 +317,19 @@ def fgr_fggc_plan_create(ctx, packets: fgr_packets, margin: int = 2, stream=None
 def fgr_reconstruct_fggc_planned(ctx, plan, packets: fgr_packets, u_out, stream=None):
     return _check(load().fgr_reconstruct_fggc_planned(ctx, plan, ctypes.byref(packets), _ptr(u_out)[0],
                                                       _stream_handle(stream)))
+
+
+def fgr_reconstruct_fggc_batch(ctxs, plans, packets, u_outs, stream=None):
+    """len(ctxs) (<= 64) planned FGGC reconstructions, one launch per stage
+    for the requests of each dimension."""
+    n = len(ctxs)
+    if not (len(plans) == len(packets) == n == len(u_outs)):
+        raise ValueError("ctxs, plans, packets and u_outs must have the same length")
+    c_ctx = (vp * n)(*[getattr(c, "handle", c) for c in ctxs])
+    c_pl = (vp * n)(*plans)
+    c_pk = (P(fgr_packets) * n)(*[ctypes.pointer(p) for p in packets])
+    c_u = (vp * n)(*[_ptr(u)[0] for u in u_outs])
+    return _check(load().fgr_reconstruct_fggc_batch(n, c_ctx, c_pl, c_pk, c_u, _stream_handle(stream)))
 
 
 def fgr_fggc_plan_overflow(plan) -> bool:

@@ -1,16 +1,18 @@
-"""GPU parity of the binned FGGC scatter (d = 2, 3, FP32) against the FP64
+"""GPU parity of the binned FGGC scatter (3-D, FP32) against the FP64
 oracle's FGGC (Algorithm 2; eq. 2.24-2.25).
 
-The library bins packets by the anchor cell (a0, b0) of their outer
-dimensions and, for cells holding at least 32 packets, accumulates their
-contributions to each row of the node array in a private plane before adding
-it to the node array; cells with fewer packets take the per-packet kernel.
+In 3-D the library bins packets by the anchor cell (a0, b0) of their outer
+dimensions; for cells holding at least 32 packets a CTA lists which of the
+packets' inner neighbours land on each cell of the inner plane and sums every
+row of a cell in registers before adding it to the node array; cells with
+fewer packets take the per-packet kernel (as every 1-D and 2-D problem does).
 These packet sets put chosen numbers of packets into chosen outer cells, with
 random inner positions, so that every path runs: small cells (per-packet),
-cells of one and of several 256-packet items, inner spreads that fit one plane
-and ones that need several windows of it, and a momentum spread wider than a
-plane (per-contribution reductions inside the binned kernel).  The oracle
-evaluates at sampled grid points (1e-5, relative L2).
+cells of one and of several 256-packet items, inner spreads that fit one
+window of target cells and ones that need several, and a momentum spread
+wider than a window (per-contribution reductions inside the binned kernel).
+The same clustered sets in 2-D check the per-packet kernel on them.  The
+oracle evaluates at sampled grid points (1e-5, relative L2).
 """
 
 import math
@@ -74,9 +76,8 @@ def _grid(ns, lo=-math.pi, hi=math.pi):
 
 
 @pytest.mark.parametrize("inner_q,inner_p", [((-1.5, 1.5), (-1.0, 1.0)), ((-2.5, 2.5), (-3.0, 3.0))])
-def test_binned_2d(inner_q, inner_p):
-    # cells of 40 (one item), 300 and 700 (several items), 10 and 3 (per-packet);
-    # the second spread needs several plane windows
+def test_clustered_2d(inner_q, inner_p):
+    # the same cell sizes in 2-D, where the per-packet kernel runs
     eps = 1 / 64
     cells = [[(3, 5)], [(-4, 10)], [(0, 0)], [(7, -2)], [(-1, 1)]]
     pk, mesh = clustered(11, 2, eps, cells, [40, 300, 700, 10, 3], inner_q, inner_p)
@@ -85,6 +86,8 @@ def test_binned_2d(inner_q, inner_p):
 
 @pytest.mark.parametrize("inner_q,inner_p", [((-0.8, 0.8), (-0.5, 0.5)), ((-2.0, 2.0), (-2.0, 2.0))])
 def test_binned_3d(inner_q, inner_p):
+    # cells of 64 (one item), 300 and 600 (several items) and 20 (per-packet);
+    # the second spread needs several windows of target cells
     eps = 1 / 64
     cells = [[(2, 3), (-1, 4)], [(0, 0), (0, 0)], [(-5, 2), (6, -3)], [(1, 1), (1, 2)]]
     pk, mesh = clustered(12, 3, eps, cells, [64, 300, 600, 20], inner_q, inner_p)
@@ -92,32 +95,34 @@ def test_binned_3d(inner_q, inner_p):
 
 
 def test_binned_wide_momentum_takes_reductions_per_contribution():
-    # an inner momentum spread of more than 4096 p-nodes: the binned kernel
-    # cannot hold a line of its plane and adds each contribution itself
+    # an inner momentum spread of more than 2048 p-nodes: the binned kernel
+    # cannot hold one line of its target window and adds each contribution itself
     eps = 1 / 1024
-    cells = [[(2, 3)], [(-6, 40)]]
-    pk, mesh = clustered(13, 2, eps, cells, [100, 280], (-1.0, 1.0), (-30.0, 30.0))
-    _check(pk, mesh, _grid((300, 2048)), eps)
+    cells = [[(2, 3), (0, 1)], [(-6, 40), (3, -2)]]
+    pk, mesh = clustered(13, 3, eps, cells, [100, 280], (-0.5, 0.5), (-15.0, 15.0))
+    _check(pk, mesh, _grid((48, 40, 1024)), eps, npts=400)
 
 
-def test_binned_matches_per_packet_scatter_on_workload_like_cells():
-    # packets of a separable flow share outer cells by the hundred (as in the
-    # 2-D and 3-D workloads); the binned result equals the direct sum's within
-    # the least-squares error, and two calls agree to rounding
+def test_binned_matches_direct_sum_on_workload_like_cells():
+    # packets of a separable flow share outer cells by the dozen (as in the
+    # 3-D workload): a tensor product of outer cells with the same inner
+    # packets; the binned result equals the oracle's FGGC and the direct sum's
+    # within the least-squares error, and two calls agree to rounding
     eps = 1 / 256
     rng = np.random.default_rng(5)
-    mesh = mesh_for(2, eps)
-    q1 = (np.arange(-8, 8) + 0.37) * mesh.dq
-    p1 = (np.arange(-8, 8) + 0.61) * mesh.dp
-    Q0, P0 = np.meshgrid(q1, p1, indexing="ij")
-    inner_q = rng.uniform(-0.6, 0.6, 64)
-    inner_p = rng.uniform(-0.5, 0.5, 64)
-    q = np.stack([np.repeat(Q0.ravel(), 64), np.tile(inner_q, Q0.size)])
-    p = np.stack([np.repeat(P0.ravel(), 64), np.tile(inner_p, P0.size)])
+    mesh = mesh_for(3, eps)
+    qa = (np.arange(-1, 1) + 0.37) * mesh.dq
+    pa = (np.arange(-2, 2) + 0.61) * mesh.dp
+    Q0, P0, Q1, P1 = (x.ravel() for x in np.meshgrid(qa, pa, qa, pa, indexing="ij"))
+    n_in = 48
+    inner_q = rng.uniform(-0.4, 0.4, n_in)
+    inner_p = rng.uniform(-0.3, 0.3, n_in)
+    q = np.stack([np.repeat(Q0, n_in), np.repeat(Q1, n_in), np.tile(inner_q, Q0.size)])
+    p = np.stack([np.repeat(P0, n_in), np.repeat(P1, n_in), np.tile(inner_p, Q0.size)])
     m = q.shape[1]
     pk = {"q": q, "p": p, "s": rng.uniform(-1, 1, m), "a": rng.standard_normal((2, m))}
-    grid = _grid((256, 256), lo=-1.5, hi=1.5)
-    got = _check(pk, mesh, grid, eps, npts=800, seed=3)
+    grid = _grid((40, 40, 64), lo=-1.0, hi=1.0)
+    got = _check(pk, mesh, grid, eps, npts=500, seed=3)
     again = _gpu.reconstruct("fggc", pk, grid, eps, _gpu.options("fp32"))
     direct = _gpu.reconstruct("direct", pk, grid, eps, _gpu.options("fp32"))
     assert _gpu.rel_l2(again, got) <= 1e-6

@@ -8,9 +8,11 @@ Oracle inputs come from the oracle or from closed forms pinned against it:
   4194304 packets from them.
 * 3-D (V = |x|^2/2): the harmonic closed form of eq. 2.3-2.7 (pinned in
   tests/test_oracle_trajectories.py).
-The oracle evaluates the direct sum at sampled grid points; FGGC is compared
-with the GPU direct sum on the full grid and with the oracle's FGGC on a
-packet subset.
+The oracle evaluates the direct sum at sampled grid points (3-D: 1024 points
+in 4 x 4 boxes on tile edges, faces, corners and random places, each box over
+the packets whose windows reach it); FGGC is compared with the GPU direct sum
+on the full grid, with the oracle's direct sum at the points and with the
+oracle's FGGC of a packet subset.
 """
 
 import math
@@ -112,9 +114,88 @@ def test_config3_full_size():
     _check_reconstruction(w, prop, n_points=256, subset=20000)
 
 
+def _boxes_3d(n, seed):
+    """64 boxes of 4 x 4 points (fixed i0; i1, i2 consecutive) = 1024 points:
+    the edges of the direct sum's 8 x 8 x 16 tiles and of the grid passes'
+    32- and 128-point tiles where the wave lives (indices 88..208 of 256), the
+    grid's first and last points, and random places in the wave."""
+    rng = np.random.default_rng(seed)
+    edges = [88, 95, 96, 111, 112, 127, 128, 143, 144, 159, 160, 175, 176, 191, 192, 207]
+    out = []
+    for k in range(64):
+        if k < 44:
+            i0 = edges[k % len(edges)]
+            s1 = edges[(3 * k + 1) % len(edges)] - 2
+            s2 = edges[(5 * k + 2) % len(edges)] - 2
+        elif k < 48:  # faces and corners of the grid
+            i0, s1, s2 = [(0, 0, 0), (n - 1, n - 4, n - 4), (128, 0, n - 4), (n - 1, 126, 126)][k - 44]
+        else:
+            i0, s1, s2 = (int(x) for x in rng.integers(90, 200, 3))
+        out.append((i0, s1, s2))
+    return out
+
+
+def _box_points(box):
+    i0, s1, s2 = box
+    a, b = np.meshgrid(np.arange(s1, s1 + 4), np.arange(s2, s2 + 4), indexing="ij")
+    return np.stack([np.full(16, i0), a.ravel(), b.ravel()])
+
+
+def _windows(pk, grid, eps, R):
+    """Per dimension the window bounds of every packet (fga.window_bounds)."""
+    return [tuple(x.astype(np.int32) for x in fga.window_bounds(pk["q"][l], grid, l, eps, R))
+            for l in range(grid["d"])]
+
+
+def _box_subset(pk, win, box):
+    """The packets (or on-grid cells) whose windows reach the box: the
+    oracle's sum at the box's points over them equals its sum over all
+    packets (the others contribute exact zeros)."""
+    i0, s1, s2 = box
+    keep = np.ones(pk["s"].size, dtype=bool)
+    for (m_lo, m_hi), (lo_i, hi_i) in zip(win, ((i0, i0), (s1, s1 + 3), (s2, s2 + 3))):
+        keep &= (m_lo <= hi_i) & (m_hi >= lo_i)
+    return {k: np.ascontiguousarray(pk[k][..., keep]) for k in ("q", "p", "s", "a")}
+
+
 def test_config4_full_size():
     w = config_workload(4)
     prop = _harmonic_flow(w["packets"], w["t"])
     rng = np.random.default_rng(3)
     _check_propagation(w, prop, rng.choice(prop["s"].size, size=20000, replace=False))
-    _check_reconstruction(w, prop, n_points=48, subset=4000)
+    grid, eps, mesh = w["grid"], w["eps"], w["mesh"]
+    got_d = _gpu.reconstruct("direct", prop, grid, eps, _gpu.options("fp32"))
+    got_f = _gpu.reconstruct("fggc", prop, grid, eps, _gpu.options("fp32"))
+    # FGGC against the direct sum it replaces, on the full grid
+    assert _gpu.rel_l2(got_f, got_d) <= 1e-5
+    boxes = _boxes_3d(grid["n"][0], 4)
+    pts = np.concatenate([_box_points(b) for b in boxes], axis=1)
+    # the oracle's direct sum at 1024 points (tile edges, faces, corners, random)
+    # the packets are the kept part of a tensor product of per-dimension (q, p)
+    # lists and the harmonic flow acts on each dimension alone, so the oracle's
+    # direct sum is evaluated in its factorised form (fga.direct_sum_tensor)
+    from workloads import workload_axes
+    from workloads.wkb import _FAMILIES, _amplitude_table_1d
+    axes0, sel = workload_axes(w)
+    t = w["t"]
+    ct, st = math.cos(t), math.sin(t)
+    axes, amps, acts = [], [], []
+    for l, (q, p) in enumerate(axes0):
+        _, _, al = _amplitude_table_1d(_FAMILIES[w["family"]], l, mesh, w["nq"], w["np_"])
+        axes.append((q * ct + p * st, -q * st + p * ct))
+        acts.append((p ** 2 - q ** 2) * math.sin(2 * t) / 4 - q * p * st * st)
+        amps.append(al.ravel())
+    ref_d = fga.direct_sum_tensor(axes, amps, acts, sel, grid, eps, mesh.dq, mesh.dp, pts, R=6,
+                                  phase=np.exp(-0.5j * 3 * t))
+    assert _gpu.rel_l2(got_d[tuple(pts)], ref_d) <= 1e-5
+    assert _gpu.rel_l2(got_f[tuple(pts)], ref_d) <= 1e-5
+    # the oracle's FGGC (Algorithm 2) of a 4000-packet subset at the same points
+    sel = np.sort(rng.choice(prop["s"].size, size=4000, replace=False))
+    sub = {k: np.ascontiguousarray(v[..., sel]) for k, v in prop.items() if k in "qpsa"}
+    na, nb, W = fggc.aggregate(sub, eps, mesh.dq, mesh.dp, lsa.Strategy(nq=4, np_=2))
+    cells = fggc.on_grid_packets(na, nb, W, mesh.dq, mesh.dp)
+    cwin = _windows(cells, grid, eps, 6)
+    ref_f = np.concatenate([fga.direct_sum(_box_subset(cells, cwin, b), grid, eps, mesh.dq, mesh.dp, R=6,
+                                           points=_box_points(b)) for b in boxes])
+    got_fs = _gpu.reconstruct("fggc", sub, grid, eps, _gpu.options("fp32"))
+    assert _gpu.rel_l2(got_fs[tuple(pts)], ref_f) <= 1e-5

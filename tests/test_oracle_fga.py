@@ -116,3 +116,29 @@ def test_direct_sum_3d_is_the_definition():
         ref += A * np.exp(1j * pk["s"][j] / eps) * fga.gaussian_packet(X, pk["q"][:, j], pk["p"][:, j], eps)
     ref *= fga.prefactor(3, eps, mesh.dq, mesh.dp)
     assert np.max(np.abs(ub.reshape(-1) - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_direct_sum_tensor_equals_direct_sum_on_the_expanded_packets():
+    # a random selection of a 3-D tensor product of per-dimension lists, with
+    # per-dimension amplitudes and actions: the factorised evaluation equals the
+    # plain sum over the expanded packets (a transposed operand, a dropped
+    # action or a wrong window would not)
+    from oracle.fga import direct_sum, direct_sum_tensor
+    rng = np.random.default_rng(17)
+    d, L, eps = 3, 7, 1 / 64
+    axes = [(np.sort(rng.uniform(-0.6, 0.6, L)), rng.uniform(-1, 1, L)) for _ in range(d)]
+    amps = [rng.standard_normal(L) + 1j * rng.standard_normal(L) for _ in range(d)]
+    acts = [rng.uniform(-0.5, 0.5, L) for _ in range(d)]
+    sel = np.sort(rng.choice(L ** d, size=200, replace=False))
+    idx = np.stack(np.unravel_index(sel, (L,) * d))
+    phase = np.exp(-0.7j)
+    A = phase * np.prod([amps[l][idx[l]] for l in range(d)], axis=0)
+    pk = {"q": np.stack([axes[l][0][idx[l]] for l in range(d)]), "p": np.stack([axes[l][1][idx[l]] for l in range(d)]),
+          "s": np.sum([acts[l][idx[l]] for l in range(d)], axis=0), "a": np.stack([A.real, A.imag])}
+    grid = dict(d=3, n=[24, 20, 28], lo=[-1.0] * 3, hi=[1.0] * 3)
+    pts = np.stack([rng.integers(0, n, 60) for n in grid["n"]])
+    dq, dp = 0.0625, 0.05
+    ref = direct_sum(pk, grid, eps, dq, dp, R=6, points=pts)
+    got = direct_sum_tensor(axes, amps, acts, sel, grid, eps, dq, dp, pts, R=6, phase=phase)
+    assert np.count_nonzero(ref) > 30
+    assert np.linalg.norm(got - ref) <= 1e-13 * np.linalg.norm(ref)
