@@ -44,7 +44,9 @@ def _requests(fgr, prec, count, seed):
         mesh = mesh_for(d, eps)
         m = int(rng.integers(200, 3000)) if d == 1 else (int(rng.integers(100, 600)) if d == 2 else 150)
         n = int(2 ** rng.integers(9, 12)) if d == 1 else ((48, 56) if d == 2 else (20, 24, 28))
-        pk = random_packets(300 + r, d, m, q_range=(-2.2, 2.2), p_range=(-2, 2), s_range=(-1, 1), mesh=mesh)
+        lim = (2.2, 2.0) if d < 3 else (0.3, 0.3)   # 3-D: a compact node box
+        pk = random_packets(300 + r, d, m, q_range=(-lim[0], lim[0]), p_range=(-lim[1], lim[1]), s_range=(-1, 1),
+                            mesh=mesh)
         grid = _grid(d, n)
         ctx = fgr.Context(d, grid, eps, _gpu.options(prec))
         arrs = _gpu.to_device(pk)
