@@ -606,9 +606,13 @@ fgr_status fgr_create(int32_t d, const fgr_grid *grid, double eps, const fgr_opt
         if (e == cudaSuccess) e = device_pool(c->device, &c->pool);
         char *slot = nullptr;
         if (e == cudaSuccess) e = pinned_slot(&slot);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&c->dev_err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(c->dev_err, 0, sizeof(int));
         if (e != cudaSuccess) {
             set_error("CUDA initialisation failed: %s", cudaGetErrorString(e));
             cudaGetLastError();
+            if (slot) release_pinned_slot(slot);
+            if (c->dev_err) cudaFree(c->dev_err);
             delete c;
             return FGR_E_CUDA;
         }
@@ -625,6 +629,10 @@ void fgr_destroy(fgr_ctx *ctx) {
     // copied at launch, scratch returns to the pool in stream order), and every
     // call that uses the pinned slot waits for it before returning.
     release_pinned_slot((char *)ctx->host_pinned);
+    if (ctx->dev_err) {
+        cudaSetDevice(ctx->device);
+        cudaFree(ctx->dev_err);
+    }
     delete ctx;
 }
 

@@ -26,6 +26,9 @@
 // nodes a whose window covers them, g in registers, W staged through shared
 // memory in chunks of b, and e^{i b dp x/eps} generated per (m, b) from a
 // phase reduced in FP64.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <climits>
 #include <memory>
 #include <vector>
@@ -396,6 +399,8 @@ __device__ __forceinline__ void grid_pass_body(const void *__restrict__ in_v, vo
     }
 }
 
+#include "fggc_tma.cuh"
+
 template <bool FP64, int MAXBAND, int TP>
 __global__ void __launch_bounds__(TP) grid_pass_kernel(const void *__restrict__ in_v, void *__restrict__ out_v,
                                                        PassParams pp, const uint8_t *__restrict__ flags,
@@ -510,10 +515,43 @@ fgr_status launch_brange(const void *in, int64_t rows, int A, int B, int2 *out, 
 // float2 units): node windows, point phases and tile bands (at most N / 32 + 1).
 inline int64_t pass_table_entries(int64_t A, int64_t N) { return A + N + N / 32 + 1; }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); nullptr when unavailable.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// Tensor map of a pass input (complex64) as lines x B cells, box kTB cells x
+// band lines.  False when the input does not meet the copy engine's rules
+// (16-byte aligned base, 16-byte multiple line stride) or encoding fails.
+bool pass_tensor_map(const void *in, const PassParams &pp, int band_lines, CUtensorMap *map) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    const int64_t lines = pp.rows * (int64_t)pp.A;
+    if (!enc || ((uintptr_t)in & 15) || (pp.B & 1) || lines >= INT_MAX - 64 || pp.B < 2) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)pp.B, (cuuint64_t)lines};
+    const cuuint64_t strides[1] = {(cuuint64_t)pp.B * 8};
+    const cuuint32_t box[2] = {(cuuint32_t)kTB, (cuuint32_t)band_lines};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void *>(in), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <bool FP64>
 fgr_status launch_pass(const void *in, void *out, const PassParams &pp, const uint8_t *flags,
                        const int2 *brange, int64_t target_ctas, int tile_pref, void *tables,
-                       cudaStream_t st, StageMarks *before_pass = nullptr) {
+                       cudaStream_t st, StageMarks *before_pass = nullptr, int *err = nullptr) {
     if (pp.rows == 0 || pp.N == 0) return FGR_OK;
     if (pp.rows > INT_MAX) {
         set_error("fggc: too many rows in a grid pass");
@@ -553,7 +591,16 @@ fgr_status launch_pass(const void *in, void *out, const PassParams &pp, const ui
     else if (band <= 32) FGR_PASS(32, TPV);                                                                 \
     else if (band <= 48) FGR_PASS(48, TPV);                                                                 \
     else FGR_PASS(64, TPV);  // wider bands are processed in chunks of 64
-    if (tp == 32) {
+    CUtensorMap map, map_half;
+    const int box_lines = band <= 16 ? 16 : 32;
+    if (!FP64 && tp == 32 && splits == 1 && err && pass_tensor_map(in, pp, box_lines, &map) &&
+        pass_tensor_map(in, pp, box_lines / 2, &map_half)) {
+        // 32-point tiles with the node tiles staged by the copy engine
+        if (band <= 16)
+            grid_pass_tma_kernel<16><<<grid, 32, 0, st>>>(map, map_half, out, pp, flags, brange, tab, err);
+        else
+            grid_pass_tma_kernel<32><<<grid, 32, 0, st>>>(map, map_half, out, pp, flags, brange, tab, err);
+    } else if (tp == 32) {
         // narrow tiles: at most 32 band factors in registers (wider bands in
         // chunks of 32), so that more warps fit an SM
         if (band <= 16) FGR_PASS(16, 32);
@@ -721,7 +768,8 @@ fgr_status make_box(const fgr_ctx *ctx, const int *hb, int margin, FggcBox *box)
         c.amin[l] = alo;
         c.A[l] = ahi - alo + 1;
         c.bmin[l] = hb[l * 4 + 2] - margin;
-        c.B[l] = hb[l * 4 + 3] - hb[l * 4 + 2] + 1 + 2 * margin;
+        // an even b extent keeps every line 16-byte aligned (tile copies)
+        c.B[l] = (hb[l * 4 + 3] - hb[l * 4 + 2] + 1 + 2 * margin + 1) & ~1;
         cells *= (int64_t)c.A[l] * c.B[l];
         if (cells > (int64_t(1) << 36)) {
             set_error("fggc: node array of more than 2^36 cells");
@@ -1059,9 +1107,9 @@ fgr_status enqueue_fggc(fgr_ctx *ctx, const PacketsDev &pk, const FggcBox &box, 
             ++*launches;  // twiddles + DFT + contraction (tables and pass counted below)
         } else {
             r = fp64 ? launch_pass<true>(cur, dst, pp, fl, b.brange, target, ctx->tune.pass_tile, b.tables, st,
-                                         &before)
+                                         &before, ctx->dev_err)
                      : launch_pass<false>(cur, dst, pp, fl, b.brange, target, ctx->tune.pass_tile, b.tables, st,
-                                          &before);
+                                          &before, ctx->dev_err);
         }
         if (r != FGR_OK) return r;
         *launches += 2;  // tables + pass
@@ -1103,7 +1151,15 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
     if (r != FGR_OK) return r;
     launches += pk.m > 0 ? 2 : 1;
     FGR_CUDA_TRY(cudaMemcpyAsync(ctx->host_pinned, bnd, sizeof(int) * 12, cudaMemcpyDeviceToHost, st));
+    int *herr = reinterpret_cast<int *>(ctx->host_pinned) + 16;
+    FGR_CUDA_TRY(cudaMemcpyAsync(herr, ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     FGR_CUDA_TRY(cudaStreamSynchronize(st));
+    if (*herr) {  // a grid pass of an earlier call gave up waiting for its tile copies
+        FGR_CUDA_TRY(cudaMemsetAsync(ctx->dev_err, 0, sizeof(int), st));
+        set_error("fggc: a grid pass of an earlier call on this context timed out waiting for its tile copies; "
+                  "that call's output is incomplete");
+        return FGR_E_TIMEOUT;
+    }
     int hb[12];
     memcpy(hb, ctx->host_pinned, sizeof(hb));
     FggcBox box;

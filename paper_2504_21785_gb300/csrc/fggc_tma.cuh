@@ -1,0 +1,216 @@
+// K5 grid pass (FP32, 32-point tiles) with the node-array tiles staged by the
+// tensor memory accelerator: the pass input, viewed as a 2-D tensor of
+// (row, a) lines by B cells, is read in boxes of 32 b-cells x MAXBAND lines by
+// cp.async.bulk.tensor into two shared-memory buffers that alternate, so the
+// next tile's copy overlaps the current tile's arithmetic (one warp per CTA:
+// lane 0 issues the copies, every lane waits on the buffer's mbarrier).
+// Same arithmetic as grid_pass_body.  Waits are bounded: a copy that does not
+// complete within the limit sets *err and the CTA returns.
+// Included by fggc.cu inside its anonymous namespace, after grid_pass_body
+// (fggc.cu includes <cuda.h> for CUtensorMap).
+#pragma once
+
+constexpr unsigned kTmaWaitLimit = 1u << 26;  // polls of an mbarrier before giving up
+constexpr int kTB = 16;                       // b cells per staged tile (a 128-byte row per line)
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// true once the barrier has completed the phase of parity `phase`
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// 2-D tile copy global -> shared, completion counted on bar (bytes)
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_addr(dst)),
+        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Bounded wait of the whole warp on a buffer's barrier (the outcome is the
+// same for every lane); false, and *err set, if it timed out.
+__device__ __forceinline__ bool tma_wait(uint64_t *bar, unsigned phase, int *err) {
+    for (unsigned it = 0; it < kTmaWaitLimit; ++it) {
+        if (__all_sync(0xffffffffu, mbar_try_wait(bar, phase))) return true;
+        if (it > 64) __nanosleep(64);
+    }
+    if ((threadIdx.x & 31) == 0) atomicExch(err, 1);
+    return false;
+}
+
+// map: boxes of MAXBAND lines; map_half: boxes of MAXBAND / 2 lines, for a
+// last band chunk that needs no more (half the copy)
+template <int MAXBAND>
+__global__ void __launch_bounds__(32) grid_pass_tma_kernel(const __grid_constant__ CUtensorMap map,
+                                                           const __grid_constant__ CUtensorMap map_half,
+                                                           void *__restrict__ out_v, PassParams pp,
+                                                           const uint8_t *__restrict__ flags,
+                                                           const int2 *__restrict__ brange, const PassTables tab,
+                                                           int *__restrict__ err) {
+    constexpr int TP = 32;
+    __shared__ __align__(128) float2 sw[2][MAXBAND][kTB];
+    __shared__ __align__(8) uint64_t bar[2];
+    const int lane = threadIdx.x;
+    const int64_t row = blockIdx.x;
+    const int tile = blockIdx.y;
+    const int64_t m = (int64_t)tile * TP + lane;
+    const bool valid = m < pp.N;
+    float2 *out = reinterpret_cast<float2 *>(out_v) + row * pp.N;
+    const int2 bnd = tab.band[tile];
+    const int a_lo = bnd.x, a_hi = bnd.y;
+    const int nb_total = a_hi - a_lo + 1;
+    int ulo = 0, uhi = pp.B - 1;
+    if (brange && nb_total > 0) {
+        int lo = INT_MAX, hi = INT_MIN;
+        for (int i = lane; i < nb_total; i += TP) {
+            const int2 r = brange[row * (int64_t)pp.A + (a_lo - pp.amin) + i];
+            lo = min(lo, r.x);
+            hi = max(hi, r.y);
+        }
+        ulo = __reduce_min_sync(0xffffffffu, lo);
+        uhi = __reduce_max_sync(0xffffffffu, hi);
+    }
+    if ((flags && !flags[row]) || ulo > uhi || nb_total <= 0) {
+        if (valid) out[m] = make_float2(0.f, 0.f);
+        return;
+    }
+    // tiles (band chunk, b chunk); b chunks start at even cells (16-byte TMA
+    // coordinates); the cell before an odd ulo is zero in every line of the band
+    const int b_start = ulo & ~1;
+    const int nbc = (uhi - b_start + kTB) / kTB;
+    const int nac = (nb_total + MAXBAND - 1) / MAXBAND;
+    const int ntiles = nac * nbc;
+    const int64_t line0 = row * (int64_t)pp.A + (a_lo - pp.amin);
+    constexpr unsigned kBytes = MAXBAND * kTB * sizeof(float2);
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async_smem();
+    }
+    __syncwarp();
+    auto issue = [&](int t) {
+        const int ac = t / nbc, bc = t - ac * nbc;
+        const bool half = nb_total - ac * MAXBAND <= MAXBAND / 2;
+        mbar_expect_tx(&bar[t & 1], half ? kBytes / 2 : kBytes);
+        tma_load_2d(&sw[t & 1][0][0], half ? &map_half : &map, b_start + bc * kTB, (int)(line0 + ac * MAXBAND),
+                    &bar[t & 1]);
+    };
+    if (lane == 0) {
+        issue(0);
+        if (ntiles > 1) issue(1);
+    }
+    const double xm = grid_x(pp.lo, pp.h, valid ? m : (int64_t)tile * TP);
+    const float2 ph = tab.ph[valid ? m : (int64_t)tile * TP];
+    const float cef = (float)(pp.neg_half_inv_eps * 1.4426950408889634);  // log2(e) / (-2 eps)
+    const float dqf = (float)pp.dq;
+    float accr = 0.f, acci = 0.f;
+    double totr = 0.0, toti = 0.0;
+    float g[MAXBAND];
+    int nb = 0;
+    unsigned phase[2] = {0u, 0u};
+    for (int t = 0; t < ntiles; ++t) {
+        const int ac = t / nbc, bc = t - ac * nbc;
+        if (bc == 0) {  // Gaussian factors of this band chunk
+            const int a_first = a_lo + ac * MAXBAND;
+            nb = min(MAXBAND, nb_total - ac * MAXBAND);
+            const double dx0 = xm - (double)a_first * pp.dq;
+            // node windows: one coalesced load, then broadcast by shuffles
+            const int2 wl = lane < nb ? tab.win[a_first - pp.amin + lane] : make_int2(1, 0);
+#pragma unroll
+            for (int i = 0; i < MAXBAND; ++i) {
+                const int wx = __shfl_sync(0xffffffffu, wl.x, i), wy = __shfl_sync(0xffffffffu, wl.y, i);
+                g[i] = 0.f;
+                if (i < nb && valid && m >= wx && m <= wy) {
+                    const float dxf = (float)dx0 - (float)i * dqf;
+                    g[i] = ex2_approx(dxf * dxf * cef);
+                }
+            }
+        }
+        const int s = t & 1;
+        if (!tma_wait(&bar[s], phase[s], err)) {
+            // leave only after this CTA's copies in flight have landed (bounded)
+            tma_wait(&bar[s], phase[s], err);
+            if (t + 1 < ntiles) tma_wait(&bar[(t + 1) & 1], phase[(t + 1) & 1], err);
+            return;
+        }
+        phase[s] ^= 1u;
+        const int b0 = b_start + bc * kTB;
+        const int nbb = min(kTB, uhi + 1 - b0);
+        if (nbb & 1) {  // the pair partner past the range must read zero
+            for (int i = lane; i < MAXBAND; i += TP) sw[s][i][nbb] = make_float2(0.f, 0.f);
+            __syncwarp();
+        }
+        // four b values at a time (eight independent accumulator chains); the
+        // b values past the range read zero (padding) or are skipped
+        for (int bb = 0; bb < nbb; bb += 4) {
+            float vr[4] = {0.f, 0.f, 0.f, 0.f}, vi[4] = {0.f, 0.f, 0.f, 0.f};
+            const bool two = bb + 2 < nbb;  // the second pair holds a b of the range
+#pragma unroll
+            for (int i = 0; i < MAXBAND; ++i) {
+                if (i < nb) {
+                    const float4 w = *reinterpret_cast<const float4 *>(&sw[s][i][bb]);
+                    vr[0] = fmaf(g[i], w.x, vr[0]);
+                    vi[0] = fmaf(g[i], w.y, vi[0]);
+                    vr[1] = fmaf(g[i], w.z, vr[1]);
+                    vi[1] = fmaf(g[i], w.w, vi[1]);
+                    if (two) {
+                        const float4 w2 = *reinterpret_cast<const float4 *>(&sw[s][i][bb + 2]);
+                        vr[2] = fmaf(g[i], w2.x, vr[2]);
+                        vi[2] = fmaf(g[i], w2.y, vi[2]);
+                        vr[3] = fmaf(g[i], w2.z, vr[3]);
+                        vi[3] = fmaf(g[i], w2.w, vi[3]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (u >= 2 && !two) break;
+                const float bf = (float)(pp.bmin + b0 + bb + u);
+                float f = bf * ph.x;
+                f -= rint_fast(f);
+                float tau = fmaf(bf, ph.y, f);
+                tau -= rint_fast(tau);
+                float sn, cs;
+                __sincosf(6.283185307179586f * tau, &sn, &cs);
+                accr += cs * vr[u] - sn * vi[u];
+                acci += cs * vi[u] + sn * vr[u];
+            }
+        }
+        totr += (double)accr;
+        toti += (double)acci;
+        accr = acci = 0.f;
+        // the buffer is free again: refill it with tile t + 2
+        __syncwarp();
+        if (lane == 0 && t + 2 < ntiles) {
+            fence_proxy_async_smem();
+            issue(t + 2);
+        }
+    }
+    if (valid) out[m] = make_float2((float)totr, (float)toti);
+}

@@ -78,6 +78,7 @@ struct fgr_ctx {
     fgr::Timing timing;
     fgr::Tuning tune;
     int fft_logn[fgr::kMaxDim] = {0, 0, 0};  // log2 N of the DFT grid stage per dimension (0: direct stage)
+    int *dev_err = nullptr;          // device word: a kernel's bounded wait gave up (reported by the next call)
     int64_t *host_pinned = nullptr;  // small pinned buffer for device->host sizes
 };
 
