@@ -457,22 +457,39 @@ __global__ void brange_kernel(const C2 *__restrict__ in, int64_t lines, int B, i
     brange_body<C2>(in, lines, B, out, blockIdx.x);
 }
 
-// The same for short lines (B <= 64): one thread per line, so a warp streams
-// 32 consecutive lines instead of leaving most of its lanes idle.
+// The same for short lines (B <= 64): a warp scans 32 consecutive lines as
+// one contiguous span, lane by lane through consecutive cells (coalesced
+// loads), and folds each cell into its line's range in shared memory.
 template <class C2>
-__global__ void brange_short_kernel(const C2 *__restrict__ in, int64_t lines, int B, int2 *__restrict__ out) {
-    const int64_t line = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (line >= lines) return;
-    const C2 *p = in + line * (int64_t)B;
-    int lo = B, hi = -1;
-    for (int b = 0; b < B; ++b) {
-        const C2 v = p[b];
-        if (v.x != 0 || v.y != 0) {
-            lo = min(lo, b);
-            hi = b;
+__global__ void __launch_bounds__(256) brange_short_kernel(const C2 *__restrict__ in, int64_t lines, int B,
+                                                           int2 *__restrict__ out) {
+    __shared__ int s_lo[256], s_hi[256];
+    const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
+    const int64_t line0 = blockIdx.x * (int64_t)blockDim.x + wbase;  // first line of this warp
+    s_lo[threadIdx.x] = B;
+    s_hi[threadIdx.x] = -1;
+    __syncwarp();
+    if (line0 < lines) {
+        const int nl = (int)(lines - line0 < 32 ? lines - line0 : 32);
+        const C2 *p = in + line0 * (int64_t)B;
+        const int cells = nl * B;
+        int l = lane / B, b = lane - l * B;  // line and cell of element e = lane
+        for (int e = lane; e < cells; e += 32) {
+            const C2 v = p[e];
+            if (v.x != 0 || v.y != 0) {
+                atomicMin(&s_lo[wbase + l], b);
+                atomicMax(&s_hi[wbase + l], b);
+            }
+            b += 32;  // advance by 32 cells
+            while (b >= B) {
+                b -= B;
+                ++l;
+            }
         }
     }
-    out[line] = make_int2(lo, hi);
+    __syncwarp();
+    const int64_t line = line0 + lane;
+    if (line < lines) out[line] = make_int2(s_lo[threadIdx.x], s_hi[threadIdx.x]);
 }
 
 // Node-point terms of one pass (timing only): over the (row, a) lines, the
@@ -643,13 +660,16 @@ fgr_status launch_fft_pass(const void *in, void *out, const PassParams &pp, cons
     }
     fft_twiddle_kernel<C2><<<(unsigned)((N / 2 + 255) / 256), 256, 0, st>>>(N, (C2 *)twiddle);
     if (before_pass) before_pass->binned();
-    const size_t smem = sizeof(C2) * (size_t)N;
+    const int lpc = dft_lines_per_cta(logn);
+    const size_t smem = sizeof(C2) * (size_t)N * lpc;
     if (smem > 48 * 1024)
         FGR_CUDA_TRY(cudaFuncSetAttribute(dft_lines_kernel<FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
     const double th = pp.phi_scale * pp.lo;  // dp lo / (2 pi eps), turns per unit b
-    dft_lines_kernel<FP64><<<(unsigned)(pp.rows * pp.A), 256, smem, st>>>(in, F, pp.rows, pp.A, pp.B, pp.bmin, th,
-                                                                          logn, brange, flags, twiddle);
+    const int64_t lines = pp.rows * (int64_t)pp.A;
+    dft_lines_kernel<FP64><<<(unsigned)((lines + lpc - 1) / lpc), 256, smem, st>>>(in, F, pp.rows, pp.A, pp.B,
+                                                                                   pp.bmin, th, logn, brange, flags,
+                                                                                   twiddle);
     band_fft_kernel<FP64><<<dim3((unsigned)pp.rows, (unsigned)mtiles), tp, 0, st>>>(F, out, pp, logn, tab);
     FGR_CUDA_TRY(cudaGetLastError());
     return FGR_OK;

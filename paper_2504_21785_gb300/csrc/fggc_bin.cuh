@@ -149,16 +149,16 @@ __device__ __forceinline__ void coeff_dim32_rolled(const Params32 &P, double Q, 
 }
 
 // Target cells of one window (node cells of the inner plane).
-constexpr int kWinCells = 2048;
+constexpr int kWinCells = 1024;
 
 template <int D, int N1>
 __host__ __device__ constexpr int binned_smem_bytes() {
     return kBinT * D * N1 * 8      // coefficients [packet][dimension][neighbour] (float2)
-           + kBinT * N1 * 8        // entry values w c_{d-1}[k] (float2)
+           + kBinT * 8             // packet weights w (float2)
            + 2 * kWinCells * 4     // per-cell entry start and cursor (int)
            + kWinCells * 4         // active cells (packed line, column)
            + (D == 3 ? N1 * N1 : N1) * 8  // W offsets of the rows (int64)
-           + kBinT * N1;           // entry packets (uint8)
+           + kBinT * N1 * 2;       // entries (packet << 4 | neighbour), uint16
 }
 
 __device__ __forceinline__ int2 block_exclusive_scan(int2 v, int2 *total);
@@ -169,29 +169,29 @@ __device__ __forceinline__ int2 block_exclusive_scan(int2 v, int2 *total);
 // sum over its entries (packet j, inner neighbour k) of
 //   w_j c_{d-1,j}[k] * c_{0,j}[k0] (* c_{1,j}[k1]).
 // Per item (and window of whole inner q-node lines of the target box) the CTA
-// lists every target cell's entries (a CSR built once, with the entry values
-// w_j c_{d-1,j}[k]); then each thread takes a cell, accumulates all rows of it
+// lists every target cell's entries (a CSR built once); then each thread takes
+// a cell (and a pass over part of the k0 values), accumulates those rows of it
 // in registers as a sum of outer products over its entries, and adds each row's
 // value to W with one 8-byte reduction (consecutive threads: consecutive cells
 // of the row).  No floating-point atomics in shared memory.
 template <int D, int N1>
-__global__ void __launch_bounds__(kBinT, 2) binned_scatter_kernel(
+__global__ void __launch_bounds__(kBinT, 3) binned_scatter_kernel(
     const double *__restrict__ q, const double *__restrict__ p, const double *__restrict__ s,
     const double *__restrict__ a, int64_t m, const __grid_constant__ Params32 P, const BinBox bb,
     const int *__restrict__ sorted, const int4 *__restrict__ items, const int2 *__restrict__ off_end,
     int *__restrict__ work, float2 *__restrict__ W, uint8_t *__restrict__ row_flag) {
     constexpr int NR = D == 3 ? N1 * N1 : N1;    // rows reached by one outer anchor cell
-    constexpr int NA = (D == 3 && N1 == 8) ? 4 : N1;  // k0 values per accumulation pass
+    constexpr int NA = (D == 3 && N1 == 8) ? 2 : N1;  // k0 values per accumulation pass
     constexpr int NK1 = D == 3 ? N1 : 1;         // k1 values
     constexpr int kPer = kWinCells / kBinT;      // target cells per thread in the CSR build
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *coef = reinterpret_cast<float2 *>(smem_raw);             // [kBinT][D][N1]
-    float2 *eval = coef + kBinT * D * N1;                            // [kBinT * N1]
-    int *cstart = reinterpret_cast<int *>(eval + kBinT * N1);        // [kWinCells]
+    float2 *wgt = coef + kBinT * D * N1;                             // [kBinT]
+    int *cstart = reinterpret_cast<int *>(wgt + kBinT);              // [kWinCells]
     int *cend = cstart + kWinCells;                                  // [kWinCells]
     unsigned *act = reinterpret_cast<unsigned *>(cend + kWinCells);  // [kWinCells]
     int64_t *rowoff = reinterpret_cast<int64_t *>(act + kWinCells);  // [NR]
-    unsigned char *ejj = reinterpret_cast<unsigned char *>(rowoff + NR);  // [kBinT * N1]
+    unsigned short *ent = reinterpret_cast<unsigned short *>(rowoff + NR);  // [kBinT * N1]
     __shared__ int s_item, s_box[4], s_nact;
     __shared__ unsigned long long s_rows;  // bit r: row r lies in the node box
     const Common &c = P.c;
@@ -245,6 +245,7 @@ __global__ void __launch_bounds__(kBinT, 2) binned_scatter_kernel(
             float sn, cs;
             sincospif(2.f * (float)ts, &sn, &cs);
             cmul((float)(a[j] * c.pref), (float)(a[m + j] * c.pref), cs, sn, wr, wi);
+            wgt[tid] = make_float2(wr, wi);
             // one dimension at a time (one copy of the evaluation) into this
             // thread's coefficient block
 #pragma unroll 1
@@ -363,11 +364,7 @@ __global__ void __launch_bounds__(kBinT, 2) binned_scatter_kernel(
                     const int ia = ra + c.dq[k] - ta0 - wa, ib = rb + c.dp[k] - tb0;
                     if ((unsigned)ia < (unsigned)wn && (unsigned)ib < (unsigned)TB) {
                         const int pos = atomicAdd(&cend[ia * TB + ib], 1);
-                        const float2 cl = cj[(D - 1) * N1 + k];
-                        float vr, vi;
-                        cmul(wr, wi, cl.x, cl.y, vr, vi);
-                        eval[pos] = make_float2(vr, vi);
-                        ejj[pos] = (unsigned char)tid;
+                        ent[pos] = (unsigned short)((tid << 4) | k);
                     }
                 }
             }
@@ -390,9 +387,12 @@ __global__ void __launch_bounds__(kBinT, 2) binned_scatter_kernel(
 #pragma unroll
                     for (int v = 0; v < NK1; ++v) accr[u][v] = acci[u][v] = 0.f;
                 for (int x = x0; x < x1; ++x) {
-                    const float2 ev = eval[x];
+                    const int en = ent[x], jj = en >> 4, kk = en & 15;
+                    const float2 wv = wgt[jj], cl = coef[(jj * D + D - 1) * N1 + kk];
+                    float2 ev;
+                    cmul(wv.x, wv.y, cl.x, cl.y, ev.x, ev.y);
                     // the packet's coefficients, 16-byte loads (two neighbours each)
-                    const float4 *cp4 = reinterpret_cast<const float4 *>(coef + (int)ejj[x] * D * N1);
+                    const float4 *cp4 = reinterpret_cast<const float4 *>(coef + jj * D * N1);
                     float2 c0v[NA];
 #pragma unroll
                     for (int u = 0; u < NA; u += 2) {
@@ -537,7 +537,7 @@ fgr_status launch_binned_d(const BinLaunch &L, cudaStream_t st, const PacketsDev
     constexpr int smem = binned_smem_bytes<D, N1>();
     FGR_CUDA_TRY(cudaFuncSetAttribute(binned_scatter_kernel<D, N1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       smem));
-    binned_scatter_kernel<D, N1><<<(unsigned)(L.num_sms * 2), kBinT, smem, st>>>(
+    binned_scatter_kernel<D, N1><<<(unsigned)(L.num_sms * 3), kBinT, smem, st>>>(
         pk.q, pk.p, pk.s, pk.a, m, P, L.box, b.sorted, b.items, b.off + K, b.ctr + 1, (float2 *)W, flags);
     constexpr int T = coeff_threads<false, N1>();
     coeff_scatter_list_kernel<D, false, N1><<<(unsigned)(L.num_sms * 4), T, 0, st>>>(

@@ -32,10 +32,14 @@ __global__ void fft_twiddle_kernel(int N, C2 *__restrict__ tw) {
 
 __device__ __forceinline__ unsigned bit_reverse(unsigned x, int logn) { return __brev(x) >> (32 - logn); }
 
-// One line (row, a) per CTA: x[k] = sum_{b = k mod N, b in the line's
-// occupied range} W'[a, b] e^{2 pi i b th}, th = dp lo / (2 pi eps); then the
-// inverse DFT of length N = 2^logn into F[line][0..N).  Lines without
-// contributions (empty b-range, or a first-pass row without a flag) get zeros.
+// Lines (row, a) of one CTA: 512 / N of them for N <= 512 (N / 2 threads per
+// line, one butterfly each per stage), else one.
+__host__ __device__ constexpr int dft_lines_per_cta(int logn) { return logn <= 9 ? (1 << (9 - logn)) : 1; }
+
+// Per line: x[k] = sum_{b = k mod N, b in the line's occupied range}
+// W'[a, b] e^{2 pi i b th}, th = dp lo / (2 pi eps); then the inverse DFT of
+// length N = 2^logn into F[line][0..N).  Lines without contributions (empty
+// b-range, or a first-pass row without a flag) get zeros.  256 threads.
 template <bool FP64>
 __global__ void __launch_bounds__(256) dft_lines_kernel(const void *__restrict__ in_v, void *__restrict__ F_v,
                                                         int64_t rows, int A, int B, int bmin, double th, int logn,
@@ -45,45 +49,46 @@ __global__ void __launch_bounds__(256) dft_lines_kernel(const void *__restrict__
     using Real = typename std::conditional<FP64, double, float>::type;
     using C2 = typename std::conditional<FP64, double2, float2>::type;
     extern __shared__ __align__(16) unsigned char fft_smem[];
-    C2 *x = reinterpret_cast<C2 *>(fft_smem);
     const int N = 1 << logn;
-    const int64_t line = blockIdx.x;
-    const int64_t row = line / A;
-    const C2 *in = reinterpret_cast<const C2 *>(in_v) + line * (int64_t)B;
-    C2 *F = reinterpret_cast<C2 *>(F_v) + line * (int64_t)N;
+    const int lpc = dft_lines_per_cta(logn);
+    const int tpl = blockDim.x / lpc;  // threads per line
+    const int sub = threadIdx.x / tpl, t = threadIdx.x - sub * tpl;
+    C2 *x = reinterpret_cast<C2 *>(fft_smem) + (int64_t)sub * N;
+    const int64_t lines = rows * (int64_t)A;
+    const int64_t line = (int64_t)blockIdx.x * lpc + sub;
+    const bool here = line < lines;
+    const C2 *in = reinterpret_cast<const C2 *>(in_v) + (here ? line : 0) * (int64_t)B;
+    C2 *F = reinterpret_cast<C2 *>(F_v) + (here ? line : 0) * (int64_t)N;
     const C2 *tw = reinterpret_cast<const C2 *>(tw_v);
     int lo = 0, hi = B - 1;
-    if (brange) {
+    if (here && brange) {
         const int2 r = brange[line];
         lo = r.x;
         hi = r.y;
     }
+    const bool active = here && !(flags && !flags[line / A]) && lo <= hi;
     C2 zero;
     zero.x = 0;
     zero.y = 0;
-    if ((flags && !flags[row]) || lo > hi) {
-        for (int k = threadIdx.x; k < N; k += blockDim.x) F[k] = zero;
-        return;
-    }
     // fold the occupied b-range modulo N (thread per residue: no collisions)
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    for (int k = t; k < N; k += tpl) {
         Real sr = 0, si = 0;
-        // first b >= bmin + lo with (b mod N) == k
-        const int b_lo = bmin + lo, b_hi = bmin + hi;
-        int b = b_lo + ((k - b_lo) % N + N) % N;
-        for (; b <= b_hi; b += N) {
-            const C2 w = in[b - bmin];
-            if (w.x == 0 && w.y == 0) continue;
-            double t = (double)b * th;
-            t -= rint(t);
-            Real sn, cs;
-            if constexpr (FP64) {
-                sincospi(2.0 * t, &sn, &cs);
-            } else {
-                sincospif(2.f * (float)t, &sn, &cs);
+        if (active) {
+            const int b_lo = bmin + lo, b_hi = bmin + hi;
+            for (int b = b_lo + ((k - b_lo) % N + N) % N; b <= b_hi; b += N) {
+                const C2 w = in[b - bmin];
+                if (w.x == 0 && w.y == 0) continue;
+                double tt = (double)b * th;
+                tt -= rint(tt);
+                Real sn, cs;
+                if constexpr (FP64) {
+                    sincospi(2.0 * tt, &sn, &cs);
+                } else {
+                    sincospif(2.f * (float)tt, &sn, &cs);
+                }
+                sr += w.x * cs - w.y * sn;
+                si += w.x * sn + w.y * cs;
             }
-            sr += w.x * cs - w.y * sn;
-            si += w.x * sn + w.y * cs;
         }
         C2 v;
         v.x = sr;
@@ -95,25 +100,28 @@ __global__ void __launch_bounds__(256) dft_lines_kernel(const void *__restrict__
     for (int s = 1; s <= logn; ++s) {
         const int half = 1 << (s - 1);
         const int stride = N >> s;  // twiddle index step
-        for (int i = threadIdx.x; i < N / 2; i += blockDim.x) {
-            const int grp = i >> (s - 1), pos = i & (half - 1);
-            const int i0 = (grp << s) + pos, i1 = i0 + half;
-            const C2 t = tw[pos * stride];
-            const C2 u = x[i0], v = x[i1];
-            C2 vt;
-            vt.x = v.x * t.x - v.y * t.y;
-            vt.y = v.x * t.y + v.y * t.x;
-            C2 r0, r1;
-            r0.x = u.x + vt.x;
-            r0.y = u.y + vt.y;
-            r1.x = u.x - vt.x;
-            r1.y = u.y - vt.y;
-            x[i0] = r0;
-            x[i1] = r1;
+        if (active) {
+            for (int i = t; i < N / 2; i += tpl) {
+                const int grp = i >> (s - 1), pos = i & (half - 1);
+                const int i0 = (grp << s) + pos, i1 = i0 + half;
+                const C2 w = tw[pos * stride];
+                const C2 u = x[i0], v = x[i1];
+                C2 vt;
+                vt.x = v.x * w.x - v.y * w.y;
+                vt.y = v.x * w.y + v.y * w.x;
+                C2 r0, r1;
+                r0.x = u.x + vt.x;
+                r0.y = u.y + vt.y;
+                r1.x = u.x - vt.x;
+                r1.y = u.y - vt.y;
+                x[i0] = r0;
+                x[i1] = r1;
+            }
         }
         __syncthreads();
     }
-    for (int k = threadIdx.x; k < N; k += blockDim.x) F[k] = x[k];
+    if (here)
+        for (int k = t; k < N; k += tpl) F[k] = active ? x[k] : zero;
 }
 
 // u[row][m] = sum over the tile's node band of g(x_m - a dq) F[row][a][m mod N]
