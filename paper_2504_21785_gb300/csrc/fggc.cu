@@ -457,39 +457,22 @@ __global__ void brange_kernel(const C2 *__restrict__ in, int64_t lines, int B, i
     brange_body<C2>(in, lines, B, out, blockIdx.x);
 }
 
-// The same for short lines (B <= 64): a warp scans 32 consecutive lines as
-// one contiguous span, lane by lane through consecutive cells (coalesced
-// loads), and folds each cell into its line's range in shared memory.
+// The same for short lines (B <= 64): one thread per line, so a warp streams
+// 32 consecutive lines instead of leaving most of its lanes idle.
 template <class C2>
-__global__ void __launch_bounds__(256) brange_short_kernel(const C2 *__restrict__ in, int64_t lines, int B,
-                                                           int2 *__restrict__ out) {
-    __shared__ int s_lo[256], s_hi[256];
-    const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
-    const int64_t line0 = blockIdx.x * (int64_t)blockDim.x + wbase;  // first line of this warp
-    s_lo[threadIdx.x] = B;
-    s_hi[threadIdx.x] = -1;
-    __syncwarp();
-    if (line0 < lines) {
-        const int nl = (int)(lines - line0 < 32 ? lines - line0 : 32);
-        const C2 *p = in + line0 * (int64_t)B;
-        const int cells = nl * B;
-        int l = lane / B, b = lane - l * B;  // line and cell of element e = lane
-        for (int e = lane; e < cells; e += 32) {
-            const C2 v = p[e];
-            if (v.x != 0 || v.y != 0) {
-                atomicMin(&s_lo[wbase + l], b);
-                atomicMax(&s_hi[wbase + l], b);
-            }
-            b += 32;  // advance by 32 cells
-            while (b >= B) {
-                b -= B;
-                ++l;
-            }
+__global__ void brange_short_kernel(const C2 *__restrict__ in, int64_t lines, int B, int2 *__restrict__ out) {
+    const int64_t line = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (line >= lines) return;
+    const C2 *p = in + line * (int64_t)B;
+    int lo = B, hi = -1;
+    for (int b = 0; b < B; ++b) {
+        const C2 v = p[b];
+        if (v.x != 0 || v.y != 0) {
+            lo = min(lo, b);
+            hi = b;
         }
     }
-    __syncwarp();
-    const int64_t line = line0 + lane;
-    if (line < lines) out[line] = make_int2(s_lo[threadIdx.x], s_hi[threadIdx.x]);
+    out[line] = make_int2(lo, hi);
 }
 
 // Node-point terms of one pass (timing only): over the (row, a) lines, the
@@ -612,11 +595,21 @@ fgr_status launch_pass(const void *in, void *out, const PassParams &pp, const ui
     const int box_lines = band <= 16 ? 16 : 32;
     if (!FP64 && tp == 32 && splits == 1 && err && pass_tensor_map(in, pp, box_lines, &map) &&
         pass_tensor_map(in, pp, box_lines / 2, &map_half)) {
-        // 32-point tiles with the node tiles staged by the copy engine
-        if (band <= 16)
-            grid_pass_tma_kernel<16><<<grid, 32, 0, st>>>(map, map_half, out, pp, flags, brange, tab, err);
-        else
-            grid_pass_tma_kernel<32><<<grid, 32, 0, st>>>(map, map_half, out, pp, flags, brange, tab, err);
+        // 32-point tiles with the node tiles staged by the copy engine; on
+        // short rows (at most 256 points: little work per row and tile) four
+        // rows per CTA share one sequence of copies
+        const int rows_per_cta = pp.N <= 256 ? 4 : 1;
+        const dim3 tgrid((unsigned)((pp.rows + rows_per_cta - 1) / rows_per_cta), (unsigned)mtiles);
+#define FGR_TMA(MB, R) \
+    grid_pass_tma_kernel<MB, R><<<tgrid, 32, 0, st>>>(map, map_half, out, pp, flags, brange, tab, err)
+        if (rows_per_cta == 4) {
+            if (band <= 16) FGR_TMA(16, 4);
+            else FGR_TMA(32, 4);
+        } else {
+            if (band <= 16) FGR_TMA(16, 1);
+            else FGR_TMA(32, 1);
+        }
+#undef FGR_TMA
     } else if (tp == 32) {
         // narrow tiles: at most 32 band factors in registers (wider bands in
         // chunks of 32), so that more warps fit an SM

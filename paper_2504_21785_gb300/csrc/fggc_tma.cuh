@@ -64,8 +64,12 @@ __device__ __forceinline__ bool tma_wait(uint64_t *bar, unsigned phase, int *err
 }
 
 // map: boxes of MAXBAND lines; map_half: boxes of MAXBAND / 2 lines, for a
-// last band chunk that needs no more (half the copy)
-template <int MAXBAND>
+// last band chunk that needs no more (half the copy).  A CTA (one warp) takes
+// one 32-point tile of RPC consecutive rows: the rows share the tile's node
+// band, Gaussian factors and windows, and their tiles form one sequence of
+// copies (band chunk, row, b chunk), so the copy of the next tile, also of
+// the next row, is in flight while the warp multiplies the current one.
+template <int MAXBAND, int RPC>
 __global__ void __launch_bounds__(32) grid_pass_tma_kernel(const __grid_constant__ CUtensorMap map,
                                                            const __grid_constant__ CUtensorMap map_half,
                                                            void *__restrict__ out_v, PassParams pp,
@@ -75,39 +79,65 @@ __global__ void __launch_bounds__(32) grid_pass_tma_kernel(const __grid_constant
     constexpr int TP = 32;
     __shared__ __align__(128) float2 sw[2][MAXBAND][kTB];
     __shared__ __align__(8) uint64_t bar[2];
+    __shared__ double2 s_tot[RPC][TP];  // per row and lane: the FP64 sum of the chunk partials
     const int lane = threadIdx.x;
-    const int64_t row = blockIdx.x;
+    const int64_t row0 = (int64_t)blockIdx.x * RPC;
     const int tile = blockIdx.y;
     const int64_t m = (int64_t)tile * TP + lane;
     const bool valid = m < pp.N;
-    float2 *out = reinterpret_cast<float2 *>(out_v) + row * pp.N;
+    float2 *out = reinterpret_cast<float2 *>(out_v);
     const int2 bnd = tab.band[tile];
     const int a_lo = bnd.x, a_hi = bnd.y;
     const int nb_total = a_hi - a_lo + 1;
-    int ulo = 0, uhi = pp.B - 1;
-    if (brange && nb_total > 0) {
-        int lo = INT_MAX, hi = INT_MIN;
-        for (int i = lane; i < nb_total; i += TP) {
-            const int2 r = brange[row * (int64_t)pp.A + (a_lo - pp.amin) + i];
-            lo = min(lo, r.x);
-            hi = max(hi, r.y);
+    // per row: occupied b-range of the band (empty: no chunks)
+    int b_start[RPC], nbc[RPC], S = 0;
+#pragma unroll
+    for (int r = 0; r < RPC; ++r) {
+        const int64_t row = row0 + r;
+        bool live = row < pp.rows && nb_total > 0 && !(flags && !flags[row]);
+        int ulo = 0, uhi = pp.B - 1;
+        if (live && brange) {
+            int lo = INT_MAX, hi = INT_MIN;
+            for (int i = lane; i < nb_total; i += TP) {
+                const int2 rg = brange[row * (int64_t)pp.A + (a_lo - pp.amin) + i];
+                lo = min(lo, rg.x);
+                hi = max(hi, rg.y);
+            }
+            ulo = __reduce_min_sync(0xffffffffu, lo);
+            uhi = __reduce_max_sync(0xffffffffu, hi);
         }
-        ulo = __reduce_min_sync(0xffffffffu, lo);
-        uhi = __reduce_max_sync(0xffffffffu, hi);
+        live = live && ulo <= uhi;
+        // b chunks start at even cells (16-byte copy coordinates); the cell
+        // before an odd ulo is zero in every line of the band
+        b_start[r] = ulo & ~1;
+        nbc[r] = live ? (uhi - b_start[r] + kTB) / kTB : 0;
+        S += nbc[r];
+        s_tot[r][lane] = make_double2(0.0, 0.0);
     }
-    if ((flags && !flags[row]) || ulo > uhi || nb_total <= 0) {
-        if (valid) out[m] = make_float2(0.f, 0.f);
-        return;
-    }
-    // tiles (band chunk, b chunk); b chunks start at even cells (16-byte TMA
-    // coordinates); the cell before an odd ulo is zero in every line of the band
-    const int b_start = ulo & ~1;
-    const int nbc = (uhi - b_start + kTB) / kTB;
-    const int nac = (nb_total + MAXBAND - 1) / MAXBAND;
-    const int ntiles = nac * nbc;
-    const int64_t line0 = row * (int64_t)pp.A + (a_lo - pp.amin);
+    const int nac = nb_total > 0 ? (nb_total + MAXBAND - 1) / MAXBAND : 0;
+    const int ntiles = nac * S;
     constexpr unsigned kBytes = MAXBAND * kTB * sizeof(float2);
-    if (lane == 0) {
+    // tile t -> (band chunk ac, row r, b chunk bc)
+    auto decode = [&](int t, int &ac, int &r, int &bc) {
+        ac = t / S;
+        int rem = t - ac * S;
+        r = 0;
+#pragma unroll
+        for (int k = 0; k < RPC; ++k)
+            if (r == k && rem >= nbc[k]) {
+                rem -= nbc[k];
+                r = k + 1;
+            }
+        bc = rem;
+    };
+    auto start_of = [&](int r) {
+        int v = 0;
+#pragma unroll
+        for (int k = 0; k < RPC; ++k)
+            if (k == r) v = b_start[k];
+        return v;
+    };
+    if (ntiles > 0 && lane == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -115,28 +145,29 @@ __global__ void __launch_bounds__(32) grid_pass_tma_kernel(const __grid_constant
     }
     __syncwarp();
     auto issue = [&](int t) {
-        const int ac = t / nbc, bc = t - ac * nbc;
+        int ac, r, bc;
+        decode(t, ac, r, bc);
         const bool half = nb_total - ac * MAXBAND <= MAXBAND / 2;
+        const int64_t line = (row0 + r) * (int64_t)pp.A + (a_lo - pp.amin) + ac * MAXBAND;
         mbar_expect_tx(&bar[t & 1], half ? kBytes / 2 : kBytes);
-        tma_load_2d(&sw[t & 1][0][0], half ? &map_half : &map, b_start + bc * kTB, (int)(line0 + ac * MAXBAND),
-                    &bar[t & 1]);
+        tma_load_2d(&sw[t & 1][0][0], half ? &map_half : &map, start_of(r) + bc * kTB, (int)line, &bar[t & 1]);
     };
     if (lane == 0) {
-        issue(0);
+        if (ntiles > 0) issue(0);
         if (ntiles > 1) issue(1);
     }
     const double xm = grid_x(pp.lo, pp.h, valid ? m : (int64_t)tile * TP);
     const float2 ph = tab.ph[valid ? m : (int64_t)tile * TP];
     const float cef = (float)(pp.neg_half_inv_eps * 1.4426950408889634);  // log2(e) / (-2 eps)
     const float dqf = (float)pp.dq;
-    float accr = 0.f, acci = 0.f;
-    double totr = 0.0, toti = 0.0;
     float g[MAXBAND];
-    int nb = 0;
+    int nb = 0, ac_cur = -1;
     unsigned phase[2] = {0u, 0u};
     for (int t = 0; t < ntiles; ++t) {
-        const int ac = t / nbc, bc = t - ac * nbc;
-        if (bc == 0) {  // Gaussian factors of this band chunk
+        int ac, r, bc;
+        decode(t, ac, r, bc);
+        if (ac != ac_cur) {  // Gaussian factors of this band chunk (shared by the rows)
+            ac_cur = ac;
             const int a_first = a_lo + ac * MAXBAND;
             nb = min(MAXBAND, nb_total - ac * MAXBAND);
             const double dx0 = xm - (double)a_first * pp.dq;
@@ -160,37 +191,30 @@ __global__ void __launch_bounds__(32) grid_pass_tma_kernel(const __grid_constant
             return;
         }
         phase[s] ^= 1u;
-        const int b0 = b_start + bc * kTB;
-        const int nbb = min(kTB, uhi + 1 - b0);
-        if (nbb & 1) {  // the pair partner past the range must read zero
-            for (int i = lane; i < MAXBAND; i += TP) sw[s][i][nbb] = make_float2(0.f, 0.f);
-            __syncwarp();
-        }
-        // four b values at a time (eight independent accumulator chains); the
-        // b values past the range read zero (padding) or are skipped
-        for (int bb = 0; bb < nbb; bb += 4) {
+        // whole chunks: cells past the band's occupied range are zero in every
+        // line of the band (and past the node box the copy fills zeros)
+        const int b0 = start_of(r) + bc * kTB;
+        float accr = 0.f, acci = 0.f;
+#pragma unroll 1
+        for (int bb = 0; bb < kTB; bb += 4) {
             float vr[4] = {0.f, 0.f, 0.f, 0.f}, vi[4] = {0.f, 0.f, 0.f, 0.f};
-            const bool two = bb + 2 < nbb;  // the second pair holds a b of the range
 #pragma unroll
             for (int i = 0; i < MAXBAND; ++i) {
                 if (i < nb) {
                     const float4 w = *reinterpret_cast<const float4 *>(&sw[s][i][bb]);
+                    const float4 w2 = *reinterpret_cast<const float4 *>(&sw[s][i][bb + 2]);
                     vr[0] = fmaf(g[i], w.x, vr[0]);
                     vi[0] = fmaf(g[i], w.y, vi[0]);
                     vr[1] = fmaf(g[i], w.z, vr[1]);
                     vi[1] = fmaf(g[i], w.w, vi[1]);
-                    if (two) {
-                        const float4 w2 = *reinterpret_cast<const float4 *>(&sw[s][i][bb + 2]);
-                        vr[2] = fmaf(g[i], w2.x, vr[2]);
-                        vi[2] = fmaf(g[i], w2.y, vi[2]);
-                        vr[3] = fmaf(g[i], w2.z, vr[3]);
-                        vi[3] = fmaf(g[i], w2.w, vi[3]);
-                    }
+                    vr[2] = fmaf(g[i], w2.x, vr[2]);
+                    vi[2] = fmaf(g[i], w2.y, vi[2]);
+                    vr[3] = fmaf(g[i], w2.z, vr[3]);
+                    vi[3] = fmaf(g[i], w2.w, vi[3]);
                 }
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                if (u >= 2 && !two) break;
                 const float bf = (float)(pp.bmin + b0 + bb + u);
                 float f = bf * ph.x;
                 f -= rint_fast(f);
@@ -202,9 +226,10 @@ __global__ void __launch_bounds__(32) grid_pass_tma_kernel(const __grid_constant
                 acci += cs * vi[u] + sn * vr[u];
             }
         }
-        totr += (double)accr;
-        toti += (double)acci;
-        accr = acci = 0.f;
+        double2 tv = s_tot[r][lane];
+        tv.x += (double)accr;
+        tv.y += (double)acci;
+        s_tot[r][lane] = tv;
         // the buffer is free again: refill it with tile t + 2
         __syncwarp();
         if (lane == 0 && t + 2 < ntiles) {
@@ -212,5 +237,12 @@ __global__ void __launch_bounds__(32) grid_pass_tma_kernel(const __grid_constant
             issue(t + 2);
         }
     }
-    if (valid) out[m] = make_float2((float)totr, (float)toti);
+#pragma unroll
+    for (int r = 0; r < RPC; ++r) {
+        const int64_t row = row0 + r;
+        if (row < pp.rows && valid) {
+            const double2 tv = s_tot[r][lane];
+            out[row * pp.N + m] = make_float2((float)tv.x, (float)tv.y);
+        }
+    }
 }
