@@ -967,6 +967,23 @@ def serving_bench(args, device_index: int):
     burst_rate = len(burst) / (time.perf_counter() - tb0)
     capacity = burst_rate
     del bouts
+    # the longest single requests of the mix, alone: every set with either
+    # method on its dimension's finest grid (best of 2 runs each; the first run
+    # of an FGGC request also builds the plan the server caches)
+    alone = []
+    for sid, d, eps, m in sets:
+        n = [32768] if d == 1 else [1024, 1024]
+        grid = dict(d=d, n=n, lo=[-np.pi] * d, hi=[np.pi] * d)
+        u = torch.zeros(tuple(n), dtype=torch.complex64, device="cuda")
+        for method in (0, 1):
+            times = []
+            for _ in range(2):
+                r = fgr.fgr_poll(srv, fgr.fgr_submit(srv, fgr.make_request(method, grid, eps, opt, sid, u)), -1)
+                times.append(r.t_done_ms - r.t_start_ms)
+            alone.append({"method": ("direct", "fggc")[method], "d": d, "packets": m, "eps": eps, "grid": n,
+                          "service_ms": min(times), "first_ms": times[0]})
+        del u
+    alone.sort(key=lambda x: -x["service_ms"])
     levels = {}
     for frac in (0.5, 0.8, 1.0):
         lam = frac * capacity
@@ -984,10 +1001,22 @@ def serving_bench(args, device_index: int):
         res = [fgr.fgr_poll(srv, t, -1) for t in tickets]
         t1 = time.perf_counter()
         lat = np.array([r.t_done_ms - r.t_submit_ms for r in res])
+        wait = np.array([r.t_start_ms - r.t_submit_ms for r in res])
+        svc = np.array([r.t_done_ms - r.t_start_ms for r in res])
+        tail = lat >= np.percentile(lat, 99)
+        kinds = {}
+        for (sid_, d_, e_, m_, g_, mth_), t_ in zip(reqs, tail):
+            if t_:
+                key = "%s %d-D" % (("direct", "fggc")[mth_], d_)
+                kinds[key] = kinds.get(key, 0) + 1
         ok = all(r.status == 0 for r in res)
         packets = sum(q[3] for q in reqs)
         levels["%.1fx" % frac] = {"lambda_req_per_s": lam, "p50_ms": float(np.percentile(lat, 50)),
-                                  "p99_ms": float(np.percentile(lat, 99)), "packets_per_s": packets / (t1 - t0),
+                                  "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
+                                  "tail_1pct": {"wait_ms_median": float(np.median(wait[tail])),
+                                                "service_ms_median": float(np.median(svc[tail])),
+                                                "kinds": kinds},
+                                  "packets_per_s": packets / (t1 - t0),
                                   "requests": len(reqs), "all_ok": ok}
         del outs
     fgr.fgr_server_destroy(srv)
@@ -996,7 +1025,9 @@ def serving_bench(args, device_index: int):
             "inflight": args.serve_inflight, "max_batch": 16, "isolated_service_ms_mean": float(np.mean(iso)),
             "isolated_service_ms_p50": float(np.percentile(iso, 50)),
             "capacity_req_per_s": capacity, "capacity_def": "saturated rate of a burst of %d requests" % len(burst),
-            "isolated_capacity_req_per_s": 1e3 / float(np.mean(iso)), "levels": levels,
+            "isolated_capacity_req_per_s": 1e3 / float(np.mean(iso)),
+            "largest_requests_alone": alone[:4], "largest_request_ms": alone[0]["service_ms"],
+            "levels": levels,
             "mix": "d in {1,2}; grids 1-D 1024..32768, 2-D 256^2..1024^2; direct/fggc 50/50; fp32"}
 
 
@@ -1304,8 +1335,9 @@ def main():
                     help="with --profile: keep only this many largest-amplitude packets")
     ap.add_argument("--profile", action="store_true",
                     help="run every kernel once on a short case (for ncu) and exit")
-    ap.add_argument("--study", choices=["multistep"], default=None,
-                    help="print the runtimes of the multi-step examples of Sec. 4.4 and exit")
+    ap.add_argument("--study", choices=["multistep", "serving"], default=None,
+                    help="print the runtimes of the multi-step examples of Sec. 4.4, or the serving "
+                         "workload's numbers alone, and exit")
     ap.add_argument("--study-precision", choices=["fp32", "fp64"], default="fp32")
     args = ap.parse_args()
     cores = os.cpu_count() or 1
@@ -1316,6 +1348,9 @@ def main():
         return
     if args.study == "multistep":
         print(json.dumps(multistep_study(args)))
+        return
+    if args.study == "serving":
+        print(json.dumps(serving_bench(args, 0)))
         return
     out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:

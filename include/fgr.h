@@ -410,8 +410,13 @@ fgr_status fgr_get_stats(const fgr_ctx *ctx, fgr_stats *out);
  * order.  Requests of one method, dimension and precision with device outputs
  * that wait together run as one group (see fgr_server_set_max_batch); FGGC
  * requests go through a plan cached per (packet set, grid, eps, options) when
- * the budget allows, freed with the set.  Free with fgr_server_destroy, which
- * cancels what has not started and waits for what has. */
+ * the budget allows, freed with the set.  Large requests (direct sums whose
+ * packets x window points put them above about 2 ms) run alone on
+ * low-priority streams and hold at most max_inflight - 1 slots; a small request
+ * may pass a waiting large one, and while small requests wait or run, a large
+ * 2-D / 3-D direct sum gives up one CTA slot per SM between its work items.
+ * Free with fgr_server_destroy, which cancels what has not started and waits
+ * for what has.  Not in the paper: a serving policy. */
 fgr_status fgr_server_create(size_t hbm_budget_bytes, int32_t max_inflight, fgr_server **out);
 void fgr_server_destroy(fgr_server *srv);
 

@@ -181,6 +181,43 @@ void release_pinned_slot(char *p) {
     g_pinned_free.push_back(p);
 }
 
+// Device error words of contexts: slabs of kErrWords per device, kept for the
+// process, so that creating or destroying a context allocates and frees no
+// device memory (cudaFree would wait for the whole device).  A context's word
+// is zeroed on a private non-blocking stream when the context takes it.
+constexpr int kErrWords = 1024;
+std::vector<int *> g_err_free[64];
+cudaStream_t g_err_stream[64] = {};
+
+cudaError_t err_word(int device, int **out) {
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_res_mu);
+    cudaError_t e = cudaSuccess;
+    if (!g_err_stream[device]) {
+        e = cudaStreamCreateWithFlags(&g_err_stream[device], cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+    }
+    if (g_err_free[device].empty()) {
+        int *slab = nullptr;
+        e = cudaMalloc((void **)&slab, sizeof(int) * kErrWords);
+        if (e != cudaSuccess) return e;
+        for (int i = kErrWords - 1; i >= 0; --i) g_err_free[device].push_back(slab + i);
+    }
+    int *w = g_err_free[device].back();
+    e = cudaMemsetAsync(w, 0, sizeof(int), g_err_stream[device]);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g_err_stream[device]);
+    if (e != cudaSuccess) return e;
+    g_err_free[device].pop_back();
+    *out = w;
+    return cudaSuccess;
+}
+
+void release_err_word(int device, int *w) {
+    if (!w || device < 0 || device >= 64) return;
+    std::lock_guard<std::mutex> lk(g_res_mu);
+    g_err_free[device].push_back(w);
+}
+
 bool is_finite(double x) { return std::isfinite(x); }
 
 fgr_status check_grid(int32_t d, const fgr_grid *g, Grid *out) {
@@ -606,13 +643,12 @@ fgr_status fgr_create(int32_t d, const fgr_grid *grid, double eps, const fgr_opt
         if (e == cudaSuccess) e = device_pool(c->device, &c->pool);
         char *slot = nullptr;
         if (e == cudaSuccess) e = pinned_slot(&slot);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&c->dev_err, sizeof(int));
-        if (e == cudaSuccess) e = cudaMemset(c->dev_err, 0, sizeof(int));
+        if (e == cudaSuccess) e = err_word(c->device, &c->dev_err);
         if (e != cudaSuccess) {
             set_error("CUDA initialisation failed: %s", cudaGetErrorString(e));
             cudaGetLastError();
             if (slot) release_pinned_slot(slot);
-            if (c->dev_err) cudaFree(c->dev_err);
+            release_err_word(c->device, c->dev_err);
             delete c;
             return FGR_E_CUDA;
         }
@@ -626,13 +662,11 @@ fgr_status fgr_create(int32_t d, const fgr_grid *grid, double eps, const fgr_opt
 void fgr_destroy(fgr_ctx *ctx) {
     if (!ctx) return;
     // Kernels in flight hold no reference to the context (parameters are
-    // copied at launch, scratch returns to the pool in stream order), and every
+    // copied at launch, scratch returns to the pool in stream order) except its
+    // error word, which only a kernel whose bounded wait gave up writes; every
     // call that uses the pinned slot waits for it before returning.
     release_pinned_slot((char *)ctx->host_pinned);
-    if (ctx->dev_err) {
-        cudaSetDevice(ctx->device);
-        cudaFree(ctx->dev_err);
-    }
+    release_err_word(ctx->device, ctx->dev_err);
     delete ctx;
 }
 
@@ -890,11 +924,18 @@ struct fgr_fggc_plan {
     int *bnd = nullptr;       // device: the packets' node bounds of the last call
     int *overflow = nullptr;  // device: set when they left the box
     size_t bin_bytes = 0;     // binning buffers (d = 3, FP32)
+    // The buffers come from the device's stream-ordered pool (allocating them
+    // does not wait for other streams' work); they go back to it once the
+    // device has finished the work issued before the release.
     void release() {
         void *ptrs[] = {buf.W,   buf.buf1, buf.buf2, buf.flags,   buf.brange, buf.tables,
                         buf.bin, buf.fft,  buf.twiddle, bnd, overflow};
-        for (void *p : ptrs)
-            if (p) cudaFree(p);
+        bool any = false;
+        for (void *p : ptrs) any = any || p;
+        if (any && cudaDeviceSynchronize() == cudaSuccess)
+            for (void *p : ptrs)
+                if (p) cudaFreeAsync(p, 0);
+        cudaGetLastError();
         buf = FggcBuffers{};
         bnd = overflow = nullptr;
     }
@@ -962,8 +1003,9 @@ fgr_status fgr_fggc_plan_create(fgr_ctx *ctx, const fgr_packets *pk, int32_t mar
             set_error("plan: device allocation failed: %s", cudaGetErrorString(e));
             return e == cudaErrorMemoryAllocation ? FGR_E_NOMEM : FGR_E_CUDA;
         };
-        cudaError_t e = cudaMalloc(&pl->bnd, sizeof(int) * 12);
-        if (e == cudaSuccess) e = cudaMalloc(&pl->overflow, sizeof(int));
+        auto palloc = [&](void **ptr, size_t bytes) { return cudaMallocFromPoolAsync(ptr, bytes, ctx->pool, st); };
+        cudaError_t e = palloc((void **)&pl->bnd, sizeof(int) * 12);
+        if (e == cudaSuccess) e = palloc((void **)&pl->overflow, sizeof(int));
         if (e != cudaSuccess) return fail(e);
         int hb[12];
         r = compute_node_bounds(ctx, dev, pl->bnd, hb, st);
@@ -979,22 +1021,25 @@ fgr_status fgr_fggc_plan_create(fgr_ctx *ctx, const fgr_packets *pk, int32_t mar
         if (!pl->box.empty) {
             const size_t eb = elem_bytes(ctx->opt.precision);
             const FggcBox &b = pl->box;
-            e = cudaMalloc(&pl->buf.W, eb * (size_t)b.cells);
-            if (e == cudaSuccess && ctx->d > 1) e = cudaMalloc(&pl->buf.buf1, eb * (size_t)b.maxbuf);
-            if (e == cudaSuccess && ctx->d > 1) e = cudaMalloc(&pl->buf.buf2, eb * (size_t)b.maxbuf);
-            if (e == cudaSuccess) e = cudaMalloc((void **)&pl->buf.flags, (size_t)b.rows0);
-            if (e == cudaSuccess) e = cudaMalloc((void **)&pl->buf.brange, sizeof(int2) * (size_t)b.max_lines);
-            if (e == cudaSuccess) e = cudaMalloc(&pl->buf.tables, 8 * (size_t)b.table_entries);
-            if (e == cudaSuccess && b.fft_elems > 0) e = cudaMalloc(&pl->buf.fft, eb * (size_t)b.fft_elems);
-            if (e == cudaSuccess && b.fft_elems > 0) e = cudaMalloc(&pl->buf.twiddle, eb * 4096);
+            e = palloc(&pl->buf.W, eb * (size_t)b.cells);
+            if (e == cudaSuccess && ctx->d > 1) e = palloc(&pl->buf.buf1, eb * (size_t)b.maxbuf);
+            if (e == cudaSuccess && ctx->d > 1) e = palloc(&pl->buf.buf2, eb * (size_t)b.maxbuf);
+            if (e == cudaSuccess) e = palloc((void **)&pl->buf.flags, (size_t)b.rows0);
+            if (e == cudaSuccess) e = palloc((void **)&pl->buf.brange, sizeof(int2) * (size_t)b.max_lines);
+            if (e == cudaSuccess) e = palloc(&pl->buf.tables, 8 * (size_t)b.table_entries);
+            if (e == cudaSuccess && b.fft_elems > 0) e = palloc(&pl->buf.fft, eb * (size_t)b.fft_elems);
+            if (e == cudaSuccess && b.fft_elems > 0) e = palloc(&pl->buf.twiddle, eb * 4096);
             BinBox bb;
             if (e == cudaSuccess && ctx->opt.precision == FGR_FP32 && make_bin_box(b, ctx->d, &bb)) {
                 pl->bin_bytes = bin_buffer_bytes(pk->m, bb);
-                e = cudaMalloc(&pl->buf.bin, pl->bin_bytes);
+                e = palloc(&pl->buf.bin, pl->bin_bytes);
                 pl->buf.bin_m = pk->m;
             }
             if (e != cudaSuccess) return fail(e);
         }
+        // the buffers are stream-ordered on st: valid for every stream once it is done
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return fail(e);
         *out = pl.release();
         return FGR_OK;
     });

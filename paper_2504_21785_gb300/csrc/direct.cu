@@ -741,19 +741,25 @@ inline size_t plan_items_capacity(int ntiles, int target) {
     return std::min<size_t>((size_t)64 * ntiles, (size_t)ntiles + (size_t)target + 64);
 }
 
-// Balanced direct sum: persistent CTAs pull the planned items in order.
+// Balanced direct sum: persistent CTAs pull the planned items in order.  With
+// a yield word, the CTAs from index keep on stop before pulling another item
+// while the word is > 0; the remaining CTAs finish every item.
 template <int D, bool FP64>
 __global__ void __launch_bounds__(kThreads) direct_items_kernel(const void *__restrict__ recs_v,
                                                                 const int64_t *__restrict__ off, DirectParams P,
                                                                 void *__restrict__ u_v,
                                                                 const int2 *__restrict__ items,
                                                                 const int *__restrict__ n_items,
-                                                                unsigned long long *__restrict__ counter) {
+                                                                unsigned long long *__restrict__ counter,
+                                                                const volatile int *yield, int keep) {
     __shared__ long long s_item;
     const long long total = *n_items;
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ULL);
+        if (threadIdx.x == 0) {
+            const bool stop = yield != nullptr && (int)blockIdx.x >= keep && *yield > 0;
+            s_item = stop ? total : (long long)atomicAdd(counter, 1ULL);
+        }
         __syncthreads();
         const long long item = s_item;
         if (item >= total) break;
@@ -980,12 +986,15 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
     else
         FGR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, direct_items_kernel<D, false>, kThreads, 0));
     const unsigned ctas = (unsigned)(ctx->num_sms * std::max(1, per_sm));
+    const int keep = std::max(ctx->num_sms, (int)ctas - ctx->num_sms);  // one slot per SM can be given up
     if (fp64)
         direct_items_kernel<D, true><<<ctas, kThreads, 0, st>>>(pr.recs, pr.off, pr.P, u_dev, items,
-                                                                reinterpret_cast<int *>(cnt + 1), cnt);
+                                                                reinterpret_cast<int *>(cnt + 1), cnt,
+                                                                ctx->yield_flag, keep);
     else
         direct_items_kernel<D, false><<<ctas, kThreads, 0, st>>>(pr.recs, pr.off, pr.P, u_dev, items,
-                                                                 reinterpret_cast<int *>(cnt + 1), cnt);
+                                                                 reinterpret_cast<int *>(cnt + 1), cnt,
+                                                                 ctx->yield_flag, keep);
     FGR_CUDA_TRY(cudaGetLastError());
     timer.mark(&ctx->timing.last.direct_ms);
     ctx->timing.last.launches = 6;

@@ -431,13 +431,20 @@ __global__ void transpose_kernel(const C2 *__restrict__ in, C2 *__restrict__ out
 }
 
 // Occupied b-range of every line [row][a][0..B): first and last b with a
-// non-zero value ((B, -1) for an empty line).  One warp per line.
+// non-zero value ((B, -1) for an empty line, and without reading it for a line
+// of a row the scatter did not mark, when row flags are given).  One warp per
+// line.
 template <class C2>
 __device__ __forceinline__ void brange_body(const C2 *__restrict__ in, int64_t lines, int B,
-                                            int2 *__restrict__ out, int64_t bid) {
+                                            int2 *__restrict__ out, int64_t bid, const uint8_t *flags = nullptr,
+                                            int A = 1) {
     const int64_t line = bid * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     if (line >= lines) return;
     const int lane = threadIdx.x & 31;
+    if (flags && !flags[line / A]) {
+        if (lane == 0) out[line] = make_int2(B, -1);
+        return;
+    }
     const C2 *p = in + line * (int64_t)B;
     int lo = INT_MAX, hi = INT_MIN;
     for (int b = lane; b < B; b += 32) {
@@ -453,19 +460,22 @@ __device__ __forceinline__ void brange_body(const C2 *__restrict__ in, int64_t l
 }
 
 template <class C2>
-__global__ void brange_kernel(const C2 *__restrict__ in, int64_t lines, int B, int2 *__restrict__ out) {
-    brange_body<C2>(in, lines, B, out, blockIdx.x);
+__global__ void brange_kernel(const C2 *__restrict__ in, int64_t lines, int B, const uint8_t *__restrict__ flags,
+                              int A, int2 *__restrict__ out) {
+    brange_body<C2>(in, lines, B, out, blockIdx.x, flags, A);
 }
 
 // The same for short lines (B <= 64): one thread per line, so a warp streams
 // 32 consecutive lines instead of leaving most of its lanes idle.
 template <class C2>
-__global__ void brange_short_kernel(const C2 *__restrict__ in, int64_t lines, int B, int2 *__restrict__ out) {
+__global__ void brange_short_kernel(const C2 *__restrict__ in, int64_t lines, int B,
+                                    const uint8_t *__restrict__ flags, int A, int2 *__restrict__ out) {
     const int64_t line = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (line >= lines) return;
     const C2 *p = in + line * (int64_t)B;
     int lo = B, hi = -1;
-    for (int b = 0; b < B; ++b) {
+    const int nb = (flags && !flags[line / A]) ? 0 : B;
+    for (int b = 0; b < nb; ++b) {
         const C2 v = p[b];
         if (v.x != 0 || v.y != 0) {
             lo = min(lo, b);
@@ -490,22 +500,24 @@ __global__ void pass_terms_kernel(const int2 *__restrict__ brange, int64_t lines
     if ((threadIdx.x & 31) == 0 && t) atomicAdd(out, t);
 }
 
+// flags: row flags of the first pass (lines of unmarked rows are empty), or null.
 template <bool FP64>
-fgr_status launch_brange(const void *in, int64_t rows, int A, int B, int2 *out, cudaStream_t st) {
+fgr_status launch_brange(const void *in, int64_t rows, int A, int B, const uint8_t *flags, int2 *out,
+                         cudaStream_t st) {
     const int64_t lines = rows * (int64_t)A;
     if (lines == 0) return FGR_OK;
     if (B <= 64) {
         const unsigned blocks = (unsigned)((lines + 255) / 256);
         if (FP64)
-            brange_short_kernel<double2><<<blocks, 256, 0, st>>>((const double2 *)in, lines, B, out);
+            brange_short_kernel<double2><<<blocks, 256, 0, st>>>((const double2 *)in, lines, B, flags, A, out);
         else
-            brange_short_kernel<float2><<<blocks, 256, 0, st>>>((const float2 *)in, lines, B, out);
+            brange_short_kernel<float2><<<blocks, 256, 0, st>>>((const float2 *)in, lines, B, flags, A, out);
     } else {
         const unsigned blocks = (unsigned)((lines + 7) / 8);
         if (FP64)
-            brange_kernel<double2><<<blocks, 256, 0, st>>>((const double2 *)in, lines, B, out);
+            brange_kernel<double2><<<blocks, 256, 0, st>>>((const double2 *)in, lines, B, flags, A, out);
         else
-            brange_kernel<float2><<<blocks, 256, 0, st>>>((const float2 *)in, lines, B, out);
+            brange_kernel<float2><<<blocks, 256, 0, st>>>((const float2 *)in, lines, B, flags, A, out);
     }
     FGR_CUDA_TRY(cudaGetLastError());
     return FGR_OK;
@@ -1057,8 +1069,14 @@ fgr_status enqueue_fggc(fgr_ctx *ctx, const PacketsDev &pk, const FggcBox &box, 
     const Lsa &L = ctx->lsa;
     const size_t eb = elem_bytes(ctx->opt.precision);
     const Common &c = box.c;
-    FGR_CUDA_TRY(cudaMemsetAsync(b.W, 0, eb * (size_t)box.cells, st));
-    // the scatter marks the rows it reaches; the single row of d = 1 is marked here
+    // FP32 3-D: the binned scatter, which marks the rows its packets reach and
+    // clears only those (the passes and b-range scans skip unmarked rows);
+    // otherwise W is cleared whole and the scatter marks the rows it reaches
+    BinLaunch bl;
+    const bool binned = !fp64 && D == 3 && b.bin && b.bin_m >= pk.m && pk.m > 0 && (L.n1 == 4 || L.n1 == 8) &&
+                        make_bin_box(box, D, &bl.box);
+    if (!binned) FGR_CUDA_TRY(cudaMemsetAsync(b.W, 0, eb * (size_t)box.cells, st));
+    // the single row of d = 1 is marked here
     FGR_CUDA_TRY(cudaMemsetAsync(b.flags, D == 1 ? 1 : 0, (size_t)box.rows0, st));
     if (timer) timer->mark(&ctx->timing.last.prep_ms);
 
@@ -1079,14 +1097,13 @@ fgr_status enqueue_fggc(fgr_ctx *ctx, const PacketsDev &pk, const FggcBox &box, 
                     P.cre[(k * kCheb + i) * kCheb + jj] = L.cheb_re[k][i][jj];
                     P.cim[(k * kCheb + i) * kCheb + jj] = L.cheb_im[k][i][jj];
                 }
-        BinLaunch bl;
-        const bool binned = D == 3 && b.bin && b.bin_m >= pk.m && pk.m > 0 && (L.n1 == 4 || L.n1 == 8) &&
-                            make_bin_box(box, D, &bl.box);
         fgr_status r;
         if (binned) {
             bin_buffers_at(b.bin, pk.m, bl.box, &bl.buf);
             bl.num_sms = ctx->num_sms;
             bl.min_count = kBinMinCount;
+            bl.clear_rows = box.rows0;
+            bl.row_cells = box.cells / box.rows0;
             StageMarks marks{timer, &ctx->timing.last.coeff_ms};
             r = launch_binned_scatter(D, L.n1, bl, st, pk, P, b.W, b.flags, &marks);
             *launches += 8;  // key, 3 scan, place, items, binned, loose
@@ -1105,13 +1122,13 @@ fgr_status enqueue_fggc(fgr_ctx *ctx, const PacketsDev &pk, const FggcBox &box, 
         const PassParams pp = pass_params(ctx, c, l, prodN_after);
         const bool last = l == 0;
         void *dst = (D == 1) ? u_dev : (cur == b.buf1 ? b.buf2 : b.buf1);
-        fgr_status r = fp64 ? launch_brange<true>(cur, pp.rows, pp.A, pp.B, b.brange, st)
-                            : launch_brange<false>(cur, pp.rows, pp.A, pp.B, b.brange, st);
+        const uint8_t *fl = l == D - 1 ? b.flags : nullptr;
+        fgr_status r = fp64 ? launch_brange<true>(cur, pp.rows, pp.A, pp.B, fl, b.brange, st)
+                            : launch_brange<false>(cur, pp.rows, pp.A, pp.B, fl, b.brange, st);
         if (r != FGR_OK) return r;
         ++*launches;
         const int64_t target = (int64_t)ctx->num_sms * ctx->tune.pass_ctas_per_sm;
         StageMarks before{timer, &ctx->timing.last.grid_ms};  // the pass kernel is timed alone
-        const uint8_t *fl = l == D - 1 ? b.flags : nullptr;
         if (ctx->fft_logn[l] > 0 && b.fft) {
             r = fp64 ? launch_fft_pass<true>(cur, dst, pp, fl, b.brange, ctx->fft_logn[l], b.fft, b.twiddle,
                                              b.tables, st, &before)

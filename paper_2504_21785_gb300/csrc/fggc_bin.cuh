@@ -97,6 +97,60 @@ __global__ void bin_items_kernel(const int2 *__restrict__ off, int64_t K, int4 *
         items[o.y + t] = make_int4((int)k, o.x + t * kBinT, min(kBinT, n - t * kBinT), 0);
 }
 
+// Before the scatter: marks every row of W that the packets of an occupied key
+// will reach (the n1^(d-1) outer neighbours of its anchor cell that lie in the
+// node box), one thread per key.  The binned and per-packet kernels reach
+// exactly these rows, so only they need clearing.
+template <int D>
+__global__ void bin_mark_rows_kernel(const int *__restrict__ count, const Common c, const BinBox bb,
+                                     uint8_t *__restrict__ row_flag) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= bb.K || count[k] == 0) return;
+    int oa[D - 1], ob[D - 1];
+    int64_t kk = k;
+#pragma unroll
+    for (int l = D - 2; l >= 0; --l) {
+        ob[l] = (int)(kk % bb.KB[l]) + bb.kb_lo[l];
+        kk /= bb.KB[l];
+        oa[l] = (int)(kk % bb.KA[l]) + bb.ka_lo[l];
+        kk /= bb.KA[l];
+    }
+    for (int k0 = 0; k0 < c.n1; ++k0) {
+        const int ia0 = oa[0] + c.dq[k0] - c.amin[0], ib0 = ob[0] + c.dp[k0] - c.bmin[0];
+        if ((unsigned)ia0 >= (unsigned)c.A[0] || (unsigned)ib0 >= (unsigned)c.B[0]) continue;
+        const int64_t row0 = (int64_t)ia0 * c.ra[0] + (int64_t)ib0 * c.rb[0];
+        if constexpr (D == 2) {
+            row_flag[row0] = 1;
+        } else {
+            for (int k1 = 0; k1 < c.n1; ++k1) {
+                const int ia1 = oa[1] + c.dq[k1] - c.amin[1], ib1 = ob[1] + c.dp[k1] - c.bmin[1];
+                if ((unsigned)ia1 >= (unsigned)c.A[1] || (unsigned)ib1 >= (unsigned)c.B[1]) continue;
+                row_flag[row0 + (int64_t)ia1 * c.ra[1] + (int64_t)ib1 * c.rb[1]] = 1;
+            }
+        }
+    }
+}
+
+// Zeroes the flagged rows of W (row_f4 16-byte words each): a warp reads the
+// flags of 32 consecutive rows at once and clears the flagged ones together.
+__global__ void __launch_bounds__(256) clear_flagged_rows_kernel(float4 *__restrict__ W,
+                                                                 const uint8_t *__restrict__ row_flag,
+                                                                 int64_t rows, int64_t row_f4) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t base = (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < rows;
+         base += nwarps * 32) {
+        const bool f = base + lane < rows && row_flag[base + lane] != 0;
+        unsigned set = __ballot_sync(0xffffffffu, f);
+        while (set) {
+            const int r = __ffs(set) - 1;
+            set &= set - 1;
+            float4 *p = W + (base + r) * row_f4;
+            for (int64_t i = lane; i < row_f4; i += 32) p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+}
+
 // coeff_dim32 with the neighbours evaluated one after the other into
 // out[k * stride] (fewer live registers than the unrolled form).
 template <int N1>
@@ -193,14 +247,24 @@ __global__ void __launch_bounds__(kBinT, 3) binned_scatter_kernel(
     int64_t *rowoff = reinterpret_cast<int64_t *>(act + kWinCells);  // [NR]
     unsigned short *ent = reinterpret_cast<unsigned short *>(rowoff + NR);  // [kBinT * N1]
     __shared__ int s_item, s_box[4], s_nact;
+    __shared__ int4 s_desc;
     __shared__ unsigned long long s_rows;  // bit r: row r lies in the node box
     const Common &c = P.c;
     const int tid = threadIdx.x;
     const int nitems = off_end->y;
+    // thread 0 fetches the next item (index and descriptor) while the CTA
+    // works on the current one
+    int next = 0;
+    int4 next_desc = make_int4(0, 0, 0, 0);
+    if (tid == 0) {
+        next = atomicAdd(work, 1);
+        if (next < nitems) next_desc = items[next];
+    }
     for (;;) {
         __syncthreads();  // the previous item's shared data are no longer read
         if (tid == 0) {
-            s_item = atomicAdd(work, 1);
+            s_item = next;
+            s_desc = next_desc;
             s_box[0] = s_box[2] = INT_MAX;
             s_box[1] = s_box[3] = INT_MIN;
             s_rows = 0ull;
@@ -208,7 +272,11 @@ __global__ void __launch_bounds__(kBinT, 3) binned_scatter_kernel(
         __syncthreads();
         const int it = s_item;
         if (it >= nitems) break;
-        const int4 item = items[it];
+        const int4 item = s_desc;
+        if (tid == 0) {
+            next = atomicAdd(work, 1);
+            if (next < nitems) next_desc = items[next];
+        }
         const bool valid = tid < item.z;
         // the rows of the item's outer anchor cell: W offsets, flags, in-box bits
         if (tid < NR) {
@@ -526,6 +594,11 @@ fgr_status launch_binned_d(const BinLaunch &L, cudaStream_t st, const PacketsDev
     FGR_CUDA_TRY(cudaMemsetAsync(b.ctr, 0, sizeof(int) * 4, st));
     const unsigned pblocks = (unsigned)((m + 255) / 256);
     bin_key_kernel<D><<<pblocks, 256, 0, st>>>(pk.q, pk.p, pk.a, m, P.c, L.box, b.key, b.count);
+    if (L.clear_rows > 0) {  // the caller cleared the row flags, not W
+        bin_mark_rows_kernel<D><<<(unsigned)((K + 255) / 256), 256, 0, st>>>(b.count, P.c, L.box, flags);
+        clear_flagged_rows_kernel<<<(unsigned)(L.num_sms * 8), 256, 0, st>>>((float4 *)W, flags, L.clear_rows,
+                                                                          L.row_cells / 2);
+    }
     const int64_t nblk = (K + 1023) / 1024;
     bin_scan1_kernel<<<(unsigned)nblk, 1024, 0, st>>>(b.count, K, L.min_count, b.off, b.bsum);
     bin_scan2_kernel<<<1, 1024, 0, st>>>(b.bsum, nblk, b.off, K);

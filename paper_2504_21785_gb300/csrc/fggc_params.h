@@ -80,6 +80,11 @@ struct BinLaunch {
     BinBuffers buf;
     int min_count = 32;  // smallest binned cell
     int num_sms = 1;
+    // rows of W (each row_cells cells) to clear before the scatter: only the
+    // rows the binned packets reach are marked and zeroed (0: W is cleared by
+    // the caller)
+    int64_t clear_rows = 0;
+    int64_t row_cells = 0;
 };
 
 // Largest key box of the binned scatter; larger boxes use the per-packet kernel.

@@ -79,6 +79,10 @@ struct fgr_ctx {
     fgr::Tuning tune;
     int fft_logn[fgr::kMaxDim] = {0, 0, 0};  // log2 N of the DFT grid stage per dimension (0: direct stage)
     int *dev_err = nullptr;          // device word: a kernel's bounded wait gave up (reported by the next call)
+    // Device view of a host word (set by the server around a large direct
+    // sum): while it is > 0 the persistent direct-sum CTAs past one per SM
+    // stop between work items, so that waiting small requests get SM slots.
+    const volatile int *yield_flag = nullptr;
     int64_t *host_pinned = nullptr;  // small pinned buffer for device->host sizes
 };
 

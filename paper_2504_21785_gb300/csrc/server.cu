@@ -16,8 +16,18 @@
 // memory counts as resident within the budget.  A group that fails is retried
 // request by request, so each request gets its own status.  Completion is
 // reported through fgr_poll with host timestamps (submit, start, done).
+//
+// Large requests (direct sums estimated above kLargeMs from their packet-point
+// pairs) never hold every worker slot: at most max_inflight - 1 run at once,
+// and a small request may pass a large one waiting at the head of the queue.
+// They run alone, on low-priority streams (small requests on high-priority
+// ones), with finer work items; while small requests are queued or running,
+// the persistent direct-sum CTAs of a large request past one per SM stop
+// between items (a pinned host word the kernel reads), so the small requests'
+// kernels find free SM slots instead of waiting for the whole large launch.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -52,6 +62,7 @@ struct Job {
     fgr_request req{};
     size_t footprint = 0;
     bool dev_out = false;
+    bool large = false;  // a long direct sum (see kLargeMs)
     St st = St::Queued;
     fgr_result res{};
 };
@@ -108,6 +119,10 @@ struct fgr_server {
     size_t plan_resident = 0;  // the part of resident held by cached plans (they can be freed)
     uint64_t plan_clock = 0;
     int running = 0;
+    int running_large = 0;     // admitted groups of a large request
+    int small_pending = 0;     // small requests queued or running
+    int *yield_host = nullptr;  // pinned, mapped: small_pending as the kernels see it
+    int *yield_dev = nullptr;
     uint64_t next_ticket = 1, next_set = 1;
     bool stop = false;
     std::thread sched;
@@ -132,7 +147,43 @@ size_t footprint(const fgr_request &r, const PacketSet &ps) {
     return f + (size_t)total * eb;  // staging of a host output
 }
 
-bool batchable(const Job &j) { return j.dev_out; }
+// Direct sums estimated above this many milliseconds are large requests.
+constexpr double kLargeMs = 2.0;
+// Work items per SM of a large request's persistent direct sum (finer than a
+// lone call's, so that CTAs reach an item boundary sooner).
+constexpr int kLargeCtasPerSm = 32;
+
+// Estimated device time of a direct sum: packets x window points per
+// dimension (the kernel's window of 2 R sqrt(eps) / h + 2 points), at rates of
+// the order this GB300 sustains (1-D: about 1.2e12 pairs/s, 2-D and 3-D with
+// their outer-product factors about 8e12; FP64 about a quarter).
+double est_direct_ms(const fgr_request &r, int64_t m) {
+    const double R = r.opt.window_r > 0 ? r.opt.window_r : (r.opt.precision == FGR_FP64 ? 8.0 : 6.0);
+    const double rs = R * std::sqrt(r.eps);
+    double pairs = (double)m;
+    for (int l = 0; l < r.d; ++l) {
+        const double n = (double)r.grid.n[l];
+        const double h = (r.grid.hi[l] - r.grid.lo[l]) / n;
+        pairs *= h > 0 ? std::min(n, std::floor(2.0 * rs / h) + 2.0) : n;
+    }
+    double rate = r.d == 1 ? 1.2e12 : 8e12;
+    if (r.opt.precision == FGR_FP64) rate *= 0.25;
+    return pairs / rate * 1e3;
+}
+
+void publish_small(fgr_server *S) {
+    if (S->yield_host) __atomic_store_n(S->yield_host, S->small_pending, __ATOMIC_RELEASE);
+}
+
+// Bookkeeping of a job that reached Done (called with the lock held).
+void job_finished(fgr_server *S, const Job &j) {
+    if (!j.large) {
+        S->small_pending -= 1;
+        publish_small(S);
+    }
+}
+
+bool batchable(const Job &j) { return j.dev_out && !j.large; }
 
 bool same_batch(const Job &a, const Job &b) {
     return a.req.method == b.req.method && a.req.d == b.req.d && a.req.opt.precision == b.req.opt.precision;
@@ -149,6 +200,10 @@ fgr_packets packets_of(const PacketSet &ps) {
     pk.reserved = 0;
     return pk;
 }
+
+// Contexts a worker keeps (a context holds a few hundred bytes of host state
+// and a device error word: keeping many avoids creating them per request).
+constexpr size_t kCtxCachePerWorker = 256;
 
 // Contexts keyed by (d, grid, eps, options), most recently used first.
 class CtxCache {
@@ -230,7 +285,17 @@ fgr_status enqueue_one(fgr_server *S, const Job &job, const PacketSet &ps, CtxCa
     fgr_status st = cache.get(r, &ctx);
     if (st != FGR_OK) return st;
     fgr_packets pk = packets_of(ps);
-    if (r.method == 0) return fgr_reconstruct_direct(ctx, &pk, r.u_out, stream);
+    if (r.method == 0) {
+        if (!job.large || !S) return fgr_reconstruct_direct(ctx, &pk, r.u_out, stream);
+        // the launch takes these at enqueue time; the cached context gets its own back
+        const int ctas_per_sm = ctx->tune.direct_ctas_per_sm;
+        ctx->tune.direct_ctas_per_sm = std::max(ctas_per_sm, kLargeCtasPerSm);
+        ctx->yield_flag = S->yield_dev;
+        st = fgr_reconstruct_direct(ctx, &pk, r.u_out, stream);
+        ctx->yield_flag = nullptr;
+        ctx->tune.direct_ctas_per_sm = ctas_per_sm;
+        return st;
+    }
     fgr_fggc_plan *plan = acquire_plan(S, job, ctx, pk, stream);
     if (!plan) return fgr_reconstruct_fggc(ctx, &pk, r.u_out, stream);
     *planned = plan;
@@ -340,8 +405,14 @@ void run_group(const Group &g, const std::vector<PacketSet> &ps, CtxCache &cache
 
 void worker_main(fgr_server *S) {
     cudaSetDevice(S->device);
-    cudaStream_t stream;
-    cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+    int prio_low = 0, prio_high = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess) {
+        cudaGetLastError();
+        prio_low = prio_high = 0;
+    }
+    cudaStream_t stream_high, stream_low;  // small requests, large requests
+    cudaStreamCreateWithPriority(&stream_high, cudaStreamNonBlocking, prio_high);
+    cudaStreamCreateWithPriority(&stream_low, cudaStreamNonBlocking, prio_low);
     CtxCache cache;
     for (;;) {
         Group group;
@@ -360,13 +431,15 @@ void worker_main(fgr_server *S) {
             }
         }
         std::vector<fgr_status> st(group.size(), FGR_OK);
+        const bool large = group[0]->large;
+        cudaStream_t stream = large ? stream_low : stream_high;
         if (group.size() == 1)
             st[0] = run_one(S, *group[0], ps[0], cache, stream);
         else if (group[0]->req.method == 0)
             run_group(group, ps, cache, stream, st);
         else
             run_fggc_group(S, group, ps, cache, stream, st);
-        cache.trim(std::max<size_t>(8, 2 * (size_t)S->max_batch));
+        cache.trim(kCtxCachePerWorker);
         {
             std::lock_guard<std::mutex> lk(S->mu);
             const double t = now_ms();
@@ -377,13 +450,16 @@ void worker_main(fgr_server *S) {
                 job.st = St::Done;
                 S->reserved -= job.footprint;
                 S->sets[job.req.set_id].users -= 1;
+                job_finished(S, job);
             }
             S->running -= 1;
+            if (large) S->running_large -= 1;
         }
         S->cv_done.notify_all();
         S->cv_sched.notify_all();
     }
-    cudaStreamDestroy(stream);
+    cudaStreamDestroy(stream_high);
+    cudaStreamDestroy(stream_low);
 }
 
 bool has_idle_plan(const fgr_server *S) {
@@ -410,16 +486,28 @@ std::vector<fgr_fggc_plan *> evict_idle_plans(fgr_server *S, size_t need) {
     return out;
 }
 
-// Completes the queue's head with FGR_E_CAPACITY: it does not fit the budget
+// The next request to admit: the head of the queue, unless it is large and the
+// large requests already hold all but one worker slot; then the first small
+// request behind it (end() if there is none).
+std::deque<std::shared_ptr<Job>>::iterator next_candidate(fgr_server *S) {
+    auto it = S->queue.begin();
+    if (it == S->queue.end() || !(*it)->large || S->running_large < std::max(1, S->max_inflight - 1)) return it;
+    return std::find_if(S->queue.begin(), S->queue.end(), [](const std::shared_ptr<Job> &j) { return !j->large; });
+}
+
+bool fits(const fgr_server *S, const Job &j) { return S->resident + S->reserved + j.footprint <= S->budget; }
+
+// Completes a queued request with FGR_E_CAPACITY: it does not fit the budget
 // even with nothing else admitted and no cached plan left.
-void fail_head_capacity(fgr_server *S) {
-    auto j = S->queue.front();
-    S->queue.pop_front();
+void fail_capacity(fgr_server *S, std::deque<std::shared_ptr<Job>>::iterator it) {
+    auto j = *it;
+    S->queue.erase(it);
     const double t = now_ms();
     j->res.status = FGR_E_CAPACITY;
     j->res.t_start_ms = j->res.t_done_ms = t;
     j->st = St::Done;
     S->sets[j->req.set_id].users -= 1;
+    job_finished(S, *j);
     S->cv_done.notify_all();
 }
 
@@ -429,15 +517,17 @@ void scheduler_main(fgr_server *S) {
         S->cv_sched.wait(lk, [&] {
             if (S->stop) return true;
             if (S->queue.empty() || S->running >= S->max_inflight) return false;
-            const auto &j = S->queue.front();
-            if (S->resident + S->reserved + j->footprint <= S->budget) return true;
-            // the head does not fit: free idle plans, or fail it when nothing
-            // that could free memory is in flight
+            auto c = next_candidate(S);
+            if (c == S->queue.end()) return false;  // only large requests wait, and their slots are taken
+            if (fits(S, **c)) return true;
+            // the candidate does not fit: free idle plans, or fail it when
+            // nothing that could free memory is in flight
             return has_idle_plan(S) || (S->running == 0 && S->reserved == 0);
         });
         if (S->stop) break;
-        if (S->resident + S->reserved + S->queue.front()->footprint > S->budget) {
-            std::vector<fgr_fggc_plan *> drop = evict_idle_plans(S, S->queue.front()->footprint);
+        auto c = next_candidate(S);
+        if (!fits(S, **c)) {
+            std::vector<fgr_fggc_plan *> drop = evict_idle_plans(S, (*c)->footprint);
             if (!drop.empty()) {
                 lk.unlock();
                 for (fgr_fggc_plan *pl : drop) fgr_fggc_plan_destroy(pl);
@@ -445,23 +535,24 @@ void scheduler_main(fgr_server *S) {
                 continue;  // look again: the queue or the memory may have changed
             }
             if (S->running == 0 && S->reserved == 0) {
-                fail_head_capacity(S);
+                fail_capacity(S, c);
                 continue;
             }
         }
-        // admit in arrival order while slots and memory allow; a batchable
-        // request takes the later compatible ones with it
-        while (!S->queue.empty() && S->running < S->max_inflight) {
-            auto j = S->queue.front();
-            if (S->resident + S->reserved + j->footprint > S->budget) break;
-            S->queue.pop_front();
+        // admit in arrival order (a small request may pass a large one, see
+        // next_candidate) while slots and memory allow; a batchable request
+        // takes the later compatible ones with it
+        while (S->running < S->max_inflight) {
+            c = next_candidate(S);
+            if (c == S->queue.end() || !fits(S, **c)) break;
+            auto j = *c;
+            S->queue.erase(c);
             S->reserved += j->footprint;
             Group g{j};
             if (batchable(*j))
                 for (auto it = S->queue.begin(); it != S->queue.end() && (int)g.size() < S->max_batch;) {
                     const auto &k = *it;
-                    if (batchable(*k) && same_batch(*j, *k) &&
-                        S->resident + S->reserved + k->footprint <= S->budget) {
+                    if (batchable(*k) && same_batch(*j, *k) && fits(S, *k)) {
                         S->reserved += k->footprint;
                         g.push_back(k);
                         it = S->queue.erase(it);
@@ -470,6 +561,7 @@ void scheduler_main(fgr_server *S) {
                     }
                 }
             S->running += 1;
+            if (j->large) S->running_large += 1;
             S->admitted.push_back(std::move(g));
         }
         S->cv_work.notify_all();
@@ -500,6 +592,17 @@ fgr_status fgr_server_create(size_t hbm_budget_bytes, int32_t max_inflight, fgr_
     }
     S->budget = hbm_budget_bytes;
     S->max_inflight = max_inflight;
+    int *word = nullptr;  // the yield word; without it large requests simply never yield
+    if (cudaHostAlloc((void **)&word, sizeof(int), cudaHostAllocMapped) == cudaSuccess) {
+        *word = 0;
+        if (cudaHostGetDevicePointer((void **)&S->yield_dev, word, 0) == cudaSuccess) {
+            S->yield_host = word;
+        } else {
+            S->yield_dev = nullptr;
+            cudaFreeHost(word);
+        }
+    }
+    cudaGetLastError();
     try {
         S->sched = std::thread(scheduler_main, S);
         for (int i = 0; i < max_inflight; ++i) S->workers.emplace_back(worker_main, S);
@@ -513,6 +616,7 @@ fgr_status fgr_server_create(size_t hbm_budget_bytes, int32_t max_inflight, fgr_
         S->cv_work.notify_all();
         if (S->sched.joinable()) S->sched.join();
         for (auto &w : S->workers) w.join();
+        if (S->yield_host) cudaFreeHost(S->yield_host);
         delete S;
         return FGR_E_INTERNAL;
     }
@@ -529,6 +633,7 @@ void fgr_server_destroy(fgr_server *S) {
             j->st = St::Done;
             j->res.status = FGR_E_CANCELLED;
             j->res.t_done_ms = now_ms();
+            job_finished(S, *j);
         }
         S->queue.clear();
     }
@@ -540,6 +645,7 @@ void fgr_server_destroy(fgr_server *S) {
     cudaSetDevice(S->device);
     for (auto &kv : S->plans) fgr_fggc_plan_destroy(kv.second.plan);
     for (auto &kv : S->sets) cudaFree(kv.second.buf);
+    if (S->yield_host) cudaFreeHost(S->yield_host);
     delete S;
 }
 
@@ -664,6 +770,7 @@ fgr_status fgr_submit(fgr_server *S, const fgr_request *req, uint64_t *ticket) {
         return FGR_E_INVALID;
     }
     j->footprint = footprint(j->req, it->second);
+    j->large = j->req.method == 0 && est_direct_ms(j->req, it->second.m) > kLargeMs;
     // cached plans do not count: the scheduler frees them for requests that need their memory
     if (S->resident - S->plan_resident + j->footprint > S->budget) {
         set_error("submit: request needs %zu bytes; budget %zu with %zu resident in packet sets", j->footprint,
@@ -676,6 +783,10 @@ fgr_status fgr_submit(fgr_server *S, const fgr_request *req, uint64_t *ticket) {
     j->res.t_submit_ms = now_ms();
     S->jobs[j->ticket] = j;
     S->queue.push_back(j);
+    if (!j->large) {
+        S->small_pending += 1;
+        publish_small(S);
+    }
     *ticket = j->ticket;
     S->cv_sched.notify_all();
     return FGR_OK;
@@ -714,6 +825,7 @@ fgr_status fgr_cancel(fgr_server *S, uint64_t ticket) {
     j->st = St::Done;
     j->res.status = FGR_E_CANCELLED;
     j->res.t_done_ms = now_ms();
+    job_finished(S, *j);
     S->cv_done.notify_all();
     S->cv_sched.notify_all();
     return FGR_OK;

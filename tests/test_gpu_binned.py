@@ -127,3 +127,26 @@ def test_binned_matches_direct_sum_on_workload_like_cells():
     direct = _gpu.reconstruct("direct", pk, grid, eps, _gpu.options("fp32"))
     assert _gpu.rel_l2(again, got) <= 1e-6
     assert _gpu.rel_l2(got, direct) <= 1e-5
+
+
+def test_rows_left_from_an_earlier_call_are_not_read():
+    # The binned path clears only the rows of the node array that its packets
+    # reach.  A first call with a wide packet set leaves non-zero rows in the
+    # context's memory; a second call with packets in other outer cells must
+    # still equal the oracle (unmarked rows are neither scanned nor contracted).
+    import paper_2504_21785_gb300 as fgr
+    eps = 1 / 64
+    grid = _grid((40, 36, 44))
+    wide, mesh = clustered(21, 3, eps, [[(c, 2 * c), (-c, c)] for c in range(-6, 7, 2)], [64] * 7,
+                           (-2.0, 2.0), (-2.0, 2.0))
+    other, _ = clustered(22, 3, eps, [[(1, -3), (2, 5)], [(-3, 0), (0, -2)]], [300, 40], (-1.0, 1.0), (-1.5, 1.5))
+    opt = _gpu.options("fp32")
+    with fgr.Context(3, grid, eps, opt) as ctx:
+        _gpu.reconstruct("fggc", wide, grid, eps, opt, ctx=ctx)
+        got = _gpu.reconstruct("fggc", other, grid, eps, opt, ctx=ctx)
+    rng = np.random.default_rng(4)
+    pts = np.stack([rng.integers(0, n, 500) for n in grid["n"]])
+    ref = fggc.reconstruct(other, grid, eps, mesh.dq, mesh.dp, lsa.Strategy(nq=4, np_=2), R=6, points=pts)
+    assert _gpu.rel_l2(got[tuple(pts)], ref) <= 1e-5
+    alone = _gpu.reconstruct("fggc", other, grid, eps, opt)
+    assert _gpu.rel_l2(got, alone) <= 1e-6

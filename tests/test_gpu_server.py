@@ -290,3 +290,40 @@ def test_cached_plans_give_way_to_a_request_that_needs_their_memory(fgr):
         assert np.linalg.norm(u.cpu().numpy() - outs[0].cpu().numpy()) <= 1e-6 * np.linalg.norm(outs[0].cpu().numpy())
     finally:
         fgr.fgr_server_destroy(srv)
+
+
+def test_small_requests_pass_a_large_direct_sum(fgr):
+    # A 2-D direct sum of 2^21 packets on 1024^2 points (about 10 ms alone) is a
+    # large request: it runs on a low-priority stream, leaves a worker slot to
+    # small requests and, while they wait, gives up a CTA slot per SM between
+    # its work items.  Small requests submitted right after it finish first,
+    # and every result equals the same request run alone.
+    import torch
+    from . import _gpu
+    big = random_packets(91, 2, 1 << 21, q_range=(-2.5, 2.5), p_range=(-2, 2), s_range=(-1, 1))
+    small = [random_packets(92 + k, 1, 6000, q_range=(-2.5, 2.5), p_range=(-2, 2), s_range=(-1, 1))
+             for k in range(2)]
+    opt = fgr.make_options(precision=fgr.FGR_FP32)
+    srv = fgr.fgr_server_create(8 << 30, 4)
+    try:
+        sid_big = fgr.fgr_register_packets(srv, 2, fgr.make_packets(*[np.ascontiguousarray(big[k]) for k in "qpsa"]))
+        sids = [fgr.fgr_register_packets(srv, 1, fgr.make_packets(*[np.ascontiguousarray(p[k]) for k in "qpsa"]))
+                for p in small]
+        g_big = _grid(2, 1024)
+        u_big = torch.zeros((1024, 1024), dtype=torch.complex64, device="cuda")
+        reqs = [(k % 2, int(2 ** (10 + k % 3)), k % 2) for k in range(16)]   # (set, n, method)
+        outs = [torch.zeros(n, dtype=torch.complex64, device="cuda") for (_, n, _) in reqs]
+        t_big = fgr.fgr_submit(srv, fgr.make_request(0, g_big, 1 / 64, opt, sid_big, u_big))
+        tickets = [fgr.fgr_submit(srv, fgr.make_request(mth, _grid(1, n), 1 / 256, opt, sids[s], u))
+                   for (s, n, mth), u in zip(reqs, outs)]
+        res = [fgr.fgr_poll(srv, t, 60000) for t in tickets]
+        r_big = fgr.fgr_poll(srv, t_big, 60000)
+        assert r_big.status == 0 and all(r.status == 0 for r in res)
+        assert max(r.t_done_ms for r in res) < r_big.t_done_ms
+        ref = _gpu.reconstruct("direct", big, g_big, 1 / 64, opt)
+        assert _gpu.rel_l2(u_big.cpu().numpy(), ref) <= 1e-6
+        for (s, n, mth), u in zip(reqs, outs):
+            ref = _gpu.reconstruct("fggc" if mth else "direct", small[s], _grid(1, n), 1 / 256, opt)
+            assert _gpu.rel_l2(u.cpu().numpy(), ref) <= 1e-6
+    finally:
+        fgr.fgr_server_destroy(srv)
