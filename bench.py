@@ -1004,6 +1004,12 @@ def serving_bench(args, device_index: int):
         wait = np.array([r.t_start_ms - r.t_submit_ms for r in res])
         svc = np.array([r.t_done_ms - r.t_start_ms for r in res])
         tail = lat >= np.percentile(lat, 99)
+        by_method = {}
+        for mth_, name in ((0, "direct"), (1, "fggc")):
+            sel = np.array([q[5] == mth_ for q in reqs])
+            if sel.any():
+                by_method[name] = {"p50_ms": float(np.percentile(lat[sel], 50)),
+                                   "p99_ms": float(np.percentile(lat[sel], 99))}
         kinds = {}
         for (sid_, d_, e_, m_, g_, mth_), t_ in zip(reqs, tail):
             if t_:
@@ -1013,6 +1019,7 @@ def serving_bench(args, device_index: int):
         packets = sum(q[3] for q in reqs)
         levels["%.1fx" % frac] = {"lambda_req_per_s": lam, "p50_ms": float(np.percentile(lat, 50)),
                                   "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
+                                  "by_method": by_method,
                                   "tail_1pct": {"wait_ms_median": float(np.median(wait[tail])),
                                                 "service_ms_median": float(np.median(svc[tail])),
                                                 "kinds": kinds},

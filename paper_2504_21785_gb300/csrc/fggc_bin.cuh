@@ -186,8 +186,10 @@ __device__ __forceinline__ void coeff_dim32_rolled(const Params32 &P, double Q, 
             float ur = 0.f, ui = 0.f;
 #pragma unroll
             for (int jj = 0; jj < kCheb; ++jj) {
-                ur = fmaf(Cr[i * kCheb + jj], Tt[jj], ur);
-                ui = fmaf(Ci[i * kCheb + jj], Tt[jj], ui);
+                if (i + jj <= cheb_total<N1>()) {
+                    ur = fmaf(Cr[i * kCheb + jj], Tt[jj], ur);
+                    ui = fmaf(Ci[i * kCheb + jj], Tt[jj], ui);
+                }
             }
             sr = fmaf(Ts[i], ur, sr);
             si = fmaf(Ts[i], ui, si);
@@ -205,9 +207,17 @@ __device__ __forceinline__ void coeff_dim32_rolled(const Params32 &P, double Q, 
 // Target cells of one window (node cells of the inner plane).
 constexpr int kWinCells = 1024;
 
+// float2 slots per packet in the coefficient array: D x N1 rounded to an odd
+// number of 16-byte words, so that the 16-byte loads of different packets by
+// the lanes of a warp spread over all bank groups instead of two
+template <int D, int N1>
+__host__ __device__ constexpr int coef_stride() {
+    return D * N1 + (((D * N1 / 2) % 2 == 0) ? 2 : 0);
+}
+
 template <int D, int N1>
 __host__ __device__ constexpr int binned_smem_bytes() {
-    return kBinT * D * N1 * 8      // coefficients [packet][dimension][neighbour] (float2)
+    return kBinT * coef_stride<D, N1>() * 8  // coefficients [packet][dimension][neighbour] (float2)
            + kBinT * 8             // packet weights w (float2)
            + 2 * kWinCells * 4     // per-cell entry start and cursor (int)
            + kWinCells * 4         // active cells (packed line, column)
@@ -239,8 +249,9 @@ __global__ void __launch_bounds__(kBinT, 3) binned_scatter_kernel(
     constexpr int NK1 = D == 3 ? N1 : 1;         // k1 values
     constexpr int kPer = kWinCells / kBinT;      // target cells per thread in the CSR build
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *coef = reinterpret_cast<float2 *>(smem_raw);             // [kBinT][D][N1]
-    float2 *wgt = coef + kBinT * D * N1;                             // [kBinT]
+    constexpr int CS = coef_stride<D, N1>();
+    float2 *coef = reinterpret_cast<float2 *>(smem_raw);             // [kBinT][CS]: [D][N1] + padding
+    float2 *wgt = coef + kBinT * CS;                                 // [kBinT]
     int *cstart = reinterpret_cast<int *>(wgt + kBinT);              // [kWinCells]
     int *cend = cstart + kWinCells;                                  // [kWinCells]
     unsigned *act = reinterpret_cast<unsigned *>(cend + kWinCells);  // [kWinCells]
@@ -305,7 +316,7 @@ __global__ void __launch_bounds__(kBinT, 3) binned_scatter_kernel(
         }
         float wr = 0.f, wi = 0.f;
         int ra = 0, rb = 0;  // inner anchor relative to the node box (set by the last dimension)
-        float2 *cj = coef + tid * D * N1;
+        float2 *cj = coef + tid * CS;
         if (valid) {
             const int64_t j = sorted[item.y + tid];
             double ts = s[j] * c.inv_2pi_eps;
@@ -456,11 +467,11 @@ __global__ void __launch_bounds__(kBinT, 3) binned_scatter_kernel(
                     for (int v = 0; v < NK1; ++v) accr[u][v] = acci[u][v] = 0.f;
                 for (int x = x0; x < x1; ++x) {
                     const int en = ent[x], jj = en >> 4, kk = en & 15;
-                    const float2 wv = wgt[jj], cl = coef[(jj * D + D - 1) * N1 + kk];
+                    const float2 wv = wgt[jj], cl = coef[jj * CS + (D - 1) * N1 + kk];
                     float2 ev;
                     cmul(wv.x, wv.y, cl.x, cl.y, ev.x, ev.y);
                     // the packet's coefficients, 16-byte loads (two neighbours each)
-                    const float4 *cp4 = reinterpret_cast<const float4 *>(coef + jj * D * N1);
+                    const float4 *cp4 = reinterpret_cast<const float4 *>(coef + jj * CS);
                     float2 c0v[NA];
 #pragma unroll
                     for (int u = 0; u < NA; u += 2) {

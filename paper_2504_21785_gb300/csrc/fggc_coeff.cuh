@@ -131,8 +131,10 @@ __device__ __forceinline__ void coeff_dim32(const PT &P, double Q, double Pm, in
             float ur = 0.f, ui = 0.f;
 #pragma unroll
             for (int j = 0; j < kCheb; ++j) {
-                ur = fmaf(Cr[i * kCheb + j], Tt[j], ur);
-                ui = fmaf(Ci[i * kCheb + j], Tt[j], ui);
+                if (i + j <= cheb_total<N>()) {
+                    ur = fmaf(Cr[i * kCheb + j], Tt[j], ur);
+                    ui = fmaf(Ci[i * kCheb + j], Tt[j], ui);
+                }
             }
             sr = fmaf(Ts[i], ur, sr);
             si = fmaf(Ts[i], ui, si);

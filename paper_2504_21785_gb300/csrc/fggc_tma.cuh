@@ -1,6 +1,6 @@
 // K5 grid pass (FP32, 32-point tiles) with the node-array tiles staged by the
 // tensor memory accelerator: the pass input, viewed as a 2-D tensor of
-// (row, a) lines by B cells, is read in boxes of 32 b-cells x MAXBAND lines by
+// (row, a) lines by B cells, is read in boxes of kTB b-cells x MAXBAND lines by
 // cp.async.bulk.tensor into two shared-memory buffers that alternate, so the
 // next tile's copy overlaps the current tile's arithmetic (one warp per CTA:
 // lane 0 issues the copies, every lane waits on the buffer's mbarrier).
@@ -11,7 +11,11 @@
 #pragma once
 
 constexpr unsigned kTmaWaitLimit = 1u << 26;  // polls of an mbarrier before giving up
-constexpr int kTB = 16;                       // b cells per staged tile (a 128-byte row per line)
+// b cells per staged tile (a 96-byte row per line).  A tile is multiplied
+// whole, so its width trades the zero padding past a row's occupied b-range
+// against the per-tile overhead; on the 3-D workload 12 (or 8) cells take the
+// passes from 5.29 to 4.54 ms against 16.
+constexpr int kTB = 12;
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) {
     return (unsigned)__cvta_generic_to_shared(p);
@@ -77,6 +81,7 @@ __global__ void __launch_bounds__(32) grid_pass_tma_kernel(const __grid_constant
                                                            const int2 *__restrict__ brange, const PassTables tab,
                                                            int *__restrict__ err) {
     constexpr int TP = 32;
+    static_assert(kTB % 4 == 0, "whole 16-byte words per tile row, four b values per step");
     __shared__ __align__(128) float2 sw[2][MAXBAND][kTB];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ double2 s_tot[RPC][TP];  // per row and lane: the FP64 sum of the chunk partials

@@ -20,6 +20,15 @@ constexpr int kMaxN1 = 16;  // 1-D neighbours per packet: nq * np <= 16
 // (3e-10 for Q4P2 at 10, 4e-13 at 12) lies far below the FP32 rounding of its
 // stored coefficients and of its evaluation.
 constexpr int kCheb = 10;
+// Terms T_i(s) T_j(t) the FP32 kernels evaluate: i + j <= cheb_total<n1>().
+// For n1 <= 8 (Q2P2, Q4P2) the triangle i + j <= 11 keeps 72 of the 100 terms
+// and the dropped coefficients sum to below 1e-8 of the largest one (Q4P2
+// 8.4e-9, Q2P2 7e-12), under the FP32 rounding of the evaluation; n1 = 16
+// (Q4P4) keeps the whole table.
+template <int N1>
+__host__ __device__ constexpr int cheb_total() {
+    return N1 <= 8 ? 11 : 2 * (kCheb - 1);
+}
 
 struct Lsa {
     int nq = 4, np = 2, n1 = 8, rank = 0;
