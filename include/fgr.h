@@ -387,7 +387,9 @@ fgr_status fgr_get_info(const fgr_ctx *ctx, fgr_info *out);
  * kernels, grid_ms = the whole grid stage (eq. 2.24), of which pass_ms is the
  * grid-pass kernels alone; pass_terms = node-point terms of the grid passes
  * (per pass, over every (row, node a) line: the occupied b-range times the
- * grid points in node a's window; counted on the device when timing is on). */
+ * grid points in node a's window; counted on the device, by one extra kernel
+ * per pass, when timing is set to 2).  fgr_set_timing: 0 off, 1 per-stage
+ * events, 2 per-stage events and pass_terms. */
 typedef struct {
     double prep_ms, coeff_ms, scatter_ms, grid_ms, direct_ms, propagate_ms, total_ms;
     int64_t launches;       /* kernels launched by the last call */

@@ -689,6 +689,7 @@ fgr_status fgr_get_info(const fgr_ctx *ctx, fgr_info *out) {
 fgr_status fgr_set_timing(fgr_ctx *ctx, int32_t enabled) {
     if (!ctx) return FGR_E_INVALID;
     ctx->timing.enabled = enabled != 0;
+    ctx->timing.count_terms = enabled >= 2;
     return FGR_OK;
 }
 

@@ -1221,7 +1221,7 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
         if (!b.bin) return FGR_E_NOMEM;
         b.bin_m = pk.m;
     }
-    if (ctx->timing.enabled) {
+    if (ctx->timing.enabled && ctx->timing.count_terms) {
         b.terms = (unsigned long long *)scratch.get(sizeof(unsigned long long));
         if (!b.terms) return FGR_E_NOMEM;
         FGR_CUDA_TRY(cudaMemsetAsync(b.terms, 0, sizeof(unsigned long long), st));
@@ -1230,11 +1230,11 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
     if (r != FGR_OK) return r;
     ctx->timing.last.launches = launches;
     timer.finish();
+    if (ctx->timing.enabled) ctx->timing.last.grid_ms += ctx->timing.last.pass_ms;  // the whole grid stage
     if (b.terms) {
         unsigned long long terms = 0;
         FGR_CUDA_TRY(cudaMemcpy(&terms, b.terms, sizeof(terms), cudaMemcpyDeviceToHost));
         ctx->timing.last.pass_terms = (int64_t)terms;
-        ctx->timing.last.grid_ms += ctx->timing.last.pass_ms;
     }
     return FGR_OK;
 }

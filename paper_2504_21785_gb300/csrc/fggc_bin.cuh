@@ -24,7 +24,8 @@
 namespace fgr {
 namespace {
 
-constexpr int kBinT = 256;  // packets (threads) per binned item
+constexpr int kBinT = 256;         // packets (threads) per binned item
+constexpr int kBinCtasPerSm = 3;   // resident binned-scatter CTAs per SM (registers, shared memory)
 
 // Warp-aggregated atomicAdd of sign on ctr[k] by the active lanes (one atomic
 // per distinct k); returns the old value plus sign times the lane's rank
@@ -239,7 +240,7 @@ __device__ __forceinline__ int2 block_exclusive_scan(int2 v, int2 *total);
 // value to W with one 8-byte reduction (consecutive threads: consecutive cells
 // of the row).  No floating-point atomics in shared memory.
 template <int D, int N1>
-__global__ void __launch_bounds__(kBinT, 3) binned_scatter_kernel(
+__global__ void __launch_bounds__(kBinT, kBinCtasPerSm) binned_scatter_kernel(
     const double *__restrict__ q, const double *__restrict__ p, const double *__restrict__ s,
     const double *__restrict__ a, int64_t m, const __grid_constant__ Params32 P, const BinBox bb,
     const int *__restrict__ sorted, const int4 *__restrict__ items, const int2 *__restrict__ off_end,
@@ -621,7 +622,7 @@ fgr_status launch_binned_d(const BinLaunch &L, cudaStream_t st, const PacketsDev
     constexpr int smem = binned_smem_bytes<D, N1>();
     FGR_CUDA_TRY(cudaFuncSetAttribute(binned_scatter_kernel<D, N1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       smem));
-    binned_scatter_kernel<D, N1><<<(unsigned)(L.num_sms * 3), kBinT, smem, st>>>(
+    binned_scatter_kernel<D, N1><<<(unsigned)(L.num_sms * kBinCtasPerSm), kBinT, smem, st>>>(
         pk.q, pk.p, pk.s, pk.a, m, P, L.box, b.sorted, b.items, b.off + K, b.ctr + 1, (float2 *)W, flags);
     constexpr int T = coeff_threads<false, N1>();
     coeff_scatter_list_kernel<D, false, N1><<<(unsigned)(L.num_sms * 4), T, 0, st>>>(

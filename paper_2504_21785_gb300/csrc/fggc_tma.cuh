@@ -67,6 +67,15 @@ __device__ __forceinline__ bool tma_wait(uint64_t *bar, unsigned phase, int *err
     return false;
 }
 
+// Compensated summation (Kahan): s += x with c carrying the negated rounding
+// error of the previous additions; the sum is s - c.
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
 // map: boxes of MAXBAND lines; map_half: boxes of MAXBAND / 2 lines, for a
 // last band chunk that needs no more (half the copy).  A CTA (one warp) takes
 // one 32-point tile of RPC consecutive rows: the rows share the tile's node
@@ -84,7 +93,9 @@ __global__ void __launch_bounds__(32) grid_pass_tma_kernel(const __grid_constant
     static_assert(kTB % 4 == 0, "whole 16-byte words per tile row, four b values per step");
     __shared__ __align__(128) float2 sw[2][MAXBAND][kTB];
     __shared__ __align__(8) uint64_t bar[2];
-    __shared__ double2 s_tot[RPC][TP];  // per row and lane: the FP64 sum of the chunk partials
+    // per row and lane: the compensated FP32 sum of the chunk partials (re, im
+    // and their running corrections; FP64 runs at 1/64 of the FP32 rate here)
+    __shared__ float4 s_tot[RPC][TP];
     const int lane = threadIdx.x;
     const int64_t row0 = (int64_t)blockIdx.x * RPC;
     const int tile = blockIdx.y;
@@ -117,7 +128,7 @@ __global__ void __launch_bounds__(32) grid_pass_tma_kernel(const __grid_constant
         b_start[r] = ulo & ~1;
         nbc[r] = live ? (uhi - b_start[r] + kTB) / kTB : 0;
         S += nbc[r];
-        s_tot[r][lane] = make_double2(0.0, 0.0);
+        s_tot[r][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     const int nac = nb_total > 0 ? (nb_total + MAXBAND - 1) / MAXBAND : 0;
     const int ntiles = nac * S;
@@ -163,6 +174,9 @@ __global__ void __launch_bounds__(32) grid_pass_tma_kernel(const __grid_constant
     }
     const double xm = grid_x(pp.lo, pp.h, valid ? m : (int64_t)tile * TP);
     const float2 ph = tab.ph[valid ? m : (int64_t)tile * TP];
+    // rotation of one b step, e^{2 pi i (ph.x + ph.y)} (accurate sine and cosine)
+    float step_r, step_i;
+    sincospif(2.f * (ph.x - rint_fast(ph.x) + ph.y), &step_i, &step_r);
     const float cef = (float)(pp.neg_half_inv_eps * 1.4426950408889634);  // log2(e) / (-2 eps)
     const float dqf = (float)pp.dq;
     float g[MAXBAND];
@@ -218,22 +232,31 @@ __global__ void __launch_bounds__(32) grid_pass_tma_kernel(const __grid_constant
                     vi[3] = fmaf(g[i], w2.w, vi[3]);
                 }
             }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const float bf = (float)(pp.bmin + b0 + bb + u);
+            // e^{i b dp x_m / eps} at the step's first b from the reduced
+            // phase, the next three b by rotation with the per-b factor
+            float zr, zi;
+            {
+                const float bf = (float)(pp.bmin + b0 + bb);
                 float f = bf * ph.x;
                 f -= rint_fast(f);
                 float tau = fmaf(bf, ph.y, f);
                 tau -= rint_fast(tau);
-                float sn, cs;
-                __sincosf(6.283185307179586f * tau, &sn, &cs);
-                accr += cs * vr[u] - sn * vi[u];
-                acci += cs * vi[u] + sn * vr[u];
+                __sincosf(6.283185307179586f * tau, &zi, &zr);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                accr += zr * vr[u] - zi * vi[u];
+                acci += zr * vi[u] + zi * vr[u];
+                if (u < 3) {
+                    const float nr = zr * step_r - zi * step_i;
+                    zi = fmaf(zr, step_i, zi * step_r);
+                    zr = nr;
+                }
             }
         }
-        double2 tv = s_tot[r][lane];
-        tv.x += (double)accr;
-        tv.y += (double)acci;
+        float4 tv = s_tot[r][lane];
+        kahan_add(tv.x, tv.z, accr);
+        kahan_add(tv.y, tv.w, acci);
         s_tot[r][lane] = tv;
         // the buffer is free again: refill it with tile t + 2
         __syncwarp();
@@ -246,8 +269,8 @@ __global__ void __launch_bounds__(32) grid_pass_tma_kernel(const __grid_constant
     for (int r = 0; r < RPC; ++r) {
         const int64_t row = row0 + r;
         if (row < pp.rows && valid) {
-            const double2 tv = s_tot[r][lane];
-            out[row * pp.N + m] = make_float2((float)tv.x, (float)tv.y);
+            const float4 tv = s_tot[r][lane];
+            out[row * pp.N + m] = make_float2(__fsub_rn(tv.x, tv.z), __fsub_rn(tv.y, tv.w));
         }
     }
 }

@@ -60,6 +60,7 @@ struct Mesh {
 
 struct Timing {
     bool enabled = false;
+    bool count_terms = false;  // also count the grid passes' node-point terms (one kernel per pass)
     fgr_stats last{};
 };
 

@@ -382,8 +382,9 @@ def fgr_get_info(ctx) -> fgr_info:
     return i
 
 
-def fgr_set_timing(ctx, enabled: bool):
-    return _check(load().fgr_set_timing(ctx, 1 if enabled else 0))
+def fgr_set_timing(ctx, enabled):
+    """0/False off, 1/True per-stage events, 2 also the grid passes' terms."""
+    return _check(load().fgr_set_timing(ctx, int(enabled)))
 
 
 def fgr_get_stats(ctx) -> fgr_stats:
