@@ -9,6 +9,7 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -289,7 +290,64 @@ bool is_device_ptr(const void *p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-fgr_status check_packets(const fgr_ctx *ctx, const fgr_packets *pk) {
+// First index i < n with x[i] not finite, or n.  Large arrays are scanned by
+// several host threads (a call on 2^24 host packets scans 1.2 GB).
+int64_t first_non_finite(const double *x, int64_t n) {
+    constexpr int64_t kChunk = int64_t(1) << 20;
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int64_t nt = std::min<int64_t>(std::max(1u, std::min(hw, 32u)), (n + kChunk - 1) / kChunk);
+    if (nt <= 1) {
+        for (int64_t i = 0; i < n; ++i)
+            if (!std::isfinite(x[i])) return i;
+        return n;
+    }
+    std::vector<int64_t> first((size_t)nt, n);
+    std::atomic<int64_t> found{n};
+    auto scan = [&](int64_t t) {
+        const int64_t lo = n * t / nt, hi = n * (t + 1) / nt;
+        for (int64_t i = lo; i < hi; ++i) {
+            if (((i - lo) & 0xffff) == 0 && found.load(std::memory_order_relaxed) < lo) return;
+            if (!std::isfinite(x[i])) {
+                first[(size_t)t] = i;
+                int64_t cur = found.load();
+                while (i < cur && !found.compare_exchange_weak(cur, i)) {
+                }
+                return;
+            }
+        }
+    };
+    std::vector<std::thread> th;
+    try {
+        for (int64_t t = 1; t < nt; ++t) th.emplace_back(scan, t);
+    } catch (...) {  // no threads to be had: scan the rest here
+        for (int64_t t = (int64_t)th.size() + 1; t < nt; ++t) scan(t);
+    }
+    scan(0);
+    for (auto &h : th) h.join();
+    int64_t best = n;
+    for (int64_t v : first) best = std::min(best, v);
+    return best;
+}
+
+// Finiteness of host packet data (Q, P, S, A).
+fgr_status check_host_finite(const fgr_ctx *ctx, const fgr_packets *pk) {
+    const int d = ctx->d;
+    const int64_t m = pk->m;
+    int64_t i = std::min(first_non_finite(pk->q, d * m), first_non_finite(pk->p, d * m));
+    if (i < d * m) {
+        set_error("packets: non-finite Q or P at %lld", (long long)i);
+        return FGR_E_INVALID;
+    }
+    i = std::min(first_non_finite(pk->s, m), std::min(first_non_finite(pk->a, m), first_non_finite(pk->a + m, m)));
+    if (i < m) {
+        set_error("packets: non-finite S or A at %lld", (long long)i);
+        return FGR_E_INVALID;
+    }
+    return FGR_OK;
+}
+
+// Arguments of a packet set, without reading the data.
+fgr_status check_packet_args(const fgr_packets *pk) {
     if (!pk || pk->m < 0 || (pk->m > 0 && (!pk->q || !pk->p || !pk->s || !pk->a))) {
         set_error("packets: need m >= 0 and non-NULL q, p, s, a");
         return FGR_E_INVALID;
@@ -302,20 +360,13 @@ fgr_status check_packets(const fgr_ctx *ctx, const fgr_packets *pk) {
         set_error("packets: on_device must be 0 or 1");
         return FGR_E_INVALID;
     }
-    if (pk->on_device == 0 && pk->m > 0) {  // host data can be checked for finiteness cheaply
-        const int d = ctx->d;
-        for (int64_t i = 0; i < d * pk->m; ++i)
-            if (!is_finite(pk->q[i]) || !is_finite(pk->p[i])) {
-                set_error("packets: non-finite Q or P at %lld", (long long)i);
-                return FGR_E_INVALID;
-            }
-        for (int64_t i = 0; i < pk->m; ++i)
-            if (!is_finite(pk->s[i]) || !is_finite(pk->a[i]) || !is_finite(pk->a[pk->m + i])) {
-                set_error("packets: non-finite S or A at %lld", (long long)i);
-                return FGR_E_INVALID;
-            }
-    }
     return FGR_OK;
+}
+
+fgr_status check_packets(const fgr_ctx *ctx, const fgr_packets *pk) {
+    fgr_status rc = check_packet_args(pk);
+    if (rc == FGR_OK && pk->on_device == 0 && pk->m > 0) rc = check_host_finite(ctx, pk);  // host data
+    return rc;
 }
 
 // Makes device copies of host packet arrays (or passes device pointers through).
@@ -444,7 +495,7 @@ fgr_status reconstruct(fgr_ctx *ctx, const fgr_packets *pk, void *u_out, void *s
         set_error("ctx and u_out must be non-NULL");
         return FGR_E_INVALID;
     }
-    fgr_status rc = check_packets(ctx, pk);
+    fgr_status rc = check_packet_args(pk);
     if (rc != FGR_OK) return rc;
     return guarded([&]() -> fgr_status {
         FGR_CUDA_TRY(cudaSetDevice(ctx->device));
@@ -455,6 +506,14 @@ fgr_status reconstruct(fgr_ctx *ctx, const fgr_packets *pk, void *u_out, void *s
         double *q, *p, *s, *a;
         fgr_status r = stage_packets(ctx, pk, st, scratch, &dev, &q, &p, &s, &a);
         if (r != FGR_OK) return r;
+        if (!pk->on_device && pk->m > 0) {
+            // host data: scanned while its copy runs, before any kernel reads it
+            r = check_host_finite(ctx, pk);
+            if (r != FGR_OK) {
+                cudaStreamSynchronize(st);  // the copy is done with the caller's arrays
+                return r;
+            }
+        }
         const size_t out_bytes = elem_bytes(ctx->opt.precision) * (size_t)ctx->grid.total;
         const bool dev_out = is_device_ptr(u_out);
         void *u_dev = u_out;

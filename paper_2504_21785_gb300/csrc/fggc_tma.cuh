@@ -11,11 +11,13 @@
 #pragma once
 
 constexpr unsigned kTmaWaitLimit = 1u << 26;  // polls of an mbarrier before giving up
-// b cells per staged tile (a 96-byte row per line).  A tile is multiplied
+// b cells per staged tile (a 64-byte row per line).  A tile is multiplied
 // whole, so its width trades the zero padding past a row's occupied b-range
-// against the per-tile overhead; on the 3-D workload 12 (or 8) cells take the
-// passes from 5.29 to 4.54 ms against 16.
-constexpr int kTB = 12;
+// against the per-tile overhead: on the 3-D workload 12 or 8 cells took the
+// passes from 5.29 to 4.54 ms against 16, and 8 cells keep the CTA's shared
+// memory (two tile buffers and the row sums) near 6 KB, so that with at most
+// 64 registers about 30 one-warp CTAs fit an SM (3.89 -> 3.76 ms against 12).
+constexpr int kTB = 8;
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) {
     return (unsigned)__cvta_generic_to_shared(p);
@@ -83,7 +85,7 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
 // copies (band chunk, row, b chunk), so the copy of the next tile, also of
 // the next row, is in flight while the warp multiplies the current one.
 template <int MAXBAND, int RPC>
-__global__ void __launch_bounds__(32) grid_pass_tma_kernel(const __grid_constant__ CUtensorMap map,
+__global__ void __launch_bounds__(32, 32) grid_pass_tma_kernel(const __grid_constant__ CUtensorMap map,
                                                            const __grid_constant__ CUtensorMap map_half,
                                                            void *__restrict__ out_v, PassParams pp,
                                                            const uint8_t *__restrict__ flags,

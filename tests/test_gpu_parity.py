@@ -397,3 +397,27 @@ def test_config2_propagation_sample(cfg2):
     Ar = ref["a"][0, idx] + 1j * ref["a"][1, idx]
     nz = np.abs(Ar) > 1e-200
     assert np.max(np.abs(A[nz] - Ar[nz]) / np.abs(Ar[nz])) <= 1e-12
+
+
+def test_non_finite_host_packets_are_rejected_in_large_sets():
+    # host packet sets of more than 2^20 values are scanned by several host
+    # threads while their copy runs; a non-finite value anywhere (here near the
+    # end of the amplitudes, then in P) still rejects the call before any
+    # kernel writes the output
+    import paper_2504_21785_gb300 as fgr
+    m = (1 << 21) + 17
+    rng = np.random.default_rng(8)
+    pk = {"q": rng.uniform(-1, 1, (1, m)), "p": rng.uniform(-1, 1, (1, m)), "s": rng.uniform(-1, 1, m),
+          "a": rng.standard_normal((2, m))}
+    grid = _grid(1, 256)
+    with fgr.Context(1, grid, 1 / 64, fgr.make_options(precision=fgr.FGR_FP32)) as ctx:
+        for key, idx in (("a", (1, m - 3)), ("p", (0, m // 2 + 1))):
+            bad = {k: np.array(v, copy=True) for k, v in pk.items()}
+            bad[key][idx] = np.inf if key == "a" else np.nan
+            host = [np.ascontiguousarray(bad[k]) for k in ("q", "p", "s", "a")]
+            u = np.full(256, 7.0, np.complex64)
+            for call in (fgr.fgr_reconstruct_fggc, fgr.fgr_reconstruct_direct):
+                with pytest.raises(fgr.FgrError) as e:
+                    call(ctx.handle, fgr.make_packets(*host), u)
+                assert e.value.status == fgr.fgr.FGR_E_INVALID
+                assert np.all(u == 7.0)
