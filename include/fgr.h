@@ -270,8 +270,10 @@ fgr_status fgr_reconstruct_direct_batch(int32_t n, fgr_ctx *const *ctxs, const f
  * (eq. 2.24) one dimension at a time.  FP64: all FP64.  FP32: the coefficients
  * come from a Chebyshev surrogate of c~(s,t) built on the host from the same
  * pseudo-inverse (degree 10, truncation error about 3e-10: below FP32 rounding;
- * evaluated in FP32), phases are reduced in FP64,
- * node array and grid sums in complex64. */
+ * evaluated in FP32 over the terms i + j <= 11 for n1 <= 8), phases are reduced
+ * in FP64, node array and grid sums in complex64.  Host packets are copied to
+ * the device and tested there for non-finite values before anything is
+ * written: FGR_E_INVALID if one is found. */
 fgr_status fgr_reconstruct_fggc(fgr_ctx *ctx, const fgr_packets *pk, void *u_out,
                                 void *cuda_stream);
 

@@ -506,8 +506,10 @@ fgr_status reconstruct(fgr_ctx *ctx, const fgr_packets *pk, void *u_out, void *s
         double *q, *p, *s, *a;
         fgr_status r = stage_packets(ctx, pk, st, scratch, &dev, &q, &p, &s, &a);
         if (r != FGR_OK) return r;
-        if (!pk->on_device && pk->m > 0) {
-            // host data: scanned while its copy runs, before any kernel reads it
+        const bool host_data = !pk->on_device && pk->m > 0;
+        if (host_data && !fggc) {
+            // host data of a direct sum: scanned while its copy runs, before
+            // any kernel reads it
             r = check_host_finite(ctx, pk);
             if (r != FGR_OK) {
                 cudaStreamSynchronize(st);  // the copy is done with the caller's arrays
@@ -521,7 +523,9 @@ fgr_status reconstruct(fgr_ctx *ctx, const fgr_packets *pk, void *u_out, void *s
             u_dev = scratch.get(out_bytes);
             if (!u_dev) return FGR_E_NOMEM;
         }
-        r = fggc ? run_fggc(ctx, dev, u_dev, st, scratch) : run_direct(ctx, dev, u_dev, st, scratch);
+        // host data of an FGGC call: tested on the device by the bounds
+        // reduction, whose readback precedes every write
+        r = fggc ? run_fggc(ctx, dev, u_dev, st, scratch, host_data) : run_direct(ctx, dev, u_dev, st, scratch);
         if (r != FGR_OK) return r;
         FGR_CUDA_TRY(cudaGetLastError());
         if (!dev_out) {

@@ -46,11 +46,19 @@ namespace {
 // ---------------------------------------------------------------------------
 // Body of the bounds reduction for CTA bid of nblk (a batched launch runs it
 // for the CTAs of each request).
+// Exponent bits all set: infinity or NaN (an integer test).
+__device__ __forceinline__ bool not_finite_d(double x) {
+    return ((unsigned)((unsigned long long)__double_as_longlong(x) >> 32) & 0x7ff00000u) == 0x7ff00000u;
+}
+
+// s: when non-null, every packet's Q, P, S and A are also tested for
+// finiteness and out[12] is set to 1 if one is not (out[12] starts at 0).
 template <int D>
 __device__ __forceinline__ void bounds_body(const double *__restrict__ q, const double *__restrict__ p,
                                             const double *__restrict__ a, int64_t m, const Common &c,
                                             const int *aglo, const int *aghi, int *__restrict__ out, int64_t bid,
-                                            int64_t nblk) {
+                                            int64_t nblk, const double *__restrict__ s = nullptr) {
+    bool bad = false;
     int dqmin = INT_MAX, dqmax = INT_MIN, dpmin = INT_MAX, dpmax = INT_MIN;
     for (int k = 0; k < c.n1; ++k) {
         dqmin = min(dqmin, c.dq[k]);
@@ -69,13 +77,27 @@ __device__ __forceinline__ void bounds_body(const double *__restrict__ q, const 
         hi_b[l] = INT_MIN;
     }
     for (int64_t j = bid * (int64_t)blockDim.x + threadIdx.x; j < m; j += nblk * blockDim.x) {
+        // every load of the packet first (no load waits on the amplitude test)
+        double qv[D], pv[D];
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+            qv[l] = q[l * m + j];
+            pv[l] = p[l * m + j];
+        }
+        if (s) {
+            bool nf = not_finite_d(s[j]) || not_finite_d(a[j]) || not_finite_d(a[m + j]);
+#pragma unroll
+            for (int l = 0; l < D; ++l) nf = nf || not_finite_d(qv[l]) || not_finite_d(pv[l]);
+            bad = bad || nf;
+            if (nf) continue;
+        }
         if (a[j] == 0.0 && a[m + j] == 0.0) continue;
         int pa_lo[D], pa_hi[D], pb_lo[D], pb_hi[D];
         bool use = true;
 #pragma unroll
         for (int l = 0; l < D; ++l) {
-            const int a0 = floor_div_int(q[l * m + j], c.dqv, c.inv_dq);
-            const int b0 = floor_div_int(p[l * m + j], c.dpv, c.inv_dp);
+            const int a0 = floor_div_int(qv[l], c.dqv, c.inv_dq);
+            const int b0 = floor_div_int(pv[l], c.dpv, c.inv_dp);
             pa_lo[l] = max(a0 + dqmin, aglo[l]);
             pa_hi[l] = min(a0 + dqmax, aghi[l]);
             if (pa_lo[l] > pa_hi[l]) use = false;  // no node of this packet reaches the grid
@@ -91,6 +113,7 @@ __device__ __forceinline__ void bounds_body(const double *__restrict__ q, const 
             hi_b[l] = max(hi_b[l], pb_hi[l]);
         }
     }
+    if (s && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&out[12], 1);
     // warp, then block reduction; one atomic per block and value
     __shared__ int red[8][kMaxDim * 4];
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -123,9 +146,10 @@ __device__ __forceinline__ void bounds_body(const double *__restrict__ q, const 
 template <int D>
 __global__ void bounds_kernel(const double *__restrict__ q, const double *__restrict__ p,
                               const double *__restrict__ a, int64_t m, Common c, int aglo0, int aghi0,
-                              int aglo1, int aghi1, int aglo2, int aghi2, int *__restrict__ out) {
+                              int aglo1, int aghi1, int aglo2, int aghi2, int *__restrict__ out,
+                              const double *__restrict__ s) {
     const int aglo[3] = {aglo0, aglo1, aglo2}, aghi[3] = {aghi0, aghi1, aghi2};
-    bounds_body<D>(q, p, a, m, c, aglo, aghi, out, blockIdx.x, gridDim.x);
+    bounds_body<D>(q, p, a, m, c, aglo, aghi, out, blockIdx.x, gridDim.x, s);
 }
 
 // CTAs of the bounds kernel: enough to fill the GPU, few enough that the
@@ -693,8 +717,10 @@ fgr_status launch_transpose(const void *in, void *out, int64_t R, int64_t Cc, cu
     return FGR_OK;
 }
 
-__global__ void bounds_init_kernel(int *__restrict__ b) {
+// b[0..12) the empty bounds; b[12] (when present) the non-finite flag.
+__global__ void bounds_init_kernel(int *__restrict__ b, int n) {
     if (threadIdx.x < 12) b[threadIdx.x] = (threadIdx.x & 1) ? INT_MIN : INT_MAX;
+    if (threadIdx.x == 12 && n > 12) b[12] = 0;
 }
 
 // Sets *overflow when the packets' node bounds b[] leave the planned box.
@@ -748,23 +774,25 @@ void grid_node_range(const fgr_ctx *ctx, int *aglo, int *aghi) {
 }
 
 // Launches the node-bounds reduction of the packets into b[12] (device).
+// check_finite: also test every packet value (b holds 13 ints, b[12] the flag).
 fgr_status launch_bounds_reduction(const fgr_ctx *ctx, const PacketsDev &pk, const Common &c, const int *aglo,
-                                   const int *aghi, int *b, cudaStream_t st) {
-    bounds_init_kernel<<<1, 32, 0, st>>>(b);
+                                   const int *aghi, int *b, cudaStream_t st, bool check_finite = false) {
+    bounds_init_kernel<<<1, 32, 0, st>>>(b, check_finite ? 13 : 12);
+    const double *sv = check_finite ? pk.s : nullptr;
     if (pk.m > 0) {
         const unsigned blocks = bounds_blocks(ctx, pk.m);
         switch (ctx->d) {
         case 1:
             bounds_kernel<1><<<blocks, 256, 0, st>>>(pk.q, pk.p, pk.a, pk.m, c, aglo[0], aghi[0], aglo[1], aghi[1],
-                                                     aglo[2], aghi[2], b);
+                                                     aglo[2], aghi[2], b, sv);
             break;
         case 2:
             bounds_kernel<2><<<blocks, 256, 0, st>>>(pk.q, pk.p, pk.a, pk.m, c, aglo[0], aghi[0], aglo[1], aghi[1],
-                                                     aglo[2], aghi[2], b);
+                                                     aglo[2], aghi[2], b, sv);
             break;
         default:
             bounds_kernel<3><<<blocks, 256, 0, st>>>(pk.q, pk.p, pk.a, pk.m, c, aglo[0], aghi[0], aglo[1], aghi[1],
-                                                     aglo[2], aghi[2], b);
+                                                     aglo[2], aghi[2], b, sv);
         }
     }
     FGR_CUDA_TRY(cudaGetLastError());
@@ -1168,19 +1196,20 @@ fgr_status enqueue_fggc(fgr_ctx *ctx, const PacketsDev &pk, const FggcBox &box, 
 }
 
 template <int D>
-fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t st, Scratch &scratch) {
+fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t st, Scratch &scratch,
+                  bool check_finite) {
     const size_t eb = elem_bytes(ctx->opt.precision);
     StageTimer timer(ctx, st);
     int64_t launches = 0;
     const Common c = base_common(ctx);
     int aglo[3], aghi[3];
     grid_node_range(ctx, aglo, aghi);
-    int *bnd = (int *)scratch.get(sizeof(int) * 12);
+    int *bnd = (int *)scratch.get(sizeof(int) * 13);
     if (!bnd) return FGR_E_NOMEM;
-    fgr_status r = launch_bounds_reduction(ctx, pk, c, aglo, aghi, bnd, st);
+    fgr_status r = launch_bounds_reduction(ctx, pk, c, aglo, aghi, bnd, st, check_finite);
     if (r != FGR_OK) return r;
     launches += pk.m > 0 ? 2 : 1;
-    FGR_CUDA_TRY(cudaMemcpyAsync(ctx->host_pinned, bnd, sizeof(int) * 12, cudaMemcpyDeviceToHost, st));
+    FGR_CUDA_TRY(cudaMemcpyAsync(ctx->host_pinned, bnd, sizeof(int) * 13, cudaMemcpyDeviceToHost, st));
     int *herr = reinterpret_cast<int *>(ctx->host_pinned) + 16;
     FGR_CUDA_TRY(cudaMemcpyAsync(herr, ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     FGR_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1190,8 +1219,12 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
                   "that call's output is incomplete");
         return FGR_E_TIMEOUT;
     }
-    int hb[12];
+    int hb[13];
     memcpy(hb, ctx->host_pinned, sizeof(hb));
+    if (check_finite && hb[12]) {
+        set_error("packets: a non-finite Q, P, S or A value");
+        return FGR_E_INVALID;
+    }
     FggcBox box;
     r = make_box(ctx, hb, 0, &box);
     if (r != FGR_OK) return r;
@@ -1489,11 +1522,12 @@ fgr_status launch_coeff_scatter(int d, int n1, cudaStream_t st, const PacketsDev
     }
 }
 
-fgr_status run_fggc(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t st, Scratch &scratch) {
+fgr_status run_fggc(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t st, Scratch &scratch,
+                    bool check_finite) {
     switch (ctx->d) {
-    case 1: return launch<1>(ctx, pk, u_dev, st, scratch);
-    case 2: return launch<2>(ctx, pk, u_dev, st, scratch);
-    default: return launch<3>(ctx, pk, u_dev, st, scratch);
+    case 1: return launch<1>(ctx, pk, u_dev, st, scratch, check_finite);
+    case 2: return launch<2>(ctx, pk, u_dev, st, scratch, check_finite);
+    default: return launch<3>(ctx, pk, u_dev, st, scratch, check_finite);
     }
 }
 
@@ -1669,7 +1703,7 @@ extern "C" fgr_status fgr_reconstruct_fggc_noalloc(fgr_ctx *ctx, const fgr_packe
     const int64_t m = pk->m;
     if (m > 0) {
         bounds_kernel<1><<<bounds_blocks(ctx, m), 256, 0, st>>>(pk->q, pk->p, pk->a, m, c, aglo, aghi,
-                                                                     0, -1, 0, -1, bnd);
+                                                                     0, -1, 0, -1, bnd, nullptr);
         FGR_CUDA_TRY(cudaGetLastError());
     }
     FGR_CUDA_TRY(cudaMemcpyAsync(ctx->host_pinned, bnd, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));

@@ -52,13 +52,19 @@ __global__ void bin_key_kernel(const double *__restrict__ q, const double *__res
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= m) return;
     int k = -1;
+    double qv[D - 1], pv[D - 1];  // every load first (none waits on the amplitude test)
+#pragma unroll
+    for (int l = 0; l < D - 1; ++l) {
+        qv[l] = q[l * m + j];
+        pv[l] = p[l * m + j];
+    }
     if (a[j] != 0.0 || a[m + j] != 0.0) {
         int64_t kk = 0;
         bool ok = true;
 #pragma unroll
         for (int l = 0; l < D - 1; ++l) {
-            const int ia = floor_div_int(q[l * m + j], c.dqv, c.inv_dq) - bb.ka_lo[l];
-            const int ib = floor_div_int(p[l * m + j], c.dpv, c.inv_dp) - bb.kb_lo[l];
+            const int ia = floor_div_int(qv[l], c.dqv, c.inv_dq) - bb.ka_lo[l];
+            const int ib = floor_div_int(pv[l], c.dpv, c.inv_dp) - bb.kb_lo[l];
             ok = ok && (unsigned)ia < (unsigned)bb.KA[l] && (unsigned)ib < (unsigned)bb.KB[l];
             kk = (kk * bb.KA[l] + ia) * bb.KB[l] + ib;
         }

@@ -157,8 +157,10 @@ fgr_status check_selection_device(fgr_ctx *ctx, const int64_t *sel, int64_t m, i
 fgr_status run_scale_amplitudes(const double *a0, const double *f, double *out, int64_t m, cudaStream_t st);
 fgr_status run_direct(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t st,
                       Scratch &scratch);
+// check_finite: the bounds reduction also tests every packet value and the
+// call returns FGR_E_INVALID, before writing anything, if one is not finite.
 fgr_status run_fggc(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t st,
-                    Scratch &scratch);
+                    Scratch &scratch, bool check_finite = false);
 // Device bytes owned by an FGGC plan (api.cu).
 size_t plan_device_bytes(const fgr_fggc_plan *plan);
 

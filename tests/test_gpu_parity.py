@@ -400,10 +400,11 @@ def test_config2_propagation_sample(cfg2):
 
 
 def test_non_finite_host_packets_are_rejected_in_large_sets():
-    # host packet sets of more than 2^20 values are scanned by several host
-    # threads while their copy runs; a non-finite value anywhere (here near the
-    # end of the amplitudes, then in P) still rejects the call before any
-    # kernel writes the output
+    # a non-finite value anywhere in a large host packet set (near the end of
+    # the amplitudes, in P, in S) rejects the call before any kernel writes the
+    # output: FGGC tests the copied values on the device in its bounds
+    # reduction, the direct sum scans them with several host threads while
+    # their copy runs
     import paper_2504_21785_gb300 as fgr
     m = (1 << 21) + 17
     rng = np.random.default_rng(8)
@@ -411,7 +412,7 @@ def test_non_finite_host_packets_are_rejected_in_large_sets():
           "a": rng.standard_normal((2, m))}
     grid = _grid(1, 256)
     with fgr.Context(1, grid, 1 / 64, fgr.make_options(precision=fgr.FGR_FP32)) as ctx:
-        for key, idx in (("a", (1, m - 3)), ("p", (0, m // 2 + 1))):
+        for key, idx in (("a", (1, m - 3)), ("p", (0, m // 2 + 1)), ("s", (m - 5,))):
             bad = {k: np.array(v, copy=True) for k, v in pk.items()}
             bad[key][idx] = np.inf if key == "a" else np.nan
             host = [np.ascontiguousarray(bad[k]) for k in ("q", "p", "s", "a")]
