@@ -78,7 +78,7 @@ struct BinBuffers {
 struct BinLaunch {
     BinBox box;
     BinBuffers buf;
-    int min_count = 32;  // smallest binned cell
+    int min_count = 8;   // smallest binned cell (kBinMinCount)
     int num_sms = 1;
     // rows of W (each row_cells cells) to clear before the scatter: only the
     // rows the binned packets reach are marked and zeroed (0: W is cleared by
@@ -90,7 +90,7 @@ struct BinLaunch {
 // Largest key box of the binned scatter; larger boxes use the per-packet kernel.
 constexpr int64_t kMaxBinKeys = int64_t(1) << 26;
 // Smallest binned cell (packets); smaller cells take the per-packet kernel.
-constexpr int kBinMinCount = 32;
+constexpr int kBinMinCount = 8;
 
 // Key box of a node box (false when the binned scatter does not apply).
 bool make_bin_box(const FggcBox &box, int d, BinBox *bb);

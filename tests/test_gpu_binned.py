@@ -2,7 +2,7 @@
 oracle's FGGC (Algorithm 2; eq. 2.24-2.25).
 
 In 3-D the library bins packets by the anchor cell (a0, b0) of their outer
-dimensions; for cells holding at least 32 packets a CTA lists which of the
+dimensions; for cells holding at least 8 packets a CTA lists which of the
 packets' inner neighbours land on each cell of the inner plane and sums every
 row of a cell in registers before adding it to the node array; cells with
 fewer packets take the per-packet kernel (as every 1-D and 2-D problem does).
@@ -86,11 +86,13 @@ def test_clustered_2d(inner_q, inner_p):
 
 @pytest.mark.parametrize("inner_q,inner_p", [((-0.8, 0.8), (-0.5, 0.5)), ((-2.0, 2.0), (-2.0, 2.0))])
 def test_binned_3d(inner_q, inner_p):
-    # cells of 64 (one item), 300 and 600 (several items) and 20 (per-packet);
-    # the second spread needs several windows of target cells
+    # cells of 64 (one item), 300 and 600 (several items), 20 and 9 (small
+    # items) and 5 (per-packet); the second spread needs several windows of
+    # target cells
     eps = 1 / 64
-    cells = [[(2, 3), (-1, 4)], [(0, 0), (0, 0)], [(-5, 2), (6, -3)], [(1, 1), (1, 2)]]
-    pk, mesh = clustered(12, 3, eps, cells, [64, 300, 600, 20], inner_q, inner_p)
+    cells = [[(2, 3), (-1, 4)], [(0, 0), (0, 0)], [(-5, 2), (6, -3)], [(1, 1), (1, 2)], [(3, -2), (-2, 0)],
+             [(-3, -1), (2, 2)]]
+    pk, mesh = clustered(12, 3, eps, cells, [64, 300, 600, 20, 9, 5], inner_q, inner_p)
     _check(pk, mesh, _grid((40, 36, 44)), eps, npts=500)
 
 
