@@ -225,7 +225,6 @@ __host__ __device__ constexpr int coef_stride() {
 template <int D, int N1>
 __host__ __device__ constexpr int binned_smem_bytes() {
     return kBinT * coef_stride<D, N1>() * 8  // coefficients [packet][dimension][neighbour] (float2)
-           + kBinT * 8             // packet weights w (float2)
            + 2 * kWinCells * 4     // per-cell entry start and cursor (int)
            + kWinCells * 4         // active cells (packed line, column)
            + (D == 3 ? N1 * N1 : N1) * 8  // W offsets of the rows (int64)
@@ -257,9 +256,10 @@ __global__ void __launch_bounds__(kBinT, kBinCtasPerSm) binned_scatter_kernel(
     constexpr int kPer = kWinCells / kBinT;      // target cells per thread in the CSR build
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int CS = coef_stride<D, N1>();
-    float2 *coef = reinterpret_cast<float2 *>(smem_raw);             // [kBinT][CS]: [D][N1] + padding
-    float2 *wgt = coef + kBinT * CS;                                 // [kBinT]
-    int *cstart = reinterpret_cast<int *>(wgt + kBinT);              // [kWinCells]
+    // [kBinT][CS]: per packet [D][N1] coefficients (the last dimension's
+    // multiplied by the packet's weight w) and padding
+    float2 *coef = reinterpret_cast<float2 *>(smem_raw);
+    int *cstart = reinterpret_cast<int *>(coef + kBinT * CS);        // [kWinCells]
     int *cend = cstart + kWinCells;                                  // [kWinCells]
     unsigned *act = reinterpret_cast<unsigned *>(cend + kWinCells);  // [kWinCells]
     int64_t *rowoff = reinterpret_cast<int64_t *>(act + kWinCells);  // [NR]
@@ -331,7 +331,6 @@ __global__ void __launch_bounds__(kBinT, kBinCtasPerSm) binned_scatter_kernel(
             float sn, cs;
             sincospif(2.f * (float)ts, &sn, &cs);
             cmul((float)(a[j] * c.pref), (float)(a[m + j] * c.pref), cs, sn, wr, wi);
-            wgt[tid] = make_float2(wr, wi);
             // one dimension at a time (one copy of the evaluation) into this
             // thread's coefficient block
 #pragma unroll 1
@@ -340,6 +339,15 @@ __global__ void __launch_bounds__(kBinT, kBinCtasPerSm) binned_scatter_kernel(
                 coeff_dim32_rolled<N1>(P, q[l * m + j], p[l * m + j], a0, b0, cj + l * N1, 1);
                 ra = a0 - c.amin[D - 1];
                 rb = b0 - c.bmin[D - 1];
+            }
+            // the weight goes with the last dimension's coefficients, once per
+            // packet rather than once per entry and accumulation pass
+#pragma unroll
+            for (int k = 0; k < N1; ++k) {
+                float2 &v = cj[(D - 1) * N1 + k];
+                float er, ei;
+                cmul(wr, wi, v.x, v.y, er, ei);
+                v = make_float2(er, ei);
             }
             atomicMin(&s_box[0], ra + bb.dqmin);
             atomicMax(&s_box[1], ra + bb.dqmax);
@@ -386,9 +394,8 @@ __global__ void __launch_bounds__(kBinT, kBinCtasPerSm) binned_scatter_kernel(
                 for (int r = 0; r < NR; ++r) {
                     if (!((rows_in >> r) & 1ull)) continue;
                     const int k0 = D == 3 ? r / N1 : r, k1 = D == 3 ? r % N1 : 0;
-                    const float2 c0 = cj[k0];
-                    float pr, pi;
-                    cmul(wr, wi, c0.x, c0.y, pr, pi);
+                    const float2 c0 = cj[k0];  // w is in cr, ci
+                    float pr = c0.x, pi = c0.y;
                     if constexpr (D == 3) {
                         const float2 c1 = cj[N1 + k1];
                         cmul(pr, pi, c1.x, c1.y, pr, pi);
@@ -474,9 +481,7 @@ __global__ void __launch_bounds__(kBinT, kBinCtasPerSm) binned_scatter_kernel(
                     for (int v = 0; v < NK1; ++v) accr[u][v] = acci[u][v] = 0.f;
                 for (int x = x0; x < x1; ++x) {
                     const int en = ent[x], jj = en >> 4, kk = en & 15;
-                    const float2 wv = wgt[jj], cl = coef[jj * CS + (D - 1) * N1 + kk];
-                    float2 ev;
-                    cmul(wv.x, wv.y, cl.x, cl.y, ev.x, ev.y);
+                    const float2 ev = coef[jj * CS + (D - 1) * N1 + kk];  // w c_{d-1}[k]
                     // the packet's coefficients, 16-byte loads (two neighbours each)
                     const float4 *cp4 = reinterpret_cast<const float4 *>(coef + jj * CS);
                     float2 c0v[NA];
