@@ -3,7 +3,8 @@ cannot allocate device memory while running (a pre-committed memory budget, a
 host framework that owns all device allocations, or a loop that cannot pay for
 cudaMalloc/cudaFree).  Its working memory is one static device array, so the
 test checks, through the C ABI, that two calls in a row each reproduce what
-the allocating entry point fgr_reconstruct_fggc returns for the same input, and
+the allocating entry point fgr_reconstruct_fggc returns for the same input,
+that its output also matches the FP64 oracle's FGGC (Algorithm 2) directly, and
 that a problem too large for the array is refused with FGR_E_CAPACITY.
 
 This file is collected last so that a run stopping at the first failure has
@@ -55,6 +56,39 @@ def test_noalloc_matches_allocating_entry_point_twice(fgr, precision, tol):
             torch.cuda.synchronize()
             r, g = ref.cpu().numpy(), got.cpu().numpy()
             assert np.linalg.norm(g - r) <= tol * np.linalg.norm(r), (call, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_noalloc_matches_oracle(fgr, precision):
+    # the no-allocation call sums the node Gaussians over every b of the node
+    # box (it keeps no b-range table), so it is compared with the oracle's
+    # Algorithm 2 directly as well, on a ragged grid with packets on nodes
+    import torch
+    from oracle import fggc, lsa
+    eps = 1 / 256
+    mesh = mesh_for(1, eps)
+    n = 3001
+    grid = dict(d=1, n=[n], lo=[-math.pi], hi=[math.pi])
+    pk = random_packets(25, 1, 700, q_range=(-3.6, 3.6), p_range=(-2.5, 2.5), s_range=(-3, 3),
+                        mesh=mesh, on_node_fraction=0.1)
+    strat = lsa.Strategy(nq=4, np_=2)
+    if precision == "fp32":
+        prec, cdt, R = fgr.FGR_FP32, torch.complex64, 6
+        tol = 1e-5
+    else:
+        prec, cdt, R = fgr.FGR_FP64, torch.complex128, 8
+        # the least-squares floor eps_mach / sqrt(lambda_min(A~)) of Q4P2
+        floor = np.finfo(float).eps / math.sqrt(strat.pinv.singular_values[strat.pinv.rank - 1])
+        tol = max(1e-12, 4 * floor)
+    ref = fggc.reconstruct(pk, grid, eps, mesh.dq, mesh.dp, strat, R=R)
+    with fgr.Context(1, grid, eps, fgr.make_options(precision=prec)) as ctx:
+        packets = fgr.make_packets(*_device_packets(pk))
+        for call in range(2):
+            got = torch.full((n,), -3.0, dtype=cdt, device="cuda")
+            fgr.fgr.fgr_reconstruct_fggc_noalloc(ctx.handle, packets, got)
+            torch.cuda.synchronize()
+            g = got.cpu().numpy()
+            assert np.linalg.norm(g - ref) <= tol * np.linalg.norm(ref), (call, precision)
 
 
 def test_noalloc_rejects_problems_beyond_its_array(fgr):
