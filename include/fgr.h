@@ -98,9 +98,14 @@ typedef struct {
  *   grid stage up to rounding.  fgr_reconstruct_fggc_noalloc ignores the flag.
  * FGR_FLAG_SNAP_CP: before anything else, cp is replaced by the nearest value
  *   that makes dimension 0 commensurate (N a power of two, as above); the
- *   least-squares constants (Tables 1-4) then belong to that cp. */
+ *   least-squares constants (Tables 1-4) then belong to that cp.
+ * FGR_FLAG_DIRECT_FMA: the FP32 direct sum of a 2-D context runs on the
+ *   CUDA cores (one complex multiply-add per packet-point pair) instead of the
+ *   tensor cores (the outer products of eq. 2.10's per-dimension factors as a
+ *   3 x TF32 matrix product); both meet the FP32 tolerance. */
 #define FGR_FLAG_FFT_GRID 1
 #define FGR_FLAG_SNAP_CP 2
+#define FGR_FLAG_DIRECT_FMA 4
 
 
 typedef struct {

@@ -16,5 +16,5 @@ from .fgr import (  # noqa: F401
     fgr_get_info, fgr_set_timing, fgr_get_stats, fgr_last_error, fgr_autotune, fgr_get_tuning,
     fgr_set_tuning,
     fgr_server_create, fgr_server_destroy, fgr_server_set_max_batch, fgr_register_packets, fgr_release_packets,
-    fgr_submit, fgr_poll, fgr_cancel, make_request, FGR_FP64, FGR_FP32, FGR_FLAG_FFT_GRID, FGR_FLAG_SNAP_CP,
+    fgr_submit, fgr_poll, fgr_cancel, make_request, FGR_FP64, FGR_FP32, FGR_FLAG_FFT_GRID, FGR_FLAG_SNAP_CP, FGR_FLAG_DIRECT_FMA,
 )

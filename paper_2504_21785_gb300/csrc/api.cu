@@ -271,9 +271,9 @@ fgr_status resolve_options(const fgr_options *in, fgr_options *out) {
     if (o.window_r == 0) o.window_r = o.precision == FGR_FP64 ? 8.0 : 6.0;
     if (!(o.cq > 0) || !(o.cp > 0) || !is_finite(o.cq) || !is_finite(o.cp) || (o.nq != 2 && o.nq != 4) ||
         (o.np != 2 && o.np != 4) || !(o.window_r > 0) || o.window_r > 40 || !(o.rcond > 0) ||
-        o.rcond >= 1 || (o.flags & ~(FGR_FLAG_FFT_GRID | FGR_FLAG_SNAP_CP)) != 0) {
+        o.rcond >= 1 || (o.flags & ~(FGR_FLAG_FFT_GRID | FGR_FLAG_SNAP_CP | FGR_FLAG_DIRECT_FMA)) != 0) {
         set_error("options out of range (cq, cp > 0; nq, np in {2,4}; 0 < window_r <= 40; "
-                  "0 < rcond < 1; flags of FGR_FLAG_FFT_GRID | FGR_FLAG_SNAP_CP)");
+                  "0 < rcond < 1; flags of FGR_FLAG_FFT_GRID | FGR_FLAG_SNAP_CP | FGR_FLAG_DIRECT_FMA)");
         return FGR_E_INVALID;
     }
     *out = o;

@@ -215,6 +215,7 @@ struct DirectParams {
     float ce_h;          // ce * h of the last dimension
     float q_last;        // e^{-h^2 / eps} of the last dimension (Gaussian ratio step)
     float q_dim[3];      // e^{-h_l^2 / eps} per dimension (factor tables, d >= 2)
+    float q8[3];         // e^{-64 h_l^2 / eps}: Gaussian ratio step over 8 grid lines (tensor-core path)
     double inv_eps;      // FP64 path
     double neg_half_inv_eps;
     int splits;
@@ -855,6 +856,8 @@ __global__ void __launch_bounds__(kThreads) direct_batch_items_kernel(const __gr
     }
 }
 
+#include "direct_tc.cuh"
+
 // Zeroes the output and bins one request's packets; fills the parameters of
 // its main kernel (pr->empty when nothing remains to sum).
 struct Prepared {
@@ -930,6 +933,7 @@ fgr_status prepare(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t
     P.ce_h = (float)(-1.4426950408889634 / (2.0 * M.eps) * g.h[D - 1]);
     P.q_last = (float)std::exp(-g.h[D - 1] * g.h[D - 1] / M.eps);
     for (int l = 0; l < D; ++l) P.q_dim[l] = (float)std::exp(-g.h[l] * g.h[l] / M.eps);
+    for (int l = 0; l < D; ++l) P.q8[l] = (float)std::exp(-64.0 * g.h[l] * g.h[l] / M.eps);
     P.inv_eps = 1.0 / M.eps;
     P.neg_half_inv_eps = -0.5 / M.eps;
     const int target = ctx->num_sms * ctx->tune.direct_ctas_per_sm;
@@ -938,6 +942,39 @@ fgr_status prepare(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t
     pr->off = off;
     pr->ntiles = ntiles;
     pr->empty = false;
+    return FGR_OK;
+}
+
+// Tensor-core direct sum (FP32, d = 2): loads of the super tiles, items
+// heaviest first, one persistent CTA per SM.
+fgr_status launch_tc(fgr_ctx *ctx, const Prepared &pr, void *u_dev, cudaStream_t st, Scratch &scratch) {
+    const GridDev &g = pr.P.g;
+    if (g.K[0] + tc::kSuper0 > 64) {
+        set_error("direct: window too wide for the tensor-core tiling");
+        return FGR_E_INVALID;
+    }
+    const int nst = ((g.nt[0] + tc::kSuper0 - 1) / tc::kSuper0) * g.nt[1];
+    auto *load = (uint32_t *)scratch.get(sizeof(uint32_t) * (size_t)nst);
+    auto *rank = (int *)scratch.get(sizeof(int) * 2 * (size_t)nst);
+    const int target = ctx->num_sms * ctx->tune.direct_ctas_per_sm;
+    auto *items = (int2 *)scratch.get(sizeof(int2) * plan_items_capacity(nst, target));
+    auto *cnt = (unsigned long long *)scratch.get(2 * sizeof(unsigned long long));
+    if (!load || !rank || !items || !cnt) return FGR_E_NOMEM;
+    FGR_CUDA_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st));
+    tc_tile_load_kernel<<<(unsigned)((nst + 255) / 256), 256, 0, st>>>(pr.off, g, load);
+    plan_items_kernel<<<1, kPlanThreads, 0, st>>>(load, nst, target, rank, rank + nst, items,
+                                                  reinterpret_cast<int *>(cnt + 1));
+    static thread_local int attr_device = -1;
+    if (attr_device != ctx->device) {
+        FGR_CUDA_TRY(cudaFuncSetAttribute(direct_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)tc::kDynSmem));
+        attr_device = ctx->device;
+    }
+    const unsigned ctas = (unsigned)ctx->num_sms;
+    direct_tc_kernel<<<ctas, tc::kThreadsTc, tc::kDynSmem, st>>>(
+        reinterpret_cast<const RecF<2> *>(pr.recs), pr.off, pr.P, reinterpret_cast<float2 *>(u_dev), items,
+        reinterpret_cast<int *>(cnt + 1), cnt, ctx->yield_flag, (int)ctas, ctx->dev_err);
+    FGR_CUDA_TRY(cudaGetLastError());
     return FGR_OK;
 }
 
@@ -963,6 +1000,14 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
         FGR_CUDA_TRY(cudaGetLastError());
         timer.mark(&ctx->timing.last.direct_ms);
         ctx->timing.last.launches = 4;
+        timer.finish();
+        return FGR_OK;
+    }
+    if (D == 2 && !fp64 && !(ctx->opt.flags & FGR_FLAG_DIRECT_FMA)) {
+        fgr_status rt = launch_tc(ctx, pr, u_dev, st, scratch);
+        if (rt != FGR_OK) return rt;
+        timer.mark(&ctx->timing.last.direct_ms);
+        ctx->timing.last.launches = 6;
         timer.finish();
         return FGR_OK;
     }

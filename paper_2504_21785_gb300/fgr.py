@@ -224,6 +224,7 @@ def fgr_default_options() -> fgr_options:
 
 FGR_FLAG_FFT_GRID = 1
 FGR_FLAG_SNAP_CP = 2
+FGR_FLAG_DIRECT_FMA = 4
 
 
 def make_options(precision=FGR_FP64, cq=0.5, cp=math.pi / 8, nq=4, np_=2, window_r=0.0,

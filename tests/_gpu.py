@@ -19,9 +19,9 @@ def to_device(pk: dict):
                  for k in ("q", "p", "s", "a"))
 
 
-def options(precision="fp64", nq=4, np_=2, window_r=0.0, cq=0.5, cp=np.pi / 8):
+def options(precision="fp64", nq=4, np_=2, window_r=0.0, cq=0.5, cp=np.pi / 8, flags=0):
     prec = fgr.FGR_FP64 if precision == "fp64" else fgr.FGR_FP32
-    return fgr.make_options(precision=prec, nq=nq, np_=np_, window_r=window_r, cq=cq, cp=cp)
+    return fgr.make_options(precision=prec, nq=nq, np_=np_, window_r=window_r, cq=cq, cp=cp, flags=flags)
 
 
 def reconstruct(method: str, pk: dict, grid: dict, eps: float, opt, on_device=True, ctx=None):
