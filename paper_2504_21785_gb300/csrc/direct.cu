@@ -945,34 +945,42 @@ fgr_status prepare(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t
     return FGR_OK;
 }
 
-// Tensor-core direct sum (FP32, d = 2): loads of the super tiles, items
+// Tensor-core direct sum (FP32, d = 2, 3): loads of the super tiles, items
 // heaviest first, one persistent CTA per SM.
+template <int D>
 fgr_status launch_tc(fgr_ctx *ctx, const Prepared &pr, void *u_dev, cudaStream_t st, Scratch &scratch) {
     const GridDev &g = pr.P.g;
-    if (g.K[0] + tc::kSuper0 > 64) {
+    int64_t runs = 1, nst = 1;
+    for (int l = 0; l < D; ++l) {
+        const int span = tc::tc_span<D>(l);
+        nst *= (g.nt[l] + span - 1) / span;
+        if (l < D - 1) runs *= (int64_t)std::min(g.K[l] + span, g.nt[l]);
+    }
+    if (runs > tc::kSegMax || nst > (int64_t)1 << 30) {
         set_error("direct: window too wide for the tensor-core tiling");
         return FGR_E_INVALID;
     }
-    const int nst = ((g.nt[0] + tc::kSuper0 - 1) / tc::kSuper0) * g.nt[1];
     auto *load = (uint32_t *)scratch.get(sizeof(uint32_t) * (size_t)nst);
     auto *rank = (int *)scratch.get(sizeof(int) * 2 * (size_t)nst);
     const int target = ctx->num_sms * ctx->tune.direct_ctas_per_sm;
-    auto *items = (int2 *)scratch.get(sizeof(int2) * plan_items_capacity(nst, target));
+    auto *items = (int2 *)scratch.get(sizeof(int2) * plan_items_capacity((int)nst, target));
     auto *cnt = (unsigned long long *)scratch.get(2 * sizeof(unsigned long long));
     if (!load || !rank || !items || !cnt) return FGR_E_NOMEM;
     FGR_CUDA_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st));
-    tc_tile_load_kernel<<<(unsigned)((nst + 255) / 256), 256, 0, st>>>(pr.off, g, load);
-    plan_items_kernel<<<1, kPlanThreads, 0, st>>>(load, nst, target, rank, rank + nst, items,
+    tc_tile_load_kernel<D><<<(unsigned)((nst + 255) / 256), 256, 0, st>>>(pr.off, g, (int)nst, load);
+    plan_items_kernel<<<1, kPlanThreads, 0, st>>>(load, (int)nst, target, rank, rank + nst, items,
                                                   reinterpret_cast<int *>(cnt + 1));
     static thread_local int attr_device = -1;
     if (attr_device != ctx->device) {
-        FGR_CUDA_TRY(cudaFuncSetAttribute(direct_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)tc::kDynSmem));
+        FGR_CUDA_TRY(cudaFuncSetAttribute(direct_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)tc::dyn_smem<2>()));
+        FGR_CUDA_TRY(cudaFuncSetAttribute(direct_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)tc::dyn_smem<3>()));
         attr_device = ctx->device;
     }
     const unsigned ctas = (unsigned)ctx->num_sms;
-    direct_tc_kernel<<<ctas, tc::kThreadsTc, tc::kDynSmem, st>>>(
-        reinterpret_cast<const RecF<2> *>(pr.recs), pr.off, pr.P, reinterpret_cast<float2 *>(u_dev), items,
+    direct_tc_kernel<D><<<ctas, tc::kThreadsTc, tc::dyn_smem<D>(), st>>>(
+        reinterpret_cast<const RecF<D> *>(pr.recs), pr.off, pr.P, reinterpret_cast<float2 *>(u_dev), items,
         reinterpret_cast<int *>(cnt + 1), cnt, ctx->yield_flag, (int)ctas, ctx->dev_err);
     FGR_CUDA_TRY(cudaGetLastError());
     return FGR_OK;
@@ -1003,8 +1011,8 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
         timer.finish();
         return FGR_OK;
     }
-    if (D == 2 && !fp64 && !(ctx->opt.flags & FGR_FLAG_DIRECT_FMA)) {
-        fgr_status rt = launch_tc(ctx, pr, u_dev, st, scratch);
+    if (D >= 2 && !fp64 && !(ctx->opt.flags & FGR_FLAG_DIRECT_FMA)) {
+        fgr_status rt = launch_tc<D == 3 ? 3 : 2>(ctx, pr, u_dev, st, scratch);
         if (rt != FGR_OK) return rt;
         timer.mark(&ctx->timing.last.direct_ms);
         ctx->timing.last.launches = 6;

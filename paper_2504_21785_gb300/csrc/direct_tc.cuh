@@ -1,46 +1,55 @@
-// K2 on the fifth-generation tensor cores (FP32 records, d = 2).
+// K2 on the fifth-generation tensor cores (FP32 records, d = 2 and 3).
 //
 // The separable form of the direct sum (eq. 2.10 with the box window): a
-// packet's term on the grid is the outer product of its per-dimension factors,
-//   u[i, j] += F0_r[i] F1_r[j],   F0_r[i] = pref A_r e^{i S_r / eps} g_r(x_i) e^{i P_r (x_i - Q_r) / eps},
-// each factor zero outside the packet's window in its dimension.  Over the
-// records r of a super tile (128 lines of dimension 0 x 32 lines of dimension 1,
-// four tiles of the binning stacked along dimension 0) this is a complex
-// matrix product U = F0 F1^T with K = the records, computed as one real
+// packet's term on the grid is the product of its per-dimension factors,
+//   F_l,r(x) = g_r(x - Q_l) e^{i P_l (x - Q_l) / eps}, zero outside the window,
+// with pref A_r e^{i S_r / eps} folded into dimension 0.  A super tile of 128
+// "rows" x 32 lines of the last dimension is a complex matrix product over the
+// records r of its list, U = F_row F_last^T: d = 2, rows = 128 lines of
+// dimension 0 (four tiles of the binning); d = 3, rows = the 8 x 16 (i, j)
+// pairs of dimensions 0 and 1 (one tile x two tiles) with F_row = F_0 F_1; the
+// last dimension spans one tile (d = 2) or two (d = 3).  It runs as one real
 // product on tcgen05.mma (kind::tf32, M = 128, N = 64, K = 8 per instruction):
-//   A[i][2r + c]  = (Re F0_r[i], Im F0_r[i])[c]
-//   B[j][2r + c]  = (Re F1_r[j], -Im F1_r[j])[c]       (row j: the real part)
-//   B[32 + j][..] = (Im F1_r[j],  Re F1_r[j])[c]       (row 32 + j: the imaginary part)
-// so D[i][j] = Re u and D[i][32 + j] = Im u, accumulated in tensor memory.
+//   A[row][2r + c]  = (Re F_row, Im F_row)[c]
+//   B[j][2r + c]    = (Re F_last,r[j], -Im F_last,r[j])[c]   (row j: the real part)
+//   B[32 + j][..]   = (Im F_last,r[j],  Re F_last,r[j])[c]   (row 32 + j: the imaginary part)
+// so D[row][j] = Re u and D[row][32 + j] = Im u, accumulated in tensor memory.
 // FP32 accuracy from TF32 operands: every factor x is split into
-// x_hi = tf32(x) and x_lo = tf32(x - x_hi), and D += A_hi B_hi + A_hi B_lo +
-// A_lo B_hi (three instructions per K step; the dropped A_lo B_lo and the
+// x_hi = tf32(x) and x_lo = tf32(x - x_hi), and D += A_lo B_hi + A_hi B_lo +
+// A_hi B_hi (three instructions per K step; the dropped A_lo B_lo and the
 // rounding of x_lo are about 2^-22 of a product).
 //
-// Pipeline: a persistent CTA of 640 threads takes (super tile, slice) items
-// from a device counter.  Records are staged 256 at a time (the next 256 are
-// loaded into registers while the current ones are used, and each record's
-// phase rotation over 8 grid lines is computed once when it is staged); for
-// every 16 of them the CTA writes the factors (hi and lo) into one of two
-// shared-memory operand stages in the canonical K-major layout without swizzle
-// (core matrices of 8 rows x 16 bytes; 128 bytes between core matrices along
-// K, 1024 bytes between 8-row groups), one thread issues the 12 MMAs and
-// commits them to the stage's mbarrier, and the CTA goes on to the other stage
-// while the tensor core works.  Factors: one unit of four lines per thread and
-// chunk; warps 0-15 tabulate dimension 0 (a thread takes one record and the
-// lines i0 + 8m, so the 16 lanes of a half warp store 16 distinct 8-byte words
-// of one 128-byte core matrix), warps 16-19 dimension 1; the first line inside
-// the window is evaluated in full (ex2 and sincos), the next by the exact
-// recurrences over 8 grid lines (Gaussian ratio 2^{ce h (16 dx + 64 h)}, itself
-// multiplied by e^{-64 h^2 / eps} per step; phase rotation e^{2 pi i 8 nu}).
+// Pipeline: a persistent CTA takes (super tile, slice) items from a device
+// counter.  20 producer warps stage the records 256 at a time (the next 256
+// are loaded into registers while the current ones are used; each record's
+// phase rotation over 8 grid lines of the dimensions tabulated with stride 8 is
+// computed once when it is staged, and for d = 3 the factors of dimensions 0
+// and 1 on the super tile's 8 + 16 lines too); for every 16 records they write
+// the operands (hi and lo) into one of three shared-memory stages in the
+// canonical K-major layout without swizzle (core matrices of 8 rows x 16
+// bytes; 128 bytes between core matrices along K, 1024 bytes between 8-row
+// groups) and arrive on the stage's "full" mbarrier; one MMA warp waits on it,
+// issues the 12 MMAs and commits them to the stage's "empty" mbarrier, which
+// the producers wait on before they reuse the stage.  Operands: one unit of
+// four rows or lines per thread and chunk; warps 0-15 the A rows (a thread
+// takes one record and the rows i0 + 8m, so the 16 lanes of a half warp store
+// 16 distinct 8-byte words of one 128-byte core matrix), warps 16-19 the last
+// dimension.  A factor along a stride-8 run of lines is evaluated in full at
+// the first line inside the window (ex2 and sincos) and by the exact
+// recurrences over 8 grid lines after it (Gaussian ratio
+// 2^{ce h (16 dx + 64 h)}, itself multiplied by e^{-64 h^2 / eps} per step;
+// phase rotation e^{2 pi i 8 nu}); the d = 3 tables of dimensions 0 and 1 use
+// the same recurrences over single grid steps.
 //
 // Accumulation: the tensor core adds into its FP32 accumulator with truncated
 // alignment, so no accumulator sums more than 4 chunks (64 records, 48
-// instructions): chunks 4k..4k+3 of an item go to TMEM accumulator k mod 2,
-// and while the next four chunks fill the other one, warps 0-15 read the
-// finished one back (tcgen05.ld, one row per lane, 8 columns per warp) into
-// FP32 registers.  At the end of an item the registers are added to the
-// zeroed output with float2 atomics.
+// instructions): chunks 4k..4k+3 of an item go to TMEM accumulator k mod 2
+// (committed to that accumulator's "full" mbarrier after its last chunk), and
+// while the next chunks fill the other one, warps 0-15 read the finished one
+// back (tcgen05.ld, one row per lane, 8 columns per warp) into FP32 registers
+// and arrive on its "empty" mbarrier, which the MMA warp waits on before it
+// starts the accumulator again.  At the end of an item the registers are added
+// to the zeroed output with float2 atomics.
 //
 // Waits on the mbarriers are bounded: on expiry the CTA sets *err, stops
 // taking items and releases its tensor memory.
@@ -49,13 +58,24 @@
 
 namespace tc {
 
-constexpr int kRows = 128;                       // M: lines of dimension 0 per super tile
-constexpr int kSuper0 = kRows / 32;              // binning tiles stacked along dimension 0
-constexpr int kCols = 32;                        // lines of dimension 1 per super tile
+// super tile: tiles of the binning per dimension
+template <int D>
+__host__ __device__ constexpr int tc_span(int l) {
+    return D == 2 ? (l == 0 ? 4 : 1) : (l == 0 ? 1 : 2);
+}
+template <int D>
+__host__ __device__ constexpr int tc_lines(int l) {
+    return tc_span<D>(l) * tileT<D>(l);
+}
+constexpr int kRows = 128;                       // M: rows of a super tile
+constexpr int kCols = 32;                        // lines of the last dimension per super tile
+static_assert(tc_lines<2>(0) == kRows && tc_lines<2>(1) == kCols, "2-D super tile");
+static_assert(tc_lines<3>(0) * tc_lines<3>(1) == kRows && tc_lines<3>(1) == 16 && tc_lines<3>(2) == kCols,
+              "3-D super tile");
 constexpr int kN = 2 * kCols;                    // N: real and imaginary outputs
 constexpr int kRec = 16;                         // records per MMA chunk
 constexpr int kK = 2 * kRec;                     // TF32 elements of K per chunk
-constexpr int kGenThreads = 640;                 // producers: 16 warps for dimension 0, 4 for dimension 1
+constexpr int kGenThreads = 640;                 // producers: 16 warps for the rows, 4 for the last dimension
 constexpr int kThreadsTc = kGenThreads + 32;     // + one warp that issues the MMAs
 constexpr int kStageRec = 256;                   // records staged in shared memory at a time
 constexpr int kPhase = 4;                        // chunks summed in one TMEM accumulator
@@ -64,10 +84,16 @@ constexpr int kBBytes = kN * kK * 4;             // 8 KB
 constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
 constexpr int kStages = 3;
 constexpr int kTmemCols = 2 * kN;                // two accumulators
+constexpr int kSegMax = 256;                     // runs of home tiles in a super tile's list
+constexpr int kF01 = 8 + 16;                     // d = 3: factor lines of dimensions 0 and 1 per record
 constexpr unsigned kWaitLimit = 1u << 24;        // polls of an mbarrier before giving up
-constexpr size_t kDynSmem =
-    (size_t)kStages * kStageBytes + (size_t)kStageRec * sizeof(RecF<2>) + (size_t)kStageRec * sizeof(float4);
+template <int D>
+constexpr size_t dyn_smem() {
+    return (size_t)kStages * kStageBytes + (size_t)kStageRec * (sizeof(RecF<D>) + sizeof(float4)) +
+           (D == 3 ? (size_t)kStageRec * kF01 * sizeof(float2) : 0);
+}
 static_assert(kTmemCols == 128, "two accumulators of N 32-bit columns");
+static_assert(dyn_smem<3>() + 4096 <= 227 * 1024, "shared memory of one CTA");
 
 // instruction descriptor: D FP32, A and B TF32, both K-major, N = 64, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kN >> 3) << 17) |
@@ -144,20 +170,22 @@ __device__ __forceinline__ void tmem_ld8(unsigned taddr, float *v) {
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Factor of dimension l of record R at the grid lines k0 + 8 m, m = 0..3 (zero
-// outside the window); rot = e^{2 pi i 8 nu_l} of the record; fold: dimension 0
-// carries log2|pref A| and the phase of pref A e^{i theta} at the window start.
-__device__ __forceinline__ void factor4(const RecF<2> &R, const int l, const int k0, const float2 rot,
-                                        const DirectParams &P, const bool fold, float2 *out) {
+// Factor of dimension l of record R at the grid lines k0 + S m, m = 0..3 (zero
+// outside the window); rot = e^{2 pi i S nu_l} and qs = e^{-S^2 h^2 / eps};
+// fold: dimension 0 carries log2|pref A| and the phase of pref A e^{i theta}
+// at the window start.
+template <int D, int S>
+__device__ __forceinline__ void factor4(const RecF<D> &R, const int l, const int k0, const float2 rot,
+                                        const float qs, const DirectParams &P, const bool fold, float2 *out) {
     const float kf0 = (float)k0 - R.mlo[l];
     const float wl = R.wlen[l];
     // first of the four lines inside the window (kf0 is integral)
-    const int m0 = kf0 >= 0.f ? 0 : (int)ceilf(-0.125f * kf0);
+    const int m0 = kf0 >= 0.f ? 0 : (S == 1 ? (int)(-kf0) : (int)ceilf(-kf0 * (1.f / S)));
     float vr = 0.f, vi = 0.f, rho = 0.f;
-    const bool any = m0 < 4 && kf0 + 8.f * (float)m0 < wl;
+    const bool any = m0 < 4 && kf0 + (float)(S * m0) < wl;
     if (any) {
         const float h = P.hf[l];
-        const float kf = kf0 + 8.f * (float)m0;
+        const float kf = kf0 + (float)(S * m0);
         const float dx = fmaf(kf, h, R.delta[l]);
         float ex = dx * dx * P.ce;
         float fr = kf * R.nuhi[l];
@@ -173,37 +201,58 @@ __device__ __forceinline__ void factor4(const RecF<2> &R, const int l, const int
         const float ga = ex2_approx(ex);
         vr = ga * cs;
         vi = ga * sn;
-        rho = ex2_approx(P.ce * h * fmaf(16.f, dx, 64.f * h));
+        rho = ex2_approx(P.ce * h * (float)S * fmaf(2.f, dx, (float)S * h));
     }
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-        const bool in = any && m >= m0 && kf0 + 8.f * (float)m < wl;
+        const bool in = any && m >= m0 && kf0 + (float)(S * m) < wl;
         out[m] = in ? make_float2(vr, vi) : make_float2(0.f, 0.f);
         if (m < 3 && m >= m0) {
             const float pr = rot.x * rho, pi = rot.y * rho;
             const float nr = vr * pr - vi * pi;
             vi = vr * pi + vi * pr;
             vr = nr;
-            rho *= P.q8[l];
+            rho *= qs;
         }
     }
 }
 
-// Writes the factors of records rec[0 .. nrec-1] (zeros for r >= nrec) into
-// one operand stage: A_hi, A_lo (128 x kK), B_hi, B_lo (64 x kK); one unit of
-// four lines per thread.
-__device__ __forceinline__ void fill_stage(unsigned char *stage, const RecF<2> *rec, const float4 *rot,
-                                           const int nrec, const int T0, const int T1, const DirectParams &P) {
+// hi and lo TF32 parts of a complex value
+__device__ __forceinline__ void split_c(const float2 v, float2 &hi, float2 &lo) {
+    hi = make_float2(tf32_round(v.x), tf32_round(v.y));
+    lo = make_float2(tf32_round(v.x - hi.x), tf32_round(v.y - hi.y));
+}
+
+// Writes the operands of records rec[0 .. nrec-1] (zeros for r >= nrec) into
+// one stage: A_hi, A_lo (128 x kK), B_hi, B_lo (64 x kK); one unit of four
+// rows or lines per thread.  rot[r]: e^{2 pi i 8 nu} of dimension 0 (.x, .y;
+// d = 2) and of the last dimension (.z, .w); f01[r] (d = 3): the record's
+// factors on the super tile's 8 lines of dimension 0 and 16 of dimension 1.
+template <int D>
+__device__ __forceinline__ void fill_stage(unsigned char *stage, const RecF<D> *rec, const float4 *rot,
+                                           const float2 *f01, const int nrec, const int *T,
+                                           const DirectParams &P) {
     const int tid = threadIdx.x;
     float2 f[4];
     if (tid < 512) {
-        // dimension 0: record 2 (tid >> 5 & 7) + (tid >> 3 & 1), rows 32 blk + (tid & 7) + 8 m,
+        // rows 32 blk + (tid & 7) + 8 m of record 2 (tid >> 5 & 7) + (tid >> 3 & 1),
         // blk = 2 (tid >> 8) + (tid >> 4 & 1)
         const int r = 2 * ((tid >> 5) & 7) + ((tid >> 3) & 1);
         const int i0 = 32 * (2 * (tid >> 8) + ((tid >> 4) & 1)) + (tid & 7);
         if (r < nrec) {
-            const float4 rr = rot[r];
-            factor4(rec[r], 0, T0 + i0, make_float2(rr.x, rr.y), P, true, f);
+            if (D == 2) {
+                const float4 rr = rot[r];
+                factor4<D, 8>(rec[r], 0, T[0] + i0, make_float2(rr.x, rr.y), P.q8[0], P, true, f);
+            } else {
+                // row = 16 i + j: F_0[i] F_1[j] from the record's tables
+                const float2 *F = f01 + r * kF01;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const int row = i0 + 8 * m;
+                    const float2 a = F[row >> 4], b = F[8 + (row & 15)];
+                    f[m] = make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+                }
+            }
         } else {
 #pragma unroll
             for (int m = 0; m < 4; ++m) f[m] = make_float2(0.f, 0.f);
@@ -211,20 +260,20 @@ __device__ __forceinline__ void fill_stage(unsigned char *stage, const RecF<2> *
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const unsigned o = kmaj(i0 + 8 * m, 2 * r);
-            const float hr = tf32_round(f[m].x), hi = tf32_round(f[m].y);
-            const float lr = tf32_round(f[m].x - hr), li = tf32_round(f[m].y - hi);
-            *reinterpret_cast<float2 *>(stage + o) = make_float2(hr, hi);
-            *reinterpret_cast<float2 *>(stage + kABytes + o) = make_float2(lr, li);
+            float2 hi, lo;
+            split_c(f[m], hi, lo);
+            *reinterpret_cast<float2 *>(stage + o) = hi;
+            *reinterpret_cast<float2 *>(stage + kABytes + o) = lo;
         }
     } else {
-        // dimension 1: record v >> 3, columns (v & 7) + 8 m
+        // last dimension: record v >> 3, lines (v & 7) + 8 m
         const int v = tid - 512;
         const int r = v >> 3, j0 = v & 7;
         unsigned char *Bh = stage + 2 * kABytes;
         unsigned char *Bl = Bh + kBBytes;
         if (r < nrec) {
             const float4 rr = rot[r];
-            factor4(rec[r], 1, T1 + j0, make_float2(rr.z, rr.w), P, false, f);
+            factor4<D, 8>(rec[r], D - 1, T[D - 1] + j0, make_float2(rr.z, rr.w), P.q8[D - 1], P, false, f);
         } else {
 #pragma unroll
             for (int m = 0; m < 4; ++m) f[m] = make_float2(0.f, 0.f);
@@ -233,31 +282,81 @@ __device__ __forceinline__ void fill_stage(unsigned char *stage, const RecF<2> *
         for (int m = 0; m < 4; ++m) {
             const int j = j0 + 8 * m;
             const unsigned o_re = kmaj(j, 2 * r), o_im = kmaj(kCols + j, 2 * r);
-            const float hr = tf32_round(f[m].x), hi = tf32_round(f[m].y);
-            const float lr = tf32_round(f[m].x - hr), li = tf32_round(f[m].y - hi);
-            *reinterpret_cast<float2 *>(Bh + o_re) = make_float2(hr, -hi);
-            *reinterpret_cast<float2 *>(Bh + o_im) = make_float2(hi, hr);
-            *reinterpret_cast<float2 *>(Bl + o_re) = make_float2(lr, -li);
-            *reinterpret_cast<float2 *>(Bl + o_im) = make_float2(li, lr);
+            float2 hi, lo;
+            split_c(f[m], hi, lo);
+            *reinterpret_cast<float2 *>(Bh + o_re) = make_float2(hi.x, -hi.y);
+            *reinterpret_cast<float2 *>(Bh + o_im) = make_float2(hi.y, hi.x);
+            *reinterpret_cast<float2 *>(Bl + o_re) = make_float2(lo.x, -lo.y);
+            *reinterpret_cast<float2 *>(Bl + o_im) = make_float2(lo.y, lo.x);
         }
     }
+}
+
+// Super tile coordinates of linear index t (row-major over the super tiles).
+template <int D>
+__device__ __forceinline__ void super_coords(const GridDev &g, int t, int *s) {
+#pragma unroll
+    for (int l = D - 1; l >= 0; --l) {
+        const int n = (g.nt[l] + tc_span<D>(l) - 1) / tc_span<D>(l);
+        s[l] = t % n;
+        t /= n;
+    }
+}
+
+// Home-tile box of super tile s: lo[l] .. hi[l] per dimension.
+template <int D>
+__device__ __forceinline__ void super_box(const GridDev &g, const int *s, int *lo, int *hi) {
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+        lo[l] = max(0, tc_span<D>(l) * s[l] - g.K[l]);
+        hi[l] = min(g.nt[l] - 1, tc_span<D>(l) * s[l] + tc_span<D>(l) - 1);
+    }
+}
+
+// Record range of the r-th run (along the last dimension) of the box.
+template <int D>
+__device__ __forceinline__ void box_run(const GridDev &g, const int64_t *off, const int *lo, const int *hi, int r,
+                                        int64_t *a0, int64_t *a1) {
+    int h[D];
+#pragma unroll
+    for (int l = D - 2; l >= 0; --l) {
+        const int cnt = hi[l] - lo[l] + 1;
+        h[l] = lo[l] + r % cnt;
+        r /= cnt;
+    }
+    h[D - 1] = lo[D - 1];
+    const int first = tile_linear<D>(g, h);
+    *a0 = off[first];
+    *a1 = off[first + hi[D - 1] - lo[D - 1] + 1];
+}
+
+template <int D>
+__device__ __forceinline__ int box_runs(const int *lo, const int *hi) {
+    int rows = 1;
+#pragma unroll
+    for (int l = 0; l < D - 1; ++l) rows *= hi[l] - lo[l] + 1;
+    return rows;
 }
 
 }  // namespace tc
 
 // Records in the list of every super tile (union of the home-tile boxes of its
-// kSuper0 tiles).
-__global__ void tc_tile_load_kernel(const int64_t *__restrict__ off, GridDev g, uint32_t *__restrict__ load) {
-    const int nst1 = g.nt[1];
-    const int nst0 = (g.nt[0] + tc::kSuper0 - 1) / tc::kSuper0;
+// tiles).
+template <int D>
+__global__ void tc_tile_load_kernel(const int64_t *__restrict__ off, GridDev g, int nst,
+                                    uint32_t *__restrict__ load) {
     const int tile = blockIdx.x * blockDim.x + threadIdx.x;
-    if (tile >= nst0 * nst1) return;
-    const int s0 = tile / nst1, s1 = tile % nst1;
-    const int h0lo = max(0, tc::kSuper0 * s0 - g.K[0]);
-    const int h0hi = min(g.nt[0] - 1, tc::kSuper0 * s0 + tc::kSuper0 - 1);
-    const int h1lo = max(0, s1 - g.K[1]);
+    if (tile >= nst) return;
+    int s[D], lo[D], hi[D];
+    tc::super_coords<D>(g, tile, s);
+    tc::super_box<D>(g, s, lo, hi);
     int64_t sum = 0;
-    for (int h0 = h0lo; h0 <= h0hi; ++h0) sum += off[h0 * nst1 + s1 + 1] - off[h0 * nst1 + h1lo];
+    const int runs = tc::box_runs<D>(lo, hi);
+    for (int r = 0; r < runs; ++r) {
+        int64_t a0, a1;
+        tc::box_run<D>(g, off, lo, hi, r, &a0, &a1);
+        sum += a1 - a0;
+    }
     load[tile] = (uint32_t)(sum < 0xffffffffLL ? sum : 0xffffffffLL);
 }
 
@@ -302,17 +401,18 @@ __device__ __forceinline__ bool producers_sync_or(bool v) {
 // through empty[s] (the MMA commit); accumulator a through acc_full[a] (MMA
 // commit after the last chunk of a phase) and acc_empty[a] (512 reader
 // arrivals after the read-back).
+template <int D>
 __global__ void __launch_bounds__(tc::kThreadsTc, 1)
-    direct_tc_kernel(const RecF<2> *__restrict__ recs, const int64_t *__restrict__ off, DirectParams P,
+    direct_tc_kernel(const RecF<D> *__restrict__ recs, const int64_t *__restrict__ off, DirectParams P,
                      float2 *__restrict__ u, const int2 *__restrict__ items, const int *__restrict__ n_items,
                      unsigned long long *__restrict__ counter, const volatile int *yield, int keep,
                      int *__restrict__ err) {
     using namespace tc;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *stages = smem;
-    RecF<2> *srec = reinterpret_cast<RecF<2> *>(smem + kStages * kStageBytes);
-    float4 *srot = reinterpret_cast<float4 *>(smem + kStages * kStageBytes + kStageRec * sizeof(RecF<2>));
-    constexpr int kSegMax = 64;  // rows of a super tile's home-tile box (checked on the host)
+    RecF<D> *srec = reinterpret_cast<RecF<D> *>(smem + kStages * kStageBytes);
+    float4 *srot = reinterpret_cast<float4 *>(smem + kStages * kStageBytes + kStageRec * sizeof(RecF<D>));
+    float2 *f01 = reinterpret_cast<float2 *>(srot + kStageRec);  // d = 3
     __shared__ uint32_t seg_start[kSegMax];
     __shared__ uint32_t seg_cum[kSegMax + 1];
     __shared__ int nseg_s;
@@ -324,7 +424,6 @@ __global__ void __launch_bounds__(tc::kThreadsTc, 1)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const GridDev &g = P.g;
-    const int nst1 = g.nt[1];
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&full[s])), "r"(kGenThreads) : "memory");
@@ -437,15 +536,17 @@ __global__ void __launch_bounds__(tc::kThreadsTc, 1)
             if (item >= total) break;
             const int2 it = items[item];
             const int split = it.y & 0xff, nsplit = it.y >> 8;
-            const int s0 = it.x / nst1, s1 = it.x % nst1;
-            if (tid == 0) {  // segments: rows of the home-tile box, each a run of tiles along dimension 1
-                const int h0lo = max(0, kSuper0 * s0 - g.K[0]);
-                const int h0hi = min(g.nt[0] - 1, kSuper0 * s0 + kSuper0 - 1);
-                const int h1lo = max(0, s1 - g.K[1]);
+            int sc[D];
+            super_coords<D>(g, it.x, sc);
+            if (tid == 0) {  // runs of home tiles along the last dimension
+                int lo[D], hi[D];
+                super_box<D>(g, sc, lo, hi);
+                const int runs = box_runs<D>(lo, hi);
                 int ns = 0;
                 int64_t cum = 0;
-                for (int h0 = h0lo; h0 <= h0hi && ns < kSegMax; ++h0) {
-                    const int64_t a0 = off[h0 * nst1 + h1lo], a1 = off[h0 * nst1 + s1 + 1];
+                for (int r = 0; r < runs && ns < kSegMax; ++r) {
+                    int64_t a0, a1;
+                    box_run<D>(g, off, lo, hi, r, &a0, &a1);
                     if (a1 > a0) {
                         seg_start[ns] = (uint32_t)a0;
                         seg_cum[ns] = (uint32_t)cum;
@@ -460,10 +561,12 @@ __global__ void __launch_bounds__(tc::kThreadsTc, 1)
             const int nseg = nseg_s;
             const int64_t L = (int64_t)seg_cum[nseg];
             const int64_t nch = (L + kStageRec - 1) / kStageRec;
-            const int T0 = s0 * kRows, T1 = s1 * kCols;
-            int4 pf[sizeof(RecF<2>) / 16];
+            int T[D];
 #pragma unroll
-            for (int w = 0; w < (int)(sizeof(RecF<2>) / 16); ++w) pf[w] = make_int4(0, 0, 0, 0);
+            for (int l = 0; l < D; ++l) T[l] = sc[l] * tc_lines<D>(l);
+            int4 pf[sizeof(RecF<D>) / 16];
+#pragma unroll
+            for (int w = 0; w < (int)(sizeof(RecF<D>) / 16); ++w) pf[w] = make_int4(0, 0, 0, 0);
             auto fetch = [&](int64_t c) {
                 const int64_t v = c * kStageRec + tid;
                 if (tid < kStageRec && c < nch && v < L) {
@@ -476,7 +579,7 @@ __global__ void __launch_bounds__(tc::kThreadsTc, 1)
                     const int64_t idx = (int64_t)seg_start[lo] + (v - (int64_t)seg_cum[lo]);
                     const int4 *src = reinterpret_cast<const int4 *>(recs + idx);
 #pragma unroll
-                    for (int w = 0; w < (int)(sizeof(RecF<2>) / 16); ++w) pf[w] = __ldg(src + w);
+                    for (int w = 0; w < (int)(sizeof(RecF<D>) / 16); ++w) pf[w] = __ldg(src + w);
                 }
             };
             fetch(split);
@@ -487,19 +590,41 @@ __global__ void __launch_bounds__(tc::kThreadsTc, 1)
                 if (tid < kStageRec) {
                     int4 *dst = reinterpret_cast<int4 *>(srec + tid);
 #pragma unroll
-                    for (int w = 0; w < (int)(sizeof(RecF<2>) / 16); ++w) dst[w] = pf[w];
-                    // the record's phase rotations over 8 grid lines, per dimension
-                    const RecF<2> &R = *reinterpret_cast<const RecF<2> *>(pf);
-                    float4 rr;
-                    float t0 = 8.f * R.nuhi[0];
-                    t0 -= rint_fast(t0);
-                    sincospif(2.f * fmaf(8.f, R.nulo[0], t0), &rr.y, &rr.x);
-                    float t1 = 8.f * R.nuhi[1];
+                    for (int w = 0; w < (int)(sizeof(RecF<D>) / 16); ++w) dst[w] = pf[w];
+                    // the record's phase rotations over 8 grid lines
+                    const RecF<D> &R = *reinterpret_cast<const RecF<D> *>(pf);
+                    float4 rr = make_float4(1.f, 0.f, 1.f, 0.f);
+                    if (D == 2) {
+                        float t0 = 8.f * R.nuhi[0];
+                        t0 -= rint_fast(t0);
+                        sincospif(2.f * fmaf(8.f, R.nulo[0], t0), &rr.y, &rr.x);
+                    }
+                    float t1 = 8.f * R.nuhi[D - 1];
                     t1 -= rint_fast(t1);
-                    sincospif(2.f * fmaf(8.f, R.nulo[1], t1), &rr.w, &rr.z);
+                    sincospif(2.f * fmaf(8.f, R.nulo[D - 1], t1), &rr.w, &rr.z);
                     srot[tid] = rr;
                 }
                 asm volatile("bar.sync 1, %0;" ::"n"(kGenThreads) : "memory");
+                if (D == 3) {
+                    // factors of dimensions 0 and 1 on the super tile's lines: six
+                    // units of four consecutive lines per record
+                    for (int e = tid; e < kStageRec * 6; e += kGenThreads) {
+                        const int r = e / 6, k = e % 6;
+                        const int l = k < 2 ? 0 : 1;
+                        const int first = l == 0 ? 4 * k : 4 * (k - 2);
+                        const RecF<D> &R = srec[r];
+                        float t = R.nuhi[l];
+                        t -= rint_fast(t);
+                        float sn, cs;
+                        __sincosf(6.283185307179586f * (t + R.nulo[l]), &sn, &cs);
+                        float2 fv[4];
+                        factor4<D, 1>(R, l, T[l] + first, make_float2(cs, sn), P.q_dim[l], P, l == 0, fv);
+                        float2 *dst = f01 + r * kF01 + (l == 0 ? 0 : 8) + first;
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) dst[m] = fv[m];
+                    }
+                    asm volatile("bar.sync 1, %0;" ::"n"(kGenThreads) : "memory");
+                }
                 fetch(c + nsplit);
                 const int64_t left = L - c * kStageRec;
                 const int nrec = left < kStageRec ? (int)left : kStageRec;
@@ -514,8 +639,9 @@ __global__ void __launch_bounds__(tc::kThreadsTc, 1)
                     }
                     const bool first = ci % kPhase == 0;
                     const bool end = ci % kPhase == kPhase - 1 || (last_block && sub + kRec >= nrec);
-                    if (!abort) tc::fill_stage(stages + s * kStageBytes, srec + sub, srot + sub, min(kRec, nrec - sub),
-                                               T0, T1, P);
+                    if (!abort)
+                        fill_stage<D>(stages + s * kStageBytes, srec + sub, srot + sub, f01 + sub * kF01,
+                                      min(kRec, nrec - sub), T, P);
                     if (tid == 0) info[s] = ChunkInfo{phase, first ? 1 : 0, end ? 1 : 0, 0};
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     bar_arrive(&full[s]);
@@ -535,13 +661,23 @@ __global__ void __launch_bounds__(tc::kThreadsTc, 1)
             if (ci > 0) {
                 if (pend >= 0) read_acc(pend);
                 if (reader && !abort) {
-                    const int64_t gi = (int64_t)s0 * kRows + 32 * q + lane;
-                    if (gi < g.n[0]) {
+                    const int row = 32 * q + lane;
+                    int64_t gi, gj0;
+                    bool ok;
+                    if (D == 2) {
+                        gi = (int64_t)T[0] + row;
+                        ok = gi < g.n[0];
+                    } else {
+                        const int64_t i = (int64_t)T[0] + (row >> 4), j = (int64_t)T[1] + (row & 15);
+                        gi = i * g.n[1] + j;
+                        ok = i < g.n[0] && j < g.n[1];
+                    }
+                    gj0 = (int64_t)T[D - 1] + 8 * cg;
+                    if (ok) {
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            const int64_t gj = (int64_t)s1 * kCols + 8 * cg + k;
-                            if (gj < g.n[1]) atomic_add_c(u + gi * g.n[1] + gj, acc_re[k], acc_im[k]);
-                        }
+                        for (int k = 0; k < 8; ++k)
+                            if (gj0 + k < g.n[D - 1])
+                                atomic_add_c(u + gi * g.n[D - 1] + gj0 + k, acc_re[k], acc_im[k]);
                     }
                 }
 #pragma unroll

@@ -1,8 +1,9 @@
-"""GPU parity of the tensor-core direct sum (FP32, d = 2; the default FP32 2-D
-path) against the FP64 oracle's windowed direct sum (eq. 2.10), and against
+"""GPU parity of the tensor-core direct sum (FP32, d = 2 and 3; the default
+FP32 path for d >= 2) against the FP64 oracle's windowed direct sum (eq. 2.10), and against
 the CUDA-core path (FGR_FLAG_DIRECT_FMA) on the same inputs.
 
-Cases: a ragged grid (neither extent a multiple of the 128 x 32 super tile)
+Cases: ragged grids (no extent a multiple of the 128 x 32 or 8 x 16 x 32 super
+tile)
 with packets whose windows leave the grid and some zero amplitudes; a dense
 case whose super tiles hold far more than 1024 records per work item, so that
 the tensor-memory accumulator is read back several times per item; an empty
@@ -89,3 +90,43 @@ def test_tc_empty_and_repeated_calls(fgr):
         b = _gpu.reconstruct("direct", pk, grid, eps, opt, ctx=ctx)
     assert _gpu.rel_l2(a, ref) <= 1e-5
     assert _gpu.rel_l2(b, ref) <= 1e-5
+
+
+def _grid3(n):
+    return dict(d=3, n=list(n), lo=[-math.pi] * 3, hi=[math.pi] * 3)
+
+
+def test_tc_3d_ragged_grid_matches_oracle(fgr):
+    # 8 x 16 x 32 super tiles on a grid that none of the extents fills
+    eps = 1 / 64
+    mesh = mesh_for(3, eps)
+    grid = _grid3((37, 29, 70))
+    pk = random_packets(35, 3, 600, q_range=(-3.5, 3.5), p_range=(-1.5, 1.5), s_range=(-3, 3), mesh=mesh,
+                        on_node_fraction=0.1)
+    pk["a"][:, ::13] = 0.0
+    ref = fga.direct_sum(pk, grid, eps, mesh.dq, mesh.dp, R=6)
+    got = _gpu.reconstruct("direct", pk, grid, eps, _gpu.options("fp32"))
+    fma = _gpu.reconstruct("direct", pk, grid, eps, _gpu.options("fp32", flags=fgr.FGR_FLAG_DIRECT_FMA))
+    e_tc, e_fma = _gpu.rel_l2(got, ref), _gpu.rel_l2(fma, ref)
+    print("3-D ragged: tensor cores %.3e, CUDA cores %.3e" % (e_tc, e_fma))
+    assert e_tc <= 1e-5
+    assert e_fma <= 1e-5
+    assert np.all(got[ref == 0] == 0)
+
+
+def test_tc_3d_dense_items(fgr):
+    # many records per item: several accumulator phases and read-backs per item
+    eps = 1 / 64
+    mesh = mesh_for(3, eps)
+    grid = _grid3((24, 40, 64))
+    pk = random_packets(36, 3, 30000, q_range=(-1.5, 1.5), p_range=(-1.0, 1.0), s_range=(-3, 3), mesh=mesh)
+    opt = _gpu.options("fp32")
+    with fgr.Context(3, grid, eps, opt) as ctx:
+        fgr.fgr_set_tuning(ctx.handle, 1, 16, 0)
+        got = _gpu.reconstruct("direct", pk, grid, eps, opt, ctx=ctx)
+    fma = _gpu.reconstruct("direct", pk, grid, eps, _gpu.options("fp32", flags=fgr.FGR_FLAG_DIRECT_FMA))
+    rng = np.random.default_rng(4)
+    pts = np.stack([rng.integers(0, n, 300) for n in (24, 40, 64)])
+    ref = fga.direct_sum(pk, grid, eps, mesh.dq, mesh.dp, R=6, points=pts)
+    assert _gpu.rel_l2(got[tuple(pts)], ref) <= 1e-5
+    assert _gpu.rel_l2(got, fma) <= 1e-5
