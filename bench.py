@@ -57,6 +57,12 @@ FP32_PEAK_TFLOPS = 74.6
 # warp reach 855e9 per second
 L2_RED_PEAK_GPS = 222.8
 L2_RED_COALESCED_GPS = 855.1
+# TF32 tensor rate: the measured bf16 GEMM rate (MEASURED_PEAKS.json, burst)
+# times the nominal TF32/bf16 ratio 1.1/2.25; a tcgen05.mma rate probe on this
+# GB300 (M 128, K 8, operands in shared memory) measured 4093 FLOP per clock
+# per SM at N >= 128 and 2725 at N = 64 (the direct sum's shape)
+BF16_MEASURED_TFLOPS = 1933.7
+TF32_PEAK_TFLOPS = BF16_MEASURED_TFLOPS * 1.1 / 2.25
 
 
 def _rank_env():
@@ -235,6 +241,9 @@ def run_ours(args):
                              direct_runs=args.direct_runs)
     ud, uf = u_d.cpu().numpy(), u_f.cpu().numpy()
     rel = float(np.linalg.norm(uf - ud) / max(np.linalg.norm(ud), 1e-300))
+    droof = None
+    if d >= 2 and prec == fgr.FGR_FP32:
+        droof = direct_roofline(window_pairs(arrs[0].cpu().numpy(), grid, eps), recon["direct"]["median_ms"])
 
     # end to end through the C ABI: packets in pinned host memory, u back to
     # pinned host memory, both copies inside the timed region
@@ -290,7 +299,8 @@ def run_ours(args):
                 "fggc_ms_mean": ms_step, "fggc_ms_median": statistics.median(step_ms),
                 "fggc_ms_min": min(step_ms), "fggc_ms_max": max(step_ms),
                 "direct_packets_per_s": direct["packets_per_s"], "direct_ms_median": direct["median_ms"],
-                "direct_runs": direct["runs"],
+                "direct_runs": direct["runs"], "direct_path": direct.get("path", "CUDA cores"),
+                "direct_roofline": droof,
                 "speedup_fggc_over_direct": (direct["median_ms"] / statistics.median(step_ms)
                                              if rel <= 1e-5 else "not at equal accuracy"),
                 "rel_l2_fggc_vs_direct": rel,
@@ -369,6 +379,37 @@ def reconstruction_roofline(d, M, nodes, kern, ms_step):
     return out
 
 
+def window_pairs(q, grid, eps, R=6.0):
+    """Packet-point pairs inside the box windows (the rule of the direct sum:
+    m_lo = ceil((Q - R sqrt(eps) - lo) / h), m_hi = floor((Q + R sqrt(eps) - lo) / h),
+    clipped to the grid), summed over the packets."""
+    import numpy as np
+    d = int(grid["d"])
+    rs = R * np.sqrt(eps)
+    prod = np.ones(q.shape[1], dtype=np.float64)
+    for l in range(d):
+        n, lo = int(grid["n"][l]), float(grid["lo"][l])
+        h = (float(grid["hi"][l]) - lo) / n
+        mlo = np.maximum(np.ceil((q[l] - rs - lo) / h), 0)
+        mhi = np.minimum(np.floor((q[l] + rs - lo) / h), n - 1)
+        prod *= np.maximum(mhi - mlo + 1, 0)
+    return float(prod.sum())
+
+
+def direct_roofline(pairs, direct_ms):
+    """Roofline block of the direct sum (FP32, d >= 2: tcgen05 kernel).  Unit:
+    a packet-point pair inside the windows, one complex multiply-add (8 real
+    FLOPs) run on the tensor pipe as three TF32 products (hi x hi, hi x lo,
+    lo x hi): 24 TF32 FLOPs per pair, against the TF32 tensor rate."""
+    ach = 24.0 * pairs / (direct_ms * 1e-3) / 1e12
+    return {"kernel": "direct_tc_kernel (K2 on tcgen05, 3 x TF32)", "bound": "tensor", "achieved": ach,
+            "peak": TF32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / TF32_PEAK_TFLOPS,
+            "units_per_launch": pairs, "pairs_per_s": pairs / (direct_ms * 1e-3), "launch_ms": direct_ms,
+            "unit_def": "packet-point pair inside the windows = one complex multiply-add, 24 TF32 FLOPs as "
+                        "three TF32 products",
+            "peak_source": "measured bf16 GEMM rate x nominal TF32/bf16 ratio 1.1/2.25 (of measured)"}
+
+
 def pipeline_bench(cfg: int, args, flush):
     """The 1-D workload as a whole pipeline: copy the t = 0 packets into the
     working buffers, fgr_propagate (A1, 10^4 RK4 steps), fgr_reconstruct_fggc
@@ -429,6 +470,9 @@ def pipeline_bench(cfg: int, args, flush):
     step_ms = statistics.mean(e[0].elapsed_time(e[3]) for e in evs)
     ud, uf = u_d.cpu().numpy(), u_f.cpu().numpy()
     rel = float(np.linalg.norm(uf - ud) / max(np.linalg.norm(ud), 1e-300))
+    droof = None
+    if d >= 2 and prec == fgr.FGR_FP32:
+        droof = direct_roofline(window_pairs(arrs[0].cpu().numpy(), grid, eps), recon["direct"]["median_ms"])
     recon = reconstruct_runs(fgr, ctx, packets, u_d, grid, d, eps, prec, flush, stream, ud, runs=20)
     decomp = decompose_runs(fgr, ctx, w, init, pot, stream, flush, runs=20)
     fgr.fgr_set_timing(ctx.handle, True)
@@ -477,10 +521,16 @@ def reconstruct_runs(fgr, ctx, packets, u_ref, grid, d, eps, prec, flush, stream
 
     q2 = fgr.Context(d, grid, eps, fgr.make_options(precision=prec, nq=2, np_=2))
     out = {}
-    for name, fn, c in (("direct", fgr.fgr_reconstruct_direct, ctx), ("fggc_q4p2", fgr.fgr_reconstruct_fggc, ctx),
-                        ("fggc_q2p2", fgr.fgr_reconstruct_fggc, q2)):
+    methods = [("direct", fgr.fgr_reconstruct_direct, ctx), ("fggc_q4p2", fgr.fgr_reconstruct_fggc, ctx),
+               ("fggc_q2p2", fgr.fgr_reconstruct_fggc, q2)]
+    fma = None
+    if d >= 2 and prec == fgr.FGR_FP32:
+        # the direct sum on the CUDA cores (FGR_FLAG_DIRECT_FMA) beside the default tensor-core path
+        fma = fgr.Context(d, grid, eps, fgr.make_options(precision=prec, flags=fgr.FGR_FLAG_DIRECT_FMA))
+        methods.insert(1, ("direct_cuda_cores", fgr.fgr_reconstruct_direct, fma))
+    for name, fn, c in methods:
         u = u_ref if name == "direct" else torch.zeros_like(u_ref)
-        nrun = direct_runs if (name == "direct" and direct_runs) else runs
+        nrun = direct_runs if (name.startswith("direct") and direct_runs) else runs
         t0 = time.perf_counter()
         fn(c.handle, packets, u, stream)
         torch.cuda.synchronize()
@@ -506,6 +556,10 @@ def reconstruct_runs(fgr, ctx, packets, u_ref, grid, d, eps, prec, flush, stream
             del u
     u = torch.zeros_like(u_ref)
     q2.close()
+    if fma is not None:
+        fma.close()
+        out["direct"]["path"] = "tensor cores (tcgen05.mma, 3 x TF32)"
+        out["direct"]["speedup_vs_cuda_cores"] = out["direct_cuda_cores"]["median_ms"] / out["direct"]["median_ms"]
     # FGGC Q4P2 through a plan: the node box fixed once for this packet set,
     # so a call waits for nothing on the host (the unplanned call reads the
     # box bounds back every time)
@@ -653,8 +707,11 @@ def reconstruct_bench(cfg: int, args, flush):
     fgr.fgr_autotune(ctx.handle, pk, ud, 3, stream)
     res, spread = {}, {}
     q2 = fgr.Context(d, grid, eps, fgr.make_options(precision=prec, nq=2, np_=2))
+    fma = fgr.Context(d, grid, eps, fgr.make_options(precision=prec, flags=fgr.FGR_FLAG_DIRECT_FMA))
     uq2 = torch.zeros(shape, dtype=cdt, device="cuda")
+    ufma = torch.zeros(shape, dtype=cdt, device="cuda")
     for name, fn, c, u in (("direct", fgr.fgr_reconstruct_direct, ctx, ud),
+                           ("direct_cuda_cores", fgr.fgr_reconstruct_direct, fma, ufma),
                            ("fggc", fgr.fgr_reconstruct_fggc, ctx, uf),
                            ("fggc_q2p2", fgr.fgr_reconstruct_fggc, q2, uq2)):
         t0 = time.perf_counter()
@@ -674,8 +731,11 @@ def reconstruct_bench(cfg: int, args, flush):
         res[name] = statistics.median(ms)
         spread[name] = {"runs": runs, "median_ms": res[name], "min_ms": min(ms), "max_ms": max(ms)}
     q2.close()
+    fma.close()
     a, b, c2 = uf.cpu().numpy(), ud.cpu().numpy(), uq2.cpu().numpy()
     rel = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    rel_fma = float(np.linalg.norm(ufma.cpu().numpy() - b) / max(np.linalg.norm(b), 1e-300))
+    del ufma
     rel_q2 = float(np.linalg.norm(c2 - b) / max(np.linalg.norm(b), 1e-300))
     fgr.fgr_set_timing(ctx.handle, True)
     fgr.fgr_reconstruct_fggc(ctx.handle, pk, uf, stream)
@@ -688,6 +748,9 @@ def reconstruct_bench(cfg: int, args, flush):
             "fggc_ms": res["fggc"], "direct_ms": res["direct"],
             "fggc_packets_per_s": M / (res["fggc"] * 1e-3), "direct_packets_per_s": M / (res["direct"] * 1e-3),
             "fggc_over_direct": res["direct"] / res["fggc"], "rel_l2_fggc_vs_direct": rel,
+            "direct_path": "tensor cores (tcgen05.mma, 3 x TF32)",
+            "direct_cuda_cores_ms": res["direct_cuda_cores"], "rel_l2_direct_cuda_cores_vs_direct": rel_fma,
+            "direct_roofline": direct_roofline(window_pairs(arrs[0].cpu().numpy(), grid, eps), res["direct"]),
             "runs": spread, "fggc_q2p2_ms": res["fggc_q2p2"], "rel_l2_fggc_q2p2_vs_direct": rel_q2,
             "fggc_q2p2_over_direct": (res["direct"] / res["fggc_q2p2"] if rel_q2 <= 1e-5
                                       else "not at equal accuracy (rel L2 > 1e-5)"),
@@ -1180,9 +1243,9 @@ def run_profile_case(args):
     propagate to t = 0.01 (100 RK4 steps), then one FGGC and one direct
     reconstruction of the propagated packets, one batched direct sum of
     eight copies of that request and one initial decomposition of the
-    reconstructed wave onto the propagated positions (FGGC only for 3-D
-    workloads); for d >= 2 one tensor-product decomposition of that wave onto
-    the t = 0 mesh."""
+    reconstructed wave onto the propagated positions (3-D workloads: FGGC, and
+    the direct sum with at most 2^21 packets kept); for d >= 2 one
+    tensor-product decomposition of that wave onto the t = 0 mesh."""
     import numpy as np
     import torch
 
@@ -1206,8 +1269,10 @@ def run_profile_case(args):
         cdt = torch.complex64 if prec == fgr.FGR_FP32 else torch.complex128
         u = torch.zeros(tuple(grid["n"][:d]), dtype=cdt, device="cuda")
         fgr.fgr_reconstruct_fggc(ctx.handle, pk, u)
-        if d < 3:  # the 3-D direct sum takes seconds: FGGC only there
+        if d < 3 or (pick is not None and pick.size <= 1 << 21):
+            # the full 3-D direct sum takes about a second: only on a reduced case
             fgr.fgr_reconstruct_direct(ctx.handle, pk, u)
+        if d < 3:
             outs = [torch.zeros_like(u) for _ in range(8)]
             fgr.fgr_reconstruct_direct_batch([ctx] * 8, [pk] * 8, outs)
             fgr.fgr_decompose(ctx.handle, u, pk)

@@ -979,9 +979,13 @@ fgr_status launch_tc(fgr_ctx *ctx, const Prepared &pr, void *u_dev, cudaStream_t
         attr_device = ctx->device;
     }
     const unsigned ctas = (unsigned)ctx->num_sms;
+    // with a yield word (a large request in the server), the CTAs of the
+    // second half of the SMs stop between items while it is set: one CTA
+    // fills an SM's registers, so that is how small requests get SMs
+    const int keep = ctx->yield_flag ? std::max(1, (int)ctas / 2) : (int)ctas;
     direct_tc_kernel<D><<<ctas, tc::kThreadsTc, tc::dyn_smem<D>(), st>>>(
         reinterpret_cast<const RecF<D> *>(pr.recs), pr.off, pr.P, reinterpret_cast<float2 *>(u_dev), items,
-        reinterpret_cast<int *>(cnt + 1), cnt, ctx->yield_flag, (int)ctas, ctx->dev_err);
+        reinterpret_cast<int *>(cnt + 1), cnt, ctx->yield_flag, keep, ctx->dev_err);
     FGR_CUDA_TRY(cudaGetLastError());
     return FGR_OK;
 }

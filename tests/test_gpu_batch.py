@@ -66,7 +66,9 @@ def test_batch_matches_single_calls_and_oracle(fgr, d, precision):
                                          [r["u"] for r in reqs])
         torch.cuda.synchronize()
         R = 8 if precision == "fp64" else 6
-        tol_single = 1e-13 if precision == "fp64" else 1e-6
+        # FP32: the batch runs the CUDA-core kernel; a single 2-D call runs the
+        # tensor-core one (3 x TF32), so the two agree to the FP32 tolerance
+        tol_single = 1e-13 if precision == "fp64" else (1e-6 if d == 1 else 1e-5)
         tol_oracle = 1e-12 if precision == "fp64" else 1e-5
         for r in reqs:
             got = r["u"].cpu().numpy()

@@ -321,7 +321,9 @@ def test_small_requests_pass_a_large_direct_sum(fgr):
         assert r_big.status == 0 and all(r.status == 0 for r in res)
         assert max(r.t_done_ms for r in res) < r_big.t_done_ms
         ref = _gpu.reconstruct("direct", big, g_big, 1 / 64, opt)
-        assert _gpu.rel_l2(u_big.cpu().numpy(), ref) <= 1e-6
+        # the server cuts the large sum into finer work items, so its FP32
+        # partial sums meet in another order: equal to the FP32 tolerance
+        assert _gpu.rel_l2(u_big.cpu().numpy(), ref) <= 1e-5
         for (s, n, mth), u in zip(reqs, outs):
             ref = _gpu.reconstruct("fggc" if mth else "direct", small[s], _grid(1, n), 1 / 256, opt)
             assert _gpu.rel_l2(u.cpu().numpy(), ref) <= 1e-6
