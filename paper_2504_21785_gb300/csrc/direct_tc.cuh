@@ -14,10 +14,10 @@
 //   B[j][2r + c]    = (Re F_last,r[j], -Im F_last,r[j])[c]   (row j: the real part)
 //   B[32 + j][..]   = (Im F_last,r[j],  Re F_last,r[j])[c]   (row 32 + j: the imaginary part)
 // so D[row][j] = Re u and D[row][32 + j] = Im u, accumulated in tensor memory.
-// FP32 accuracy from TF32 operands: every factor x is split into
-// x_hi = tf32(x) and x_lo = tf32(x - x_hi), and D += A_lo B_hi + A_hi B_lo +
+// FP32 accuracy from TF32 operands: every factor x is split into x_hi (x
+// truncated to TF32) and x_lo = x - x_hi, and D += A_lo B_hi + A_hi B_lo +
 // A_hi B_hi (three instructions per K step; the dropped A_lo B_lo and the
-// rounding of x_lo are about 2^-22 of a product).
+// truncation of x_lo to TF32 are below 2^-20 of a product each).
 //
 // Pipeline: a persistent CTA takes (super tile, slice) items from a device
 // counter.  20 producer warps stage the records 256 at a time (the next 256
@@ -113,12 +113,8 @@ __device__ __forceinline__ uint64_t sdesc(unsigned addr) {
            (1ull << 46);
 }
 
-// x rounded to TF32 (10 explicit mantissa bits), nearest with ties away from
-// zero, for finite x: add half a TF32 unit to the magnitude bits and clear the
-// 13 dropped bits
-__device__ __forceinline__ float tf32_round(float x) {
-    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
-}
+// x truncated to TF32 (10 explicit mantissa bits): the 13 dropped bits cleared
+__device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
 
 __device__ __forceinline__ void mma_tf32(unsigned tmem, uint64_t a, uint64_t b, unsigned acc) {
     asm volatile(
@@ -217,10 +213,12 @@ __device__ __forceinline__ void factor4(const RecF<D> &R, const int l, const int
     }
 }
 
-// hi and lo TF32 parts of a complex value
+// hi and lo TF32 parts of a complex value: hi = x truncated to TF32, lo = x - hi
+// (exact in FP32; the tensor core reads its leading 11 bits, so lo is
+// truncated once more there): |x - hi - lo_tf32| < 2^-20 |x|
 __device__ __forceinline__ void split_c(const float2 v, float2 &hi, float2 &lo) {
-    hi = make_float2(tf32_round(v.x), tf32_round(v.y));
-    lo = make_float2(tf32_round(v.x - hi.x), tf32_round(v.y - hi.y));
+    hi = make_float2(tf32_trunc(v.x), tf32_trunc(v.y));
+    lo = make_float2(v.x - hi.x, v.y - hi.y);
 }
 
 // Writes the operands of records rec[0 .. nrec-1] (zeros for r >= nrec) into
@@ -360,20 +358,22 @@ __global__ void tc_tile_load_kernel(const int64_t *__restrict__ off, GridDev g, 
     load[tile] = (uint32_t)(sum < 0xffffffffLL ? sum : 0xffffffffLL);
 }
 
-// what the MMA warp needs to know about the chunk in a stage
-struct ChunkInfo {
-    int phase;      // accumulator phase (accumulator phase & 1)
-    int first;      // first chunk of the phase: the first MMA overwrites the accumulator
-    int phase_end;  // last chunk of the phase: commit the accumulator's barrier too
-    int stop;       // no more chunks
-};
+// what the MMA warp needs to know about the chunk in a stage, in one word:
+// bits 0-27 the accumulator phase (accumulator = phase & 1); bit 28: first
+// chunk of the phase (the first MMA overwrites the accumulator); bit 29: last
+// chunk of the phase (commit the accumulator's barrier too); bit 30: no more
+// chunks
+constexpr unsigned kInfoFirst = 1u << 28, kInfoEnd = 1u << 29, kInfoStop = 1u << 30;
 
-// bounded wait that also gives up once another thread has reported a failure
+// Bounded wait that also gives up once another thread has reported a failure.
+// SLEEP (the producers): back off after every failed poll, so that waiting
+// warps leave the issue slots to the MMA warp, which polls without a pause.
+template <bool SLEEP>
 __device__ __forceinline__ bool bar_wait_or_abort(uint64_t *bar, unsigned parity, const volatile int *abort) {
     for (unsigned it = 0; it < tc::kWaitLimit; ++it) {
         if (tc::bar_try(bar, parity)) return true;
         if ((it & 63) == 63 && *abort) return false;
-        if (it > 32) __nanosleep(32);
+        if (SLEEP) __nanosleep(64);
     }
     return false;
 }
@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(tc::kThreadsTc, 1)
     __shared__ uint32_t seg_cum[kSegMax + 1];
     __shared__ int nseg_s;
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2];
-    __shared__ ChunkInfo info[kStages];
+    __shared__ unsigned info[kStages];
     __shared__ unsigned s_tmem;
     __shared__ long long s_item;
     __shared__ volatile int s_abort;
@@ -450,40 +450,50 @@ __global__ void __launch_bounds__(tc::kThreadsTc, 1)
     if (warp == kGenThreads / 32) {
         // ---- MMA issuer (one thread) ----
         if (lane == 0) {
-            for (uint32_t gc = 0;; ++gc) {
-                const int s = gc % kStages;
-                if (!bar_wait_or_abort(&full[s], (gc / kStages) & 1, &s_abort)) {
+            int s = 0;
+            unsigned fpar = 0;  // parity of full[s]'s phase for this pass over the stages
+            for (;;) {
+                if (!bar_wait_or_abort<false>(&full[s], fpar, &s_abort)) {
                     s_abort = 1;
                     break;
                 }
-                const volatile ChunkInfo *vi = &info[s];
-                const ChunkInfo ci{vi->phase, vi->first, vi->phase_end, vi->stop};
-                if (ci.stop) break;
-                const int a = ci.phase & 1;
-                if (ci.first && ci.phase >= 2 &&
-                    !bar_wait_or_abort(&acc_empty[a], ((ci.phase >> 1) - 1) & 1, &s_abort)) {
+                const unsigned ci = *const_cast<const volatile unsigned *>(&info[s]);
+                if (ci & kInfoStop) break;
+                const int phase = (int)(ci & (kInfoFirst - 1));
+                const bool first = (ci & kInfoFirst) != 0;
+                const int a = phase & 1;
+                if (first && phase >= 2 &&
+                    !bar_wait_or_abort<false>(&acc_empty[a], ((phase >> 1) - 1) & 1, &s_abort)) {
                     s_abort = 1;
                     break;
                 }
                 fence_after();
+                // descriptors of the stage's four operands; a K step of 8 TF32
+                // (256 bytes) adds 16 to the start-address field
                 const unsigned sa = saddr(stages + s * kStageBytes);
+                const uint64_t ah = sdesc(sa), al = sdesc(sa + kABytes);
+                const uint64_t bh = sdesc(sa + 2 * kABytes), bl = sdesc(sa + 2 * kABytes + kBBytes);
                 const unsigned d = tmem + (unsigned)(a * kN);
 #pragma unroll
                 for (int ks = 0; ks < kK / 8; ++ks) {
-                    const unsigned o = 256u * ks;
-                    const uint64_t ah = sdesc(sa + o), al = sdesc(sa + kABytes + o);
-                    const uint64_t bh = sdesc(sa + 2 * kABytes + o), bl = sdesc(sa + 2 * kABytes + kBBytes + o);
-                    mma_tf32(d, al, bh, (ci.first && ks == 0) ? 0u : 1u);
-                    mma_tf32(d, ah, bl, 1u);
-                    mma_tf32(d, ah, bh, 1u);
+                    const uint64_t o = 16u * ks;
+                    mma_tf32(d, al + o, bh + o, (first && ks == 0) ? 0u : 1u);
+                    mma_tf32(d, ah + o, bl + o, 1u);
+                    mma_tf32(d, ah + o, bh + o, 1u);
                 }
                 mma_commit(&empty[s]);
-                if (ci.phase_end) mma_commit(&acc_full[a]);
+                if (ci & kInfoEnd) mma_commit(&acc_full[a]);
+                if (++s == kStages) {
+                    s = 0;
+                    fpar ^= 1u;
+                }
             }
         }
     } else {
         // ---- producers and accumulator readers ----
         uint32_t gc = 0;   // chunks produced by this CTA
+        int st = 0;        // their stage: gc mod kStages
+        unsigned epar = 1; // parity of empty[st]'s phase to wait for (the first pass waits for nothing)
         int phase = 0;     // accumulator phases started by this CTA
         bool abort = false;
         const long long total = *n_items;
@@ -496,7 +506,7 @@ __global__ void __launch_bounds__(tc::kThreadsTc, 1)
         auto read_acc = [&](int ph) {
             if (!reader || abort) return;
             const int a = ph & 1;
-            if (!bar_wait_or_abort(&acc_full[a], (ph >> 1) & 1, &s_abort)) {
+            if (!bar_wait_or_abort<true>(&acc_full[a], (ph >> 1) & 1, &s_abort)) {
                 abort = true;
                 s_abort = 1;
                 return;
@@ -517,10 +527,16 @@ __global__ void __launch_bounds__(tc::kThreadsTc, 1)
         };
         // waits for stage s to be free and hands chunk info over with the stage
         auto stage_free = [&](int s) {
-            if (gc >= (uint32_t)kStages && !abort &&
-                !bar_wait_or_abort(&empty[s], ((gc / kStages) - 1) & 1, &s_abort)) {
+            if (gc >= (uint32_t)kStages && !abort && !bar_wait_or_abort<true>(&empty[s], epar, &s_abort)) {
                 abort = true;
                 s_abort = 1;
+            }
+        };
+        auto next_stage = [&]() {
+            ++gc;
+            if (++st == kStages) {
+                st = 0;
+                epar ^= 1u;
             }
         };
         for (;;) {
@@ -629,8 +645,8 @@ __global__ void __launch_bounds__(tc::kThreadsTc, 1)
                 const int64_t left = L - c * kStageRec;
                 const int nrec = left < kStageRec ? (int)left : kStageRec;
                 const bool last_block = c + nsplit >= nch;
-                for (int sub = 0; sub < nrec; sub += kRec, ++ci, ++gc) {
-                    const int s = gc % kStages;
+                for (int sub = 0; sub < nrec; sub += kRec, ++ci, next_stage()) {
+                    const int s = st;
                     stage_free(s);  // the MMAs of chunk gc - kStages are complete
                     // a phase whose last chunk is 3 chunks back: its MMAs are complete
                     if (pend >= 0 && ci >= pend_ci + kStages) {
@@ -642,7 +658,7 @@ __global__ void __launch_bounds__(tc::kThreadsTc, 1)
                     if (!abort)
                         fill_stage<D>(stages + s * kStageBytes, srec + sub, srot + sub, f01 + sub * kF01,
                                       min(kRec, nrec - sub), T, P);
-                    if (tid == 0) info[s] = ChunkInfo{phase, first ? 1 : 0, end ? 1 : 0, 0};
+                    if (tid == 0) info[s] = (unsigned)phase | (first ? kInfoFirst : 0u) | (end ? kInfoEnd : 0u);
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     bar_arrive(&full[s]);
                     if (end) {
@@ -686,9 +702,9 @@ __global__ void __launch_bounds__(tc::kThreadsTc, 1)
         }
         // tell the MMA warp to stop
         if (!abort) {
-            const int s = gc % kStages;
+            const int s = st;
             stage_free(s);
-            if (tid == 0) info[s] = ChunkInfo{0, 0, 0, 1};
+            if (tid == 0) info[s] = kInfoStop;
             bar_arrive(&full[s]);
         }
         if (abort) {
