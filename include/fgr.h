@@ -238,13 +238,19 @@ fgr_status fgr_fggc_multistep_tensor(fgr_ctx *ctx, const fgr_axis *axes, const i
  * d = 1: of every 4 consecutive grid points the first term is evaluated with
  * exp, sin and cos in FP32 and the next three by the exact recurrences of the
  * Gaussian factor and the phase (one complex multiply each).  d = 2, 3: the
- * term factorises over dimensions; each packet's per-dimension factors are
- * tabulated on an output tile's grid lines (the same recurrences, four lines
- * at a time) and every packet-point pair costs one complex multiply-add of
- * those factors.  Partial sums are folded into FP64; complex64 out.  The work
- * is cut into (output tile, packet slice) items: d = 1 the same number of
+ * term factorises over dimensions, so on a tile of the grid the sum is a
+ * complex matrix product of the packets' per-dimension factors (tabulated on
+ * the tile's grid lines by the same recurrences).  By default it runs on the
+ * tensor cores: 128 x 32-point super tiles (d = 2: 128 x 32; d = 3:
+ * 8 x 16 x 32), each factor split into two TF32 parts and the product taken
+ * as three TF32 products into FP32 accumulators of 64 packets each, summed in
+ * FP32; with FGR_FLAG_DIRECT_FMA on the CUDA cores, one complex multiply-add
+ * per packet-point pair, partial sums folded into FP64.  Complex64 out.  The
+ * work is cut into (tile, packet slice) items: d = 1 the same number of
  * slices per tile, d >= 2 slices in proportion to each tile's packet count,
- * heaviest first, taken by persistent CTAs (no host wait). */
+ * heaviest first, taken by persistent CTAs (no host wait).  A tensor-core
+ * launch that gives up waiting on its own pipeline (a bounded wait) sets the
+ * context's error word; the next FGGC call on the context reports it. */
 fgr_status fgr_reconstruct_direct(fgr_ctx *ctx, const fgr_packets *pk, void *u_out,
                                   void *cuda_stream);
 

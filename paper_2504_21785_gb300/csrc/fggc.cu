@@ -1213,10 +1213,10 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
     int *herr = reinterpret_cast<int *>(ctx->host_pinned) + 16;
     FGR_CUDA_TRY(cudaMemcpyAsync(herr, ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     FGR_CUDA_TRY(cudaStreamSynchronize(st));
-    if (*herr) {  // a grid pass of an earlier call gave up waiting for its tile copies
+    if (*herr) {  // a kernel of an earlier call gave up one of its bounded waits
         FGR_CUDA_TRY(cudaMemsetAsync(ctx->dev_err, 0, sizeof(int), st));
-        set_error("fggc: a grid pass of an earlier call on this context timed out waiting for its tile copies; "
-                  "that call's output is incomplete");
+        set_error("fggc: a kernel of an earlier call on this context timed out waiting (grid-pass tile copies "
+                  "or the tensor-core direct sum's pipeline); that call's output is incomplete");
         return FGR_E_TIMEOUT;
     }
     int hb[13];
