@@ -4,16 +4,19 @@
 // packet's term on the grid is the product of its per-dimension factors,
 //   F_l,r(x) = g_r(x - Q_l) e^{i P_l (x - Q_l) / eps}, zero outside the window,
 // with pref A_r e^{i S_r / eps} folded into dimension 0.  A super tile of 128
-// "rows" x 32 lines of the last dimension is a complex matrix product over the
+// "rows" x 64 lines of the last dimension is a complex matrix product over the
 // records r of its list, U = F_row F_last^T: d = 2, rows = 128 lines of
 // dimension 0 (four tiles of the binning); d = 3, rows = the 8 x 16 (i, j)
 // pairs of dimensions 0 and 1 (one tile x two tiles) with F_row = F_0 F_1; the
-// last dimension spans one tile (d = 2) or two (d = 3).  It runs as one real
-// product on tcgen05.mma (kind::tf32, M = 128, N = 64, K = 8 per instruction):
+// last dimension spans two tiles (d = 2) or four (d = 3).  It runs as one real
+// product on tcgen05.mma (kind::tf32, M = 128, N = 128, K = 8 per instruction):
 //   A[row][2r + c]  = (Re F_row, Im F_row)[c]
 //   B[j][2r + c]    = (Re F_last,r[j], -Im F_last,r[j])[c]   (row j: the real part)
-//   B[32 + j][..]   = (Im F_last,r[j],  Re F_last,r[j])[c]   (row 32 + j: the imaginary part)
-// so D[row][j] = Re u and D[row][32 + j] = Im u, accumulated in tensor memory.
+//   B[64 + j][..]   = (Im F_last,r[j],  Re F_last,r[j])[c]   (row 64 + j: the imaginary part)
+// so D[row][j] = Re u and D[row][64 + j] = Im u, accumulated in tensor memory.
+// N = 128 rather than 64: an MMA of N = 64 takes 48 clocks against 64 at
+// N = 128 (twice the work), and a wider last dimension lists each record in
+// fewer super tiles.
 // FP32 accuracy from TF32 operands: every factor x is split into x_hi (x
 // truncated to TF32) and x_lo = x - x_hi, and D += A_lo B_hi + A_hi B_lo +
 // A_hi B_hi (three instructions per K step; the dropped A_lo B_lo and the
@@ -25,16 +28,16 @@
 // phase rotation over 8 grid lines of the dimensions tabulated with stride 8 is
 // computed once when it is staged, and for d = 3 the factors of dimensions 0
 // and 1 on the super tile's 8 + 16 lines too); for every 16 records they write
-// the operands (hi and lo) into one of three shared-memory stages in the
+// the operands (hi and lo) into one of three (d = 2) or two (d = 3) stages in the
 // canonical K-major layout without swizzle (core matrices of 8 rows x 16
 // bytes; 128 bytes between core matrices along K, 1024 bytes between 8-row
 // groups) and arrive on the stage's "full" mbarrier; one MMA warp waits on it,
 // issues the 12 MMAs and commits them to the stage's "empty" mbarrier, which
-// the producers wait on before they reuse the stage.  Operands: one unit of
-// four rows or lines per thread and chunk; warps 0-15 the A rows (a thread
-// takes one record and the rows i0 + 8m, so the 16 lanes of a half warp store
-// 16 distinct 8-byte words of one 128-byte core matrix), warps 16-19 the last
-// dimension.  A factor along a stride-8 run of lines is evaluated in full at
+// the producers wait on before they reuse the stage.  Operands: per thread and
+// chunk, warps 0-15 take four A rows (one record, the rows i0 + 8m, so the 16
+// lanes of a half warp store 16 distinct 8-byte words of one 128-byte core
+// matrix) and warps 16-19 eight lines of the last dimension (one record, the
+// lines j0 + 8m, the same pattern).  A factor along a stride-8 run of lines is evaluated in full at
 // the first line inside the window (ex2 and sincos) and by the exact
 // recurrences over 8 grid lines after it (Gaussian ratio
 // 2^{ce h (16 dx + 64 h)}, itself multiplied by e^{-64 h^2 / eps} per step;
@@ -45,11 +48,12 @@
 // alignment, so no accumulator sums more than 4 chunks (64 records, 48
 // instructions): chunks 4k..4k+3 of an item go to TMEM accumulator k mod 2
 // (committed to that accumulator's "full" mbarrier after its last chunk), and
-// while the next chunks fill the other one, warps 0-15 read the finished one
-// back (tcgen05.ld, one row per lane, 8 columns per warp) into FP32 registers
-// and arrive on its "empty" mbarrier, which the MMA warp waits on before it
-// starts the accumulator again.  At the end of an item the registers are added
-// to the zeroed output with float2 atomics.
+// while the next chunks fill the other one, warps 0-15 add the finished one
+// (tcgen05.ld, one row per lane, 16 complex columns per warp, 8 TMEM columns
+// at a time) to the item's FP32 running sums, which live in a third TMEM
+// region (tcgen05.st), and arrive on its "empty" mbarrier, which the MMA warp
+// waits on before it starts the accumulator again.  At the end of an item the
+// running sums are added to the zeroed output with float2 atomics.
 //
 // Waits on the mbarriers are bounded: on expiry the CTA sets *err, stops
 // taking items and releases its tensor memory.
@@ -61,14 +65,14 @@ namespace tc {
 // super tile: tiles of the binning per dimension
 template <int D>
 __host__ __device__ constexpr int tc_span(int l) {
-    return D == 2 ? (l == 0 ? 4 : 1) : (l == 0 ? 1 : 2);
+    return D == 2 ? (l == 0 ? 4 : 2) : (l == 0 ? 1 : (l == 1 ? 2 : 4));
 }
 template <int D>
 __host__ __device__ constexpr int tc_lines(int l) {
     return tc_span<D>(l) * tileT<D>(l);
 }
 constexpr int kRows = 128;                       // M: rows of a super tile
-constexpr int kCols = 32;                        // lines of the last dimension per super tile
+constexpr int kCols = 64;                        // lines of the last dimension per super tile
 static_assert(tc_lines<2>(0) == kRows && tc_lines<2>(1) == kCols, "2-D super tile");
 static_assert(tc_lines<3>(0) * tc_lines<3>(1) == kRows && tc_lines<3>(1) == 16 && tc_lines<3>(2) == kCols,
               "3-D super tile");
@@ -80,22 +84,28 @@ constexpr int kThreadsTc = kGenThreads + 32;     // + one warp that issues the M
 constexpr int kStageRec = 256;                   // records staged in shared memory at a time
 constexpr int kPhase = 4;                        // chunks summed in one TMEM accumulator
 constexpr int kABytes = kRows * kK * 4;          // 16 KB
-constexpr int kBBytes = kN * kK * 4;             // 8 KB
+constexpr int kBBytes = kN * kK * 4;             // 16 KB
 constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
-constexpr int kStages = 3;
-constexpr int kTmemCols = 2 * kN;                // two accumulators
+constexpr int kMaxStages = 3;
+// operand stages: three for d = 2; two for d = 3, whose factor tables take
+// the shared memory of the third
+template <int D>
+__host__ __device__ constexpr int tc_stages() {
+    return D == 2 ? 3 : 2;
+}
+constexpr int kTmemCols = 4 * kN;                // two accumulators, the running sums, one unused
 constexpr int kSegMax = 256;                     // runs of home tiles in a super tile's list
 constexpr int kF01 = 8 + 16;                     // d = 3: factor lines of dimensions 0 and 1 per record
 constexpr unsigned kWaitLimit = 1u << 24;        // polls of an mbarrier before giving up
 template <int D>
 constexpr size_t dyn_smem() {
-    return (size_t)kStages * kStageBytes + (size_t)kStageRec * (sizeof(RecF<D>) + sizeof(float4)) +
+    return (size_t)tc_stages<D>() * kStageBytes + (size_t)kStageRec * (sizeof(RecF<D>) + sizeof(float4)) +
            (D == 3 ? (size_t)kStageRec * kF01 * sizeof(float2) : 0);
 }
-static_assert(kTmemCols == 128, "two accumulators of N 32-bit columns");
-static_assert(dyn_smem<3>() + 4096 <= 227 * 1024, "shared memory of one CTA");
+static_assert(kTmemCols == 512, "two accumulators and the running sums of N 32-bit columns each");
+static_assert(dyn_smem<2>() + 4096 <= 227 * 1024 && dyn_smem<3>() + 4096 <= 227 * 1024, "shared memory of one CTA");
 
-// instruction descriptor: D FP32, A and B TF32, both K-major, N = 64, M = 128
+// instruction descriptor: D FP32, A and B TF32, both K-major, N = 128, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kN >> 3) << 17) |
                             ((uint32_t)(kRows >> 4) << 24);
 
@@ -164,21 +174,44 @@ __device__ __forceinline__ void tmem_ld8(unsigned taddr, float *v) {
     for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+__device__ __forceinline__ void tmem_st8(unsigned taddr, const float *v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                 "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                 "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// 16 consecutive 32-bit TMEM columns of the warp's 32 lanes (one row per lane)
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float *v) {
+    unsigned r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Factor of dimension l of record R at the grid lines k0 + S m, m = 0..3 (zero
-// outside the window); rot = e^{2 pi i S nu_l} and qs = e^{-S^2 h^2 / eps};
+// Factor of dimension l of record R at the grid lines k0 + S m, m = 0..NL-1
+// (zero outside the window); rot = e^{2 pi i S nu_l} and qs = e^{-S^2 h^2 / eps};
 // fold: dimension 0 carries log2|pref A| and the phase of pref A e^{i theta}
 // at the window start.
-template <int D, int S>
-__device__ __forceinline__ void factor4(const RecF<D> &R, const int l, const int k0, const float2 rot,
-                                        const float qs, const DirectParams &P, const bool fold, float2 *out) {
+template <int D, int S, int NL>
+__device__ __forceinline__ void factor_run(const RecF<D> &R, const int l, const int k0, const float2 rot,
+                                           const float qs, const DirectParams &P, const bool fold, float2 *out) {
     const float kf0 = (float)k0 - R.mlo[l];
     const float wl = R.wlen[l];
-    // first of the four lines inside the window (kf0 is integral)
+    // first of the lines inside the window (kf0 is integral)
     const int m0 = kf0 >= 0.f ? 0 : (S == 1 ? (int)(-kf0) : (int)ceilf(-kf0 * (1.f / S)));
     float vr = 0.f, vi = 0.f, rho = 0.f;
-    const bool any = m0 < 4 && kf0 + (float)(S * m0) < wl;
+    const bool any = m0 < NL && kf0 + (float)(S * m0) < wl;
     if (any) {
         const float h = P.hf[l];
         const float kf = kf0 + (float)(S * m0);
@@ -200,10 +233,54 @@ __device__ __forceinline__ void factor4(const RecF<D> &R, const int l, const int
         rho = ex2_approx(P.ce * h * (float)S * fmaf(2.f, dx, (float)S * h));
     }
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
+    for (int m = 0; m < NL; ++m) {
         const bool in = any && m >= m0 && kf0 + (float)(S * m) < wl;
         out[m] = in ? make_float2(vr, vi) : make_float2(0.f, 0.f);
-        if (m < 3 && m >= m0) {
+        if (m < NL - 1 && m >= m0) {
+            const float pr = rot.x * rho, pi = rot.y * rho;
+            const float nr = vr * pr - vi * pi;
+            vi = vr * pi + vi * pr;
+            vr = nr;
+            rho *= qs;
+        }
+    }
+}
+
+// factor_run, handing each value to sink(m, value) as soon as it is known
+// instead of returning them all (fewer live registers for long runs)
+template <int D, int S, int NL, class Sink>
+__device__ __forceinline__ void factor_run_to(const RecF<D> &R, const int l, const int k0, const float2 rot,
+                                              const float qs, const DirectParams &P, const bool fold, Sink sink) {
+    const float kf0 = (float)k0 - R.mlo[l];
+    const float wl = R.wlen[l];
+    const int m0 = kf0 >= 0.f ? 0 : (S == 1 ? (int)(-kf0) : (int)ceilf(-kf0 * (1.f / S)));
+    float vr = 0.f, vi = 0.f, rho = 0.f;
+    const bool any = m0 < NL && kf0 + (float)(S * m0) < wl;
+    if (any) {
+        const float h = P.hf[l];
+        const float kf = kf0 + (float)(S * m0);
+        const float dx = fmaf(kf, h, R.delta[l]);
+        float ex = dx * dx * P.ce;
+        float fr = kf * R.nuhi[l];
+        fr -= rint_fast(fr);
+        float tau = fmaf(kf, R.nulo[l], fr);
+        if (fold) {
+            ex += R.la;
+            tau += R.tau0;
+        }
+        tau -= rint_fast(tau);
+        float sn, cs;
+        __sincosf(6.283185307179586f * tau, &sn, &cs);
+        const float ga = ex2_approx(ex);
+        vr = ga * cs;
+        vi = ga * sn;
+        rho = ex2_approx(P.ce * h * (float)S * fmaf(2.f, dx, (float)S * h));
+    }
+#pragma unroll
+    for (int m = 0; m < NL; ++m) {
+        const bool in = any && m >= m0 && kf0 + (float)(S * m) < wl;
+        sink(m, in ? make_float2(vr, vi) : make_float2(0.f, 0.f));
+        if (m < NL - 1 && m >= m0) {
             const float pr = rot.x * rho, pi = rot.y * rho;
             const float nr = vr * pr - vi * pi;
             vi = vr * pi + vi * pr;
@@ -222,8 +299,8 @@ __device__ __forceinline__ void split_c(const float2 v, float2 &hi, float2 &lo) 
 }
 
 // Writes the operands of records rec[0 .. nrec-1] (zeros for r >= nrec) into
-// one stage: A_hi, A_lo (128 x kK), B_hi, B_lo (64 x kK); one unit of four
-// rows or lines per thread.  rot[r]: e^{2 pi i 8 nu} of dimension 0 (.x, .y;
+// one stage: A_hi, A_lo (128 x kK), B_hi, B_lo (128 x kK); per thread one
+// unit of four rows (A) or eight lines of the last dimension (B).  rot[r]: e^{2 pi i 8 nu} of dimension 0 (.x, .y;
 // d = 2) and of the last dimension (.z, .w); f01[r] (d = 3): the record's
 // factors on the super tile's 8 lines of dimension 0 and 16 of dimension 1.
 template <int D>
@@ -240,7 +317,7 @@ __device__ __forceinline__ void fill_stage(unsigned char *stage, const RecF<D> *
         if (r < nrec) {
             if (D == 2) {
                 const float4 rr = rot[r];
-                factor4<D, 8>(rec[r], 0, T[0] + i0, make_float2(rr.x, rr.y), P.q8[0], P, true, f);
+                factor_run<D, 8, 4>(rec[r], 0, T[0] + i0, make_float2(rr.x, rr.y), P.q8[0], P, true, f);
             } else {
                 // row = 16 i + j: F_0[i] F_1[j] from the record's tables
                 const float2 *F = f01 + r * kF01;
@@ -264,28 +341,27 @@ __device__ __forceinline__ void fill_stage(unsigned char *stage, const RecF<D> *
             *reinterpret_cast<float2 *>(stage + kABytes + o) = lo;
         }
     } else {
-        // last dimension: record v >> 3, lines (v & 7) + 8 m
+        // last dimension: record v >> 3, lines (v & 7) + 8 m, m = 0..7
         const int v = tid - 512;
         const int r = v >> 3, j0 = v & 7;
         unsigned char *Bh = stage + 2 * kABytes;
         unsigned char *Bl = Bh + kBBytes;
-        if (r < nrec) {
-            const float4 rr = rot[r];
-            factor4<D, 8>(rec[r], D - 1, T[D - 1] + j0, make_float2(rr.z, rr.w), P.q8[D - 1], P, false, f);
-        } else {
-#pragma unroll
-            for (int m = 0; m < 4; ++m) f[m] = make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
+        auto put = [&](int m, float2 val) {
             const int j = j0 + 8 * m;
             const unsigned o_re = kmaj(j, 2 * r), o_im = kmaj(kCols + j, 2 * r);
             float2 hi, lo;
-            split_c(f[m], hi, lo);
+            split_c(val, hi, lo);
             *reinterpret_cast<float2 *>(Bh + o_re) = make_float2(hi.x, -hi.y);
             *reinterpret_cast<float2 *>(Bh + o_im) = make_float2(hi.y, hi.x);
             *reinterpret_cast<float2 *>(Bl + o_re) = make_float2(lo.x, -lo.y);
             *reinterpret_cast<float2 *>(Bl + o_im) = make_float2(lo.y, lo.x);
+        };
+        if (r < nrec) {
+            const float4 rr = rot[r];
+            factor_run_to<D, 8, 8>(rec[r], D - 1, T[D - 1] + j0, make_float2(rr.z, rr.w), P.q8[D - 1], P, false, put);
+        } else {
+#pragma unroll
+            for (int m = 0; m < 8; ++m) put(m, make_float2(0.f, 0.f));
         }
     }
 }
@@ -410,14 +486,15 @@ __global__ void __launch_bounds__(tc::kThreadsTc, 1)
     using namespace tc;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *stages = smem;
+    constexpr int kStages = tc_stages<D>();
     RecF<D> *srec = reinterpret_cast<RecF<D> *>(smem + kStages * kStageBytes);
     float4 *srot = reinterpret_cast<float4 *>(smem + kStages * kStageBytes + kStageRec * sizeof(RecF<D>));
     float2 *f01 = reinterpret_cast<float2 *>(srot + kStageRec);  // d = 3
     __shared__ uint32_t seg_start[kSegMax];
     __shared__ uint32_t seg_cum[kSegMax + 1];
     __shared__ int nseg_s;
-    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2];
-    __shared__ unsigned info[kStages];
+    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], acc_full[2], acc_empty[2];
+    __shared__ unsigned info[kMaxStages];
     __shared__ unsigned s_tmem;
     __shared__ long long s_item;
     __shared__ volatile int s_abort;
@@ -497,12 +574,15 @@ __global__ void __launch_bounds__(tc::kThreadsTc, 1)
         int phase = 0;     // accumulator phases started by this CTA
         bool abort = false;
         const long long total = *n_items;
-        // warps 0-15 read the accumulators: lane quarter q (rows 32 q + lane), columns 8 cg .. 8 cg + 7
+        // warps 0-15 read the accumulators: lane quarter q (rows 32 q + lane),
+        // complex columns kRC cg .. kRC cg + kRC - 1; the item's running sums
+        // stay in TMEM columns [2 kN, 3 kN) of the same lanes
         const int q = warp & 3, cg = (warp >> 2) & 3;
         const bool reader = warp < 16;
-        float acc_re[8], acc_im[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) acc_re[k] = acc_im[k] = 0.f;
+        constexpr int kRC = kCols / 4;  // complex columns per reader
+        const unsigned lanes = tmem + ((unsigned)(32 * q) << 16);
+        const unsigned run = lanes + 2 * kN;
+        bool fresh = true;              // the item's first read-back stores instead of adding
         auto read_acc = [&](int ph) {
             if (!reader || abort) return;
             const int a = ph & 1;
@@ -512,16 +592,20 @@ __global__ void __launch_bounds__(tc::kThreadsTc, 1)
                 return;
             }
             fence_after();
-            const unsigned base = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(a * kN);
-            float re[8], im[8];
-            tmem_ld8(base + 8 * cg, re);
-            tmem_ld8(base + kCols + 8 * cg, im);
-            tmem_wait_ld();
+            const unsigned acc = lanes + (unsigned)(a * kN);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                acc_re[k] += re[k];
-                acc_im[k] += im[k];
+            for (int part = 0; part < 2 * kRC / 8; ++part) {
+                const unsigned col = (part / (kRC / 8)) * kCols + kRC * cg + 8 * (part % (kRC / 8));
+                float p[8], r[8];
+                tmem_ld8(acc + col, p);
+                if (!fresh) tmem_ld8(run + col, r);
+                tmem_wait_ld();
+#pragma unroll
+                for (int k = 0; k < 8; ++k) r[k] = fresh ? p[k] : r[k] + p[k];
+                tmem_st8(run + col, r);
             }
+            tmem_wait_st();
+            fresh = false;
             fence_before();
             bar_arrive(&acc_empty[a]);
         };
@@ -634,7 +718,7 @@ __global__ void __launch_bounds__(tc::kThreadsTc, 1)
                         float sn, cs;
                         __sincosf(6.283185307179586f * (t + R.nulo[l]), &sn, &cs);
                         float2 fv[4];
-                        factor4<D, 1>(R, l, T[l] + first, make_float2(cs, sn), P.q_dim[l], P, l == 0, fv);
+                        factor_run<D, 1, 4>(R, l, T[l] + first, make_float2(cs, sn), P.q_dim[l], P, l == 0, fv);
                         float2 *dst = f01 + r * kF01 + (l == 0 ? 0 : 8) + first;
 #pragma unroll
                         for (int m = 0; m < 4; ++m) dst[m] = fv[m];
@@ -678,7 +762,7 @@ __global__ void __launch_bounds__(tc::kThreadsTc, 1)
                 if (pend >= 0) read_acc(pend);
                 if (reader && !abort) {
                     const int row = 32 * q + lane;
-                    int64_t gi, gj0;
+                    int64_t gi;
                     bool ok;
                     if (D == 2) {
                         gi = (int64_t)T[0] + row;
@@ -688,16 +772,25 @@ __global__ void __launch_bounds__(tc::kThreadsTc, 1)
                         gi = i * g.n[1] + j;
                         ok = i < g.n[0] && j < g.n[1];
                     }
-                    gj0 = (int64_t)T[D - 1] + 8 * cg;
-                    if (ok) {
+                    fence_after();
 #pragma unroll
-                        for (int k = 0; k < 8; ++k)
-                            if (gj0 + k < g.n[D - 1])
-                                atomic_add_c(u + gi * g.n[D - 1] + gj0 + k, acc_re[k], acc_im[k]);
+                    for (int h = 0; h < kRC / 8; ++h) {
+                        const unsigned col = kRC * cg + 8 * h;
+                        float re[8], im[8];
+                        tmem_ld8(run + col, re);
+                        tmem_ld8(run + kCols + col, im);
+                        tmem_wait_ld();
+                        const int64_t gj0 = (int64_t)T[D - 1] + col;
+                        if (ok) {
+#pragma unroll
+                            for (int k = 0; k < 8; ++k)
+                                if (gj0 + k < g.n[D - 1])
+                                    atomic_add_c(u + gi * g.n[D - 1] + gj0 + k, re[k], im[k]);
+                        }
                     }
+                    fence_before();
                 }
-#pragma unroll
-                for (int k = 0; k < 8; ++k) acc_re[k] = acc_im[k] = 0.f;
+                fresh = true;
             }
         }
         // tell the MMA warp to stop
