@@ -241,8 +241,8 @@ fgr_status fgr_fggc_multistep_tensor(fgr_ctx *ctx, const fgr_axis *axes, const i
  * term factorises over dimensions, so on a tile of the grid the sum is a
  * complex matrix product of the packets' per-dimension factors (tabulated on
  * the tile's grid lines by the same recurrences).  By default it runs on the
- * tensor cores: 128 x 32-point super tiles (d = 2: 128 x 32; d = 3:
- * 8 x 16 x 32), each factor split into two TF32 parts and the product taken
+ * tensor cores: super tiles of 128 x 64 points (d = 2) or 8 x 16 x 64
+ * (d = 3), each factor split into two TF32 parts and the product taken
  * as three TF32 products into FP32 accumulators of 64 packets each, summed in
  * FP32; with FGR_FLAG_DIRECT_FMA on the CUDA cores, one complex multiply-add
  * per packet-point pair, partial sums folded into FP64.  Complex64 out.  The

@@ -2,7 +2,7 @@
 FP32 path for d >= 2) against the FP64 oracle's windowed direct sum (eq. 2.10), and against
 the CUDA-core path (FGR_FLAG_DIRECT_FMA) on the same inputs.
 
-Cases: ragged grids (no extent a multiple of the 128 x 32 or 8 x 16 x 32 super
+Cases: ragged grids (no extent a multiple of the 128 x 64 or 8 x 16 x 64 super
 tile)
 with packets whose windows leave the grid and some zero amplitudes; a dense
 case whose super tiles hold far more than 1024 records per work item, so that
@@ -97,7 +97,7 @@ def _grid3(n):
 
 
 def test_tc_3d_ragged_grid_matches_oracle(fgr):
-    # 8 x 16 x 32 super tiles on a grid that none of the extents fills
+    # 8 x 16 x 64 super tiles on a grid that none of the extents fills
     eps = 1 / 64
     mesh = mesh_for(3, eps)
     grid = _grid3((37, 29, 70))
