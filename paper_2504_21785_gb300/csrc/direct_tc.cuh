@@ -200,54 +200,11 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float *v) {
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Factor of dimension l of record R at the grid lines k0 + S m, m = 0..NL-1
-// (zero outside the window); rot = e^{2 pi i S nu_l} and qs = e^{-S^2 h^2 / eps};
-// fold: dimension 0 carries log2|pref A| and the phase of pref A e^{i theta}
-// at the window start.
-template <int D, int S, int NL>
-__device__ __forceinline__ void factor_run(const RecF<D> &R, const int l, const int k0, const float2 rot,
-                                           const float qs, const DirectParams &P, const bool fold, float2 *out) {
-    const float kf0 = (float)k0 - R.mlo[l];
-    const float wl = R.wlen[l];
-    // first of the lines inside the window (kf0 is integral)
-    const int m0 = kf0 >= 0.f ? 0 : (S == 1 ? (int)(-kf0) : (int)ceilf(-kf0 * (1.f / S)));
-    float vr = 0.f, vi = 0.f, rho = 0.f;
-    const bool any = m0 < NL && kf0 + (float)(S * m0) < wl;
-    if (any) {
-        const float h = P.hf[l];
-        const float kf = kf0 + (float)(S * m0);
-        const float dx = fmaf(kf, h, R.delta[l]);
-        float ex = dx * dx * P.ce;
-        float fr = kf * R.nuhi[l];
-        fr -= rint_fast(fr);
-        float tau = fmaf(kf, R.nulo[l], fr);
-        if (fold) {
-            ex += R.la;
-            tau += R.tau0;
-        }
-        tau -= rint_fast(tau);
-        float sn, cs;
-        __sincosf(6.283185307179586f * tau, &sn, &cs);
-        const float ga = ex2_approx(ex);
-        vr = ga * cs;
-        vi = ga * sn;
-        rho = ex2_approx(P.ce * h * (float)S * fmaf(2.f, dx, (float)S * h));
-    }
-#pragma unroll
-    for (int m = 0; m < NL; ++m) {
-        const bool in = any && m >= m0 && kf0 + (float)(S * m) < wl;
-        out[m] = in ? make_float2(vr, vi) : make_float2(0.f, 0.f);
-        if (m < NL - 1 && m >= m0) {
-            const float pr = rot.x * rho, pi = rot.y * rho;
-            const float nr = vr * pr - vi * pi;
-            vi = vr * pi + vi * pr;
-            vr = nr;
-            rho *= qs;
-        }
-    }
-}
-
-// factor_run, handing each value to sink(m, value) as soon as it is known
-// instead of returning them all (fewer live registers for long runs)
+// (zero outside the window), each handed to sink(m, value) as soon as it is
+// known; rot = e^{2 pi i S nu_l} and qs = e^{-S^2 h^2 / eps}; fold: dimension 0
+// carries log2|pref A| and the phase of pref A e^{i theta} at the window
+// start.  The first line inside the window (kf0 is integral) is evaluated in
+// full, the next by the recurrences.
 template <int D, int S, int NL, class Sink>
 __device__ __forceinline__ void factor_run_to(const RecF<D> &R, const int l, const int k0, const float2 rot,
                                               const float qs, const DirectParams &P, const bool fold, Sink sink) {
@@ -288,6 +245,13 @@ __device__ __forceinline__ void factor_run_to(const RecF<D> &R, const int l, con
             rho *= qs;
         }
     }
+}
+
+// factor_run_to into an array
+template <int D, int S, int NL>
+__device__ __forceinline__ void factor_run(const RecF<D> &R, const int l, const int k0, const float2 rot,
+                                           const float qs, const DirectParams &P, const bool fold, float2 *out) {
+    factor_run_to<D, S, NL>(R, l, k0, rot, qs, P, fold, [&](int m, float2 v) { out[m] = v; });
 }
 
 // hi and lo TF32 parts of a complex value: hi = x truncated to TF32, lo = x - hi
