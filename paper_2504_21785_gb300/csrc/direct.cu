@@ -17,7 +17,10 @@
 // every pair is evaluated in full.  FP32 sums run over one chunk of 256
 // records and are folded into FP64 totals (a point can collect 10^4-10^5
 // packets: a single FP32 running sum would drift by ~sqrt(N) ulps).  Slices
-// are combined with atomic adds into the zeroed output.
+// are combined with atomic adds into the zeroed output.  This CUDA-core
+// evaluation serves FP64, 1-D, batched calls and FGR_FLAG_DIRECT_FMA; a single
+// FP32 call with d >= 2 runs the same binned records through the tensor-core
+// kernel of direct_tc.cuh (super tiles of several tiles, 3 x TF32 MMAs).
 //
 // FP32 records carry the per-packet phase reduced in FP64 to turns at the
 // window start (tau0) and the per-grid-step increment nu split into a coarse
