@@ -244,8 +244,10 @@ fgr_status fgr_fggc_multistep_tensor(fgr_ctx *ctx, const fgr_axis *axes, const i
  * tensor cores: super tiles of 128 x 64 points (d = 2) or 8 x 16 x 64
  * (d = 3), each factor split into two TF32 parts and the product taken
  * as three TF32 products into FP32 accumulators of 64 packets each, summed in
- * FP32; with FGR_FLAG_DIRECT_FMA on the CUDA cores, one complex multiply-add
- * per packet-point pair, partial sums folded into FP64.  Complex64 out.  The
+ * FP32; with FGR_FLAG_DIRECT_FMA (and for windows too wide for the super
+ * tiles' lists: beyond about 110 lines of dimensions 0 and 1 in 3-D) on the
+ * CUDA cores, one complex multiply-add per packet-point pair, partial sums
+ * folded into FP64.  Complex64 out.  The
  * work is cut into (tile, packet slice) items: d = 1 the same number of
  * slices per tile, d >= 2 slices in proportion to each tile's packet count,
  * heaviest first, taken by persistent CTAs (no host wait).  A tensor-core

@@ -948,20 +948,31 @@ fgr_status prepare(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t
     return FGR_OK;
 }
 
-// Tensor-core direct sum (FP32, d = 2, 3): loads of the super tiles, items
-// heaviest first, one persistent CTA per SM.
+// Whether the tensor-core kernel can take a grid: a super tile's list is at
+// most kSegMax runs of home tiles (windows of up to about 8,000 lines of
+// dimension 0 in 2-D, about 110 lines of dimensions 0 and 1 in 3-D); wider
+// windows go to the CUDA-core kernel.
 template <int D>
-fgr_status launch_tc(fgr_ctx *ctx, const Prepared &pr, void *u_dev, cudaStream_t st, Scratch &scratch) {
-    const GridDev &g = pr.P.g;
+bool tc_fits(const GridDev &g, int64_t *nst_out) {
     int64_t runs = 1, nst = 1;
     for (int l = 0; l < D; ++l) {
         const int span = tc::tc_span<D>(l);
         nst *= (g.nt[l] + span - 1) / span;
         if (l < D - 1) runs *= (int64_t)std::min(g.K[l] + span, g.nt[l]);
     }
-    if (runs > tc::kSegMax || nst > (int64_t)1 << 30) {
+    if (nst_out) *nst_out = nst;
+    return runs <= tc::kSegMax && nst <= ((int64_t)1 << 30);
+}
+
+// Tensor-core direct sum (FP32, d = 2, 3): loads of the super tiles, items
+// heaviest first, one persistent CTA per SM.
+template <int D>
+fgr_status launch_tc(fgr_ctx *ctx, const Prepared &pr, void *u_dev, cudaStream_t st, Scratch &scratch) {
+    const GridDev &g = pr.P.g;
+    int64_t nst = 0;
+    if (!tc_fits<D>(g, &nst)) {
         set_error("direct: window too wide for the tensor-core tiling");
-        return FGR_E_INVALID;
+        return FGR_E_INTERNAL;
     }
     auto *load = (uint32_t *)scratch.get(sizeof(uint32_t) * (size_t)nst);
     auto *rank = (int *)scratch.get(sizeof(int) * 2 * (size_t)nst);
@@ -1018,7 +1029,7 @@ fgr_status launch(fgr_ctx *ctx, const PacketsDev &pk, void *u_dev, cudaStream_t 
         timer.finish();
         return FGR_OK;
     }
-    if (D >= 2 && !fp64 && !(ctx->opt.flags & FGR_FLAG_DIRECT_FMA)) {
+    if (D >= 2 && !fp64 && !(ctx->opt.flags & FGR_FLAG_DIRECT_FMA) && tc_fits<D == 3 ? 3 : 2>(pr.P.g, nullptr)) {
         fgr_status rt = launch_tc<D == 3 ? 3 : 2>(ctx, pr, u_dev, st, scratch);
         if (rt != FGR_OK) return rt;
         timer.mark(&ctx->timing.last.direct_ms);
